@@ -1,0 +1,338 @@
+"""The M2M training step, written out plainly (oracle; test infrastructure only).
+
+Section 2 of the paper: an N-body system is trained to reproduce the
+observables of a target galaxy by maximising F = -1/2 chi^2 + mu S (Eq. 1)
+with respect to the particle weights w_i, S = -sum_i w_i ln(w_i/w_hat_i)
+(Eq. 2), while the particles are evolved in the potential.  Section 2.1: flat
+priors w_hat_i = 1/N, or moving priors that follow the weight distribution in
+integral-of-motion space.
+
+One step t -> t+1, in this order:
+
+1. push      KDK leapfrog: v += dt/2 a(x); x += dt v; v += dt/2 a(x)
+2. observe   y_j = sum_i w_i K_j(x_i, v_i) at the new positions, old weights
+3. residual  Delta_j = (y_j - Y_j)/sigma_j (0 where sigma_j <= 0);
+             Delta~_j <- alpha Delta_j + (1-alpha) Delta~_j;
+             chi2 = sum_j Delta~_j^2, chi2_raw = sum_j Delta_j^2
+4. update    G_i = mu (-ln(w_i/w_hat_i) - c) - sum_j K_ij Delta~_j/sigma_j,
+             w_i <- w_i exp(eps dt G_i)   (c = 1: the derivative of Eq. 2)
+5. priors    if moving and (t+1) % period == 0: w_hat_i = mean w over the
+             cell of i, cells from (x_{t+1}, v_{t+1}), weights w_{t+1}
+6. record    S_t, sum w_t (the weights that produced y), F_t = -chi2/2 + mu S_t
+
+At initialisation Delta~ := Delta of an observe at (x_0, w_0).
+
+Bin and cell membership is taken in the state precision (float64 or
+float32) from values computed in a fixed order (see :func:`sky`,
+:func:`cells_and_kernels`, :func:`prior_cells`) and compared with float64
+edge tables: a value v is in cell j iff e_j <= v < e_{j+1}; anything else,
+NaN included, is in no cell.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gh as _gh
+from .potentials import acceleration, potential
+
+
+def state_dtype(precision):
+    return np.float64 if precision == "fp64" else np.float32
+
+
+# --------------------------------------------------------------------------
+# 1. push
+# --------------------------------------------------------------------------
+def kdk(x, y, z, vx, vy, vz, comps, dt):
+    """One kick-drift-kick step in the dtype of the arrays; returns new arrays.
+
+    dt/2 and dt are rounded once from float64 to the state precision."""
+    T = x.dtype.type
+    h = T(np.float64(0.5) * np.float64(dt))
+    d = T(dt)
+    ax, ay, az = acceleration(x, y, z, comps)
+    vx = vx + h * ax
+    vy = vy + h * ay
+    vz = vz + h * az
+    x = x + d * vx
+    y = y + d * vy
+    z = z + d * vz
+    ax, ay, az = acceleration(x, y, z, comps)
+    vx = vx + h * ax
+    vy = vy + h * ay
+    vz = vz + h * az
+    return x, y, z, vx, vy, vz
+
+
+# --------------------------------------------------------------------------
+# 2. observables
+# --------------------------------------------------------------------------
+def bin_index(v, edges):
+    """Cell j with edges[j] <= v < edges[j+1] (compared in float64), else -1."""
+    e = np.asarray(edges, dtype=np.float64)
+    vd = np.asarray(v).astype(np.float64)
+    j = np.searchsorted(e, vd, side="right") - 1
+    bad = (j < 0) | (j >= len(e) - 1) | np.isnan(vd)
+    return np.where(bad, -1, j).astype(np.int64)
+
+
+def sky(x, y, z, vx, vy, vz, sin_i, cos_i):
+    """Sky-plane coordinates and line-of-sight velocity for the line of sight
+    s = (0, sin i, cos i), in the state precision:
+    X = x, Y = z*sin i - y*cos i, v_los = vy*sin i + vz*cos i."""
+    T = x.dtype.type
+    s, c = T(sin_i), T(cos_i)
+    return x, z * s - y * c, vy * s + vz * c
+
+
+def cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i):
+    """Per observable set: (cell index per particle, K per particle (n, nmom))."""
+    X, Ys, _ = sky(x, y, z, vx, vy, vz, sin_i, cos_i)
+    # the kernel values are float64 functions of the stored state
+    vd = (np.asarray(vy, np.float64) * np.float64(sin_i)
+          + np.asarray(vz, np.float64) * np.float64(cos_i))
+    out = []
+    for s in obs_sets:
+        if s.geom == "shell":
+            cell = bin_index((x * x + y * y) + z * z, s.edges_x)
+        elif s.geom == "annulus":
+            cell = bin_index(X * X + Ys * Ys, s.edges_x)
+        elif s.geom == "grid":
+            ix = bin_index(X, s.edges_x)
+            iy = bin_index(Ys, s.edges_y)
+            cell = np.where((ix >= 0) & (iy >= 0), iy * s.nx + ix, -1)
+        else:
+            raise ValueError(s.geom)
+        if s.quant == "mass":
+            K = np.ones((x.shape[0], 1))
+        elif s.quant == "vlos2":
+            K = (vd * vd)[:, None]
+        elif s.quant == "gh":
+            cc = np.where(cell >= 0, cell, 0)
+            V = np.asarray(s.gh_V, np.float64)[cc]
+            S = np.asarray(s.gh_S, np.float64)[cc]
+            K = _gh.gh_kernel((vd - V) / S, s.sigma_kernel / S)
+        else:
+            raise ValueError(s.quant)
+        out.append((cell, K))
+    return out
+
+
+def observe_from(kern, w, obs_sets):
+    """y = concatenation over sets of sum_i w_i K_i into each cell (cell-major,
+    moment-minor), summed in float64."""
+    ys = []
+    for (cell, K), s in zip(kern, obs_sets):
+        m = cell >= 0
+        blk = np.zeros((s.ncells, s.nmom))
+        for n in range(s.nmom):
+            blk[:, n] = np.bincount(cell[m], weights=w[m] * K[m, n],
+                                    minlength=s.ncells)
+        ys.append(blk.reshape(-1))
+    return np.concatenate(ys)
+
+
+def observe(x, y, z, vx, vy, vz, w, obs_sets, sin_i, cos_i):
+    kern = cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i)
+    return observe_from(kern, np.asarray(w, np.float64), obs_sets)
+
+
+# --------------------------------------------------------------------------
+# 3. residuals
+# --------------------------------------------------------------------------
+def residual(yv, Y, sigma, Dt_prev, alpha, first):
+    """Returns (Delta, Delta~, coef = Delta~/sigma, chi2, chi2_raw)."""
+    valid = sigma > 0
+    ss = np.where(valid, sigma, 1.0)
+    Delta = np.where(valid, (yv - Y) / ss, 0.0)
+    if first:
+        Dt = Delta.copy()
+    else:
+        Dt = alpha * Delta + (1.0 - alpha) * Dt_prev
+    coef = np.where(valid, Dt / ss, 0.0)
+    return Delta, Dt, coef, float(np.sum(Dt * Dt)), float(np.sum(Delta * Delta))
+
+
+# --------------------------------------------------------------------------
+# 4. weight update, entropy, merit
+# --------------------------------------------------------------------------
+def kernel_dot(kern, coef, obs_sets, n):
+    """sum_j K_ij coef_j per particle (sets in order, moments in order)."""
+    dot = np.zeros(n)
+    off = 0
+    for (cell, K), s in zip(kern, obs_sets):
+        m = cell >= 0
+        for k in range(s.nmom):
+            dot[m] += K[m, k] * coef[off + cell[m] * s.nmom + k]
+        off += s.nobs
+    return dot
+
+
+def entropy(w, what):
+    """S = -sum_i w_i ln(w_i/w_hat_i) (Eq. 2), terms with w_i = 0 are 0."""
+    m = w > 0
+    return float(-np.sum(w[m] * np.log(w[m] / what[m])))
+
+
+def update_weights(w, what, dot, eps, mu, dt, entropy_const=1.0):
+    """w_i <- w_i exp(eps dt G_i), G_i = mu(-ln(w_i/w_hat_i) - c) - dot_i."""
+    w_new = w.copy()
+    m = w > 0
+    G = mu * (-np.log(w[m] / what[m]) - entropy_const) - dot[m]
+    w_new[m] = w[m] * np.exp(eps * dt * G)
+    return w_new
+
+
+def merit(chi2, S, mu):
+    """F = -1/2 chi^2 + mu S (Eq. 1)."""
+    return -0.5 * chi2 + mu * S
+
+
+# --------------------------------------------------------------------------
+# 5. priors
+# --------------------------------------------------------------------------
+def _count_edges_le(v, lo, hi, ncell):
+    """Number of interior edges e_k = lo + k*((hi-lo)/ncell), k = 1..ncell-1,
+    with e_k <= v (float64 compare); NaN counts 0.  Result in [0, ncell-1]."""
+    width = (np.float64(hi) - np.float64(lo)) / np.float64(ncell)
+    k = np.arange(1, ncell, dtype=np.float64)
+    e = np.float64(lo) + k * width
+    vd = np.asarray(v).astype(np.float64)
+    cnt = np.searchsorted(e, vd, side="right")
+    return np.where(np.isnan(vd), 0, cnt).astype(np.int64)
+
+
+def prior_cells(x, y, z, vx, vy, vz, prior, comps):
+    """Cell of every particle in integral-of-motion space (Section 2.1).
+
+    Computed in the state precision, in this order:
+      v2 = (vx*vx + vy*vy) + vz*vz;  E = 0.5*v2 + Phi(x)
+      'e_lz': Lz = x*vy - y*vx; cells on [min E, max E] x [-max|Lz|, max|Lz|]
+      'e_lc': L = x cross v, L2 = (Lx*Lx + Ly*Ly) + Lz*Lz; for the Hernquist
+              (GM, a) circular orbit of energy E (E < 0):
+                ed = E*k (k = a/GM), sq = sqrt(1 - 8*ed),
+                s = (-1 - sq)/(4*ed)   [= (r_c + a)/a],
+                sm = s - 1, Lc2 = gma*(((sm*sm)*sm)/(s*s))   (gma = GM*a),
+                X = L2/Lc2;
+              cells on [min E, 0) x [0, 1]; E >= 0 -> the extra cell nE*nL.
+    Returns int64 cell ids.
+    """
+    T = x.dtype.type
+    v2 = (vx * vx + vy * vy) + vz * vz
+    with np.errstate(divide="ignore", invalid="ignore"):
+        E = T(0.5) * v2 + potential(x, y, z, comps)
+        if prior.kind == "e_lz":
+            Lz = x * vy - y * vx
+            lo, hi = np.float64(E.min()), np.float64(E.max())
+            Lm = np.float64(np.abs(Lz).max())
+            iE = _count_edges_le(E, lo, hi, prior.nE)
+            iL = _count_edges_le(Lz, -Lm, Lm, prior.nL)
+            return iE * prior.nL + iL
+        if prior.kind == "e_lc":
+            GM, a = prior.hernquist
+            k = T(a / GM)
+            gma = T(GM * a)
+            Lx = y * vz - z * vy
+            Ly = z * vx - x * vz
+            Lz = x * vy - y * vx
+            L2 = (Lx * Lx + Ly * Ly) + Lz * Lz
+            ed = E * k
+            sq = np.sqrt(T(1) - T(8) * ed)
+            s = (T(-1) - sq) / (T(4) * ed)
+            sm = s - T(1)
+            Lc2 = gma * (((sm * sm) * sm) / (s * s))
+            X = L2 / Lc2
+            lo = np.float64(E.min())
+            iE = _count_edges_le(E, lo, 0.0, prior.nE)
+            iL = _count_edges_le(X, 0.0, 1.0, prior.nL)
+            cell = iE * prior.nL + iL
+            return np.where(E >= 0, prior.nE * prior.nL, cell).astype(np.int64)
+    raise ValueError(prior.kind)
+
+
+def prior_means(w, cells, ncells):
+    """w_hat_i = (sum of w over i's cell) / (number of particles in it)."""
+    sums = np.bincount(cells, weights=w, minlength=ncells)
+    cnt = np.bincount(cells, minlength=ncells)
+    return sums[cells] / cnt[cells]
+
+
+# --------------------------------------------------------------------------
+# 6. the step loop
+# --------------------------------------------------------------------------
+@dataclass
+class State:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    w: np.ndarray
+    what: np.ndarray
+    Dt: np.ndarray
+    coef: np.ndarray
+    t: int = 0
+    y_obs: np.ndarray = None
+    Delta: np.ndarray = None
+    history: list = field(default_factory=list)
+
+    @property
+    def pos(self):
+        return (self.x, self.y, self.z)
+
+    @property
+    def vel(self):
+        return (self.vx, self.vy, self.vz)
+
+
+def init(problem, precision=None):
+    """State at t = 0: positions in the state precision, w = w0, w_hat =
+    what0, Delta~ = Delta of the initial observe."""
+    T = state_dtype(precision or problem.precision)
+    x, y, z = (np.ascontiguousarray(a, dtype=T) for a in problem.pos)
+    vx, vy, vz = (np.ascontiguousarray(a, dtype=T) for a in problem.vel)
+    w = np.array(problem.w0, dtype=np.float64)
+    what = np.array(problem.what0, dtype=np.float64)
+    yv = observe(x, y, z, vx, vy, vz, w, problem.obs, problem.incl_sin,
+                 problem.incl_cos)
+    Delta, Dt, coef, _, _ = residual(yv, problem.Y, problem.sigma, None,
+                                     problem.alpha, True)
+    return State(x, y, z, vx, vy, vz, w, what, Dt, coef, 0, yv, Delta)
+
+
+def step(st, problem, push=True):
+    """Advance `st` by one M2M step in place; returns the step's record."""
+    P = problem
+    w_used = st.w
+    S_t = entropy(st.w, st.what)
+    sumw_t = float(np.sum(st.w))
+    if push:
+        st.x, st.y, st.z, st.vx, st.vy, st.vz = kdk(
+            st.x, st.y, st.z, st.vx, st.vy, st.vz, P.potential, P.dt)
+    kern = cells_and_kernels(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.obs,
+                             P.incl_sin, P.incl_cos)
+    yv = observe_from(kern, w_used, P.obs)
+    Delta, Dt, coef, chi2, chi2_raw = residual(yv, P.Y, P.sigma, st.Dt,
+                                               P.alpha, False)
+    dot = kernel_dot(kern, coef, P.obs, st.w.shape[0])
+    st.w = update_weights(st.w, st.what, dot, P.eps, P.mu, P.dt,
+                          P.entropy_const)
+    st.t += 1
+    if P.prior.kind != "flat" and st.t % P.prior.period == 0:
+        cells = prior_cells(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.prior,
+                            P.potential)
+        st.what = prior_means(st.w, cells, P.prior.ncells)
+    st.Dt, st.coef, st.y_obs, st.Delta = Dt, coef, yv, Delta
+    rec = dict(t=st.t, chi2=chi2, chi2_raw=chi2_raw, S=S_t, sum_w=sumw_t,
+               F=merit(chi2, S_t, P.mu))
+    st.history.append(rec)
+    return rec
+
+
+def run(problem, nsteps, precision=None, push=True, state=None):
+    """Initialise (unless `state` is given) and take `nsteps` steps."""
+    st = state if state is not None else init(problem, precision)
+    for _ in range(nsteps):
+        step(st, problem, push=push)
+    return st

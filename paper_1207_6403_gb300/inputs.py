@@ -1,0 +1,474 @@
+"""Seeded synthetic inputs for the made-to-measure (M2M) training step.
+
+This module is shared by the CUDA path and by the test oracle, so it holds
+none of the M2M step's own arithmetic: no orbit push, no bin membership, no
+observable kernel, no residual, weight update or prior.  It only
+
+* draws particle realisations (initial models and target galaxies) from
+  Philox-seeded numpy generators (Salmon et al. 2011 counter-based RNG);
+* builds the bin-edge tables that *define* the observables (squared radii for
+  3D shells and projected annuli, x/y edges for pixel and aperture grids);
+* fixes the per-aperture Gauss-Hermite reference velocity and width;
+* states the observational error model sigma_j (2% of the target value);
+* describes each workload as plain data (:class:`Problem`).
+
+The target observables Y_j are *not* produced here: a caller observes the
+target realisation with whichever implementation it trusts (the oracle in the
+tests, the library itself when timing), then applies :func:`error_model`.
+
+Physical units: G = 1 throughout.  The workloads follow the paper's problem
+statement (Section 2: particles with weights w_i in a potential, observables
+with errors, priors w_hat_i; Section 2.1: flat priors 1/N and moving priors
+in integral-of-motion space) at the sizes of the five benchmark workloads:
+
+  plain-fp64    N=20,000 Hernquist, 40 shells + 20 annuli (mass, v_los^2), FP64
+  moving-priors N=1,000,000 Hernquist, 100 shells + 60 annuli x h0..h4, (E, L^2/Lc^2) priors
+  flat-log      N=4,000,000 flattened logarithmic potential at 60 deg, 64x64 pixels +
+                20x20 apertures x h0..h4, (E, L_z) priors
+  batched       48 Hernquist+NFW models of uneven N (not built by this module yet)
+  sh-selfcons   8,000,000-particle disc+bulge with a spherical-harmonic potential
+                (not built by this module yet)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
+
+import numpy as np
+
+__all__ = [
+    "PotentialComponent", "ObservableSet", "PriorSpec", "Problem",
+    "rng", "hernquist_positions", "hernquist_isotropic", "hernquist_om_target",
+    "log_flattened_realisation", "log_shell_edges", "uniform_edges",
+    "error_model", "make_problem", "WORKLOADS",
+]
+
+
+# --------------------------------------------------------------------------
+# Plain-data workload description
+# --------------------------------------------------------------------------
+@dataclass
+class PotentialComponent:
+    """One analytic potential component; the potential is the sum of them.
+
+    kind 'hernquist': params (GM, a)           Phi = -GM/(r+a)
+    kind 'nfw':       params (rho_s, r_s)      Phi = -4 pi rho_s r_s^3 ln(1+r/r_s)/r
+    kind 'log':       params (v0, Rc, q)       Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)
+    """
+    kind: str
+    params: tuple
+
+
+@dataclass
+class ObservableSet:
+    """One set of observables y_j = sum_i w_i K_j(x_i, v_i).
+
+    geom  'shell'   : cells are 3D radial shells, edges_x are edges of r^2
+          'annulus' : cells are projected annuli, edges_x are edges of R^2
+          'grid'    : cells are rectangles of the sky plane (pixels or IFU
+                      apertures), edges_x / edges_y are edges of X / Y
+    quant 'mass'    : K = 1 in the cell
+          'vlos2'   : K = v_los^2 in the cell (luminosity-weighted 2nd moment)
+          'gh'      : K_n = Gauss-Hermite kernel u_n, n = 0..4, in the cell,
+                      about (gh_V, gh_S) per cell, convolved with a Gaussian
+                      velocity kernel of width sigma_kernel
+    Cell index: grid cell = iy * nx + ix.  Observable index inside the set =
+    cell * nmom + n.  Edge arrays are float64 and strictly increasing; the
+    membership of a value v in cell j is e_j <= v < e_{j+1}.
+    """
+    geom: str
+    quant: str
+    edges_x: np.ndarray
+    edges_y: Optional[np.ndarray] = None
+    gh_V: Optional[np.ndarray] = None
+    gh_S: Optional[np.ndarray] = None
+    sigma_kernel: float = 0.0
+
+    @property
+    def nx(self) -> int:
+        return len(self.edges_x) - 1
+
+    @property
+    def ny(self) -> int:
+        return 1 if self.edges_y is None else len(self.edges_y) - 1
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def nmom(self) -> int:
+        return 5 if self.quant == "gh" else 1
+
+    @property
+    def nobs(self) -> int:
+        return self.ncells * self.nmom
+
+
+@dataclass
+class PriorSpec:
+    """How the priors w_hat_i are set (Section 2.1).
+
+    kind 'flat' : w_hat_i stay at their initial value (1/N).
+    kind 'e_lc' : every `period` steps, w_hat_i = mean weight of the particles
+                  in i's cell of an nE x nL grid in (E, L^2/Lc^2(E)) for a
+                  Hernquist potential (GM, a) = hernquist; E-cells are uniform
+                  on [min E, 0), unbound particles share one extra cell.
+    kind 'e_lz' : the same on an nE x nL grid in (E, L_z), uniform on
+                  [min E, max E] x [-max|L_z|, max|L_z|].
+    """
+    kind: str = "flat"
+    nE: int = 1
+    nL: int = 1
+    period: int = 25
+    hernquist: tuple = (1.0, 1.0)
+
+    @property
+    def ncells(self) -> int:
+        if self.kind == "flat":
+            return 0
+        return self.nE * self.nL + (1 if self.kind == "e_lc" else 0)
+
+
+@dataclass
+class Problem:
+    """A complete M2M workload as plain arrays and numbers."""
+    name: str
+    n: int
+    pos: np.ndarray            # (3, n) float64
+    vel: np.ndarray            # (3, n) float64
+    w0: np.ndarray             # (n,) float64
+    what0: np.ndarray          # (n,) float64
+    potential: List[PotentialComponent]
+    obs: List[ObservableSet]
+    incl_sin: float            # line of sight s = (0, sin i, cos i)
+    incl_cos: float
+    eps: float                 # effective epsilon (the workload's epsilon / N)
+    mu: float
+    dt: float
+    alpha: float
+    prior: PriorSpec
+    nsteps: int
+    precision: str             # 'fp64' or 'fp32c'
+    entropy_const: float = 1.0  # dS/dw_i = -ln(w_i/w_hat_i) - entropy_const
+    target_pos: Optional[np.ndarray] = None
+    target_vel: Optional[np.ndarray] = None
+    target_w: Optional[np.ndarray] = None
+    Y: Optional[np.ndarray] = None
+    sigma: Optional[np.ndarray] = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nobs(self) -> int:
+        return sum(s.nobs for s in self.obs)
+
+    def with_targets(self, Y: np.ndarray) -> "Problem":
+        """Return a copy carrying targets Y and the 2% error model."""
+        Y = np.asarray(Y, dtype=np.float64)
+        return replace(self, Y=Y, sigma=error_model(Y, self.obs))
+
+
+# --------------------------------------------------------------------------
+# Random streams
+# --------------------------------------------------------------------------
+def rng(seed: int) -> np.random.Generator:
+    """Philox4x32-10 counter-based stream (Salmon et al. 2011) for one seed."""
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def _isotropic_directions(g: np.random.Generator, n: int):
+    cth = g.uniform(-1.0, 1.0, n)
+    phi = g.uniform(0.0, 2.0 * math.pi, n)
+    sth = np.sqrt(np.maximum(0.0, 1.0 - cth * cth))
+    return sth * np.cos(phi), sth * np.sin(phi), cth
+
+
+# --------------------------------------------------------------------------
+# Hernquist model (Hernquist 1990, ApJ 356, 359), G = 1
+# --------------------------------------------------------------------------
+def _hernquist_rho(r, M=1.0, a=1.0):
+    return M * a / (2.0 * math.pi * r * (r + a) ** 3)
+
+
+def _hernquist_mass(r, M=1.0, a=1.0):
+    return M * r * r / ((r + a) ** 2)
+
+
+def _jeans_sigma_r2_table(rho, mass, ra=None, rmin=1e-5, rmax=1e4, npts=480):
+    """sigma_r^2(r) on a log grid from the spherical Jeans equation.
+
+    Isotropic (ra None):  rho sigma^2 = int_r^inf rho M / r'^2 dr'.
+    Osipkov-Merritt-like beta = r^2/(r^2+ra^2):
+        rho (r^2+ra^2) sigma_r^2 = int_r^inf (r'^2+ra^2) rho M / r'^2 dr'.
+    Integrated in ln r' with composite Simpson on a fine grid plus an
+    analytic r'^-4 tail beyond rmax.
+    """
+    lr = np.linspace(math.log(rmin), math.log(rmax), 8 * npts + 1)
+    r = np.exp(lr)
+    g = np.ones_like(r) if ra is None else r * r + ra * ra
+    f = g * rho(r) * mass(r) / (r * r) * r          # integrand in d ln r
+    # cumulative integral from each grid point to rmax (trapezoid on a fine grid
+    # is refined by Richardson with the half grid: error ~ h^4)
+    h = lr[1] - lr[0]
+    seg = 0.5 * h * (f[1:] + f[:-1])
+    tail_fine = np.concatenate([np.cumsum(seg[::-1])[::-1], [0.0]])
+    f2 = f[::2]
+    seg2 = 0.5 * (2 * h) * (f2[1:] + f2[:-1])
+    tail_coarse = np.concatenate([np.cumsum(seg2[::-1])[::-1], [0.0]])
+    tail = (4.0 * tail_fine[::2] - tail_coarse) / 3.0
+    rr = r[::2]
+    # analytic continuation past rmax: integrand ~ C r'^-3 (isotropic) or r'^-1... use
+    # the local power law of f to extend
+    slope = (math.log(f[-1]) - math.log(f[-9])) / (lr[-1] - lr[-9])
+    extra = -f[-1] / slope if slope < 0 else 0.0
+    tail = tail + extra
+    gg = g[::2]
+    sig2 = tail / (gg * rho(rr))
+    return rr, sig2
+
+
+class _Interp:
+    def __init__(self, r, y):
+        self.lr = np.log(r)
+        self.ly = np.log(np.maximum(y, 1e-300))
+
+    def __call__(self, r):
+        return np.exp(np.interp(np.log(r), self.lr, self.ly))
+
+
+def hernquist_sigma_iso(GM=1.0, a=1.0):
+    """Callable isotropic sigma^2(r) of a Hernquist sphere (Jeans quadrature)."""
+    rr, s2 = _jeans_sigma_r2_table(lambda r: _hernquist_rho(r, GM, a),
+                                   lambda r: _hernquist_mass(r, GM, a))
+    return _Interp(rr, s2)
+
+
+def hernquist_positions(n, seed, GM=1.0, a=1.0, rmax=100.0):
+    """Positions (3, n) of a Hernquist sphere truncated at rmax, sorted by r.
+
+    Radius by the inverse of M(<r)/M = r^2/(r+a)^2: r = a sqrt(u)/(1-sqrt(u)).
+    Returns (pos, r, g) where g is the generator, so velocities come from the
+    same stream.
+    """
+    g = rng(seed)
+    umax = (rmax / (rmax + a)) ** 2
+    u = g.uniform(0.0, umax, n)
+    su = np.sqrt(u)
+    r = a * su / (1.0 - su)
+    r.sort()
+    ex, ey, ez = _isotropic_directions(g, n)
+    pos = np.stack([r * ex, r * ey, r * ez])
+    return pos, r, g
+
+
+def _spherical_gaussian_velocities(g, pos, r, sig_r, sig_t):
+    """Gaussian velocities with radial / tangential dispersions (local frame)."""
+    n = r.shape[0]
+    vr = g.standard_normal(n) * sig_r
+    vt1 = g.standard_normal(n) * sig_t
+    vt2 = g.standard_normal(n) * sig_t
+    rs = np.where(r > 0, r, 1.0)
+    er = pos / rs
+    # tangential basis: e_theta, e_phi from er
+    x, y, z = er
+    Rxy = np.sqrt(x * x + y * y)
+    Rs = np.where(Rxy > 0, Rxy, 1.0)
+    ephi = np.stack([-y / Rs, x / Rs, np.zeros_like(x)])
+    eth = np.stack([z * x / Rs, z * y / Rs, -Rxy])
+    return er * vr + eth * vt1 + ephi * vt2
+
+
+def hernquist_isotropic(n, seed, GM=1.0, a=1.0, rmax=100.0):
+    """Isotropic Hernquist realisation: positions by inverse CDF, velocities
+    Gaussian with the isotropic Jeans sigma(r)."""
+    pos, r, g = hernquist_positions(n, seed, GM, a, rmax)
+    s2 = hernquist_sigma_iso(GM, a)(r)
+    s = np.sqrt(s2)
+    vel = _spherical_gaussian_velocities(g, pos, r, s, s)
+    return pos, vel
+
+
+def hernquist_om_target(n, seed, ra=1.0, GM=1.0, a=1.0, rmax=100.0):
+    """Osipkov-Merritt-like Hernquist target: beta(r) = r^2/(r^2+ra^2),
+    sigma_t = sqrt(1-beta) sigma_r, Gaussian velocities."""
+    pos, r, g = hernquist_positions(n, seed, GM, a, rmax)
+    rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x, GM, a),
+                                   lambda x: _hernquist_mass(x, GM, a), ra=ra)
+    sr = np.sqrt(_Interp(rr, s2)(r))
+    beta = r * r / (r * r + ra * ra)
+    st = np.sqrt(1.0 - beta) * sr
+    vel = _spherical_gaussian_velocities(g, pos, r, sr, st)
+    return pos, vel
+
+
+# --------------------------------------------------------------------------
+# Flattened logarithmic potential (Binney & Tremaine eq. 2.71)
+# --------------------------------------------------------------------------
+def log_flattened_density(x, y, z, v0=1.0, Rc=0.1, q=0.8):
+    """Density generating Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2), G = 1."""
+    R2 = x * x + y * y
+    D = Rc * Rc + R2 + z * z / (q * q)
+    num = (2 * q * q + 1) * Rc * Rc + R2 + (2 - 1 / (q * q)) * z * z
+    return v0 * v0 / (4 * math.pi * q * q) * num / (D * D)
+
+
+def log_flattened_realisation(n, seed, v0=1.0, Rc=0.1, q=0.8, mmax=5.0,
+                              stream_frac=0.0):
+    """Particles of the flattened-log density truncated at
+    m = sqrt(R^2 + z^2/q^2) <= mmax, sorted by m.
+
+    Proposal: m with density ~ m^2/(Rc^2+m^2) on [0, mmax], isotropic
+    direction in ellipsoidal coordinates (x, y, z) = m (sin t cos p,
+    sin t sin p, q cos t); accepted with probability rho/(proposal) divided by
+    its bound (2 q^2 + 1).  Velocities isotropic Gaussian, sigma^2 = v0^2/2,
+    plus an azimuthal streaming stream_frac * v_c(R),
+    v_c^2 = v0^2 R^2/(Rc^2 + R^2).
+    """
+    g = rng(seed)
+    out = []
+    have = 0
+    bound = 2 * q * q + 1
+    while have < n:
+        k = int((n - have) * 2.4) + 1024
+        m = g.uniform(0.0, mmax, k)
+        keep_m = g.uniform(0.0, 1.0, k) < (m * m / (Rc * Rc + m * m))
+        m = m[keep_m]
+        kk = m.shape[0]
+        ex, ey, ez = _isotropic_directions(g, kk)
+        x, y, z = m * ex, m * ey, q * m * ez
+        R2 = x * x + y * y
+        num = (2 * q * q + 1) * Rc * Rc + R2 + (2 - 1 / (q * q)) * z * z
+        ratio = num / (Rc * Rc + m * m)
+        acc = g.uniform(0.0, bound, kk) < ratio
+        out.append(np.stack([x[acc], y[acc], z[acc]]))
+        have += int(acc.sum())
+    pos = np.concatenate(out, axis=1)[:, :n]
+    mm = np.sqrt(pos[0] ** 2 + pos[1] ** 2 + (pos[2] / q) ** 2)
+    order = np.argsort(mm, kind="stable")
+    pos = np.ascontiguousarray(pos[:, order])
+    sig = v0 / math.sqrt(2.0)
+    vel = g.standard_normal((3, n)) * sig
+    if stream_frac:
+        R = np.sqrt(pos[0] ** 2 + pos[1] ** 2)
+        vc = v0 * R / np.sqrt(Rc * Rc + R * R)
+        Rs = np.where(R > 0, R, 1.0)
+        vel[0] += stream_frac * vc * (-pos[1] / Rs)
+        vel[1] += stream_frac * vc * (pos[0] / Rs)
+    return pos, vel
+
+
+# --------------------------------------------------------------------------
+# Edge tables and the error model
+# --------------------------------------------------------------------------
+def log_shell_edges(nbins, rmin, rmax):
+    """Squared edges r_k^2 of nbins log-spaced radial bins in [rmin, rmax]."""
+    k = np.arange(nbins + 1, dtype=np.float64)
+    r = rmin * (rmax / rmin) ** (k / nbins)
+    return r * r
+
+
+def uniform_edges(nbins, lo, hi):
+    """nbins+1 uniform edges lo + k (hi-lo)/nbins (float64)."""
+    k = np.arange(nbins + 1, dtype=np.float64)
+    return lo + k * ((hi - lo) / nbins)
+
+
+def error_model(Y, obs_sets, frac=0.02):
+    """Observational errors: sigma_j = 2% of the target value for masses and
+    v_los^2 moments; for Gauss-Hermite moments sigma_{p,n} = 2% of the
+    aperture's h0 observable Y_{p,0} (an absolute 0.02 in h_n units).
+    A target <= 0 masks the observable (sigma = 0)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    sig = np.zeros_like(Y)
+    off = 0
+    for s in obs_sets:
+        blk = Y[off:off + s.nobs].reshape(s.ncells, s.nmom)
+        ref = blk[:, 0:1]
+        sb = np.where(ref > 0, frac * ref, 0.0) * np.ones((1, s.nmom))
+        sig[off:off + s.nobs] = sb.reshape(-1)
+        off += s.nobs
+    return sig
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+WORKLOADS = ("plain-fp64", "moving-priors", "flat-log")
+
+_DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000,
+              "flat-log": 4_000_000}
+
+
+def _gh_set_annuli(nb, rmin, rmax, sigma_kernel, GM=1.0, a=1.0):
+    e = log_shell_edges(nb, rmin, rmax)
+    rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+    S = np.sqrt(hernquist_sigma_iso(GM, a)(rmid))
+    return ObservableSet("annulus", "gh", e, gh_V=np.zeros(nb), gh_S=S,
+                         sigma_kernel=sigma_kernel)
+
+
+def make_problem(name, n=None, precision=None, seed_model=None,
+                 seed_target=None, with_target=True, nsteps=None):
+    """Build the workload `name` (see module docstring), optionally at another
+    particle count `n` with the same structure.  Weights and priors start at
+    1/N; eps is the workload's epsilon scaled by 1/N."""
+    if n is None:
+        n = _DEFAULT_N[name]
+    if name == "plain-fp64":
+        sm, st = seed_model or 1, seed_target or 2
+        pos, vel = hernquist_isotropic(n, sm)
+        tp = tv = None
+        if with_target:
+            tp, tv = hernquist_om_target(n, st, ra=1.0)
+        ann = log_shell_edges(20, 0.05, 20.0)
+        obs = [ObservableSet("shell", "mass", log_shell_edges(40, 0.05, 20.0)),
+               ObservableSet("annulus", "mass", ann),
+               ObservableSet("annulus", "vlos2", ann.copy())]
+        pot = [PotentialComponent("hernquist", (1.0, 1.0))]
+        prior = PriorSpec("flat")
+        sin_i, cos_i = 0.0, 1.0
+        prec = precision or "fp64"
+        steps = nsteps or 2000
+    elif name == "moving-priors":
+        sm, st = seed_model or 3, seed_target or 4
+        pos, vel = hernquist_isotropic(n, sm)
+        tp = tv = None
+        if with_target:
+            tp, tv = hernquist_om_target(n, st, ra=1.0)
+        obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+               _gh_set_annuli(60, 0.05, 20.0, 0.1)]
+        pot = [PotentialComponent("hernquist", (1.0, 1.0))]
+        prior = PriorSpec("e_lc", nE=64, nL=32, period=25, hernquist=(1.0, 1.0))
+        sin_i, cos_i = 0.0, 1.0
+        prec = precision or "fp32c"
+        steps = nsteps or 5000
+    elif name == "flat-log":
+        sm, st = seed_model or 5, seed_target or 6
+        v0, Rc, q = 1.0, 0.1, 0.8
+        pos, vel = log_flattened_realisation(n, sm, v0, Rc, q)
+        tp = tv = None
+        if with_target:
+            tp, tv = log_flattened_realisation(n, st, v0, Rc, q, stream_frac=0.5)
+        ap = uniform_edges(20, -2.0, 2.0)
+        obs = [ObservableSet("grid", "mass", uniform_edges(64, -3.2, 3.2),
+                             uniform_edges(64, -3.2, 3.2)),
+               ObservableSet("grid", "gh", ap, ap.copy(),
+                             gh_V=np.zeros(400), gh_S=np.full(400, v0 / math.sqrt(2.0)),
+                             sigma_kernel=0.1)]
+        pot = [PotentialComponent("log", (v0, Rc, q))]
+        prior = PriorSpec("e_lz", nE=128, nL=64, period=25)
+        inc = math.radians(60.0)
+        sin_i, cos_i = math.sin(inc), math.cos(inc)
+        prec = precision or "fp32c"
+        steps = nsteps or 5000
+    else:
+        raise ValueError(f"unknown workload {name!r}")
+    w0 = np.full(n, 1.0 / n)
+    tw = None if tp is None else np.full(n, 1.0 / n)
+    return Problem(name=name, n=n, pos=np.ascontiguousarray(pos),
+                   vel=np.ascontiguousarray(vel), w0=w0, what0=w0.copy(),
+                   potential=pot, obs=obs, incl_sin=sin_i, incl_cos=cos_i,
+                   eps=0.05 / n, mu=1e-3, dt=0.01, alpha=0.02, prior=prior,
+                   nsteps=steps, precision=prec, target_pos=tp, target_vel=tv,
+                   target_w=tw)

@@ -1,0 +1,578 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+No test here retypes an oracle formula: each compares the oracle with a
+closed form, an invariant, a limit, a hand-worked example (tests/golden/), a
+brute-force loop or an independent numerical method (finite differences,
+quadrature, Newton's method).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+from oracle import gh as G
+from oracle import m2m as O
+from oracle import potentials as PT
+from paper_1207_6403_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            out[k] = np.array([float(t) for t in v])
+    return out
+
+
+def _pts(n, seed, scale=3.0):
+    g = np.random.default_rng(seed)
+    return g.normal(size=(3, n)) * scale
+
+
+# ---------------------------------------------------------------- potentials
+def _fd_grad(phi, x, y, z, h=1e-5):
+    gx = (phi(x + h, y, z) - phi(x - h, y, z)) / (2 * h)
+    gy = (phi(x, y + h, z) - phi(x, y - h, z)) / (2 * h)
+    gz = (phi(x, y, z + h) - phi(x, y, z - h)) / (2 * h)
+    return gx, gy, gz
+
+
+@pytest.mark.parametrize("comp,phi", [
+    (I.PotentialComponent("hernquist", (1.3, 0.7)),
+     lambda x, y, z: -1.3 / (np.sqrt(x * x + y * y + z * z) + 0.7)),
+    (I.PotentialComponent("log", (1.1, 0.1, 0.8)),
+     lambda x, y, z: 0.5 * 1.21 * np.log(0.01 + x * x + y * y + z * z / 0.64)),
+    (I.PotentialComponent("nfw", (0.02, 5.0)),
+     lambda x, y, z: -4 * math.pi * 0.02 * 125.0
+     * np.log1p(np.sqrt(x * x + y * y + z * z) / 5.0) / np.sqrt(x * x + y * y + z * z)),
+])
+def test_acceleration_is_minus_grad_phi(comp, phi):
+    x, y, z = _pts(200, 1)
+    ax, ay, az = PT.acceleration(x, y, z, [comp])
+    gx, gy, gz = _fd_grad(phi, x, y, z)
+    scale = np.sqrt(gx ** 2 + gy ** 2 + gz ** 2)
+    for a, g in ((ax, gx), (ay, gy), (az, gz)):
+        assert np.all(np.abs(a + g) <= 1e-7 * scale + 1e-12)
+    # and the oracle's own potential() agrees with the closed form
+    np.testing.assert_allclose(PT.potential(x, y, z, [comp]), phi(x, y, z), rtol=1e-13)
+
+
+def test_hernquist_closed_forms_golden():
+    g = _golden("hernquist_r1.txt")
+    comp = I.PotentialComponent("hernquist", (1.0, 1.0))
+    x, y, z = np.array([1.0]), np.array([0.0]), np.array([0.0])
+    ax, _, _ = PT.acceleration(x, y, z, [comp])
+    # |a| r^2 / G = M(<r)
+    assert -ax[0] == g["M"][0]
+    assert PT.potential(x, y, z, [comp])[0] == g["Phi"][0]
+    # vc^2 = r |a|
+    assert -ax[0] * 1.0 == g["vc2"][0]
+    assert I._hernquist_rho(1.0) == pytest.approx(g["rho"][0], rel=1e-15)
+
+
+def test_nfw_enclosed_mass_by_quadrature():
+    rho_s, r_s = 0.02, 5.0
+    comp = I.PotentialComponent("nfw", (rho_s, r_s))
+    for r in (1e-4, 0.05, 1.0, 7.0, 40.0):
+        ax, _, _ = PT.acceleration(np.array([r]), np.array([0.0]), np.array([0.0]), [comp])
+        M = integrate.quad(lambda s: 4 * math.pi * s * s * rho_s / ((s / r_s) * (1 + s / r_s) ** 2),
+                           0, r, limit=200, epsabs=0, epsrel=1e-12)[0]
+        assert -ax[0] * r * r == pytest.approx(M, rel=1e-9)
+
+
+def test_log_density_is_laplacian_over_4pi():
+    v0, Rc, q = 1.0, 0.1, 0.8
+    phi = lambda x, y, z: 0.5 * v0 ** 2 * np.log(Rc ** 2 + x * x + y * y + z * z / q ** 2)  # noqa: E731
+    x, y, z = _pts(50, 3, 1.0)
+    h = 1e-4
+    lap = sum((phi(*(c + h * (k == i) for k, c in enumerate((x, y, z))))
+               - 2 * phi(x, y, z)
+               + phi(*(c - h * (k == i) for k, c in enumerate((x, y, z))))) / h ** 2
+              for i in range(3))
+    np.testing.assert_allclose(I.log_flattened_density(x, y, z, v0, Rc, q),
+                               lap / (4 * math.pi), rtol=1e-5)
+
+
+# ---------------------------------------------------------------------- push
+def _hernquist_problem_state(n=2000, seed=11):
+    pos, vel = I.hernquist_isotropic(n, seed)
+    return [a.copy() for a in pos] + [a.copy() for a in vel]
+
+
+def test_kdk_conserves_angular_momentum_and_energy():
+    comps = [I.PotentialComponent("hernquist", (1.0, 1.0))]
+    x, y, z, vx, vy, vz = _hernquist_problem_state()
+    r0 = np.sqrt(x * x + y * y + z * z)
+
+    def L(x, y, z, vx, vy, vz):
+        return np.stack([y * vz - z * vy, z * vx - x * vz, x * vy - y * vx])
+
+    def E(x, y, z, vx, vy, vz):
+        return 0.5 * (vx * vx + vy * vy + vz * vz) - 1.0 / (np.sqrt(x * x + y * y + z * z) + 1.0)
+
+    L0, E0 = L(x, y, z, vx, vy, vz), E(x, y, z, vx, vy, vz)
+    s = (x, y, z, vx, vy, vz)
+    maxdE = np.zeros_like(E0)
+    rmin = r0.copy()
+    for _ in range(2000):
+        s = O.kdk(*s, comps, 0.01)
+        maxdE = np.maximum(maxdE, np.abs(E(*s) - E0))
+        rmin = np.minimum(rmin, np.sqrt(s[0] ** 2 + s[1] ** 2 + s[2] ** 2))
+    L1 = L(*s)
+    Lmag = np.sqrt((L0 ** 2).sum(0))
+    rel = np.sqrt(((L1 - L0) ** 2).sum(0)) / Lmag
+    assert np.max(rel[Lmag > 1e-3]) < 1e-11
+    # bounded, second-order energy error for orbits resolved by dt (pericentre
+    # passage at r >= 0.2 has a dynamical time of ~300 steps)
+    sel = (rmin > 0.2) & (E0 < -0.05)
+    assert sel.sum() > 500
+    assert np.max(maxdE[sel] / np.abs(E0[sel])) < 1e-3
+    assert np.median(maxdE[sel] / np.abs(E0[sel])) < 1e-5
+
+
+def test_kdk_is_time_reversible():
+    comps = [I.PotentialComponent("hernquist", (1.0, 1.0))]
+    s0 = _hernquist_problem_state(500, 12)
+    s = tuple(s0)
+    for _ in range(1000):
+        s = O.kdk(*s, comps, 0.01)
+    s = (s[0], s[1], s[2], -s[3], -s[4], -s[5])
+    for _ in range(1000):
+        s = O.kdk(*s, comps, 0.01)
+    for a, b in zip(s[:3], s0[:3]):
+        assert np.max(np.abs(a - b)) < 1e-9
+
+
+def test_kdk_circular_orbit_stays_circular():
+    # v = vc(r) tangential in a Hernquist sphere: radius stays r to O(dt^2)
+    comps = [I.PotentialComponent("hernquist", (1.0, 1.0))]
+    r = np.array([0.5, 1.0, 2.0, 5.0])
+    vc = np.sqrt(r / (1 + r) ** 2)
+    s = (r.copy(), np.zeros(4), np.zeros(4), np.zeros(4), vc.copy(), np.zeros(4))
+    for _ in range(3000):
+        s = O.kdk(*s, comps, 0.01)
+    rr = np.sqrt(s[0] ** 2 + s[1] ** 2 + s[2] ** 2)
+    np.testing.assert_allclose(rr, r, rtol=2e-5)
+
+
+def test_kdk_float32_state_stays_float32_and_close():
+    comps = [I.PotentialComponent("log", (1.0, 0.1, 0.8))]
+    s64 = tuple(a for a in _hernquist_problem_state(300, 13))
+    s32 = tuple(a.astype(np.float32) for a in s64)
+    for _ in range(100):
+        s64 = O.kdk(*s64, comps, 0.01)
+        s32 = O.kdk(*s32, comps, 0.01)
+    assert all(a.dtype == np.float32 for a in s32)
+    for a, b in zip(s32, s64):
+        assert np.max(np.abs(a - b)) < 1e-3
+
+
+# --------------------------------------------------------------- observables
+def _brute_cells(X, edges):
+    out = []
+    for v in X:
+        j = -1
+        for k in range(len(edges) - 1):
+            if float(edges[k]) <= float(v) < float(edges[k + 1]):
+                j = k
+        out.append(j)
+    return np.array(out)
+
+
+def test_bin_membership_matches_brute_force_including_edges_and_nan():
+    edges = np.array([0.1, 0.25, 0.5, 1.0, 3.0])
+    v = np.array([0.1, 0.25, 0.2499999, 3.0, 2.9999, 0.05, np.nan, np.inf, -np.inf, 1.0, 0.5])
+    np.testing.assert_array_equal(O.bin_index(v, edges), _brute_cells(v, edges))
+    assert O.bin_index(np.array([0.25]), edges)[0] == 1          # lower edge inclusive
+    assert O.bin_index(np.array([3.0]), edges)[0] == -1          # top edge exclusive
+    # float32 values compare exactly against float64 edges
+    e = np.array([0.0, 0.1, 0.2])
+    f = np.float32(0.1)       # float32(0.1) > 0.1 in float64
+    assert float(f) > 0.1 and O.bin_index(np.array([f]), e)[0] == 1
+    g = np.nextafter(np.float32(0.1), np.float32(0))  # just below 0.1
+    assert O.bin_index(np.array([g]), e)[0] == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_observe_matches_per_particle_loop(dtype):
+    g = np.random.default_rng(5)
+    n = 400
+    x, y, z = (g.normal(size=n) * 1.5).astype(dtype), (g.normal(size=n) * 1.5).astype(dtype), \
+        (g.normal(size=n) * 1.5).astype(dtype)
+    vx, vy, vz = (g.normal(size=n) * 0.5).astype(dtype), (g.normal(size=n) * 0.5).astype(dtype), \
+        (g.normal(size=n) * 0.5).astype(dtype)
+    w = g.uniform(0.5, 1.5, n) / n
+    si, ci = math.sin(math.radians(60)), math.cos(math.radians(60))
+    ap = I.uniform_edges(4, -2.0, 2.0)
+    sets = [I.ObservableSet("shell", "mass", I.log_shell_edges(6, 0.1, 5.0)),
+            I.ObservableSet("annulus", "vlos2", I.log_shell_edges(5, 0.1, 4.0)),
+            I.ObservableSet("grid", "mass", I.uniform_edges(5, -3.0, 3.0), I.uniform_edges(3, -2.0, 2.0)),
+            I.ObservableSet("grid", "gh", ap, ap.copy(), gh_V=g.normal(size=16) * 0.1,
+                            gh_S=g.uniform(0.4, 0.8, 16), sigma_kernel=0.1)]
+    yv = O.observe(x, y, z, vx, vy, vz, w, sets, si, ci)
+    # brute force: explicit geometry per particle
+    T = np.dtype(dtype).type
+    ref = []
+    for s in sets:
+        acc = np.zeros((s.ncells, s.nmom))
+        for i in range(n):
+            X = x[i]
+            Ys = T(z[i] * T(si)) - T(y[i] * T(ci))
+            vlos = float(vy[i]) * si + float(vz[i]) * ci
+            if s.geom == "shell":
+                q = T(T(x[i] * x[i]) + T(y[i] * y[i])) + T(z[i] * z[i])
+                c = _brute_cells([q], s.edges_x)[0]
+            elif s.geom == "annulus":
+                q = T(X * X) + T(Ys * Ys)
+                c = _brute_cells([q], s.edges_x)[0]
+            else:
+                cx = _brute_cells([X], s.edges_x)[0]
+                cy = _brute_cells([Ys], s.edges_y)[0]
+                c = cy * s.nx + cx if (cx >= 0 and cy >= 0) else -1
+            if c < 0:
+                continue
+            if s.quant == "mass":
+                acc[c, 0] += w[i]
+            elif s.quant == "vlos2":
+                acc[c, 0] += w[i] * vlos * vlos
+            else:
+                nu = (vlos - s.gh_V[c]) / s.gh_S[c]
+                sk = s.sigma_kernel / s.gh_S[c]
+                # quadrature of the smoothed kernel's definition
+                for k in range(5):
+                    f = lambda t: (np.exp(-0.5 * (t - nu) ** 2 / sk ** 2) / (sk * math.sqrt(2 * math.pi))  # noqa
+                                   * G.alpha(t) * G.hermite(t)[k])
+                    acc[c, k] += w[i] * 2 * math.sqrt(math.pi) * integrate.quad(
+                        f, nu - 12 * sk, nu + 12 * sk, epsabs=1e-14, epsrel=1e-12)[0]
+        ref.append(acc.reshape(-1))
+    ref = np.concatenate(ref)
+    np.testing.assert_allclose(yv, ref, rtol=1e-9, atol=1e-14)
+
+
+def test_complete_grid_sums_to_total_weight_exactly():
+    g = np.random.default_rng(7)
+    n = 5000
+    x, y, z = g.uniform(-1.9, 1.9, (3, n))
+    w = 2.0 ** -g.integers(10, 20, n).astype(np.float64)
+    s = I.ObservableSet("grid", "mass", I.uniform_edges(8, -2.0, 2.0), I.uniform_edges(8, -2.0, 2.0))
+    yv = O.observe(x, y, z, x * 0, y * 0, z * 0, w, [s], 0.0, 1.0)
+    assert yv.sum() == w.sum()
+
+
+def test_gh_orthonormality_by_gauss_hermite_quadrature():
+    xk, wk = np.polynomial.hermite.hermgauss(64)
+    H = G.hermite(xk)
+    # 2 sqrt(pi) int alpha^2 H_m H_n dy, alpha^2 = exp(-y^2)/(2 pi)
+    M = (2 * math.sqrt(math.pi) / (2 * math.pi)) * (H.T * wk) @ H
+    np.testing.assert_allclose(M, np.eye(5), atol=1e-13)
+
+
+def test_gh_smoothed_kernel_matches_quadrature_and_point_limit():
+    for nu in (-2.3, -0.4, 0.0, 0.7, 3.1):
+        for s in (0.05, 0.2, 0.8):
+            u = G.gh_kernel(nu, s)
+            for k in range(5):
+                f = lambda t: (np.exp(-0.5 * (t - nu) ** 2 / s ** 2) / (s * math.sqrt(2 * math.pi))  # noqa
+                               * G.alpha(t) * G.hermite(t)[k])
+                q = 2 * math.sqrt(math.pi) * integrate.quad(f, nu - 14 * s, nu + 14 * s,
+                                                            epsabs=1e-15, epsrel=1e-13)[0]
+                assert abs(u[k] - q) < 1e-12
+        np.testing.assert_allclose(G.gh_kernel(nu, 0.0), G.gh_point(nu), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(G.gh_kernel(nu, 1e-7), G.gh_point(nu), atol=1e-12)
+
+
+def test_gh_moments_of_gaussian_losvd():
+    # particles with v ~ N(V, S^2), point kernel -> h0 = 1, h1..h4 = 0 (shot noise)
+    g = np.random.default_rng(9)
+    n = 400_000
+    V, S = 0.3, 0.7
+    v = g.normal(V, S, n)
+    u = G.gh_point((v - V) / S).mean(0)
+    np.testing.assert_allclose(u, [1, 0, 0, 0, 0], atol=6e-3)
+
+
+@pytest.mark.slow
+def test_equilibrium_hernquist_observables():
+    """Shell masses and projected v_rms of an isotropic Hernquist realisation
+    against the closed-form M(<r) and the Abel projection of the closed-form
+    isotropic sigma^2(r) (Hernquist 1990)."""
+    n = 1_000_000
+    P = I.make_problem("plain-fp64", n=n, with_target=False)
+    rmax = 100.0
+    Mtot = (rmax / (1 + rmax)) ** 2
+    yv = O.observe(*P.pos, *P.vel, P.w0, P.obs, P.incl_sin, P.incl_cos)
+    shells = yv[:40]
+    r = np.sqrt(P.obs[0].edges_x)
+    p = (r[1:] ** 2 / (1 + r[1:]) ** 2 - r[:-1] ** 2 / (1 + r[:-1]) ** 2) / Mtot
+    sig = np.sqrt(p * (1 - p) / n)
+    assert np.all(np.abs(shells - p) < 4.5 * sig)
+
+    def s2cf(rr):
+        return (1 / 12.) * (12 * rr * (1 + rr) ** 3 * np.log1p(1 / rr)
+                            - rr / (1 + rr) * (25 + 52 * rr + 42 * rr ** 2 + 12 * rr ** 3))
+
+    def proj(R, f):
+        # 2 int_R^rmax f(r) r dr / sqrt(r^2 - R^2), r = R cosh t
+        g_ = lambda t: 2 * f(R * np.cosh(t)) * R * np.cosh(t)  # noqa: E731
+        return integrate.quad(g_, 0, np.arccosh(rmax / R), limit=400, epsrel=1e-10)[0]
+
+    mass_ann = yv[40:60]
+    v2_ann = yv[60:80]
+    Re = np.sqrt(P.obs[1].edges_x)
+    for j in range(3, 17):
+        Rm = math.sqrt(Re[j] * Re[j + 1])
+        num = proj(Rm, lambda rr: I._hernquist_rho(rr) * s2cf(rr))
+        den = proj(Rm, lambda rr: I._hernquist_rho(rr))
+        model = v2_ann[j] / mass_ann[j]
+        npart = mass_ann[j] * n
+        # annulus-averaged vs mid-radius value (smooth profile) + shot noise
+        assert abs(model / (num / den) - 1) < 0.02 + 4 * math.sqrt(2.0 / npart)
+
+
+def test_jeans_quadrature_matches_hernquist_closed_form():
+    g = _golden("hernquist_r1.txt")
+    rr, s2 = I._jeans_sigma_r2_table(I._hernquist_rho, I._hernquist_mass)
+
+    def cf(r):
+        return (1 / 12.) * (12 * r * (1 + r) ** 3 * np.log1p(1 / r)
+                            - r / (1 + r) * (25 + 52 * r + 42 * r ** 2 + 12 * r ** 3))
+
+    sel = (rr > 1e-3) & (rr < 5)
+    np.testing.assert_allclose(s2[sel], cf(rr[sel]), rtol=1e-8)
+    assert cf(1.0) == pytest.approx(g["sigma2_iso"][0], rel=1e-13)
+    # Osipkov-Merritt with ra -> infinity reduces to isotropic
+    rr2, s2om = I._jeans_sigma_r2_table(I._hernquist_rho, I._hernquist_mass, ra=1e6)
+    np.testing.assert_allclose(s2om[sel], s2[sel], rtol=1e-8)
+
+
+# ------------------------------------------------------------------ residual
+def test_residual_hand_worked_golden():
+    g = _golden("residual_3bin.txt")
+    D, Dt, coef, chi2, chi2r = O.residual(g["y"], g["Y"], g["sigma"], g["Dt_prev"],
+                                          g["alpha"][0], False)
+    np.testing.assert_array_equal(D, g["Delta"])
+    np.testing.assert_array_equal(Dt, g["Dt"])
+    np.testing.assert_array_equal(coef, g["coef"])
+    assert chi2 == g["chi2"][0] and chi2r == g["chi2_raw"][0]
+
+
+def test_residual_alpha_one_and_first_reduce_to_raw():
+    g = np.random.default_rng(3)
+    y, Y = g.uniform(1, 2, 9), g.uniform(1, 2, 9)
+    s = g.uniform(0.01, 0.1, 9)
+    D, Dt, _, chi2, chi2r = O.residual(y, Y, s, g.normal(size=9), 1.0, False)
+    np.testing.assert_array_equal(D, Dt)
+    assert chi2 == chi2r
+    D2, Dt2, _, _, _ = O.residual(y, Y, s, None, 0.3, True)
+    np.testing.assert_array_equal(D2, Dt2)
+
+
+# -------------------------------------------------------------------- update
+def _tiny(seed=0, n=8, nb=3):
+    g = np.random.default_rng(seed)
+    cells = g.integers(0, nb, n)
+    K = np.zeros((n, nb))
+    K[np.arange(n), cells] = g.uniform(0.5, 2.0, n)
+    Y = g.uniform(0.5, 1.5, nb) / nb
+    sig = 0.05 * Y
+    what = np.full(n, 1.0 / n)
+    return K, Y, sig, what
+
+
+def _F(w, K, Y, sig, what, mu):
+    # Eq. 1 and Eq. 2 written out directly
+    D = (w @ K - Y) / sig
+    S = -np.sum(w * np.log(w / what))
+    return -0.5 * np.sum(D * D) + mu * S
+
+
+def _oracle_G(w, K, Y, sig, what, mu, eps=1e-3, dt=1.0):
+    """Recover G_i = log(w_new/w)/(eps dt) from one oracle update (alpha=1)."""
+    D, Dt, coef, _, _ = O.residual(w @ K, Y, sig, None, 1.0, True)
+    dot = K @ coef
+    w1 = O.update_weights(w, what, dot, eps, mu, dt, 1.0)
+    return np.log(w1 / w) / (eps * dt)
+
+
+def test_update_direction_is_gradient_of_F():
+    K, Y, sig, what = _tiny()
+    mu = 0.3
+    w = np.random.default_rng(1).uniform(0.5, 1.5, 8) / 8
+    Gi = _oracle_G(w, K, Y, sig, what, mu)
+    h = 1e-7 * w
+    fd = np.array([(_F(w + h[i] * (np.arange(8) == i), K, Y, sig, what, mu)
+                    - _F(w - h[i] * (np.arange(8) == i), K, Y, sig, what, mu)) / (2 * h[i])
+                   for i in range(8)])
+    np.testing.assert_allclose(Gi, fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+def _frozen_problem(K, Y, sig, what, mu, eps, alpha=1.0):
+    """Frozen positions: particle i sits in a cell given by K's column."""
+    n, nb = K.shape
+    cells = np.argmax(K, axis=1)
+    # encode the cell as an x-coordinate in a 1D grid, K value via vlos^2
+    x = cells.astype(np.float64) + 0.5
+    vz = np.sqrt(K[np.arange(n), cells])
+    obs = [I.ObservableSet("grid", "vlos2", np.arange(nb + 1, dtype=np.float64),
+                           np.array([-1.0, 1.0]))]
+    P = I.Problem("frozen", n, np.stack([x, 0 * x, 0 * x]), np.stack([0 * x, 0 * x, vz]),
+                  np.full(n, 1.0 / n), what.copy(), [], obs, 0.0, 1.0, eps, mu, 1.0,
+                  alpha, I.PriorSpec("flat"), 0, "fp64", Y=Y, sigma=sig)
+    return P
+
+
+def test_F_rises_monotonically_and_reaches_newton_maximiser():
+    K, Y, sig, what = _tiny(2)
+    # data modes relax at eps*sum_i w K^2/sigma^2 ~ 0.7 per step (no overshoot),
+    # the 5 data-free directions at eps*mu = 2.5e-3 per step
+    mu = 5.0
+    P = _frozen_problem(K, Y, sig, what, mu, eps=5e-4)
+    st = O.init(P)
+    Fs = []
+    for _ in range(4000):
+        O.step(st, P, push=False)
+        Fs.append(st.history[-1]["F"])
+    Fs = np.array(Fs)
+    assert np.all(np.diff(Fs) > -1e-12 * np.abs(Fs[:-1]))
+    # independent maximiser: Newton on grad F = 0 in u = ln w
+    n = K.shape[0]
+
+    def grad_u(u):
+        w = np.exp(u)
+        D = (w @ K - Y) / sig
+        g = -(K @ (D / sig)) + mu * (-np.log(w / what) - 1.0)
+        return g * w
+
+    sol = optimize.root(grad_u, np.log(np.full(n, 1.0 / n)), tol=1e-13, method="hybr")
+    assert np.max(np.abs(grad_u(sol.x))) < 1e-10
+    w_star = np.exp(sol.x)
+    for _ in range(40000):
+        O.step(st, P, push=False)
+    np.testing.assert_allclose(st.w, w_star, rtol=1e-9)
+
+
+def test_flat_prior_limits():
+    # no data pull (coef = 0): dw/dt = eps mu w (-ln(w/what) - c)
+    n = 6
+    what = np.full(n, 1.0 / n)
+    w = what * np.array([0.5, 0.8, 1.0, 1.3, 2.0, 3.0])
+    for c, target in ((1.0, what * math.exp(-1.0)), (0.0, what)):
+        ww = w.copy()
+        for _ in range(6000):
+            ww = O.update_weights(ww, what, np.zeros(n), 1.0, 1.0, 0.01, c)
+        np.testing.assert_allclose(ww, target, rtol=1e-10)
+
+
+def test_stationary_when_model_matches_targets_and_mu_zero():
+    P = I.make_problem("plain-fp64", n=3000, with_target=False)
+    Y = O.observe(*P.pos, *P.vel, P.w0, P.obs, P.incl_sin, P.incl_cos)
+    P = P.with_targets(Y)
+    P.mu = 0.0
+    P.potential = []          # no force, v = 0: frozen
+    P.vel = P.vel * 0.0
+    st = O.init(P)
+    w0 = st.w.copy()
+    for _ in range(5):
+        O.step(st, P)
+    np.testing.assert_array_equal(st.w, w0)
+
+
+# -------------------------------------------------------------------- priors
+def test_prior_means_equal_weights_exact_and_sum_preserved():
+    g = np.random.default_rng(4)
+    n = 5000
+    cells = g.integers(0, 37, n)
+    w = np.full(n, 2.0 ** -20)
+    np.testing.assert_array_equal(O.prior_means(w, cells, 37), w)
+    w2 = g.uniform(0.1, 2.0, n) / n
+    wh = O.prior_means(w2, cells, 37)
+    assert abs(wh.sum() - w2.sum()) < 1e-13
+    # a singleton cell keeps its weight
+    cells[17] = 37
+    wh = O.prior_means(w2, cells, 38)
+    assert wh[17] == w2[17]
+
+
+def test_hernquist_circular_Lc_golden_and_round_trip():
+    g = _golden("hernquist_r1.txt")
+    prior = I.PriorSpec("e_lc", nE=4, nL=4, hernquist=(1.0, 1.0))
+    comps = [I.PotentialComponent("hernquist", (1.0, 1.0))]
+    # circular orbits at many radii: L^2/Lc^2(E) must be 1 (last L-cell)
+    r = np.geomspace(0.01, 50, 200)
+    vc = np.sqrt(r / (1 + r) ** 2)
+    z0 = 0 * r
+    cells = O.prior_cells(r, z0, z0, z0, vc, z0, prior, comps)
+    assert np.all(cells % 4 == 3)
+    # the closed form at r = 1 (E = -3/8): Lc^2 = 1/4 -> X = 1 exactly
+    E = g["E_circ"][0]
+    ed = E * 1.0
+    s = (-1 - math.sqrt(1 - 8 * ed)) / (4 * ed)
+    assert (s - 1) ** 3 / s ** 2 == g["Lc2"][0]
+    # radial orbits (L = 0) land in the first L-cell
+    cells = O.prior_cells(r, z0, z0, 0.3 * vc, z0, z0, prior, comps)
+    assert np.all(cells % 4 == 0)
+
+
+def test_prior_cells_match_brute_force():
+    P = I.make_problem("moving-priors", n=3000, with_target=False)
+    x, y, z = P.pos
+    vx, vy, vz = P.vel
+    cells = O.prior_cells(x, y, z, vx, vy, vz, P.prior, P.potential)
+    E = 0.5 * (vx * vx + vy * vy + vz * vz) - 1 / (np.sqrt(x * x + y * y + z * z) + 1)
+    L2 = (y * vz - z * vy) ** 2 + (z * vx - x * vz) ** 2 + (x * vy - y * vx) ** 2
+    Emin = E.min()
+    nE, nL = P.prior.nE, P.prior.nL
+    mism = 0
+    for i in range(0, 3000, 7):
+        if E[i] >= 0:
+            ref = nE * nL
+        else:
+            # circular orbit of energy E by bisection on r (independent of the closed form)
+            f = lambda rr: -1 / (1 + rr) + 0.5 * rr / (1 + rr) ** 2 - E[i]  # noqa: E731
+            rc = optimize.brentq(f, 1e-12, 1e8, xtol=1e-15, rtol=1e-15)
+            Lc2 = rc ** 3 / (1 + rc) ** 2
+            iE = min(nE - 1, int((E[i] - Emin) / (-Emin) * nE))
+            iL = min(nL - 1, int(L2[i] / Lc2 * nL))
+            ref = iE * nL + iL
+        if cells[i] != ref:
+            mism += 1
+    assert mism <= 2   # only particles within rounding of an edge may differ
+
+
+def test_prior_cells_e_lz_ranges():
+    P = I.make_problem("flat-log", n=20000, with_target=False)
+    cells = O.prior_cells(*P.pos, *P.vel, P.prior, P.potential)
+    assert cells.min() >= 0 and cells.max() < P.prior.nE * P.prior.nL
+    # the particle with the largest |Lz| lands in an extreme L-cell, and the
+    # most / least bound ones in the extreme E-cells
+    x, y, z = P.pos
+    vx, vy, vz = P.vel
+    Lz = x * vy - y * vx
+    i = np.argmax(np.abs(Lz))
+    assert cells[i] % P.prior.nL == (P.prior.nL - 1 if Lz[i] > 0 else 0)
+    E = 0.5 * (vx * vx + vy * vy + vz * vz) + 0.5 * np.log(0.01 + x * x + y * y + z * z / 0.64)
+    assert cells[np.argmin(E)] // P.prior.nL == 0
+    assert cells[np.argmax(E)] // P.prior.nL == P.prior.nE - 1
+
+
+# ---------------------------------------------------------------- whole runs
+@pytest.mark.slow
+def test_plain_run_chi2_falls_and_mass_is_kept():
+    """Model and target drawn from the same isotropic sphere: chi^2 falls and
+    sum w stays within the 2% error level over the full 2000 steps."""
+    P = I.make_problem("plain-fp64", n=20000, with_target=False)
+    T = I.make_problem("plain-fp64", n=20000, seed_model=2, with_target=False)
+    Y = O.observe(*T.pos, *T.vel, T.w0, P.obs, P.incl_sin, P.incl_cos)
+    P = P.with_targets(Y)
+    st = O.run(P, 2000)
+    h = st.history
+    assert h[-1]["chi2_raw"] < 0.75 * h[0]["chi2_raw"]
+    assert abs(h[-1]["sum_w"] - 1.0) < 0.02
