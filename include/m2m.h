@@ -1,0 +1,239 @@
+/*
+ * m2m.h -- C-ABI of libm2m.so, a GB300 (sm_103a) implementation of the
+ * made-to-measure (M2M) particle-model training step of Morganti & Gerhard,
+ * "NMAGIC made-to-measure particle models of galaxies" (arXiv:1207.6403).
+ *
+ * Section 2 of the paper: an N-body system with particle weights w_i is
+ * trained to reproduce target observables Y_j (with errors sigma_j) by
+ * maximising F = -1/2 chi^2 + mu S (Eq. 1), S = -sum_i w_i ln(w_i/w_hat_i)
+ * (Eq. 2), adapting the weights while the particles are evolved in the
+ * gravitational potential.  Section 2.1: the priors w_hat_i are flat (1/N)
+ * or "moving": the mean weight of the particles sharing a cell of
+ * integral-of-motion space.
+ *
+ * One step t -> t+1 (the order every entry point below follows):
+ *   1. kick-drift-kick leapfrog push of every particle in the potential;
+ *   2. scatter y_j = sum_i w_i K_j(x_i, v_i) at the new positions;
+ *   3. Delta_j = (y_j - Y_j)/sigma_j, smoothed Delta~_j <- alpha Delta_j +
+ *      (1 - alpha) Delta~_j, chi^2 = sum_j Delta~_j^2;
+ *   4. w_i <- w_i exp(eps dt G_i), G_i = mu (-ln(w_i/w_hat_i) - c)
+ *      - sum_j K_ij Delta~_j / sigma_j  (c = entropy_const, 1 for Eq. 2);
+ *   5. moving priors every `period` steps.
+ *
+ * Conventions common to all calls
+ *  - Every call returns an int status (M2M_OK = 0 or a negative M2M_ERR_*);
+ *    nothing aborts or throws across the ABI.  m2m_last_error() gives text.
+ *  - Work is enqueued on the stream given to m2m_init; calls return without
+ *    synchronising except those that return host values (m2m_get_*).
+ *  - Particle arrays are CALLER-OWNED DEVICE memory, borrowed until
+ *    m2m_free: positions x,y,z and velocities vx,vy,vz are float (M2M_FP32C)
+ *    or double (M2M_FP64) arrays of n elements, each 16-byte aligned; w and
+ *    w_hat are double arrays of n elements, 16-byte aligned, w_hat_i > 0.
+ *  - Host arrays passed in descriptors (edges, targets, GH parameters) are
+ *    copied during the call; the caller may free them afterwards.
+ *  - Scratch memory (partial histograms, cell tables) is library-owned,
+ *    allocated in m2m_init and freed by m2m_free.
+ *  - Errors found by kernels (non-finite weights, fixed-point overflow) are
+ *    sticky and reported by the next m2m_get_* call.
+ */
+#ifndef M2M_H
+#define M2M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
+
+#define M2M_OK             0
+#define M2M_ERR_ARG       -1   /* invalid argument, size or alignment */
+#define M2M_ERR_CUDA      -2   /* a CUDA runtime call failed */
+#define M2M_ERR_NONFINITE -3   /* a weight became non-finite or negative */
+#define M2M_ERR_STATE     -5   /* call not valid in the context's state */
+#define M2M_ERR_NOMEM     -6   /* device allocation failed */
+#define M2M_ERR_OVERFLOW  -7   /* fixed-point histogram range exceeded */
+
+/* Arithmetic of the particle path.
+ * M2M_FP64:  positions, push, bins and kernels in double; double sums.
+ * M2M_FP32C: positions, push, bins and kernels in float; weights stored and
+ *   updated in double; histogram sums exact in 64-bit fixed point
+ *   (resolution 2^-50 of the initial total weight); chi^2, entropy and the
+ *   prior-cell means reduced in double. */
+#define M2M_FP64  0
+#define M2M_FP32C 1
+
+/* ---- potential: Phi = sum of up to M2M_MAX_POT components (G = 1) ----
+ * HERNQUIST p = {GM, a}:        Phi = -GM/(r+a)
+ * NFW       p = {rho_s, r_s}:   Phi = -4 pi rho_s r_s^3 ln(1+r/r_s)/r
+ * LOG       p = {v0, Rc, q}:    Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)   */
+#define M2M_MAX_POT 4
+#define M2M_POT_HERNQUIST 1
+#define M2M_POT_NFW       2
+#define M2M_POT_LOG       3
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double p[4];
+} m2m_potential_desc;
+
+/* ---- observables: up to M2M_MAX_SETS sets, concatenated ----
+ * The observables of Section 1-2 (photometry, absorption-line kinematics).
+ * geom SHELL:   3D shells, cells by edges of r^2 = (x*x + y*y) + z*z
+ *      ANNULUS: projected annuli, edges of R^2 = X*X + Y*Y
+ *      GRID:    sky rectangles (pixels, IFU apertures), edges of X and of Y,
+ *               cell = iy*nx + ix
+ * Sky coordinates for the line of sight s = (0, sin i, cos i):
+ *   X = x, Y = z*sin_i - y*cos_i, v_los = vy*sin_i + vz*cos_i.
+ * quant MASS:  K = 1;  VLOS2: K = v_los^2;
+ *       GH:    K_n, n=0..4 = Gauss-Hermite kernels (van der Marel & Franx
+ *              1993 normalisation) about (gh_V, gh_S) of the cell, smoothed
+ *              by a Gaussian velocity kernel of width sigma_kernel.
+ * Membership: value v is in cell j iff edge_j <= v < edge_{j+1}, compared
+ * exactly (float values against the double edges), else in no cell.
+ * Observable index inside a set: cell*nmom + n (nmom = 5 for GH, else 1). */
+#define M2M_MAX_SETS 4
+#define M2M_GEOM_SHELL   1
+#define M2M_GEOM_ANNULUS 2
+#define M2M_GEOM_GRID    3
+#define M2M_Q_MASS  1
+#define M2M_Q_VLOS2 2
+#define M2M_Q_GH    3
+typedef struct {
+    int32_t geom, quant;
+    int32_t nx, ny;             /* ny = 1 unless GRID */
+    const double *edges_x;      /* host, nx+1 strictly increasing */
+    const double *edges_y;      /* host, ny+1 (GRID) or NULL */
+    const double *gh_V;         /* host, nx*ny (GH) or NULL */
+    const double *gh_S;         /* host, nx*ny (GH), > 0, or NULL */
+    double sigma_kernel;        /* GH velocity kernel width (>= 0) */
+} m2m_obs_desc;
+
+/* ---- priors (Section 2.1) ----
+ * FLAT: w_hat stays as passed.
+ * E_LC: every `period` steps, w_hat_i = mean w over i's cell of an nE x nL
+ *       grid in (E, L^2/Lc^2(E)) for the Hernquist (GM, a) circular orbit;
+ *       E cells uniform on [min E, 0), unbound particles in one extra cell.
+ * E_LZ: the same on an nE x nL grid in (E, L_z) uniform on
+ *       [min E, max E] x [-max|L_z|, max|L_z|].
+ * E = 1/2 v^2 + Phi(x) in the state precision. */
+#define M2M_PRIOR_FLAT 0
+#define M2M_PRIOR_E_LC 1
+#define M2M_PRIOR_E_LZ 2
+typedef struct {
+    int32_t kind, nE, nL, period;
+    double hernquist_GM, hernquist_a;
+} m2m_prior_desc;
+
+/* ---- step parameters ---- */
+typedef struct {
+    double eps;             /* weight-adaptation rate (already divided by N if wanted) */
+    double mu;              /* entropy weight of Eq. 1 */
+    double dt;              /* leapfrog time step */
+    double alpha;           /* smoothing: Delta~ <- alpha Delta + (1-alpha) Delta~ */
+    double entropy_const;   /* c in dS/dw_i = -ln(w_i/w_hat_i) - c (1 = Eq. 2) */
+    double incl_sin, incl_cos;
+} m2m_params;
+
+/* One record per step t: chi^2 of Delta~ and of Delta after the step's
+ * scatter, and S, sum w of the weights that produced that scatter;
+ * F = -1/2 chi2 + mu S. */
+typedef struct {
+    int64_t step;
+    double chi2, chi2_raw, S, sum_w, F;
+    double max_abs_dt;       /* max_j |Delta~_j| */
+} m2m_record;
+
+/* Create a context.  Validates all sizes and alignments (M2M_ERR_ARG),
+ * copies the tables, runs an initial scatter at (x_0, w_0) and sets
+ * Delta~ = Delta (as the first step's smoothing state).
+ *   ctx_out      receives the context (NULL on error)
+ *   precision    M2M_FP64 or M2M_FP32C (type of x..vz)
+ *   n            particle count, 1 <= n < 2^31
+ *   x..vz, w, what  caller-owned device arrays (see conventions)
+ *   pot, npot    potential components (0 <= npot <= M2M_MAX_POT)
+ *   obs, nsets   observable sets (1 <= nsets <= M2M_MAX_SETS), total
+ *                observables <= 8192
+ *   Y, sigma     host arrays of the total observable count, or NULL (all
+ *                masked: sigma_j <= 0 masks observable j)
+ *   par          step parameters;  prior: NULL means FLAT
+ *   stream       cudaStream_t to enqueue on (NULL = default stream)
+ * Cites: Section 2, Eq. 1-2; Section 2.1 (priors). */
+int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n,
+             void *x, void *y, void *z, void *vx, void *vy, void *vz,
+             double *w, double *what,
+             const m2m_potential_desc *pot, int32_t npot,
+             const m2m_obs_desc *obs, int32_t nsets,
+             const double *Y, const double *sigma,
+             const m2m_params *par, const m2m_prior_desc *prior,
+             void *stream);
+
+/* Replace targets and errors (host arrays of the observable count; sigma
+ * <= 0 masks).  Cites Section 2 (observables with errors). */
+int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma);
+
+/* Replace the potential (fixed, known potential of Section 2). */
+int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot);
+
+/* Scatter + residual at the current state, no push and no weight change.
+ * mode 0: compute y and Delta only (Delta~ untouched);
+ * mode 1: also smooth Delta~ <- alpha Delta + (1-alpha) Delta~;
+ * mode 2: also reset Delta~ = Delta.  Writes a record (step unchanged). */
+int m2m_observe(m2m_ctx *ctx, int32_t mode);
+
+/* Weight update (step 4) with the current Delta~ at the current positions:
+ * w_i <- w_i exp(eps dt G_i).  Cites Eq. 1-2 and the adaptation
+ * prescription that follows them. */
+int m2m_update_weights(m2m_ctx *ctx);
+
+/* Moving-prior recompute now (step 5) from the current positions and
+ * weights; M2M_ERR_STATE for FLAT priors.  Cites Section 2.1. */
+int m2m_priors(m2m_ctx *ctx);
+
+/* KDK leapfrog push only, nsteps times (step 1). */
+int m2m_push(m2m_ctx *ctx, int64_t nsteps);
+
+/* nsteps full M2M steps (1-5 above).  On return the particle arrays, w and
+ * w_hat hold the state after the last step. */
+int m2m_step(m2m_ctx *ctx, int64_t nsteps);
+
+/* Host copies (synchronise the stream).  Any pointer may be NULL.
+ * y, Delta, Dt: observable count doubles (last scatter).  Returns the
+ * sticky kernel error if one was raised. */
+int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt);
+
+/* Last record and the number of records available in the ring
+ * (capacity M2M_HISTORY). */
+#define M2M_HISTORY 16384
+int m2m_get_record(m2m_ctx *ctx, m2m_record *out);
+
+/* Records for steps [first, first+count) still in the ring, to host. */
+int m2m_get_history(m2m_ctx *ctx, int64_t first, int64_t count, m2m_record *out);
+
+/* Cell index of every particle at the current positions, to caller-owned
+ * DEVICE int32 arrays: obs_cells[s*n + i] for set s (-1 = none) and, if
+ * prior_cells is not NULL and priors are moving, the prior cell of i from
+ * the current positions (grid bounds from the current particles). */
+int m2m_get_cells(m2m_ctx *ctx, int32_t *obs_cells, int32_t *prior_cells);
+
+/* Sizes. */
+int64_t m2m_nobs(const m2m_ctx *ctx);
+int64_t m2m_steps_taken(const m2m_ctx *ctx);
+
+/* Launch shape of the particle kernels: threads per block (multiple of
+ * 32, <= 1024) and blocks per SM (0 = as many as fit).  Takes effect on the
+ * next launch. */
+int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
+
+/* Text of the last error on this context (or of the last failed m2m_init
+ * when ctx is NULL). */
+const char *m2m_last_error(const m2m_ctx *ctx);
+
+/* Release library-owned memory; particle arrays are not touched. */
+int m2m_free(m2m_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* M2M_H */

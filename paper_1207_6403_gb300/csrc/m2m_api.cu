@@ -1,0 +1,676 @@
+// C-ABI of libm2m.so: context, tables, launch sequencing of the M2M step.
+//
+// The step sequence on the caller's stream (Section 2 of the paper; the
+// order is push, scatter, residual, weight update, priors):
+//
+//   k_pass   [pending update at x_t] + push x_t -> x_{t+1} + scatter w_t
+//            at x_{t+1} + S, sum w of w_t      (+ (E, L_z) range if priors due)
+//   k_residual  y, Delta, Delta~, coef, chi^2, record t+1
+//   -> the update w_t -> w_{t+1} (needs coef of this residual) is carried
+//      into the next k_pass, so each particle is read and written once per
+//      step; a call ends with an update-only pass so the arrays hold w_{t+1};
+//   every `period` steps: update + prior cells pass, cell means, gather.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/m2m.h"
+#include "m2m_kernels.cuh"
+
+using namespace m2m;
+
+namespace {
+
+std::string g_init_error;
+
+struct LaunchShape {
+    void *fn;
+    int nt;
+};
+
+}  // namespace
+
+struct m2m_ctx {
+    int prec;
+    long long n;
+    void *x, *y, *z, *vx, *vy, *vz;
+    double *w, *what;
+    cudaStream_t st;
+    int nsm;
+    int threads, bps_req;
+    int nsets, nobs, npot;
+    SetDev sets[MAXSETS];
+    PotDev pot[MAXPOT];
+    m2m_params par;
+    m2m_prior_desc prior;
+    int ncells;
+    int edge_len, gh_len;
+    void *d_edges, *d_gh;
+    double *d_Y, *d_sigma, *d_Dt, *d_y, *d_Delta, *d_coef_d;
+    void *d_coef_r;
+    void *d_slots;
+    int slot_cap;
+    double *d_stat_slots, *d_chi_slots;
+    unsigned *d_ticket;
+    m2m_record *d_ring, *d_last;
+    int *d_err;
+    void *d_mm_slots;
+    int mm_nblocks;
+    int *d_cell_ids;
+    void *d_cell_acc;
+    unsigned *d_cell_cnt;
+    double *d_cell_mean;
+    int fx_shift;
+    double fx_q;
+    long long t;
+    bool pending;
+    int last_grid;       // grid of the last scatter pass (slots to reduce)
+    std::string err;
+};
+
+namespace {
+
+int set_err(m2m_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_init_error = buf;
+    return code;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return set_err(ctx, M2M_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+float ceil_float(double e) {
+    float f = (float)e;
+    if ((double)f < e) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Index guess for an edge table: linear or logarithmic if either predicts
+// every edge within half a cell, else bisection.
+void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
+    double span = e[nb] - e[0];
+    bool lin_ok = span > 0 && isfinite(span);
+    if (lin_ok) {
+        double a = nb / span, b = -e[0] * a;
+        for (int k = 0; k <= nb && lin_ok; ++k)
+            if (fabs(a * e[k] + b - k) > 0.25) lin_ok = false;
+        if (lin_ok) { *mode = G_LIN; *ga = (float)a; *gb = (float)b; return; }
+    }
+    if (e[0] > 0) {
+        double l0 = log2(e[0]), l1 = log2(e[nb]);
+        bool ok = l1 > l0;
+        double a = ok ? nb / (l1 - l0) : 0, b = -l0 * a;
+        for (int k = 0; k <= nb && ok; ++k)
+            if (fabs(a * log2(e[k]) + b - k) > 0.25) ok = false;
+        if (ok) { *mode = G_LOG; *ga = (float)a; *gb = (float)b; return; }
+    }
+    *mode = G_BIS; *ga = 0.f; *gb = 0.f;
+}
+
+size_t pass_smem(const m2m_ctx *c, int flags) {
+    size_t rs = c->prec == M2M_FP32C ? 4 : 8;
+    size_t b = 0;
+    if (flags & F_SCAT) b += 8 * (size_t)((c->nobs + 1) & ~1);
+    if (flags & F_UPD) b += rs * (size_t)((c->nobs + 3) & ~3);
+    b += rs * (size_t)((c->edge_len + 3) & ~3);
+    b += rs * (size_t)((c->gh_len + 3) & ~3);
+    if (flags & F_CELLS) {
+        b += rs * (size_t)((c->prior.nE + 4) & ~3) + rs * (size_t)((c->prior.nL + 4) & ~3) + 16;
+        if (c->prec == M2M_FP32C) b += 12 * (size_t)((c->ncells + 3) & ~3);
+        else b += 8 * (size_t)((c->ncells + 1) & ~1) + 4 * (size_t)((c->ncells + 3) & ~3);
+    }
+    return b;
+}
+
+LaunchShape pick_kernel(const m2m_ctx *c) {
+    if (c->prec == M2M_FP32C) {
+        switch (c->threads) {
+            case 256: return {(void *)k_pass<float, 256, 2>, 256};
+            case 1024: return {(void *)k_pass<float, 1024, 1>, 1024};
+            default: return {(void *)k_pass<float, 512, 2>, 512};
+        }
+    }
+    switch (c->threads) {
+        case 512: return {(void *)k_pass<double, 512, 1>, 512};
+        default: return {(void *)k_pass<double, 256, 1>, 256};
+    }
+}
+
+void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
+    memset(&a, 0, sizeof a);
+    a.x = c->x; a.y = c->y; a.z = c->z; a.vx = c->vx; a.vy = c->vy; a.vz = c->vz;
+    a.w = c->w; a.what = c->what; a.n = c->n; a.flags = flags;
+    a.nsets = c->nsets; a.nobs = c->nobs; a.npot = c->npot;
+    memcpy(a.sets, c->sets, sizeof a.sets);
+    memcpy(a.pot, c->pot, sizeof a.pot);
+    a.eps_dt = c->par.eps * c->par.dt;
+    a.mu = c->par.mu; a.ent_c = c->par.entropy_const;
+    a.hdt = 0.5 * c->par.dt; a.dt = c->par.dt;
+    a.sin_i = c->par.incl_sin; a.cos_i = c->par.incl_cos;
+    a.edge_tab = c->d_edges; a.edge_len = c->edge_len;
+    a.gh_tab = c->d_gh; a.gh_len = c->gh_len;
+    a.coef = c->d_coef_r;
+    a.slots = c->d_slots; a.fx_shift = c->fx_shift;
+    a.stat_slots = c->d_stat_slots;
+    a.prior_kind = c->prior.kind; a.nE = c->prior.nE; a.nL = c->prior.nL; a.ncells = c->ncells;
+    a.pk = c->prior.hernquist_a / c->prior.hernquist_GM;
+    a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
+    a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
+    a.cell_ids = c->d_cell_ids; a.cell_acc = c->d_cell_acc; a.cell_cnt = c->d_cell_cnt;
+    a.err = c->d_err;
+}
+
+int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
+    PassArgs a;
+    fill_args(ctx, a, flags);
+    LaunchShape ks = pick_kernel(ctx);
+    size_t sm = pass_smem(ctx, flags);
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
+    if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "pass needs %zu B shared memory: does not fit", sm);
+    int bps = occ;
+    if (ctx->bps_req > 0 && ctx->bps_req < bps) bps = ctx->bps_req;
+    long long nch = (ctx->n + (ctx->prec == M2M_FP32C ? 3 : 1)) / (ctx->prec == M2M_FP32C ? 4 : 2);
+    long long need = (nch + ks.nt - 1) / ks.nt;
+    long long grid = (long long)ctx->nsm * bps;
+    if (grid > ctx->slot_cap) grid = ctx->slot_cap;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    void *args[] = {&a};
+    CU(cudaLaunchKernel(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
+    if (flags & F_SCAT) ctx->last_grid = (int)grid;
+    if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
+    if (grid_out) *grid_out = (int)grid;
+    return M2M_OK;
+}
+
+int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, int stat_nblk) {
+    ResArgs r;
+    memset(&r, 0, sizeof r);
+    r.slots = ctx->d_slots; r.nblk = ctx->last_grid; r.nobs = ctx->nobs;
+    r.fixed = ctx->prec == M2M_FP32C; r.q = ctx->fx_q;
+    r.Y = ctx->d_Y; r.sigma = ctx->d_sigma; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
+    r.coef_d = ctx->d_coef_d; r.coef_r = ctx->d_coef_r; r.r_float = ctx->prec == M2M_FP32C;
+    r.mode = mode; r.alpha = ctx->par.alpha; r.mu = ctx->par.mu;
+    r.stat_slots = ctx->d_stat_slots; r.stat_nblk = stat_nblk;
+    r.chi_slots = ctx->d_chi_slots; r.ticket = ctx->d_ticket;
+    r.ring = ctx->d_ring; r.last = ctx->d_last; r.rec_step = rec_step; r.write_ring = write_ring;
+    r.err = ctx->d_err;
+    int nb = (ctx->nobs + 31) / 32;
+    void *args[] = {&r};
+    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(256), args, 0, ctx->st));
+    return M2M_OK;
+}
+
+// scatter + residual at the current state
+int observe_now(m2m_ctx *ctx, int extra_flags, int mode, long long rec_step, int write_ring) {
+    int g = 0;
+    int rc = launch_pass(ctx, F_SCAT | F_STATS | extra_flags, &g);
+    if (rc) return rc;
+    return launch_residual(ctx, mode, rec_step, write_ring, g);
+}
+
+int prior_recompute(m2m_ctx *ctx, int pass_flags) {
+    // pass_flags: F_UPD to apply a pending update in the same pass
+    size_t acc_b = (size_t)ctx->ncells * 8;
+    CU(cudaMemsetAsync(ctx->d_cell_acc, 0, acc_b, ctx->st));
+    CU(cudaMemsetAsync(ctx->d_cell_cnt, 0, (size_t)ctx->ncells * 4, ctx->st));
+    int rc = launch_pass(ctx, F_CELLS | pass_flags);
+    if (rc) return rc;
+    int nb = (ctx->ncells + 255) / 256;
+    k_prior_mean<<<nb, 256, 0, ctx->st>>>(ctx->d_cell_acc, ctx->d_cell_cnt, ctx->ncells,
+                                          ctx->prec == M2M_FP32C, ctx->fx_q, ctx->d_cell_mean);
+    CU(cudaGetLastError());
+    int g = ctx->nsm * 8;
+    long long need = (ctx->n + 255) / 256;
+    if (g > need) g = (int)need;
+    k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->n);
+    CU(cudaGetLastError());
+    return M2M_OK;
+}
+
+int check_err_word(m2m_ctx *ctx) {
+    int h = 0;
+    CU(cudaMemcpyAsync(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
+    CU(cudaStreamSynchronize(ctx->st));
+    if (h & ERR_NONFINITE) return set_err(ctx, M2M_ERR_NONFINITE, "a weight or a reduction became non-finite");
+    if (h & ERR_OVERFLOW) return set_err(ctx, M2M_ERR_OVERFLOW, "fixed-point histogram range exceeded");
+    return M2M_OK;
+}
+
+void free_all(m2m_ctx *c) {
+    void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
+                    c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
+                    c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
+                    c->d_cell_mean};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
+    if (npot < 0 || npot > MAXPOT) return set_err(ctx, M2M_ERR_ARG, "npot=%d out of [0,%d]", npot, MAXPOT);
+    if (npot > 0 && !pot) return set_err(ctx, M2M_ERR_ARG, "pot is NULL");
+    PotDev tmp[MAXPOT];
+    memset(tmp, 0, sizeof tmp);
+    for (int k = 0; k < npot; ++k) {
+        const double *p = pot[k].p;
+        PotDev &d = tmp[k];
+        d.kind = pot[k].kind;
+        if (pot[k].kind == M2M_POT_HERNQUIST) {
+            if (!(p[0] > 0 && p[1] > 0)) return set_err(ctx, M2M_ERR_ARG, "hernquist needs GM>0, a>0");
+            d.c[0] = p[0]; d.c[1] = p[1];
+        } else if (pot[k].kind == M2M_POT_LOG) {
+            if (!(p[0] > 0 && p[1] > 0 && p[2] > 0)) return set_err(ctx, M2M_ERR_ARG, "log needs v0, Rc, q > 0");
+            d.c[0] = p[1] * p[1]; d.c[1] = 1.0 / (p[2] * p[2]); d.c[2] = p[0] * p[0]; d.c[3] = 0.5 * p[0] * p[0];
+        } else if (pot[k].kind == M2M_POT_NFW) {
+            if (!(p[0] > 0 && p[1] > 0)) return set_err(ctx, M2M_ERR_ARG, "nfw needs rho_s>0, r_s>0");
+            d.c[0] = 4.0 * M_PI * p[0] * p[1] * p[1] * p[1]; d.c[1] = p[1]; d.c[2] = 1.0 / p[1];
+        } else {
+            return set_err(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot[k].kind);
+        }
+    }
+    memcpy(ctx->pot, tmp, sizeof tmp);
+    ctx->npot = npot;
+    return M2M_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, void *z, void *vx,
+             void *vy, void *vz, double *w, double *what, const m2m_potential_desc *pot, int32_t npot,
+             const m2m_obs_desc *obs, int32_t nsets, const double *Y, const double *sigma,
+             const m2m_params *par, const m2m_prior_desc *prior, void *stream) {
+    m2m_ctx *ctx = nullptr;
+    if (!ctx_out) return set_err(nullptr, M2M_ERR_ARG, "ctx_out is NULL");
+    *ctx_out = nullptr;
+    if (precision != M2M_FP64 && precision != M2M_FP32C)
+        return set_err(nullptr, M2M_ERR_ARG, "precision %d unknown", precision);
+    if (n < 1 || n >= (1ll << 31)) return set_err(nullptr, M2M_ERR_ARG, "n=%lld out of [1, 2^31)", (long long)n);
+    void *arrs[] = {x, y, z, vx, vy, vz, w, what};
+    for (int k = 0; k < 8; ++k)
+        if (!arrs[k] || !aligned16(arrs[k]))
+            return set_err(nullptr, M2M_ERR_ARG, "particle array %d is NULL or not 16-byte aligned", k);
+    if (!par) return set_err(nullptr, M2M_ERR_ARG, "par is NULL");
+    if (!(isfinite(par->eps) && isfinite(par->mu) && isfinite(par->dt) && isfinite(par->alpha) &&
+          isfinite(par->entropy_const) && isfinite(par->incl_sin) && isfinite(par->incl_cos)))
+        return set_err(nullptr, M2M_ERR_ARG, "non-finite parameter");
+    if (!(par->alpha > 0 && par->alpha <= 1)) return set_err(nullptr, M2M_ERR_ARG, "alpha must be in (0,1]");
+    if (nsets < 1 || nsets > MAXSETS || !obs)
+        return set_err(nullptr, M2M_ERR_ARG, "nsets=%d out of [1,%d]", nsets, MAXSETS);
+
+    ctx = new m2m_ctx();   // value-initialised: all pointers NULL
+    ctx->prec = precision;
+    ctx->n = n;
+    ctx->x = x; ctx->y = y; ctx->z = z; ctx->vx = vx; ctx->vy = vy; ctx->vz = vz;
+    ctx->w = w; ctx->what = what;
+    ctx->st = (cudaStream_t)stream;
+    ctx->par = *par;
+    ctx->threads = precision == M2M_FP32C ? 512 : 256;
+    ctx->bps_req = 0;
+    int rc = build_potential(ctx, pot, npot);
+    if (rc) { g_init_error = ctx->err; delete ctx; return rc; }
+
+    // observable tables
+    const bool f32 = precision == M2M_FP32C;
+    std::vector<double> edges_d;
+    std::vector<double> gh_d;
+    int nobs = 0;
+    for (int s = 0; s < nsets; ++s) {
+        const m2m_obs_desc &o = obs[s];
+        SetDev &d = ctx->sets[s];
+        memset(&d, 0, sizeof d);
+        d.geom = o.geom; d.quant = o.quant; d.nx = o.nx; d.ny = o.geom == M2M_GEOM_GRID ? o.ny : 1;
+        if (o.geom < 1 || o.geom > 3 || o.quant < 1 || o.quant > 3 || o.nx < 1 || d.ny < 1 || !o.edges_x ||
+            (o.geom == M2M_GEOM_GRID && !o.edges_y)) {
+            set_err(nullptr, M2M_ERR_ARG, "observable set %d: bad geometry/quantity/sizes/edges", s);
+            delete ctx; return M2M_ERR_ARG;
+        }
+        d.nmom = o.quant == M2M_Q_GH ? 5 : 1;
+        long long cells = (long long)d.nx * d.ny;
+        d.obs_off = nobs;
+        if (nobs + cells * d.nmom > MAXOBS) {
+            set_err(nullptr, M2M_ERR_ARG, "more than %d observables", MAXOBS);
+            delete ctx; return M2M_ERR_ARG;
+        }
+        nobs += (int)(cells * d.nmom);
+        for (int ax = 0; ax < (o.geom == M2M_GEOM_GRID ? 2 : 1); ++ax) {
+            const double *e = ax == 0 ? o.edges_x : o.edges_y;
+            int nb = ax == 0 ? d.nx : d.ny;
+            for (int k = 0; k <= nb; ++k) {
+                if (!(e[k] == e[k]) || (k > 0 && !(e[k] > e[k - 1]))) {
+                    set_err(nullptr, M2M_ERR_ARG, "observable set %d: edges must be strictly increasing", s);
+                    delete ctx; return M2M_ERR_ARG;
+                }
+            }
+            int off = (int)edges_d.size();
+            edges_d.insert(edges_d.end(), e, e + nb + 1);
+            if (ax == 0) { d.ex_off = off; guess_params(e, nb, &d.gx_mode, &d.gx_a, &d.gx_b); }
+            else { d.ey_off = off; guess_params(e, nb, &d.gy_mode, &d.gy_a, &d.gy_b); }
+        }
+        if (o.quant == M2M_Q_GH) {
+            if (!o.gh_V || !o.gh_S || !(o.sigma_kernel >= 0)) {
+                set_err(nullptr, M2M_ERR_ARG, "observable set %d: GH needs gh_V, gh_S, sigma_kernel>=0", s);
+                delete ctx; return M2M_ERR_ARG;
+            }
+            d.gh_off = (int)gh_d.size();
+            for (long long c = 0; c < cells; ++c) {
+                double S = o.gh_S[c];
+                if (!(S > 0) || !isfinite(o.gh_V[c])) {
+                    set_err(nullptr, M2M_ERR_ARG, "observable set %d: gh_S must be > 0", s);
+                    delete ctx; return M2M_ERR_ARG;
+                }
+                double sk = o.sigma_kernel / S;
+                double d1 = 1.0 + sk * sk;
+                gh_d.push_back(o.gh_V[c]);
+                gh_d.push_back(1.0 / S);
+                gh_d.push_back(1.0 / d1);
+                gh_d.push_back(sk * sk / d1);
+                gh_d.push_back(2.0 * sqrt(M_PI) / sqrt(2.0 * M_PI * d1));
+            }
+        }
+    }
+    ctx->nsets = nsets;
+    ctx->nobs = nobs;
+    ctx->edge_len = (int)edges_d.size();
+    ctx->gh_len = (int)gh_d.size();
+
+    // priors
+    if (prior && prior->kind != M2M_PRIOR_FLAT) {
+        ctx->prior = *prior;
+        if ((prior->kind != M2M_PRIOR_E_LC && prior->kind != M2M_PRIOR_E_LZ) || prior->nE < 1 ||
+            prior->nL < 1 || prior->period < 1 ||
+            (long long)prior->nE * prior->nL + 1 > MAXCELLS ||
+            (prior->kind == M2M_PRIOR_E_LC && !(prior->hernquist_GM > 0 && prior->hernquist_a > 0))) {
+            set_err(nullptr, M2M_ERR_ARG, "bad prior descriptor");
+            delete ctx; return M2M_ERR_ARG;
+        }
+        ctx->ncells = prior->nE * prior->nL + (prior->kind == M2M_PRIOR_E_LC ? 1 : 0);
+    } else {
+        memset(&ctx->prior, 0, sizeof ctx->prior);
+        ctx->prior.kind = M2M_PRIOR_FLAT;
+        ctx->prior.nE = ctx->prior.nL = 1;
+        ctx->prior.hernquist_GM = ctx->prior.hernquist_a = 1.0;
+        ctx->ncells = 0;
+    }
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) {
+        set_err(nullptr, M2M_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+        delete ctx; return M2M_ERR_CUDA;
+    }
+    ctx->slot_cap = ctx->nsm * 4;
+
+#define ALLOC(ptr, bytes)                                                               \
+    do {                                                                                \
+        if (cudaMalloc((void **)&(ptr), (bytes) ? (bytes) : 16) != cudaSuccess) {       \
+            set_err(nullptr, M2M_ERR_NOMEM, "cudaMalloc(%zu) failed", (size_t)(bytes)); \
+            free_all(ctx); delete ctx; return M2M_ERR_NOMEM;                            \
+        }                                                                               \
+    } while (0)
+    size_t rs = f32 ? 4 : 8;
+    ALLOC(ctx->d_edges, rs * ctx->edge_len);
+    ALLOC(ctx->d_gh, rs * (ctx->gh_len + 1));
+    ALLOC(ctx->d_Y, 8 * nobs); ALLOC(ctx->d_sigma, 8 * nobs); ALLOC(ctx->d_Dt, 8 * nobs);
+    ALLOC(ctx->d_y, 8 * nobs); ALLOC(ctx->d_Delta, 8 * nobs); ALLOC(ctx->d_coef_d, 8 * nobs);
+    ALLOC(ctx->d_coef_r, rs * nobs);
+    ALLOC(ctx->d_slots, (size_t)8 * nobs * ctx->slot_cap);
+    ALLOC(ctx->d_stat_slots, (size_t)16 * ctx->slot_cap);
+    ALLOC(ctx->d_chi_slots, (size_t)24 * ((nobs + 31) / 32));
+    ALLOC(ctx->d_ticket, 4);
+    ALLOC(ctx->d_ring, sizeof(m2m_record) * M2M_HISTORY);
+    ALLOC(ctx->d_last, sizeof(m2m_record));
+    ALLOC(ctx->d_err, 4);
+    ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
+    if (ctx->ncells) {
+        ALLOC(ctx->d_cell_ids, 4 * (size_t)n);
+        ALLOC(ctx->d_cell_acc, 8 * (size_t)ctx->ncells);
+        ALLOC(ctx->d_cell_cnt, 4 * (size_t)ctx->ncells);
+        ALLOC(ctx->d_cell_mean, 8 * (size_t)ctx->ncells);
+    }
+#undef ALLOC
+
+    // tables: float edges are the smallest float >= the double edge
+    {
+        std::vector<unsigned char> buf(rs * (edges_d.size() + gh_d.size() + 1));
+        if (f32) {
+            float *e = (float *)buf.data();
+            for (size_t k = 0; k < edges_d.size(); ++k) e[k] = ceil_float(edges_d[k]);
+            float *g = e + edges_d.size();
+            for (size_t k = 0; k < gh_d.size(); ++k) g[k] = (float)gh_d[k];
+        } else {
+            double *e = (double *)buf.data();
+            memcpy(e, edges_d.data(), 8 * edges_d.size());
+            memcpy(e + edges_d.size(), gh_d.data(), 8 * gh_d.size());
+        }
+        cudaError_t e1 = cudaMemcpy(ctx->d_edges, buf.data(), rs * edges_d.size(), cudaMemcpyHostToDevice);
+        cudaError_t e2 = cudaMemcpy(ctx->d_gh, buf.data() + rs * edges_d.size(), rs * gh_d.size(),
+                                    cudaMemcpyHostToDevice);
+        std::vector<double> zero(nobs, 0.0);
+        cudaError_t e3 = cudaMemcpy(ctx->d_Y, Y ? Y : zero.data(), 8 * nobs, cudaMemcpyHostToDevice);
+        cudaError_t e4 = cudaMemcpy(ctx->d_sigma, sigma ? sigma : zero.data(), 8 * nobs, cudaMemcpyHostToDevice);
+        cudaError_t e5 = cudaMemset(ctx->d_Dt, 0, 8 * nobs);
+        cudaError_t e6 = cudaMemset(ctx->d_ticket, 0, 4);
+        cudaError_t e7 = cudaMemset(ctx->d_err, 0, 4);
+        cudaError_t e8 = cudaMemset(ctx->d_coef_r, 0, rs * nobs);
+        cudaError_t e9 = cudaMemset(ctx->d_ring, 0, sizeof(m2m_record) * M2M_HISTORY);
+        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9};
+        for (cudaError_t e : es)
+            if (e != cudaSuccess) {
+                set_err(nullptr, M2M_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+                free_all(ctx); delete ctx; return M2M_ERR_CUDA;
+            }
+    }
+    // the pass kernels may use more than 48 KB of shared memory
+    void *kfns[] = {(void *)k_pass<float, 256, 2>, (void *)k_pass<float, 512, 2>, (void *)k_pass<float, 1024, 1>,
+                    (void *)k_pass<double, 256, 1>, (void *)k_pass<double, 512, 1>,
+                    (void *)k_cells<float>, (void *)k_cells<double>};
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (void *f : kfns) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) {
+            set_err(nullptr, M2M_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            free_all(ctx); delete ctx; return M2M_ERR_CUDA;
+        }
+    }
+
+    // fixed-point scale from the initial total weight: resolution
+    // 2^-50 * 2^ceil(log2 sum w), range 2^13 times that total
+    ctx->fx_shift = 50;
+    ctx->fx_q = ldexp(1.0, -50);
+    int g = 0;
+    rc = launch_pass(ctx, F_STATS, &g);
+    if (rc == M2M_OK) {
+        std::vector<double> st(2 * g);
+        cudaError_t e = cudaMemcpyAsync(st.data(), ctx->d_stat_slots, 16 * g, cudaMemcpyDeviceToHost, ctx->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+        if (e != cudaSuccess) rc = set_err(ctx, M2M_ERR_CUDA, "init reduction: %s", cudaGetErrorString(e));
+        double W = 0.0;
+        for (int b = 0; b < g; ++b) W += st[2 * b + 1];
+        if (rc == M2M_OK && !(W >= 0 && isfinite(W))) rc = set_err(ctx, M2M_ERR_NONFINITE, "sum of weights not finite");
+        if (rc == M2M_OK && W > 0) {
+            int e2 = (int)ceil(log2(W));
+            ctx->fx_shift = 50 - e2;
+            ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
+        }
+    }
+    if (rc == M2M_OK) rc = observe_now(ctx, 0, 2, 0, 0);
+    if (rc == M2M_OK) rc = check_err_word(ctx);
+    if (rc != M2M_OK) {
+        g_init_error = ctx->err;
+        free_all(ctx); delete ctx; return rc;
+    }
+    ctx->t = 0;
+    ctx->pending = false;
+    *ctx_out = ctx;
+    return M2M_OK;
+}
+
+int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma) {
+    if (!ctx || !Y || !sigma) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(ctx->d_Y, Y, 8 * (size_t)ctx->nobs, cudaMemcpyHostToDevice, ctx->st));
+    CU(cudaMemcpyAsync(ctx->d_sigma, sigma, 8 * (size_t)ctx->nobs, cudaMemcpyHostToDevice, ctx->st));
+    return M2M_OK;
+}
+
+int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
+    if (!ctx) return M2M_ERR_ARG;
+    return build_potential(ctx, pot, npot);
+}
+
+int m2m_observe(m2m_ctx *ctx, int32_t mode) {
+    if (!ctx || mode < 0 || mode > 2) return set_err(ctx, M2M_ERR_ARG, "bad context or mode");
+    if (ctx->pending) return set_err(ctx, M2M_ERR_STATE, "update pending");
+    return observe_now(ctx, 0, mode, ctx->t, 0);
+}
+
+int m2m_update_weights(m2m_ctx *ctx) {
+    if (!ctx) return M2M_ERR_ARG;
+    return launch_pass(ctx, F_UPD);
+}
+
+int m2m_priors(m2m_ctx *ctx) {
+    if (!ctx) return M2M_ERR_ARG;
+    if (ctx->prior.kind == M2M_PRIOR_FLAT) return set_err(ctx, M2M_ERR_STATE, "priors are flat");
+    int rc = launch_pass(ctx, F_MINMAX);
+    if (rc) return rc;
+    return prior_recompute(ctx, 0);
+}
+
+int m2m_push(m2m_ctx *ctx, int64_t nsteps) {
+    if (!ctx || nsteps < 0) return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int rc = launch_pass(ctx, F_PUSH);
+        if (rc) return rc;
+    }
+    return M2M_OK;
+}
+
+int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
+    if (!ctx || nsteps < 0) return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    const bool moving = ctx->prior.kind != M2M_PRIOR_FLAT;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        long long t1 = ctx->t + 1;
+        bool prior_due = moving && (t1 % ctx->prior.period == 0);
+        int fl = F_PUSH | F_SCAT | F_STATS | (ctx->pending ? F_UPD : 0) | (prior_due ? F_MINMAX : 0);
+        int g = 0;
+        int rc = launch_pass(ctx, fl, &g);
+        if (rc) return rc;
+        rc = launch_residual(ctx, 1, t1, 1, g);
+        if (rc) return rc;
+        ctx->t = t1;
+        ctx->pending = true;
+        if (prior_due) {
+            rc = prior_recompute(ctx, F_UPD);
+            if (rc) return rc;
+            ctx->pending = false;
+        }
+    }
+    if (ctx->pending) {
+        int rc = launch_pass(ctx, F_UPD);
+        if (rc) return rc;
+        ctx->pending = false;
+    }
+    return M2M_OK;
+}
+
+int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt) {
+    if (!ctx) return M2M_ERR_ARG;
+    size_t b = 8 * (size_t)ctx->nobs;
+    if (y) CU(cudaMemcpyAsync(y, ctx->d_y, b, cudaMemcpyDeviceToHost, ctx->st));
+    if (Delta) CU(cudaMemcpyAsync(Delta, ctx->d_Delta, b, cudaMemcpyDeviceToHost, ctx->st));
+    if (Dt) CU(cudaMemcpyAsync(Dt, ctx->d_Dt, b, cudaMemcpyDeviceToHost, ctx->st));
+    return check_err_word(ctx);
+}
+
+int m2m_get_record(m2m_ctx *ctx, m2m_record *out) {
+    if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(out, ctx->d_last, sizeof *out, cudaMemcpyDeviceToHost, ctx->st));
+    return check_err_word(ctx);
+}
+
+int m2m_get_history(m2m_ctx *ctx, int64_t first, int64_t count, m2m_record *out) {
+    if (!ctx || !out || count < 0) return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    long long lo = ctx->t - M2M_HISTORY + 1;
+    if (lo < 1) lo = 1;
+    if (first < lo || first + count - 1 > ctx->t)
+        return set_err(ctx, M2M_ERR_ARG, "records [%lld, %lld) not in the ring [%lld, %lld]", (long long)first,
+                       (long long)(first + count), lo, ctx->t);
+    for (int64_t k = 0; k < count;) {
+        long long idx = (first + k) % M2M_HISTORY;
+        long long run = M2M_HISTORY - idx;
+        if (run > count - k) run = count - k;
+        CU(cudaMemcpyAsync(out + k, ctx->d_ring + idx, sizeof(m2m_record) * run, cudaMemcpyDeviceToHost, ctx->st));
+        k += run;
+    }
+    return check_err_word(ctx);
+}
+
+int m2m_get_cells(m2m_ctx *ctx, int32_t *obs_cells, int32_t *prior_cells) {
+    if (!ctx || !obs_cells) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    if (prior_cells && ctx->prior.kind == M2M_PRIOR_FLAT) return set_err(ctx, M2M_ERR_STATE, "priors are flat");
+    if (prior_cells) {
+        int rc = launch_pass(ctx, F_MINMAX);
+        if (rc) return rc;
+    }
+    PassArgs a;
+    fill_args(ctx, a, 0);
+    size_t rs = ctx->prec == M2M_FP32C ? 4 : 8;
+    size_t sm = rs * ((ctx->edge_len + 3) & ~3) + rs * ((ctx->prior.nE + 4) & ~3) + rs * ((ctx->prior.nL + 4) & ~3) + 16;
+    int g = ctx->nsm * 4;
+    long long need = (ctx->n + 255) / 256;
+    if (g > need) g = (int)need;
+    void *args[] = {&a, &obs_cells, &prior_cells};
+    void *fn = ctx->prec == M2M_FP32C ? (void *)k_cells<float> : (void *)k_cells<double>;
+    CU(cudaLaunchKernel(fn, dim3(g), dim3(256), args, sm, ctx->st));
+    return M2M_OK;
+}
+
+int64_t m2m_nobs(const m2m_ctx *ctx) { return ctx ? ctx->nobs : -1; }
+int64_t m2m_steps_taken(const m2m_ctx *ctx) { return ctx ? ctx->t : -1; }
+
+int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm) {
+    if (!ctx) return M2M_ERR_ARG;
+    bool ok = ctx->prec == M2M_FP32C ? (threads == 256 || threads == 512 || threads == 1024)
+                                     : (threads == 256 || threads == 512);
+    if (!ok || blocks_per_sm < 0 || blocks_per_sm > 4)
+        return set_err(ctx, M2M_ERR_ARG, "launch shape %d threads x %d blocks/SM not supported", threads, blocks_per_sm);
+    ctx->threads = threads;
+    ctx->bps_req = blocks_per_sm;
+    return M2M_OK;
+}
+
+const char *m2m_last_error(const m2m_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+int m2m_free(m2m_ctx *ctx) {
+    if (!ctx) return M2M_OK;
+    cudaStreamSynchronize(ctx->st);
+    free_all(ctx);
+    delete ctx;
+    return M2M_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,342 @@
+// Device-side building blocks of the M2M step (sm_103a).
+//
+// Everything that decides an integer (bin and cell membership) or feeds one
+// (the orbit push) is evaluated in the state precision R with a fixed
+// operation order and no contraction (the library is compiled with
+// -fmad=false; fmaf/fma are written out only where rounding order does not
+// matter).  Membership is "edge_j <= v < edge_{j+1}" against edge tables
+// that, for R = float, hold the smallest float >= each double edge, which is
+// exactly the same test as comparing against the double edge.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace m2m {
+
+constexpr int MAXSETS = 4;
+constexpr int MAXPOT = 4;
+constexpr int MAXOBS = 8192;
+constexpr int MAXCELLS = 16385;
+
+enum { F_UPD = 1, F_PUSH = 2, F_SCAT = 4, F_STATS = 8, F_MINMAX = 16, F_CELLS = 32 };
+enum { G_LIN = 0, G_LOG = 1, G_BIS = 2 };
+enum { ERR_NONFINITE = 1, ERR_OVERFLOW = 2 };
+
+struct SetDev {
+    int geom, quant, nx, ny, nmom;
+    int obs_off;          // first observable of this set
+    int ex_off, ey_off;   // offsets into the edge table
+    int gh_off;           // offset into the GH table (5 values per cell)
+    int gx_mode, gy_mode; // index guess for the x / y edges
+    float gx_a, gx_b, gy_a, gy_b;
+};
+
+struct PotDev {
+    int kind;             // 1 hernquist, 2 nfw, 3 log
+    double c[6];          // hernquist: GM, a;  log: Rc2, iq2, v0sq, hv;  nfw: C=4 pi rho_s r_s^3, r_s, 1/r_s
+};
+
+struct PassArgs {
+    void *x, *y, *z, *vx, *vy, *vz;
+    double *w, *what;
+    long long n;
+    int flags;
+    int nsets, nobs, npot;
+    SetDev sets[MAXSETS];
+    PotDev pot[MAXPOT];
+    double eps_dt, mu, ent_c, hdt, dt, sin_i, cos_i;
+    const void *edge_tab; int edge_len;     // R
+    const void *gh_tab;   int gh_len;       // R, 5 per GH cell: V, 1/S, c1, t2, norm
+    const void *coef;                       // R[nobs]
+    void *slots;                            // [grid][nobs]: int64 (fixed point) or double
+    int fx_shift;                           // fixed point: value * 2^fx_shift
+    double *stat_slots;                     // [grid][2]: S, sum w
+    // priors
+    int prior_kind, nE, nL, ncells;
+    double pk, pgma;                        // e_lc: a/GM, GM*a
+    void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
+    int *cell_ids;                          // [n]
+    void *cell_acc;                         // [ncells] int64 fixed point or double (global atomics)
+    unsigned *cell_cnt;                     // [ncells]
+    int *err;
+};
+
+// ------------------------------------------------------------ conversions
+// Positive doubles in [2^-126, 1) -> float by truncation with integer ops
+// (the FP64 pipe of this part is ~1.75 ops/clk/SM); anything else goes
+// through the hardware conversion.
+__device__ __forceinline__ float d2f_fast(double d) {
+    unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    unsigned e = hi >> 20;                        // sign bit lands at bit 11
+    if (e - 897u <= 125u)
+        return __uint_as_float(__funnelshift_l(lo, hi, 3) - (384u << 23));
+    return __double2float_rn(d);
+}
+
+// Normal float -> double with integer ops; zero and subnormals via hardware.
+__device__ __forceinline__ double f2d_fast(float f) {
+    unsigned b = __float_as_uint(f);
+    unsigned ex = (b >> 23) & 0xffu;
+    if (ex - 1u <= 253u) {
+        unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+        unsigned lo = b << 29;
+        return __hiloint2double((int)hi, (int)lo);
+    }
+    return (double)f;
+}
+
+// round(f * 2^sh) as a 64-bit integer from the float's bits (round half away
+// from zero); sets *ovf when |f| * 2^sh >= 2^63.
+__device__ __forceinline__ long long f2fixed(float f, int sh, bool &ovf) {
+    unsigned b = __float_as_uint(f);
+    int ex = (int)((b >> 23) & 0xffu);
+    if (ex == 0) return 0;                         // zero / subnormal: below resolution
+    if (ex == 255) { ovf = true; return 0; }
+    unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+    int s = ex - 150 + sh;
+    unsigned long long v;
+    if (s >= 0) {
+        if (s > 39) { ovf = true; return 0; }
+        v = m << s;
+    } else if (s > -25) {
+        v = (m + (1ull << (-s - 1))) >> (-s);
+    } else {
+        v = 0;
+    }
+    long long r = (long long)v;
+    return (b >> 31) ? -r : r;
+}
+
+// round(d * 2^sh) for a double (prior-cell sums of FP64 weights).
+__device__ __forceinline__ long long d2fixed(double d, int sh, bool &ovf) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    int ex = (int)((b >> 52) & 0x7ffull);
+    if (ex == 0) return 0;
+    if (ex == 2047) { ovf = true; return 0; }
+    unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+    int s = ex - 1075 + sh;
+    unsigned long long v;
+    if (s >= 0) {
+        if (s > 10) { ovf = true; return 0; }
+        v = m << s;
+    } else if (s > -54) {
+        v = (m + (1ull << (-s - 1))) >> (-s);
+    } else {
+        v = 0;
+    }
+    long long r = (long long)v;
+    return (b >> 63) ? -r : r;
+}
+
+// Exact 64-bit accumulation into a shared (lo, hi) pair of u32 words with
+// the fast 32-bit shared atomics: the carry out of the low word is detected
+// from the returned old value and folded into the high-word increment, which
+// is usually zero (small terms of either sign), so most updates cost one
+// atomic.
+__device__ __forceinline__ void fixed_add(unsigned *lo, unsigned *hi, int b, long long v) {
+    unsigned vl = (unsigned)(unsigned long long)v;
+    unsigned vh = (unsigned)((unsigned long long)v >> 32);
+    unsigned old = atomicAdd(lo + b, vl);
+    unsigned carry = (old + vl) < old ? 1u : 0u;
+    unsigned inc = vh + carry;
+    if (inc) atomicAdd(hi + b, inc);
+}
+
+// ------------------------------------------------------------ potentials
+template <class R> struct Acc3 { R x, y, z; };
+
+__device__ __forceinline__ float nfw_f(float r, const PotDev &p) {
+    // M(r)/r^3, M = C [ln(1+u) - u/(1+u)], u = r/r_s
+    float u = r * (float)p.c[2];
+    float mu;
+    if (u < 1e-2f) {
+        mu = u * u * (0.5f - u * (0.6666667f - u * (0.75f - u * (0.8f - u * 0.8333333f))));
+    } else {
+        mu = log1pf(u) - u / (1.0f + u);
+    }
+    float r3 = r * r * r;
+    return r > 0.f ? (float)p.c[0] * mu / r3 : 0.f;
+}
+__device__ __forceinline__ double nfw_f(double r, const PotDev &p) {
+    double u = r * p.c[2];
+    double mu;
+    if (u < 1e-3) {
+        mu = u * u * (0.5 - u * (2.0 / 3.0 - u * (0.75 - 0.8 * u)));
+    } else {
+        mu = log1p(u) - u / (1.0 + u);
+    }
+    double r3 = r * r * r;
+    return r > 0. ? p.c[0] * mu / r3 : 0.;
+}
+
+template <class R>
+__device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a) {
+    Acc3<R> g{R(0), R(0), R(0)};
+    for (int k = 0; k < a.npot; ++k) {
+        const PotDev &p = a.pot[k];
+        if (p.kind == 1) {            // Hernquist
+            R GM = (R)p.c[0], aa = (R)p.c[1];
+            R r2 = (x * x + y * y) + z * z;
+            R r = sqrt(r2);
+            R s = r + aa;
+            R f = r2 > R(0) ? GM / ((r * s) * s) : R(0);
+            g.x = g.x + (-(f * x));
+            g.y = g.y + (-(f * y));
+            g.z = g.z + (-(f * z));
+        } else if (p.kind == 3) {     // flattened logarithmic
+            R Rc2 = (R)p.c[0], iq2 = (R)p.c[1], v0sq = (R)p.c[2];
+            R R2 = x * x + y * y;
+            R D = (Rc2 + R2) + (z * z) * iq2;
+            R f = v0sq / D;
+            g.x = g.x + (-(f * x));
+            g.y = g.y + (-(f * y));
+            g.z = g.z + (-((f * iq2) * z));
+        } else if (p.kind == 2) {     // NFW
+            R r2 = (x * x + y * y) + z * z;
+            R f = nfw_f(sqrt(r2), p);
+            g.x = g.x + (-(f * x));
+            g.y = g.y + (-(f * y));
+            g.z = g.z + (-(f * z));
+        }
+    }
+    return g;
+}
+
+__device__ __forceinline__ float plog(float v) { return logf(v); }
+__device__ __forceinline__ double plog(double v) { return log(v); }
+
+template <class R>
+__device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a) {
+    R phi = R(0);
+    for (int k = 0; k < a.npot; ++k) {
+        const PotDev &p = a.pot[k];
+        if (p.kind == 1) {
+            R GM = (R)p.c[0], aa = (R)p.c[1];
+            R r2 = (x * x + y * y) + z * z;
+            phi = phi + (-(GM / (sqrt(r2) + aa)));
+        } else if (p.kind == 3) {
+            R Rc2 = (R)p.c[0], iq2 = (R)p.c[1], hv = (R)p.c[3];
+            R R2 = x * x + y * y;
+            R D = (Rc2 + R2) + (z * z) * iq2;
+            phi = phi + hv * plog(D);
+        } else if (p.kind == 2) {
+            // Phi = -C ln(1+u)/r, C = 4 pi rho_s r_s^3, evaluated in double
+            // and rounded once; the r -> 0 limit is -C / r_s
+            double xd = x, yd = y, zd = z;
+            double r = sqrt(xd * xd + yd * yd + zd * zd);
+            double u = r * p.c[2];
+            double v = r > 0 ? -p.c[0] * log1p(u) / r : -p.c[0] * p.c[2];
+            phi = phi + (R)v;
+        }
+    }
+    return phi;
+}
+
+template <class R>
+__device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a) {
+    R h = (R)a.hdt, d = (R)a.dt;
+    Acc3<R> g = accel<R>(x, y, z, a);
+    vx = vx + h * g.x;
+    vy = vy + h * g.y;
+    vz = vz + h * g.z;
+    x = x + d * vx;
+    y = y + d * vy;
+    z = z + d * vz;
+    g = accel<R>(x, y, z, a);
+    vx = vx + h * g.x;
+    vy = vy + h * g.y;
+    vz = vz + h * g.z;
+}
+
+// ------------------------------------------------------------ bin search
+// Cell j with e[j] <= v < e[j+1], j in [0, nb), else -1.  The guess only
+// shortens the search; the result is fixed by the comparisons.
+template <class R>
+__device__ __forceinline__ int find_bin(R v, const R *e, int nb, int mode, float ga, float gb) {
+    if (!(v >= e[0] && v < e[nb])) return -1;
+    int j;
+    if (mode == G_BIS) {
+        int lo = 0, hi = nb;              // e[lo] <= v < e[hi]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (v >= e[mid]) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    float fv = (float)v;
+    float gg = (mode == G_LOG) ? fmaf(ga, __log2f(fv), gb) : fmaf(ga, fv, gb);
+    j = (gg >= 0.f) ? (int)gg : 0;
+    j = j < nb - 1 ? j : nb - 1;
+    while (v < e[j]) --j;                 // terminates: v >= e[0]
+    while (v >= e[j + 1]) ++j;            // terminates: v < e[nb]
+    return j;
+}
+
+// Number of interior edges e[1..nc-1] with e[k] <= v (NaN -> 0), in [0, nc-1];
+// e[] is indexed 0..nc with e[0], e[nc] unused.
+template <class R>
+__device__ __forceinline__ int count_le(R v, const R *e, int nc, float ga, float gb) {
+    if (!(v == v)) return 0;
+    float gg = fmaf(ga, (float)v, gb);
+    int j = (gg >= 0.f) ? (gg < (float)nc ? (int)gg : nc - 1) : 0;
+    if (j > nc - 1) j = nc - 1;
+    while (j > 0 && !(e[j] <= v)) --j;
+    while (j < nc - 1 && e[j + 1] <= v) ++j;
+    return j;
+}
+
+// ------------------------------------------------------------ GH kernel
+// u_n(nu; s) = 2 sqrt(pi) N(nu; 0, 1+s^2) E_{N(m, t2)}[H_n], m = nu c1,
+// c1 = 1/(1+s^2), t2 = s^2 c1; table per cell: V, 1/S, c1, t2, norm with
+// norm = 2 sqrt(pi) / sqrt(2 pi (1+s^2)).
+__device__ __forceinline__ void gh_eval(float vlos, const float *g, float u[5]) {
+    const float SQ2 = 1.41421356237f, ISQ2 = 0.707106781187f, ISQ3 = 0.57735026919f,
+                ISQ24 = 0.204124145232f;
+    float nu = (vlos - g[0]) * g[1];
+    float c1 = g[2], t2 = g[3];
+    float gs = g[4] * __expf(-0.5f * nu * nu * c1);
+    float m = nu * c1, m2 = m * m;
+    float E2 = m2 + t2;
+    float E3 = m * fmaf(3.f, t2, m2);
+    float E4 = fmaf(m2, m2, fmaf(6.f * m2, t2, 3.f * t2 * t2));
+    u[0] = gs;
+    u[1] = gs * (SQ2 * m);
+    u[2] = gs * (fmaf(2.f, E2, -1.f) * ISQ2);
+    u[3] = gs * (fmaf(2.f, E3, -3.f * m) * ISQ3);
+    u[4] = gs * (fmaf(4.f, E4, fmaf(-12.f, E2, 3.f)) * ISQ24);
+}
+__device__ __forceinline__ void gh_eval(double vlos, const double *g, double u[5]) {
+    const double SQ2 = 1.4142135623730951, SQ3 = 1.7320508075688772, SQ24 = 4.898979485566356;
+    double nu = (vlos - g[0]) * g[1];
+    double c1 = g[2], t2 = g[3];
+    double gs = g[4] * exp(-0.5 * nu * nu * c1);
+    double m = nu * c1, m2 = m * m;
+    double E2 = m2 + t2;
+    double E3 = m * m2 + 3.0 * m * t2;
+    double E4 = m2 * m2 + 6.0 * m2 * t2 + 3.0 * t2 * t2;
+    u[0] = gs;
+    u[1] = gs * (SQ2 * m);
+    u[2] = gs * ((2.0 * E2 - 1.0) / SQ2);
+    u[3] = gs * ((2.0 * E3 - 3.0 * m) / SQ3);
+    u[4] = gs * ((4.0 * E4 - 12.0 * E2 + 3.0) / SQ24);
+}
+
+// Cell of particle in set s (-1 = none).  X = x, Ys = z*sin - y*cos.
+template <class R>
+__device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R y, R z, R X, R Ys) {
+    if (s.geom == 1) {
+        R r2 = (x * x + y * y) + z * z;
+        return find_bin<R>(r2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b);
+    } else if (s.geom == 2) {
+        R R2 = X * X + Ys * Ys;
+        return find_bin<R>(R2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b);
+    } else {
+        int ix = find_bin<R>(X, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b);
+        if (ix < 0) return -1;
+        int iy = find_bin<R>(Ys, edges + s.ey_off, s.ny, s.gy_mode, s.gy_a, s.gy_b);
+        if (iy < 0) return -1;
+        return iy * s.nx + ix;
+    }
+}
+
+}  // namespace m2m

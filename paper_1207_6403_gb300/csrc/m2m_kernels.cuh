@@ -1,0 +1,622 @@
+// Kernels of the M2M step.
+//
+// k_pass      one streaming pass over the particles that does, per particle
+//             and as the flags ask: the weight update pending from the last
+//             residual (at the current positions), the entropy / total
+//             weight partials, the KDK push, the weighted scatter into a
+//             block-private shared histogram (flushed once per block into a
+//             per-block slot), the (E, L_z) range for the priors, and the
+//             prior-cell assignment with block-private cell sums.
+// k_residual  per-bin reduction of the block slots in a fixed order, the
+//             residuals, smoothing and coefficients, chi^2 by a warp-shuffle
+//             reduction and, in the last block to finish, the step record.
+// k_prior_mean, k_prior_gather
+//             cell means sum/count and w_hat_i = mean of i's cell.
+// k_cells     cell export for tests.
+#pragma once
+#include <math.h>
+#include "m2m_device.cuh"
+#include "../../include/m2m.h"
+
+namespace m2m {
+
+template <class R> struct Vec;
+template <> struct Vec<float> { static constexpr int N = 4; using T = float4; };
+template <> struct Vec<double> { static constexpr int N = 2; using T = double2; };
+
+__device__ __forceinline__ float ceil_to(double e, float *) {
+    float f = __double2float_rn(e);
+    if ((double)f < e) f = nextafterf(f, INFINITY);
+    return f;
+}
+__device__ __forceinline__ double ceil_to(double e, double *) { return e; }
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shape), result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    return t;
+}
+
+// ----------------------------------------------------------------- priors
+// Grid of the prior cells from the range slots of the preceding k_pass
+// (F_MINMAX): interior edges lo + k*((hi-lo)/n) in double, held as the
+// smallest R >= edge.  pe/pl are indexed 0..n (entries 1..n-1 used).
+template <class R>
+__device__ void prior_setup(const PassArgs &a, R *pe, R *pl, float *gp) {
+    __shared__ double red[3][32];
+    const R *mm = (const R *)a.mm_slots;
+    R emin = R(INFINITY), emax = R(-INFINITY), lm = R(0);
+    for (int b = threadIdx.x; b < a.mm_nblocks; b += blockDim.x) {
+        emin = fmin(emin, mm[4 * b + 0]);
+        emax = fmax(emax, mm[4 * b + 1]);
+        lm = fmax(lm, mm[4 * b + 2]);
+    }
+    double de = (double)emin, dx = (double)emax, dl = (double)lm;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        de = fmin(de, __shfl_xor_sync(0xffffffffu, de, o));
+        dx = fmax(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+        dl = fmax(dl, __shfl_xor_sync(0xffffffffu, dl, o));
+    }
+    int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wp] = de; red[1][wp] = dx; red[2][wp] = dl; }
+    __syncthreads();
+    __shared__ double rng[4];
+    if (threadIdx.x == 0) {
+        double a0 = red[0][0], a1 = red[1][0], a2 = red[2][0];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            a0 = fmin(a0, red[0][k]); a1 = fmax(a1, red[1][k]); a2 = fmax(a2, red[2][k]);
+        }
+        double lo = a0, hi = (a.prior_kind == M2M_PRIOR_E_LZ) ? a1 : 0.0;
+        double l0 = (a.prior_kind == M2M_PRIOR_E_LZ) ? -a2 : 0.0;
+        double l1 = (a.prior_kind == M2M_PRIOR_E_LZ) ? a2 : 1.0;
+        rng[0] = lo; rng[1] = (hi - lo) / (double)a.nE;
+        rng[2] = l0; rng[3] = (l1 - l0) / (double)a.nL;
+    }
+    __syncthreads();
+    double lo = rng[0], we = rng[1], l0 = rng[2], wl = rng[3];
+    for (int k = threadIdx.x; k <= a.nE; k += blockDim.x)
+        pe[k] = (k >= 1 && k < a.nE) ? ceil_to(lo + (double)k * we, (R *)nullptr) : R(0);
+    for (int k = threadIdx.x; k <= a.nL; k += blockDim.x)
+        pl[k] = (k >= 1 && k < a.nL) ? ceil_to(l0 + (double)k * wl, (R *)nullptr) : R(0);
+    if (threadIdx.x == 0) {
+        gp[0] = we > 0 ? (float)(1.0 / we) : 0.f;
+        gp[1] = we > 0 ? (float)(-lo / we) : 0.f;
+        gp[2] = wl > 0 ? (float)(1.0 / wl) : 0.f;
+        gp[3] = wl > 0 ? (float)(-l0 / wl) : 0.f;
+    }
+    __syncthreads();
+}
+
+template <class R>
+__device__ __forceinline__ void energy_lz(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a, R &E, R &Lz) {
+    R v2 = (vx * vx + vy * vy) + vz * vz;
+    E = R(0.5) * v2 + potential<R>(x, y, z, a);
+    Lz = x * vy - y * vx;
+}
+
+template <class R>
+__device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a,
+                                          const R *pe, const R *pl, const float *gp) {
+    R E, Lz;
+    energy_lz<R>(x, y, z, vx, vy, vz, a, E, Lz);
+    if (a.prior_kind == M2M_PRIOR_E_LZ) {
+        int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
+        int iL = count_le<R>(Lz, pl, a.nL, gp[2], gp[3]);
+        return iE * a.nL + iL;
+    }
+    // E_LC: Hernquist circular-orbit angular momentum at energy E
+    if (E >= R(0)) return a.nE * a.nL;
+    R Lx = y * vz - z * vy;
+    R Ly = z * vx - x * vz;
+    R L2 = (Lx * Lx + Ly * Ly) + Lz * Lz;
+    R ed = E * (R)a.pk;
+    R sq = sqrt(R(1) - R(8) * ed);
+    R s = (R(-1) - sq) / (R(4) * ed);
+    R sm = s - R(1);
+    R Lc2 = (R)a.pgma * (((sm * sm) * sm) / (s * s));
+    R X = L2 / Lc2;
+    int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
+    int iL = count_le<R>(X, pl, a.nL, gp[2], gp[3]);
+    return iE * a.nL + iL;
+}
+
+// ----------------------------------------------------------------- k_pass
+template <class R>
+struct PassSmem {
+    unsigned *h_lo, *h_hi;   // FP32C histogram (exact fixed point)
+    double *h_d;             // FP64 histogram
+    const R *coef, *edges, *gh;
+    R *pe, *pl;
+    float *gp;
+    unsigned *c_lo, *c_hi, *c_cnt;   // FP32C prior-cell sums / counts
+    double *c_d;                     // FP64 prior-cell sums
+};
+
+// dot = sum_j K_j coef_j over the particle's cells, in set and moment order
+template <class R>
+__device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
+                                     R X, R Ys, R vlos) {
+    R dot = R(0);
+    for (int k = 0; k < a.nsets; ++k) {
+        const SetDev &s = a.sets[k];
+        int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+        if (c < 0) continue;
+        int b = s.obs_off + c * s.nmom;
+        if (s.quant == M2M_Q_MASS) {
+            dot = dot + S.coef[b];
+        } else if (s.quant == M2M_Q_VLOS2) {
+            dot = dot + (vlos * vlos) * S.coef[b];
+        } else {
+            R u[5];
+            gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) dot = dot + u[m] * S.coef[b + m];
+        }
+    }
+    return dot;
+}
+
+__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, int sh, bool &ovf) {
+    long long q = f2fixed(v, sh, ovf);
+    if (q) fixed_add(S.h_lo, S.h_hi, b, q);
+}
+__device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, int, bool &) {
+    atomicAdd(S.h_d + b, v);
+}
+
+template <class R>
+__device__ __forceinline__ void scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
+                                        R X, R Ys, R vlos, R wv, bool &ovf) {
+    for (int k = 0; k < a.nsets; ++k) {
+        const SetDev &s = a.sets[k];
+        int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+        if (c < 0) continue;
+        int b = s.obs_off + c * s.nmom;
+        if (s.quant == M2M_Q_MASS) {
+            hist_add(S, b, wv, a.fx_shift, ovf);
+        } else if (s.quant == M2M_Q_VLOS2) {
+            hist_add(S, b, wv * (vlos * vlos), a.fx_shift, ovf);
+        } else {
+            R u[5];
+            gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], a.fx_shift, ovf);
+        }
+    }
+}
+
+struct ThreadAcc {
+    double s_d, w_d;     // FP64 path
+    float s_f, w_f;      // FP32C path
+    bool ovf, bad;
+};
+
+// The weight update of one particle: returns the new weight; L1 = ln(w_new/w_hat)
+__device__ __forceinline__ double upd_weight(double w, double what, float dot, const PassArgs &a, float &wnf, float &L1) {
+    float wf = d2f_fast(w), whf = d2f_fast(what);
+    float L = logf(__fdividef(wf, whf));
+    float G = (float)a.mu * (-L - (float)a.ent_c) - dot;
+    float d = (float)a.eps_dt * G;
+    float e = expm1f(d);
+    double wn = fma(w, f2d_fast(e), w);
+    wnf = d2f_fast(wn);
+    L1 = L + d;
+    return wn;
+}
+__device__ __forceinline__ double upd_weight(double w, double what, double dot, const PassArgs &a, double &wnd, double &L1) {
+    double L = log(w / what);
+    double G = a.mu * (-L - a.ent_c) - dot;
+    double d = a.eps_dt * G;
+    double wn = w * exp(d);
+    wnd = wn;
+    L1 = L + d;
+    return wn;
+}
+
+__device__ __forceinline__ void acc_stats(ThreadAcc &t, float wnf, float L1) {
+    t.s_f += -wnf * L1;
+    t.w_f += wnf;
+}
+__device__ __forceinline__ void acc_stats(ThreadAcc &t, double wnd, double L1) {
+    t.s_d += -wnd * L1;
+    t.w_d += wnd;
+}
+__device__ __forceinline__ float to_r(double v, float *) { return d2f_fast(v); }
+__device__ __forceinline__ double to_r(double v, double *) { return v; }
+__device__ __forceinline__ float rlog_ratio(double w, double what, float *) {
+    return logf(__fdividef(d2f_fast(w), d2f_fast(what)));
+}
+__device__ __forceinline__ double rlog_ratio(double w, double what, double *) { return log(w / what); }
+
+template <class R>
+__device__ __forceinline__ void cell_add(const PassArgs &a, const PassSmem<R> &S, int c, double wv, bool &ovf);
+template <>
+__device__ __forceinline__ void cell_add<float>(const PassArgs &a, const PassSmem<float> &S, int c, double wv, bool &ovf) {
+    long long q = d2fixed(wv, a.fx_shift, ovf);
+    if (q) fixed_add(S.c_lo, S.c_hi, c, q);
+    atomicAdd(S.c_cnt + c, 1u);
+}
+template <>
+__device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSmem<double> &S, int c, double wv, bool &) {
+    atomicAdd(S.c_d + c, wv);
+    atomicAdd((unsigned *)(S.c_lo) + c, 1u);
+}
+
+template <class R>
+__device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, long long i,
+                                         R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
+                                         ThreadAcc &t, R &emin, R &emax, R &lzm) {
+    const int fl = a.flags;
+    double wn = w;
+    if (fl & (F_UPD | F_STATS)) {
+        if (w > 0.0) {
+            R L1;
+            R wr;
+            if (fl & F_UPD) {
+                R s = (R)a.sin_i, c = (R)a.cos_i;
+                R X = x, Ys = z * s - y * c, vlos = vy * s + vz * c;
+                R dot = obs_dot<R>(a, S, x, y, z, X, Ys, vlos);
+                wn = upd_weight(w, what, dot, a, wr, L1);
+                if (!(wn >= 0.0) || wn > 1e300) t.bad = true;
+            } else {
+                wr = to_r(w, (R *)nullptr);
+                L1 = rlog_ratio(w, what, (R *)nullptr);
+            }
+            if (fl & F_STATS) acc_stats(t, wr, L1);
+        } else if (!(w == 0.0)) {
+            t.bad = true;       // negative or NaN weight
+        }
+    }
+    if (fl & F_PUSH) kdk<R>(x, y, z, vx, vy, vz, a);
+    if (fl & F_SCAT) {
+        R s = (R)a.sin_i, c = (R)a.cos_i;
+        R X = x, Ys = z * s - y * c, vlos = vy * s + vz * c;
+        R wv = to_r(wn, (R *)nullptr);
+        if (wv != R(0)) scatter<R>(a, S, x, y, z, X, Ys, vlos, wv, t.ovf);
+    }
+    if (fl & F_MINMAX) {
+        R E, Lz;
+        energy_lz<R>(x, y, z, vx, vy, vz, a, E, Lz);
+        emin = fmin(emin, E);
+        emax = fmax(emax, E);
+        lzm = fmax(lzm, fabs(Lz));
+    }
+    if (fl & F_CELLS) {
+        int c = prior_cell<R>(x, y, z, vx, vy, vz, a, S.pe, S.pl, S.gp);
+        a.cell_ids[i] = c;
+        cell_add<R>(a, S, c, wn, t.ovf);
+    }
+    w = wn;
+}
+
+template <class R>
+__device__ __forceinline__ R ld(const void *p, long long i) { return ((const R *)p)[i]; }
+
+template <class R, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    constexpr bool FX = sizeof(R) == 4;
+    const int fl = a.flags;
+    PassSmem<R> S{};
+    unsigned char *p = smem;
+    const int nobs = a.nobs;
+    if (fl & F_SCAT) {
+        if (FX) { S.h_lo = (unsigned *)p; S.h_hi = S.h_lo + nobs; }
+        else { S.h_d = (double *)p; }
+        p += 8 * ((nobs + 1) & ~1);
+    }
+    if (fl & F_UPD) { S.coef = (const R *)p; p += sizeof(R) * ((nobs + 3) & ~3); }
+    S.edges = (const R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
+    S.gh = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3);
+    if (fl & F_CELLS) {
+        S.pe = (R *)p; p += sizeof(R) * ((a.nE + 4) & ~3);
+        S.pl = (R *)p; p += sizeof(R) * ((a.nL + 4) & ~3);
+        S.gp = (float *)p; p += 16;
+        if (FX) {
+            S.c_lo = (unsigned *)p; S.c_hi = S.c_lo + a.ncells; S.c_cnt = S.c_hi + a.ncells;
+            p += 12 * ((a.ncells + 3) & ~3);
+        } else {
+            S.c_d = (double *)p; p += 8 * ((a.ncells + 1) & ~1);
+            S.c_lo = (unsigned *)p; p += 4 * ((a.ncells + 3) & ~3);   // counts
+        }
+    }
+    // prologue: clear histograms, stage the tables
+    if (fl & F_SCAT) {
+        unsigned *hz = FX ? S.h_lo : (unsigned *)S.h_d;
+        for (int k = threadIdx.x; k < 2 * nobs; k += NT) hz[k] = 0u;
+    }
+    if (fl & F_UPD)
+        for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
+    for (int k = threadIdx.x; k < a.edge_len; k += NT) ((R *)S.edges)[k] = ((const R *)a.edge_tab)[k];
+    for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    if (fl & F_CELLS) {
+        if (FX) {
+            for (int k = threadIdx.x; k < 3 * a.ncells; k += NT) S.c_lo[k] = 0u;   // lo, hi, cnt
+        } else {
+            for (int k = threadIdx.x; k < a.ncells; k += NT) { S.c_d[k] = 0.0; S.c_lo[k] = 0u; }
+        }
+        prior_setup<R>(a, S.pe, S.pl, S.gp);
+    }
+    __syncthreads();
+
+    ThreadAcc t{0.0, 0.0, 0.f, 0.f, false, false};
+    R emin = R(INFINITY), emax = R(-INFINITY), lzm = R(0);
+    constexpr int V = Vec<R>::N;
+    using VT = typename Vec<R>::T;
+    const long long n = a.n;
+    const long long nch = (n + V - 1) / V;
+    R *px = (R *)a.x, *py = (R *)a.y, *pz = (R *)a.z, *pvx = (R *)a.vx, *pvy = (R *)a.vy, *pvz = (R *)a.vz;
+    const bool wr_pos = (fl & F_PUSH) != 0;
+    const bool wr_w = (fl & F_UPD) != 0;
+    for (long long ch = (long long)blockIdx.x * NT + threadIdx.x; ch < nch; ch += (long long)gridDim.x * NT) {
+        const long long i0 = ch * V;
+        if (i0 + V <= n) {
+            VT X4 = ((const VT *)px)[ch], Y4 = ((const VT *)py)[ch], Z4 = ((const VT *)pz)[ch];
+            VT U4 = ((const VT *)pvx)[ch], V4 = ((const VT *)pvy)[ch], W4 = ((const VT *)pvz)[ch];
+            double wv[V], wh[V];
+            if (V == 4) {
+                double2 w0 = ((const double2 *)a.w)[2 * ch], w1 = ((const double2 *)a.w)[2 * ch + 1];
+                double2 h0 = ((const double2 *)a.what)[2 * ch], h1 = ((const double2 *)a.what)[2 * ch + 1];
+                wv[0] = w0.x; wv[1] = w0.y; wv[V > 2 ? 2 : 0] = w1.x; wv[V > 3 ? 3 : 1] = w1.y;
+                wh[0] = h0.x; wh[1] = h0.y; wh[V > 2 ? 2 : 0] = h1.x; wh[V > 3 ? 3 : 1] = h1.y;
+            } else {
+                double2 w0 = ((const double2 *)a.w)[ch];
+                double2 h0 = ((const double2 *)a.what)[ch];
+                wv[0] = w0.x; wv[1] = w0.y; wh[0] = h0.x; wh[1] = h0.y;
+            }
+            R *xs = (R *)&X4, *ys = (R *)&Y4, *zs = (R *)&Z4, *us = (R *)&U4, *vs = (R *)&V4, *ws = (R *)&W4;
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                particle<R>(a, S, i0 + k, xs[k], ys[k], zs[k], us[k], vs[k], ws[k], wv[k], wh[k], t, emin, emax, lzm);
+            if (wr_pos) {
+                ((VT *)px)[ch] = X4; ((VT *)py)[ch] = Y4; ((VT *)pz)[ch] = Z4;
+                ((VT *)pvx)[ch] = U4; ((VT *)pvy)[ch] = V4; ((VT *)pvz)[ch] = W4;
+            }
+            if (wr_w) {
+                if (V == 4) {
+                    ((double2 *)a.w)[2 * ch] = make_double2(wv[0], wv[1]);
+                    ((double2 *)a.w)[2 * ch + 1] = make_double2(wv[V > 2 ? 2 : 0], wv[V > 3 ? 3 : 1]);
+                } else {
+                    ((double2 *)a.w)[ch] = make_double2(wv[0], wv[1]);
+                }
+            }
+        } else {
+            for (long long i = i0; i < n; ++i) {
+                R x = px[i], y = py[i], z = pz[i], vx = pvx[i], vy = pvy[i], vz = pvz[i];
+                double w = a.w[i];
+                particle<R>(a, S, i, x, y, z, vx, vy, vz, w, a.what[i], t, emin, emax, lzm);
+                if (wr_pos) { px[i] = x; py[i] = y; pz[i] = z; pvx[i] = vx; pvy[i] = vy; pvz[i] = vz; }
+                if (wr_w) a.w[i] = w;
+            }
+        }
+    }
+    __syncthreads();
+    // epilogue: flush the block-private histograms and partial sums
+    if (fl & F_SCAT) {
+        if (FX) {
+            long long *sl = (long long *)a.slots + (long long)blockIdx.x * nobs;
+            for (int k = threadIdx.x; k < nobs; k += NT)
+                sl[k] = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
+        } else {
+            double *sl = (double *)a.slots + (long long)blockIdx.x * nobs;
+            for (int k = threadIdx.x; k < nobs; k += NT) sl[k] = S.h_d[k];
+        }
+    }
+    if (fl & F_CELLS) {
+        if (FX) {
+            for (int k = threadIdx.x; k < a.ncells; k += NT) {
+                unsigned cn = S.c_cnt[k];
+                if (cn) {
+                    long long v = (long long)(((unsigned long long)S.c_hi[k] << 32) | (unsigned long long)S.c_lo[k]);
+                    atomicAdd((unsigned long long *)a.cell_acc + k, (unsigned long long)v);
+                    atomicAdd(a.cell_cnt + k, cn);
+                }
+            }
+        } else {
+            for (int k = threadIdx.x; k < a.ncells; k += NT) {
+                unsigned cn = S.c_lo[k];
+                if (cn) {
+                    atomicAdd((double *)a.cell_acc + k, S.c_d[k]);
+                    atomicAdd(a.cell_cnt + k, cn);
+                }
+            }
+        }
+    }
+    if (fl & F_STATS) {
+        double sv = FX ? (double)t.s_f : t.s_d;
+        double wv = FX ? (double)t.w_f : t.w_d;
+        double s_tot = block_sum(sv, red);
+        double w_tot = block_sum(wv, red);
+        if (threadIdx.x == 0) {
+            a.stat_slots[2 * blockIdx.x] = s_tot;
+            a.stat_slots[2 * blockIdx.x + 1] = w_tot;
+        }
+    }
+    if (fl & F_MINMAX) {
+        __shared__ R mm[3][32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+            emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            lzm = fmax(lzm, __shfl_xor_sync(0xffffffffu, lzm, o));
+        }
+        int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        if (lane == 0) { mm[0][wp] = emin; mm[1][wp] = emax; mm[2][wp] = lzm; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 1; k < NT / 32; ++k) {
+                emin = fmin(emin, mm[0][k]); emax = fmax(emax, mm[1][k]); lzm = fmax(lzm, mm[2][k]);
+            }
+            R *o = (R *)a.mm_slots + 4 * blockIdx.x;
+            o[0] = mm[0][0] < emin ? mm[0][0] : emin;
+            o[1] = mm[1][0] > emax ? mm[1][0] : emax;
+            o[2] = mm[2][0] > lzm ? mm[2][0] : lzm;
+            o[3] = R(0);
+        }
+    }
+    if (t.ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (t.bad) atomicOr(a.err, ERR_NONFINITE);
+}
+
+// ------------------------------------------------------------- k_residual
+struct ResArgs {
+    const void *slots; int nblk; int nobs; int fixed; double q;
+    const double *Y, *sigma;
+    double *Dt, *y, *Delta, *coef_d; void *coef_r; int r_float;
+    int mode; double alpha, mu;
+    const double *stat_slots; int stat_nblk;
+    double *chi_slots; unsigned *ticket;
+    m2m_record *ring, *last; long long rec_step; int write_ring;
+    int *err;
+};
+
+// Deterministic strided sum over the block: thread k adds k, k+NT, ... in
+// order, then a fixed shuffle tree.
+__device__ __forceinline__ double block_sum_strided(const double *v, int stride, int off, int cnt, double *red) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += v[(long long)k * stride + off];
+    return block_sum(s, red);
+}
+
+__global__ void __launch_bounds__(256) k_residual(const __grid_constant__ ResArgs a) {
+    __shared__ unsigned long long si[8][32];
+    __shared__ double sd[8][32];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    if (j < a.nobs) {
+        if (a.fixed) {
+            unsigned long long acc = 0; double ap = 0.0;
+            const long long *sl = (const long long *)a.slots;
+            for (int b = wp; b < a.nblk; b += 8) {
+                long long v = sl[(long long)b * a.nobs + j];
+                acc += (unsigned long long)v;
+                ap += (double)v;
+            }
+            si[wp][lane] = acc; sd[wp][lane] = ap;
+        } else {
+            double acc = 0.0;
+            const double *sl = (const double *)a.slots;
+            for (int b = wp; b < a.nblk; b += 8) acc += sl[(long long)b * a.nobs + j];
+            sd[wp][lane] = acc;
+        }
+    }
+    __syncthreads();
+    if (wp == 0) {
+        double c2 = 0.0, c2r = 0.0, mx = 0.0;
+        if (j < a.nobs) {
+            double yv;
+            if (a.fixed) {
+                unsigned long long tot = 0; double ap = 0.0;
+                for (int k = 0; k < 8; ++k) { tot += si[k][lane]; ap += sd[k][lane]; }
+                double exact = (double)(long long)tot;
+                if (fabs(exact - ap) > 1e-6 * fabs(ap) + 1.0) atomicOr(a.err, ERR_OVERFLOW);
+                yv = exact * a.q;
+            } else {
+                yv = 0.0;
+                for (int k = 0; k < 8; ++k) yv += sd[k][lane];
+            }
+            double s = a.sigma[j];
+            bool valid = s > 0.0;
+            double D = valid ? (yv - a.Y[j]) / s : 0.0;
+            double dold = a.Dt[j];
+            double dn = (a.mode == 1) ? a.alpha * D + (1.0 - a.alpha) * dold : (a.mode == 2 ? D : dold);
+            double cf = valid ? dn / s : 0.0;
+            a.y[j] = yv;
+            a.Delta[j] = D;
+            if (a.mode != 0) a.Dt[j] = dn;
+            a.coef_d[j] = cf;
+            if (a.r_float) ((float *)a.coef_r)[j] = (float)cf;
+            else ((double *)a.coef_r)[j] = cf;
+            c2 = dn * dn; c2r = D * D; mx = fabs(dn);
+        }
+        c2 = warp_sum(c2);
+        c2r = warp_sum(c2r);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            a.chi_slots[3 * blockIdx.x] = c2;
+            a.chi_slots[3 * blockIdx.x + 1] = c2r;
+            a.chi_slots[3 * blockIdx.x + 2] = mx;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double c2 = block_sum_strided(a.chi_slots, 3, 0, gridDim.x, red);
+    double c2r = block_sum_strided(a.chi_slots, 3, 1, gridDim.x, red);
+    double S = block_sum_strided(a.stat_slots, 2, 0, a.stat_nblk, red);
+    double W = block_sum_strided(a.stat_slots, 2, 1, a.stat_nblk, red);
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) mx = fmax(mx, a.chi_slots[3 * b + 2]);
+        m2m_record r;
+        r.step = a.rec_step;
+        r.chi2 = c2; r.chi2_raw = c2r; r.S = S; r.sum_w = W;
+        r.F = -0.5 * c2 + a.mu * S;
+        r.max_abs_dt = mx;
+        *a.last = r;
+        if (a.write_ring) a.ring[a.rec_step % M2M_HISTORY] = r;
+        if (!(isfinite(c2) && isfinite(S) && isfinite(W))) atomicOr(a.err, ERR_NONFINITE);
+        *a.ticket = 0u;
+    }
+}
+
+// ----------------------------------------------------------- prior means
+// mean[c] = sum[c] / count[c]; then w_hat_i = mean[cell_i].
+__global__ void k_prior_mean(const void *acc, const unsigned *cnt, int ncells, int fixed, double q, double *mean) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    unsigned k = cnt[c];
+    double s = fixed ? (double)((const long long *)acc)[c] * q : ((const double *)acc)[c];
+    mean[c] = k ? s / (double)k : 0.0;
+}
+
+__global__ void k_prior_gather(const int *cell, const double *mean, double *what, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        what[i] = mean[cell[i]];
+}
+
+// ------------------------------------------------------------- k_cells
+template <class R>
+__global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int *prior_cells) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *p = smem;
+    R *edges = (R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
+    R *pe = (R *)p; p += sizeof(R) * ((a.nE + 4) & ~3);
+    R *pl = (R *)p; p += sizeof(R) * ((a.nL + 4) & ~3);
+    float *gp = (float *)p;
+    for (int k = threadIdx.x; k < a.edge_len; k += blockDim.x) edges[k] = ((const R *)a.edge_tab)[k];
+    if (prior_cells) prior_setup<R>(a, pe, pl, gp);
+    __syncthreads();
+    R s = (R)a.sin_i, c = (R)a.cos_i;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
+        R x = ((const R *)a.x)[i], y = ((const R *)a.y)[i], z = ((const R *)a.z)[i];
+        R vx = ((const R *)a.vx)[i], vy = ((const R *)a.vy)[i], vz = ((const R *)a.vz)[i];
+        R X = x, Ys = z * s - y * c;
+        for (int k = 0; k < a.nsets; ++k) obs_cells[(long long)k * a.n + i] = set_cell<R>(a.sets[k], edges, x, y, z, X, Ys);
+        if (prior_cells) prior_cells[i] = prior_cell<R>(x, y, z, vx, vy, vz, a, pe, pl, gp);
+    }
+}
+
+}  // namespace m2m

@@ -412,9 +412,12 @@ def make_problem(name, n=None, precision=None, seed_model=None,
                  seed_target=None, with_target=True, nsteps=None):
     """Build the workload `name` (see module docstring), optionally at another
     particle count `n` with the same structure.  Weights and priors start at
-    1/N; eps is the workload's epsilon scaled by 1/N."""
+    1/n.  eps is the workload's epsilon divided by the workload's nominal N
+    (not by n): the relaxation rate of bin j, eps Y_j / sigma_j^2, then does
+    not depend on how many particles a reduced test case uses."""
+    nominal = _DEFAULT_N[name]
     if n is None:
-        n = _DEFAULT_N[name]
+        n = nominal
     if name == "plain-fp64":
         sm, st = seed_model or 1, seed_target or 2
         pos, vel = hernquist_isotropic(n, sm)
@@ -469,6 +472,6 @@ def make_problem(name, n=None, precision=None, seed_model=None,
     return Problem(name=name, n=n, pos=np.ascontiguousarray(pos),
                    vel=np.ascontiguousarray(vel), w0=w0, what0=w0.copy(),
                    potential=pot, obs=obs, incl_sin=sin_i, incl_cos=cos_i,
-                   eps=0.05 / n, mu=1e-3, dt=0.01, alpha=0.02, prior=prior,
+                   eps=0.05 / nominal, mu=1e-3, dt=0.01, alpha=0.02, prior=prior,
                    nsteps=steps, precision=prec, target_pos=tp, target_vel=tv,
                    target_w=tw)

@@ -1,0 +1,312 @@
+"""Thin Python binding of libm2m.so (argument marshalling only).
+
+Every entry point of ``include/m2m.h`` has a same-named function here; all
+arithmetic of the M2M step runs in the library's CUDA kernels.  PyTorch
+provides the device memory (particle arrays are torch tensors that the
+context borrows) and the stream.  There is no fallback: if the library
+cannot be built or loaded, or no GPU is present, these functions raise.
+"""
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+M2M_OK = 0
+ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE",
+          -5: "M2M_ERR_STATE", -6: "M2M_ERR_NOMEM", -7: "M2M_ERR_OVERFLOW"}
+FP64, FP32C = 0, 1
+POT = {"hernquist": 1, "nfw": 2, "log": 3}
+GEOM = {"shell": 1, "annulus": 2, "grid": 3}
+QUANT = {"mass": 1, "vlos2": 2, "gh": 3}
+PRIOR = {"flat": 0, "e_lc": 1, "e_lz": 2}
+HISTORY = 16384
+
+
+class m2m_potential_desc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("reserved", c_int32), ("p", c_double * 4)]
+
+
+class m2m_obs_desc(ctypes.Structure):
+    _fields_ = [("geom", c_int32), ("quant", c_int32), ("nx", c_int32), ("ny", c_int32),
+                ("edges_x", POINTER(c_double)), ("edges_y", POINTER(c_double)),
+                ("gh_V", POINTER(c_double)), ("gh_S", POINTER(c_double)),
+                ("sigma_kernel", c_double)]
+
+
+class m2m_prior_desc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("nE", c_int32), ("nL", c_int32), ("period", c_int32),
+                ("hernquist_GM", c_double), ("hernquist_a", c_double)]
+
+
+class m2m_params(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("mu", c_double), ("dt", c_double), ("alpha", c_double),
+                ("entropy_const", c_double), ("incl_sin", c_double), ("incl_cos", c_double)]
+
+
+class m2m_record(ctypes.Structure):
+    _fields_ = [("step", c_int64), ("chi2", c_double), ("chi2_raw", c_double), ("S", c_double),
+                ("sum_w", c_double), ("F", c_double), ("max_abs_dt", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def library():
+    """Build (if stale) and load libm2m.so; raises if that is impossible."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        path = _build.build()
+    L = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "m2m_init": (c_int32, [POINTER(P), c_int32, c_int64, P, P, P, P, P, P, P, P,
+                               POINTER(m2m_potential_desc), c_int32, POINTER(m2m_obs_desc), c_int32,
+                               POINTER(c_double), POINTER(c_double), POINTER(m2m_params),
+                               POINTER(m2m_prior_desc), P]),
+        "m2m_set_targets": (c_int32, [P, POINTER(c_double), POINTER(c_double)]),
+        "m2m_potential": (c_int32, [P, POINTER(m2m_potential_desc), c_int32]),
+        "m2m_observe": (c_int32, [P, c_int32]),
+        "m2m_update_weights": (c_int32, [P]),
+        "m2m_priors": (c_int32, [P]),
+        "m2m_push": (c_int32, [P, c_int64]),
+        "m2m_step": (c_int32, [P, c_int64]),
+        "m2m_get_obs": (c_int32, [P, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+        "m2m_get_record": (c_int32, [P, POINTER(m2m_record)]),
+        "m2m_get_history": (c_int32, [P, c_int64, c_int64, POINTER(m2m_record)]),
+        "m2m_get_cells": (c_int32, [P, P, P]),
+        "m2m_nobs": (c_int64, [P]),
+        "m2m_steps_taken": (c_int64, [P]),
+        "m2m_set_launch": (c_int32, [P, c_int32, c_int32]),
+        "m2m_last_error": (ctypes.c_char_p, [P]),
+        "m2m_free": (c_int32, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+class M2MError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx_ptr=None):
+    if rc != M2M_OK:
+        msg = library().m2m_last_error(ctx_ptr)
+        raise M2MError(rc, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+class Context:
+    """A library context plus the tensors and host tables it borrows."""
+
+    def __init__(self, ptr, tensors, keep, nobs, precision):
+        self.ptr = ptr
+        self.t = tensors          # dict name -> torch tensor (device)
+        self._keep = keep
+        self.nobs = nobs
+        self.precision = precision
+
+    # -- the C entry points, same names --
+    def m2m_set_targets(self, Y, sigma):
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        assert Y.shape == (self.nobs,) and sigma.shape == (self.nobs,)
+        self._keep["Y"], self._keep["sigma"] = Y, sigma
+        _check(library().m2m_set_targets(self.ptr, _dptr(Y), _dptr(sigma)), self.ptr)
+
+    def m2m_potential(self, comps):
+        arr, n = _pot_array(comps)
+        self._keep["pot"] = arr
+        _check(library().m2m_potential(self.ptr, arr, n), self.ptr)
+
+    def m2m_observe(self, mode=0):
+        _check(library().m2m_observe(self.ptr, mode), self.ptr)
+
+    def m2m_update_weights(self):
+        _check(library().m2m_update_weights(self.ptr), self.ptr)
+
+    def m2m_priors(self):
+        _check(library().m2m_priors(self.ptr), self.ptr)
+
+    def m2m_push(self, nsteps=1):
+        _check(library().m2m_push(self.ptr, nsteps), self.ptr)
+
+    def m2m_step(self, nsteps=1):
+        _check(library().m2m_step(self.ptr, nsteps), self.ptr)
+
+    def m2m_get_obs(self):
+        y, D, Dt = (np.empty(self.nobs) for _ in range(3))
+        _check(library().m2m_get_obs(self.ptr, _dptr(y), _dptr(D), _dptr(Dt)), self.ptr)
+        return y, D, Dt
+
+    def m2m_get_record(self):
+        r = m2m_record()
+        _check(library().m2m_get_record(self.ptr, byref(r)), self.ptr)
+        return r.as_dict()
+
+    def m2m_get_history(self, first, count):
+        out = (m2m_record * count)()
+        _check(library().m2m_get_history(self.ptr, first, count, out), self.ptr)
+        return [r.as_dict() for r in out]
+
+    def m2m_get_cells(self, with_prior=False):
+        import torch
+        n = self.t["w"].shape[0]
+        nsets = self._keep["nsets"]
+        oc = torch.empty(nsets * n, dtype=torch.int32, device=self.t["w"].device)
+        pc = torch.empty(n, dtype=torch.int32, device=self.t["w"].device) if with_prior else None
+        _check(library().m2m_get_cells(self.ptr, c_void_p(oc.data_ptr()),
+                                       c_void_p(pc.data_ptr()) if pc is not None else None), self.ptr)
+        torch.cuda.current_stream().synchronize()
+        return oc.view(nsets, n), pc
+
+    def m2m_nobs(self):
+        return library().m2m_nobs(self.ptr)
+
+    def m2m_steps_taken(self):
+        return library().m2m_steps_taken(self.ptr)
+
+    def m2m_set_launch(self, threads, blocks_per_sm=0):
+        _check(library().m2m_set_launch(self.ptr, threads, blocks_per_sm), self.ptr)
+
+    def m2m_free(self):
+        if self.ptr:
+            library().m2m_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.m2m_free()
+        except Exception:
+            pass
+
+    # -- conveniences --
+    def state(self):
+        """Host copies of the particle state (synchronises)."""
+        import torch
+        torch.cuda.current_stream().synchronize()
+        return {k: v.cpu().numpy() for k, v in self.t.items()}
+
+
+def _pot_array(comps):
+    n = len(comps)
+    arr = (m2m_potential_desc * max(n, 1))()
+    for k, c in enumerate(comps):
+        arr[k].kind = POT[c.kind]
+        for j, v in enumerate(c.params):
+            arr[k].p[j] = float(v)
+    return arr, n
+
+
+def m2m_init(precision, pos, vel, w, what, potential, obs, params, prior=None, Y=None,
+             sigma=None, device="cuda:0"):
+    """Create a context.
+
+    pos, vel: (3, n) arrays (host numpy or device tensors) -- copied into new
+    device tensors of the precision's dtype; w, what: (n,) float64.
+    potential: list of inputs.PotentialComponent; obs: list of
+    inputs.ObservableSet; params: dict(eps, mu, dt, alpha, entropy_const,
+    incl_sin, incl_cos); prior: inputs.PriorSpec or None.
+    """
+    import torch
+    lib = library()
+    prec = {"fp64": FP64, "fp32c": FP32C}[precision] if isinstance(precision, str) else precision
+    dt = torch.float64 if prec == FP64 else torch.float32
+    dev = torch.device(device)
+    t = {}
+    for k, name in enumerate(("x", "y", "z")):
+        t[name] = torch.as_tensor(np.asarray(pos[k]) if not torch.is_tensor(pos[k]) else pos[k]) \
+            .to(device=dev, dtype=dt).contiguous().clone()
+    for k, name in enumerate(("vx", "vy", "vz")):
+        t[name] = torch.as_tensor(np.asarray(vel[k]) if not torch.is_tensor(vel[k]) else vel[k]) \
+            .to(device=dev, dtype=dt).contiguous().clone()
+    t["w"] = torch.as_tensor(w).to(device=dev, dtype=torch.float64).contiguous().clone()
+    t["what"] = torch.as_tensor(what).to(device=dev, dtype=torch.float64).contiguous().clone()
+    n = t["w"].shape[0]
+    keep = {}
+    pot_arr, npot = _pot_array(potential)
+    keep["pot"] = pot_arr
+    od = (m2m_obs_desc * len(obs))()
+    for k, s in enumerate(obs):
+        ex = np.ascontiguousarray(s.edges_x, dtype=np.float64)
+        keep[f"ex{k}"] = ex
+        od[k].geom, od[k].quant = GEOM[s.geom], QUANT[s.quant]
+        od[k].nx, od[k].ny = len(ex) - 1, (1 if s.edges_y is None else len(s.edges_y) - 1)
+        od[k].edges_x = _dptr(ex)
+        if s.edges_y is not None:
+            ey = np.ascontiguousarray(s.edges_y, dtype=np.float64)
+            keep[f"ey{k}"] = ey
+            od[k].edges_y = _dptr(ey)
+        if s.quant == "gh":
+            V = np.ascontiguousarray(s.gh_V, dtype=np.float64)
+            S = np.ascontiguousarray(s.gh_S, dtype=np.float64)
+            keep[f"V{k}"], keep[f"S{k}"] = V, S
+            od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
+        od[k].sigma_kernel = float(s.sigma_kernel)
+    keep["obs"] = od
+    keep["nsets"] = len(obs)
+    nobs = sum(s.nobs for s in obs)
+    par = m2m_params(**{k: float(params[k]) for k in
+                        ("eps", "mu", "dt", "alpha", "entropy_const", "incl_sin", "incl_cos")})
+    keep["par"] = par
+    pd = None
+    if prior is not None and prior.kind != "flat":
+        pd = m2m_prior_desc(PRIOR[prior.kind], prior.nE, prior.nL, prior.period,
+                            float(prior.hernquist[0]), float(prior.hernquist[1]))
+        keep["prior"] = pd
+    Yp = sp = None
+    if Y is not None:
+        keep["Y"] = np.ascontiguousarray(Y, dtype=np.float64)
+        keep["sigma"] = np.ascontiguousarray(sigma, dtype=np.float64)
+        Yp, sp = _dptr(keep["Y"]), _dptr(keep["sigma"])
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ptr = c_void_p()
+    rc = lib.m2m_init(byref(ptr), prec, n,
+                      *[c_void_p(t[k].data_ptr()) for k in ("x", "y", "z", "vx", "vy", "vz", "w", "what")],
+                      pot_arr, npot, od, len(obs), Yp, sp, byref(par),
+                      byref(pd) if pd is not None else None, c_void_p(stream))
+    _check(rc, None)
+    return Context(ptr, t, keep, nobs, prec)
+
+
+def params_of(problem):
+    """Step parameters of an inputs.Problem as the dict m2m_init takes."""
+    return dict(eps=problem.eps, mu=problem.mu, dt=problem.dt, alpha=problem.alpha,
+                entropy_const=problem.entropy_const, incl_sin=problem.incl_sin,
+                incl_cos=problem.incl_cos)
+
+
+def from_problem(problem, precision=None, device="cuda:0", targets=True):
+    """m2m_init from an inputs.Problem (model particles, tables, targets)."""
+    prec = precision or problem.precision
+    return m2m_init(prec, problem.pos, problem.vel, problem.w0, problem.what0, problem.potential,
+                    problem.obs, params_of(problem), problem.prior,
+                    problem.Y if targets else None, problem.sigma if targets else None, device)
+
+
+def observe_targets(problem, precision=None, device="cuda:0"):
+    """Observables of the problem's target realisation, computed by the
+    library (a context over the target particles, one scatter)."""
+    ctx = m2m_init(precision or problem.precision, problem.target_pos, problem.target_vel,
+                   problem.target_w, problem.target_w, problem.potential, problem.obs,
+                   params_of(problem), None, None, None, device)
+    y, _, _ = ctx.m2m_get_obs()
+    ctx.m2m_free()
+    return y

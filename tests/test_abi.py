@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/m2m.h declares; argument validation needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1207_6403_gb300 import m2m as B
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "m2m.h")
+
+
+def declared():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(m2m_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for required in ("m2m_init", "m2m_step", "m2m_observe", "m2m_update_weights",
+                     "m2m_priors", "m2m_potential", "m2m_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.library()
+    for name in declared():
+        assert hasattr(L, name), name
+
+
+def test_struct_layouts_match_header_sizes():
+    assert ctypes.sizeof(B.m2m_potential_desc) == 40
+    assert ctypes.sizeof(B.m2m_obs_desc) == 56
+    assert ctypes.sizeof(B.m2m_prior_desc) == 32
+    assert ctypes.sizeof(B.m2m_params) == 56
+    assert ctypes.sizeof(B.m2m_record) == 56
+
+
+def _init(**kw):
+    L = B.library()
+    P = ctypes.c_void_p
+    args = dict(prec=B.FP32C, n=100, ptrs=[P(1 << 20)] * 8, nsets=1, par=B.m2m_params(0, 0, 0.01, 0.5, 1, 0, 1))
+    args.update(kw)
+    ex = (ctypes.c_double * 3)(0.0, 1.0, 2.0)
+    od = (B.m2m_obs_desc * 1)()
+    od[0].geom, od[0].quant, od[0].nx, od[0].ny = 1, 1, 2, 1
+    od[0].edges_x = ctypes.cast(ex, ctypes.POINTER(ctypes.c_double))
+    ctx = P()
+    rc = L.m2m_init(ctypes.byref(ctx), args["prec"], args["n"], *args["ptrs"], None, 0, od,
+                    args["nsets"], None, None, ctypes.byref(args["par"]), None, None)
+    return rc, ctx, L.m2m_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(prec=7), "precision"),
+    (dict(n=0), "n="),
+    (dict(ptrs=[ctypes.c_void_p(1 << 20)] * 7 + [ctypes.c_void_p((1 << 20) + 8)]), "aligned"),
+    (dict(ptrs=[None] + [ctypes.c_void_p(1 << 20)] * 7), "NULL"),
+    (dict(nsets=0), "nsets"),
+    (dict(par=B.m2m_params(0, 0, 0.01, 0.0, 1, 0, 1)), "alpha"),
+    (dict(par=B.m2m_params(float("nan"), 0, 0.01, 0.5, 1, 0, 1)), "non-finite"),
+])
+def test_init_rejects_bad_arguments_without_touching_memory(kw, needle):
+    rc, ctx, msg = _init(**kw)
+    assert rc == -1 and not ctx.value
+    assert needle in msg

@@ -1,0 +1,306 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle on the
+same seeded inputs, called through the C-ABI (thin binding).
+
+Tolerances (written here, derived in the design doc):
+* bin and prior-cell indices: bit-exact (float and double), except prior
+  cells built on the logarithmic potential (its E contains ln), where a
+  mismatch is allowed only for particles whose E sits within a few ulp of a
+  cell edge, and then only into the adjacent cell;
+* positions/velocities of the Hernquist and logarithmic pushes: bit-exact;
+* FP64 path: 1e-10 relative on every floating output;
+* FP32-compensated path: observables |dy| <= 1e-5 * scale_j (scale_j =
+  max(|y_j|, sigma_j/0.02), the bin's reference value), weights 1e-4
+  relative after 1000 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import m2m as O
+from paper_1207_6403_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1207_6403_gb300 import m2m as B  # noqa: E402
+
+_CACHE = {}
+
+
+def problem(name, n, precision=None, **kw):
+    key = (name, n, precision, tuple(sorted(kw.items())))
+    if key not in _CACHE:
+        P = I.make_problem(name, n=n, precision=precision, **kw)
+        Y = O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos)
+        _CACHE[key] = P.with_targets(Y)
+    return _CACHE[key]
+
+
+def oracle_state_arrays(st):
+    return dict(x=st.x, y=st.y, z=st.z, vx=st.vx, vy=st.vy, vz=st.vz, w=st.w, what=st.what)
+
+
+def obs_scale(y, sigma):
+    return np.maximum(np.maximum(np.abs(y), sigma / 0.02), 1e-300)
+
+
+def assert_obs_close(y_gpu, y_orc, sigma, tol):
+    err = np.abs(y_gpu - y_orc) / obs_scale(y_orc, sigma)
+    assert err.max() <= tol, f"max scaled error {err.max():.3e} at {err.argmax()}"
+
+
+# ------------------------------------------------------------------ push
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name", ["plain-fp64", "flat-log"])
+def test_push_is_bit_exact(prec, name):
+    P = problem(name, 4097, prec)
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(150)
+    g = ctx.state()
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for _ in range(150):
+        s = O.kdk(*s, P.potential, P.dt)
+    for a, k in zip(s, ("x", "y", "z", "vx", "vy", "vz")):
+        assert np.array_equal(g[k], a), k
+    # weights untouched by a pure push
+    assert np.array_equal(g["w"], P.w0)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-12), ("fp32c", 2e-5)])
+def test_push_nfw_plus_hernquist_close(prec, rtol):
+    P = problem("plain-fp64", 3001, prec)
+    comps = [I.PotentialComponent("hernquist", (1.0, 1.0)), I.PotentialComponent("nfw", (0.02, 5.0))]
+    P = I.Problem(**{**P.__dict__, "potential": comps})
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(50)
+    g = ctx.state()
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for _ in range(50):
+        s = O.kdk(*s, comps, P.dt)
+    for a, k in zip(s, ("x", "y", "z", "vx", "vy", "vz")):
+        np.testing.assert_allclose(g[k], a, rtol=rtol, atol=rtol * np.abs(a).max())
+
+
+# ------------------------------------------------------------------ cells
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log"])
+def test_observable_cells_are_bit_exact(prec, name):
+    P = problem(name, 20011, prec)
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(7)
+    oc, _ = ctx.m2m_get_cells()
+    oc = oc.cpu().numpy()
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for _ in range(7):
+        s = O.kdk(*s, P.potential, P.dt)
+    kern = O.cells_and_kernels(*s, P.obs, P.incl_sin, P.incl_cos)
+    for k, (cell, _) in enumerate(kern):
+        assert np.array_equal(oc[k], cell), f"set {k}: {np.sum(oc[k] != cell)} mismatches"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_cells_on_edges_nan_and_out_of_range(prec):
+    T = np.float64 if prec == "fp64" else np.float32
+    ex = I.uniform_edges(8, -2.0, 2.0)
+    ey = I.uniform_edges(4, -1.0, 1.0)
+    obs = [I.ObservableSet("grid", "mass", ex, ey),
+           I.ObservableSet("shell", "mass", I.log_shell_edges(5, 0.1, 3.0))]
+    xs = np.concatenate([ex.astype(T), ex.astype(T) - np.abs(ex.astype(T)) * 1e-7,
+                         np.array([np.nan, np.inf, -np.inf, 2.0, -2.0, 0.0], T)])
+    n = xs.size
+    ys = np.zeros(n, T)
+    zs = np.zeros(n, T)
+    ys[::3] = T(1.0)           # top y-edge: outside (half-open)
+    ys[1::3] = T(-1.0)         # bottom y-edge: inside
+    pos = np.stack([xs, ys, zs]).astype(np.float64)
+    vel = np.zeros((3, n))
+    w = np.full(n, 1.0 / n)
+    ctx = B.m2m_init(prec, pos.astype(T), vel.astype(T), w, w, [], obs,
+                     dict(eps=0, mu=0, dt=0.01, alpha=1, entropy_const=1, incl_sin=0.0, incl_cos=1.0))
+    oc, _ = ctx.m2m_get_cells()
+    oc = oc.cpu().numpy()
+    kern = O.cells_and_kernels(xs, ys, zs, zs, zs, zs, obs, 0.0, 1.0)
+    for k, (cell, _) in enumerate(kern):
+        assert np.array_equal(oc[k], cell)
+
+
+def _prior_cells_oracle(P, prec, nsteps):
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for _ in range(nsteps):
+        s = O.kdk(*s, P.potential, P.dt)
+    return s, O.prior_cells(*s, P.prior, P.potential)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_prior_cells_hernquist_bit_exact(prec):
+    P = problem("moving-priors", 30007, prec)
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(3)
+    _, pc = ctx.m2m_get_cells(with_prior=True)
+    _, ref = _prior_cells_oracle(P, prec, 3)
+    assert np.array_equal(pc.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_prior_cells_log_potential_match_except_at_edges(prec):
+    P = problem("flat-log", 30007, prec)
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(3)
+    _, pc = ctx.m2m_get_cells(with_prior=True)
+    pc = pc.cpu().numpy()
+    s, ref = _prior_cells_oracle(P, prec, 3)
+    bad = np.nonzero(pc != ref)[0]
+    assert bad.size <= max(3, ref.size // 5000)
+    # every mismatch is one E-cell across an edge the oracle's E nearly touches
+    T = s[0].dtype.type
+    E = T(0.5) * ((s[3] * s[3] + s[4] * s[4]) + s[5] * s[5]) + \
+        O.potential(*s[:3], P.potential)
+    lo, hi = float(E.min()), float(E.max())
+    width = (hi - lo) / P.prior.nE
+    for i in bad:
+        assert abs(pc[i] - ref[i]) == P.prior.nL
+        frac = (float(E[i]) - lo) / width
+        assert abs(frac - round(frac)) * width < 8 * np.spacing(abs(T(E[i])))
+
+
+# --------------------------------------------------------- observe, update
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 1e-5)])
+@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log"])
+def test_observe_residual_and_update_match(prec, tol, name):
+    P = problem(name, 20011, prec)
+    ctx = B.from_problem(P, prec)
+    st = O.init(P, prec)
+    y, D, Dt = ctx.m2m_get_obs()
+    assert_obs_close(y, st.y_obs, P.sigma, tol)
+    np.testing.assert_allclose(Dt, st.Dt, rtol=0, atol=tol / 0.02 * 5)   # Delta in sigma units
+    np.testing.assert_allclose(D, st.Delta, rtol=0, atol=tol / 0.02 * 5)
+    # one weight update with the initial Delta~
+    ctx.m2m_update_weights()
+    g = ctx.state()
+    kern = O.cells_and_kernels(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.obs, P.incl_sin, P.incl_cos)
+    dot = O.kernel_dot(kern, st.coef, P.obs, P.n)
+    w1 = O.update_weights(st.w, st.what, dot, P.eps, P.mu, P.dt, P.entropy_const)
+    np.testing.assert_allclose(g["w"], w1, rtol=1e-12 if prec == "fp64" else 2e-7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name", ["moving-priors", "flat-log"])
+def test_priors_match(prec, name):
+    P = problem(name, 20011, prec)
+    g0 = np.random.default_rng(3)
+    w = P.w0 * g0.uniform(0.5, 1.5, P.n)
+    P = I.Problem(**{**P.__dict__, "w0": w})
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_priors()
+    g = ctx.state()
+    st = O.init(P, prec)
+    cells = O.prior_cells(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.prior, P.potential)
+    ref = O.prior_means(st.w, cells, P.prior.ncells)
+    if name == "moving-priors":
+        np.testing.assert_allclose(g["what"], ref, rtol=1e-12 if prec == "fp64" else 1e-8)
+    else:
+        err = np.abs(g["what"] / ref - 1)
+        assert np.mean(err > 1e-8) < 1e-3
+
+
+# ------------------------------------------------------------ end to end
+def _run_both(P, prec, nsteps):
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_step(nsteps)
+    g = ctx.state()
+    y, D, Dt = ctx.m2m_get_obs()
+    hist = ctx.m2m_get_history(1, nsteps)
+    st = O.run(P, nsteps, precision=prec)
+    return g, (y, D, Dt), hist, st
+
+
+def test_plain_fp64_end_to_end_full_run():
+    """The plain-method workload as stated: N=20,000, 2000 steps, FP64."""
+    P = problem("plain-fp64", 20000, "fp64")
+    g, (y, D, Dt), hist, st = _run_both(P, "fp64", 2000)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-10)
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-10)
+    np.testing.assert_allclose(Dt, st.Dt, rtol=1e-10, atol=1e-10)
+    for a, b in zip(hist, st.history):
+        assert a["step"] == b["t"]
+        for k in ("chi2", "chi2_raw", "S", "sum_w", "F"):
+            assert a[k] == pytest.approx(b[k], rel=1e-10, abs=1e-12), (k, a["step"])
+
+
+def test_moving_priors_fp32c_1000_steps():
+    P = problem("moving-priors", 20000, "fp32c")
+    g, (y, D, Dt), hist, st = _run_both(P, "fp32c", 1000)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-4)
+    np.testing.assert_allclose(g["what"], st.what, rtol=1e-4)
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
+    for a, b in zip(hist[::50], st.history[::50]):
+        assert a["sum_w"] == pytest.approx(b["sum_w"], rel=1e-4)
+        assert a["chi2"] == pytest.approx(b["chi2"], rel=1e-4)
+
+
+def test_flat_log_fp32c_200_steps():
+    P = problem("flat-log", 40000, "fp32c")
+    g, (y, D, Dt), hist, st = _run_both(P, "fp32c", 200)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    # prior cells of the log potential may differ for particles at an edge
+    rel = np.abs(g["w"] / st.w - 1)
+    assert np.quantile(rel, 0.999) < 1e-4
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("n", [1, 3, 31, 33, 4097])
+def test_small_and_ragged_sizes(prec, n):
+    P = problem("moving-priors", n, prec)
+    P = I.Problem(**{**P.__dict__, "prior": I.PriorSpec("e_lc", 4, 4, 5, (1.0, 1.0))})
+    g, (y, D, Dt), hist, st = _run_both(P, prec, 12)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-10 if prec == "fp64" else 1e-5)
+    np.testing.assert_allclose(g["what"], st.what, rtol=1e-10 if prec == "fp64" else 1e-5)
+
+
+def test_zero_weights_stay_zero_and_nonfinite_is_reported():
+    P = problem("plain-fp64", 5000, "fp64")
+    w = P.w0.copy()
+    w[::7] = 0.0
+    P2 = I.Problem(**{**P.__dict__, "w0": w})
+    ctx = B.from_problem(P2, "fp64")
+    ctx.m2m_step(20)
+    g = ctx.state()
+    assert np.all(g["w"][::7] == 0.0) and np.all(np.isfinite(g["w"]))
+    st = O.run(P2, 20, precision="fp64")
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-10)
+    # a NaN weight is caught by the kernels and surfaces on the next read
+    ctx.t["w"][3] = float("nan")
+    ctx.m2m_step(1)
+    with pytest.raises(B.M2MError) as e:
+        ctx.m2m_get_record()
+    assert e.value.code == -3
+
+
+def test_full_size_flat_log_one_step_sampled():
+    """The benchmark's workload and launch: N = 4,000,000, one step."""
+    P = problem("flat-log", 4_000_000, "fp32c")
+    ctx = B.from_problem(P, "fp32c")
+    ctx.m2m_step(1)
+    g = ctx.state()
+    y, _, _ = ctx.m2m_get_obs()
+    st = O.run(P, 1, precision="fp32c")
+    idx = np.random.default_rng(0).choice(P.n, 20000, replace=False)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k][idx], getattr(st, k)[idx]), k
+    np.testing.assert_allclose(g["w"][idx], st.w[idx], rtol=1e-6)
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
+    r = ctx.m2m_get_record()
+    assert r["sum_w"] == pytest.approx(st.history[-1]["sum_w"], rel=1e-6)
