@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the M2M training step: particle-steps/s and HBM roofline.
+
+Workload (the headline configuration): N = 4,000,000 particles in the
+flattened logarithmic potential (v0=1, Rc=0.1, q=0.8) seen at 60 deg;
+observables 64x64 surface-density pixels + 20x20 IFU apertures x h0..h4
+(6096); moving priors on a 128x64 (E, L_z) grid every 25 steps.  Inputs are
+synthetic (Philox-seeded realisations), resident in HBM when timing starts;
+the particle arrays (288 MB per step of traffic) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
+FP64 GPU path is measured on the same box and reported under "fp64_gpu".
+Under torchrun (N > 1) every rank advances its own independent model
+(another seed) with no data-path collective: weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "flat-log"
+N_DEFAULT = 4_000_000
+METRIC = "M2M particle-steps/s at N=4M (FP32-compensated vs FP64 GPU), % of HBM roofline"
+# algorithmic bytes per particle of one steady-state step pass (FP32C):
+# read x,y,z,vx,vy,vz (24) + w (8) + w_hat (8); write x..vz (24) + w (8)
+BYTES_PER_PARTICLE_FP32C = 72
+BYTES_PER_PARTICLE_FP64 = 120
+PROFILE_JSON = os.path.join(ROOT, "profiles", "k_pass_flat_log_4M.json")
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1207_6403_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        return self.reduce(x, "max")
+
+    def sum(self, x):
+        return self.reduce(x, "sum")
+
+    def reduce(self, x, op):
+        if not self.pg:
+            return x
+        import torch
+        dev = f"cuda:{self.local}" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons in the background."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    ts += float("0." + f[0].split(".")[1]) if "." in f[0] else 0.0
+                except Exception:
+                    ts = None
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        inside = [r for r in rows if r[0] is not None and t0 - 0.15 <= r[0] <= t1 + 0.15]
+        note = None
+        if not inside:
+            inside = rows
+            note = "timed region shorter than the sampling interval: all samples"
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower() == "active"})
+        out = {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+               "reasons": reasons, "samples": len(inside)}
+        if note:
+            out["note"] = note
+        return out
+
+
+# ------------------------------------------------------------ workload
+def workload(n, rank=0, precision="fp32c", device="cuda:0", targets_by="gpu"):
+    from paper_1207_6403_gb300 import inputs as I
+    P = I.make_problem(WORKLOAD, n=n, precision=precision,
+                       seed_model=5 + 1000 * rank, seed_target=6 + 1000 * rank)
+    if targets_by == "gpu":
+        from paper_1207_6403_gb300 import m2m as B
+        Y = B.observe_targets(P, "fp32c", device)
+    else:
+        from oracle import m2m as O
+        Y = O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos)
+    return P.with_targets(Y)
+
+
+def config(n, world):
+    return {"workload": f"{WORKLOAD}: N={n:,} particles per GPU, flattened logarithmic potential "
+                        "(v0=1, Rc=0.1, q=0.8) at 60 deg, 64x64 pixels + 20x20 IFU apertures x h0..h4 "
+                        "(6096 observables), (E, L_z) 128x64 moving priors every 25 steps, dt=0.01",
+            "n_particles": n, "observables": 6096, "global_particles": n * world,
+            "parallelism": "replicas" if world == 1 else f"{world} independent models, one per GPU",
+            "l2": "particle arrays (288 MB/step) exceed the 129 MB L2; no flush needed"}
+
+
+# ------------------------------------------------------------ oracle arm
+def time_oracle(P, nsteps, sample_stride):
+    """Oracle on a strided sample of the workload; returns (particle-steps/s, n_sample, s)."""
+    from oracle import m2m as O
+    from paper_1207_6403_gb300 import inputs as I
+    sl = slice(0, None, sample_stride)
+    # the sample carries the whole model's weight, so the residuals and
+    # updates it computes are those of the full workload
+    S = I.Problem(**{**P.__dict__, "n": P.pos[:, sl].shape[1], "pos": P.pos[:, sl].copy(),
+                     "vel": P.vel[:, sl].copy(), "w0": P.w0[sl] * sample_stride,
+                     "what0": P.what0[sl] * sample_stride})
+    st = O.init(S, "fp32c")
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        O.step(st, S)
+    dt = time.perf_counter() - t0
+    return S.n * nsteps / dt, S.n, dt
+
+
+def run_reference(args, D):
+    if D.rank != 0:
+        return
+    P = workload(args.n, 0, targets_by="oracle")
+    # calibrate the sample so the whole warm-up + timed run takes ~2 minutes
+    rate, _, _ = time_oracle(P, 1, 40)
+    budget = 120.0
+    per_step = budget / max(1, args.steps + args.warmup)
+    n_sample = max(2000, min(args.n, int(rate * per_step)))
+    stride = max(1, args.n // n_sample)
+    time_oracle(P, args.warmup, stride) if args.warmup else None
+    value, ns, secs = time_oracle(P, args.steps, stride)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (state f32)", "data": "synthetic", "config": config(args.n, 1),
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"every {stride}th particle ({ns:,} of {args.n:,}) of the workload, "
+                                       f"{args.steps} oracle steps"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, D):
+    import torch
+    from paper_1207_6403_gb300 import m2m as B
+    dev = f"cuda:{D.local}"
+    torch.cuda.set_device(dev)
+    P = workload(args.n, D.rank, device=dev)
+    n = P.n
+    stream = torch.cuda.current_stream()
+
+    # ---- FP32-compensated path: the headline number
+    ctx = B.from_problem(P, "fp32c", device=dev)
+    ctx.m2m_step(args.warmup)
+    torch.cuda.synchronize()
+    ctx.m2m_get_timing()                     # reset the launch counter
+    clocks = Clocks(D.local)
+    clocks.start()
+    D.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(stream)
+    ctx.m2m_step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    D.barrier()
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.m2m_get_timing()["kernels_total"]
+    ms_max = D.max(ms)
+    value = D.world * n * args.steps / (ms_max * 1e-3)
+
+    # ---- dominant kernel, per-launch device time (events on the launching stream)
+    k_roof = min(args.steps, 2000)
+    ctx.m2m_set_timing(True)
+    ctx.m2m_step(k_roof)
+    tm = ctx.m2m_get_timing()
+    ctx.m2m_set_timing(False)
+    tot_ms = sum(tm["ms"].values())
+    shares = {k: round(v / tot_ms, 4) for k, v in tm["ms"].items() if v > 0}
+    pass_ms = tm["ms"]["step_upd"] / max(1, tm["launches"]["step_upd"])
+    achieved = BYTES_PER_PARTICLE_FP32C * n / (pass_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    try:
+        with open(PROFILE_JSON) as f:
+            prof = json.load(f)
+        if prof.get("src_sha") == src_hash():
+            traffic = prof.get("traffic_bytes_per_launch")
+    except Exception:
+        pass
+    rec = ctx.m2m_get_record()
+    ctx.m2m_free()
+
+    # ---- FP64 GPU path on the same box
+    k64 = max(5, min(200, args.steps // 50))
+    c64 = B.from_problem(P, "fp64", device=dev)
+    c64.m2m_step(2)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    c64.m2m_step(k64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = D.max(f0.elapsed_time(f1))
+    value64 = D.world * n * k64 / (ms64 * 1e-3)
+    c64.m2m_free()
+
+    # ---- equal weight accuracy: both GPU forms from the same state, 50 steps
+    ca, cb = B.from_problem(P, "fp32c", device=dev), B.from_problem(P, "fp64", device=dev)
+    ca.m2m_step(50)
+    cb.m2m_step(50)
+    torch.cuda.synchronize()
+    wrel = float(((ca.t["w"] - cb.t["w"]).abs() / cb.t["w"].abs().clamp_min(1e-300)).max().item())
+    ca.m2m_free()
+    cb.m2m_free()
+
+    # ---- end to end through the C-ABI with host buffers: every step uploads
+    # the step's targets and errors from pinned host memory and reads the
+    # step's record (chi^2, S, F) back
+    ce = B.from_problem(P, "fp32c", device=dev)
+    Yp = torch.from_numpy(P.Y).pin_memory()
+    Sp = torch.from_numpy(P.sigma).pin_memory()
+    Yn, Sn = Yp.numpy(), Sp.numpy()
+    k_e2e = min(args.steps, 2000)
+    for _ in range(3):
+        ce.m2m_set_targets(Yn, Sn)
+        ce.m2m_step(1)
+        ce.m2m_get_record()
+    D.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ce.m2m_set_targets(Yn, Sn)
+        ce.m2m_step(1)
+        ce.m2m_get_record()
+    t_e2e = D.max(time.perf_counter() - t0)
+    ce.m2m_free()
+    e2e = D.world * n * k_e2e / t_e2e
+
+    cpu = None
+    if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
+        rate, ns, secs = time_oracle(P, 3, 8)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"every 8th particle ({ns:,} of {n:,}) of the workload, 3 oracle steps "
+                         f"({secs:.1f} s, numpy, one thread)"}
+
+    if D.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": D.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (FP32-compensated; f64 weights)", "data": "synthetic",
+                "config": config(n, D.world),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "k_pass (steady-state step pass: update+push+scatter)",
+                             "bytes_per_particle": BYTES_PER_PARTICLE_FP32C, "launch_ms": pass_ms,
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                             "kernel_time_shares": shares},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e, "unit": "particle-steps/s",
+                        "h2d_bytes_per_step": int(2 * 8 * P.nobs), "d2h_bytes_per_step": 56 + 4,
+                        "how": "per step: m2m_set_targets (pinned host Y, sigma) + m2m_step(1) + "
+                               "m2m_get_record (host)"},
+                "gpu_launches": int(launches),
+                "clocks": clocks.summary(w0, w1),
+                "fp64_gpu": {"value": value64, "unit": "particle-steps/s", "steps": k64,
+                             "ms_per_step": ms64 / k64,
+                             "hbm_frac_at_120B": BYTES_PER_PARTICLE_FP64 * n * k64 / (ms64 * 1e-3) / 1e9 / peak},
+                "fp32c_over_fp64": value / value64,
+                "w_max_rel_diff_fp32c_vs_fp64_50_steps": wrel,
+                "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    D = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, D)
+        else:
+            run_ours(args, D)
+    finally:
+        D.close()
+
+
+if __name__ == "__main__":
+    main()

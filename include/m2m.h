@@ -226,6 +226,37 @@ int64_t m2m_steps_taken(const m2m_ctx *ctx);
  * next launch. */
 int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
 
+/* Observable layout of the particle kernels: the common set combinations
+ * (pixels + IFU GH apertures; shells + GH annuli; shells + mass and v_los^2
+ * annuli) run as code compiled for them when every edge table is uniform in
+ * value or in log; anything else walks the sets at run time.  layout -1:
+ * automatic (the default); 0: force the run-time walk; 1-3: the compiled
+ * layout, only if it matches (else M2M_ERR_ARG).  Results are identical. */
+int m2m_set_layout(m2m_ctx *ctx, int32_t layout);
+
+/* Device timing of the library's own launches, by kernel class, with CUDA
+ * events recorded on the context's stream around every launch while
+ * enabled.  Classes: */
+#define M2M_TK_STEP_UPD  0   /* step pass that also applies the pending update */
+#define M2M_TK_STEP      1   /* step pass without a pending update */
+#define M2M_TK_RESIDUAL  2   /* residual / chi^2 / record */
+#define M2M_TK_UPDATE    3   /* update-only pass (end of a call, m2m_update_weights) */
+#define M2M_TK_PRIOR     4   /* update + prior-cell pass, cell means, gather */
+#define M2M_TK_OTHER     5   /* observe, push, range and cell-export passes */
+#define M2M_TK_N         6
+typedef struct {
+    int64_t launches[M2M_TK_N];  /* launches timed since the last read */
+    double ms[M2M_TK_N];         /* summed device milliseconds */
+    int64_t kernels_total;       /* all kernels launched since the last read,
+                                    timed or not */
+} m2m_timing;
+
+/* enable != 0: record events around each launch from now on. */
+int m2m_set_timing(m2m_ctx *ctx, int32_t enable);
+
+/* Synchronises, fills *out for the launches since the last call, resets. */
+int m2m_get_timing(m2m_ctx *ctx, m2m_timing *out);
+
 /* Text of the last error on this context (or of the last failed m2m_init
  * when ctx is NULL). */
 const char *m2m_last_error(const m2m_ctx *ctx);

@@ -12,7 +12,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "m2m_api.cu")
+SRCS = [os.path.join(HERE, "csrc", f) for f in ("m2m_api.cu", "m2m_pass_f32.cu", "m2m_pass_f64.cu")]
 HDRS = [os.path.join(HERE, "csrc", f) for f in ("m2m_device.cuh", "m2m_kernels.cuh")] + [
     os.path.join(ROOT, "include", "m2m.h")]
 OUT_DIR = os.path.join(HERE, "lib")
@@ -28,8 +28,8 @@ def nvcc():
 
 
 def flags(verbose=False):
-    f = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--shared",
-         "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"), "-lcudart"]
+    f = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false",
+         "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -39,7 +39,7 @@ def up_to_date():
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in [SRC] + HDRS + [__file__])
+    return all(os.path.getmtime(p) <= t for p in SRCS + HDRS + [__file__])
 
 
 def build(force=False, verbose=False):
@@ -47,14 +47,26 @@ def build(force=False, verbose=False):
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    objs, procs = [], []
+    for src in SRCS:           # one translation unit per precision, in parallel
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc()] + flags(verbose) + ["-c", "-o", obj, src],
+                                      stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True))
+    failed = False
+    for pr in procs:
+        out, _ = pr.communicate()
+        if pr.returncode != 0 or verbose:
+            sys.stderr.write(out)
+        failed |= pr.returncode != 0
+    if failed:
+        raise RuntimeError("nvcc failed building libm2m.so")
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + flags(verbose) + ["-o", tmp, SRC]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    r = subprocess.run([nvcc(), ARCH, "--shared", "-o", tmp] + objs + ["-lcudart"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libm2m.so")
-    if verbose:
-        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed linking libm2m.so")
     os.replace(tmp, LIB)
     return LIB
 

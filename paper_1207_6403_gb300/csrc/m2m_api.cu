@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/m2m.h"
+#define M2M_COMMON_KERNELS
 #include "m2m_kernels.cuh"
 
 using namespace m2m;
@@ -70,6 +71,13 @@ struct m2m_ctx {
     long long t;
     bool pending;
     int last_grid;       // grid of the last scatter pass (slots to reduce)
+    int layout;          // compiled observable layout of the pass kernel
+    // timing of the library's launches
+    bool timing;
+    long long kernels_total;
+    struct Ev { int kind; cudaEvent_t a, b; };
+    std::vector<Ev> evs;
+    std::vector<cudaEvent_t> ev_free;
     std::string err;
 };
 
@@ -94,6 +102,42 @@ int set_err(m2m_ctx *c, int code, const char *fmt, ...) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+cudaEvent_t ev_get(m2m_ctx *c) {
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets one launch: kernel counter always, events while timing is on.
+struct LaunchTimer {
+    m2m_ctx *c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    LaunchTimer(m2m_ctx *c_, int kind_) : c(c_), kind(kind_) {
+        c->kernels_total++;
+        if (c->timing && (a = ev_get(c))) cudaEventRecord(a, c->st);
+    }
+    ~LaunchTimer() {
+        if (!a) return;
+        cudaEvent_t b = ev_get(c);
+        if (!b) { c->ev_free.push_back(a); return; }
+        cudaEventRecord(b, c->st);
+        c->evs.push_back({kind, a, b});
+    }
+};
+
+int pass_kind(int flags) {
+    if ((flags & F_PUSH) && (flags & F_SCAT)) return (flags & F_UPD) ? M2M_TK_STEP_UPD : M2M_TK_STEP;
+    if (flags & F_CELLS) return M2M_TK_PRIOR;
+    if (flags == F_UPD) return M2M_TK_UPDATE;
+    return M2M_TK_OTHER;
+}
+
 float ceil_float(double e) {
     float f = (float)e;
     if ((double)f < e) f = nextafterf(f, INFINITY);
@@ -108,7 +152,7 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
     if (lin_ok) {
         double a = nb / span, b = -e[0] * a;
         for (int k = 0; k <= nb && lin_ok; ++k)
-            if (fabs(a * e[k] + b - k) > 0.25) lin_ok = false;
+            if (fabs(a * e[k] + b - k) > 0.01) lin_ok = false;
         if (lin_ok) { *mode = G_LIN; *ga = (float)a; *gb = (float)b; return; }
     }
     if (e[0] > 0) {
@@ -116,7 +160,7 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
         bool ok = l1 > l0;
         double a = ok ? nb / (l1 - l0) : 0, b = -l0 * a;
         for (int k = 0; k <= nb && ok; ++k)
-            if (fabs(a * log2(e[k]) + b - k) > 0.25) ok = false;
+            if (fabs(a * log2(e[k]) + b - k) > 0.01) ok = false;
         if (ok) { *mode = G_LOG; *ga = (float)a; *gb = (float)b; return; }
     }
     *mode = G_BIS; *ga = 0.f; *gb = 0.f;
@@ -137,18 +181,26 @@ size_t pass_smem(const m2m_ctx *c, int flags) {
     return b;
 }
 
+// Compile-time observable layout matching the context's sets (see
+// for_each_set); 0 = generic.  Layouts need index guesses good to one cell.
+int detect_layout(const m2m_ctx *c) {
+    for (int k = 0; k < c->nsets; ++k) {
+        const SetDev &s = c->sets[k];
+        if (s.gx_mode == G_BIS || (s.geom == M2M_GEOM_GRID && s.gy_mode == G_BIS)) return 0;
+    }
+    auto is = [&](int k, int g, int q) { return c->sets[k].geom == g && c->sets[k].quant == q; };
+    if (c->nsets == 2 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) && is(1, M2M_GEOM_GRID, M2M_Q_GH)) return 1;
+    if (c->nsets == 2 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_GH)) return 2;
+    if (c->nsets == 3 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_MASS) &&
+        is(2, M2M_GEOM_ANNULUS, M2M_Q_VLOS2))
+        return 3;
+    return 0;
+}
+
 LaunchShape pick_kernel(const m2m_ctx *c) {
-    if (c->prec == M2M_FP32C) {
-        switch (c->threads) {
-            case 256: return {(void *)k_pass<float, 256, 2>, 256};
-            case 1024: return {(void *)k_pass<float, 1024, 1>, 1024};
-            default: return {(void *)k_pass<float, 512, 2>, 512};
-        }
-    }
-    switch (c->threads) {
-        case 512: return {(void *)k_pass<double, 512, 1>, 512};
-        default: return {(void *)k_pass<double, 256, 1>, 256};
-    }
+    int nt = c->threads;
+    if (c->prec == M2M_FP32C) return {pass_kernel_f32(nt, c->layout), nt};
+    return {pass_kernel_f64(nt, c->layout), nt};
 }
 
 void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
@@ -162,6 +214,8 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.mu = c->par.mu; a.ent_c = c->par.entropy_const;
     a.hdt = 0.5 * c->par.dt; a.dt = c->par.dt;
     a.sin_i = c->par.incl_sin; a.cos_i = c->par.incl_cos;
+    a.f_eps_dt = (float)a.eps_dt; a.f_mu = (float)a.mu; a.f_ent_c = (float)a.ent_c;
+    a.f_hdt = (float)a.hdt; a.f_dt = (float)a.dt; a.f_sin_i = (float)a.sin_i; a.f_cos_i = (float)a.cos_i;
     a.edge_tab = c->d_edges; a.edge_len = c->edge_len;
     a.gh_tab = c->d_gh; a.gh_len = c->gh_len;
     a.coef = c->d_coef_r;
@@ -170,6 +224,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.prior_kind = c->prior.kind; a.nE = c->prior.nE; a.nL = c->prior.nL; a.ncells = c->ncells;
     a.pk = c->prior.hernquist_a / c->prior.hernquist_GM;
     a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
+    a.f_pk = (float)a.pk; a.f_pgma = (float)a.pgma;
     a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
     a.cell_ids = c->d_cell_ids; a.cell_acc = c->d_cell_acc; a.cell_cnt = c->d_cell_cnt;
     a.err = c->d_err;
@@ -192,7 +247,10 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     void *args[] = {&a};
-    CU(cudaLaunchKernel(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
+    {
+        LaunchTimer lt(ctx, pass_kind(flags));
+        CU(cudaLaunchKernel(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
+    }
     if (flags & F_SCAT) ctx->last_grid = (int)grid;
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
     if (grid_out) *grid_out = (int)grid;
@@ -213,7 +271,8 @@ int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, 
     r.err = ctx->d_err;
     int nb = (ctx->nobs + 31) / 32;
     void *args[] = {&r};
-    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(256), args, 0, ctx->st));
+    LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
+    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(RES_NT), args, 0, ctx->st));
     return M2M_OK;
 }
 
@@ -233,14 +292,20 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
     int rc = launch_pass(ctx, F_CELLS | pass_flags);
     if (rc) return rc;
     int nb = (ctx->ncells + 255) / 256;
-    k_prior_mean<<<nb, 256, 0, ctx->st>>>(ctx->d_cell_acc, ctx->d_cell_cnt, ctx->ncells,
-                                          ctx->prec == M2M_FP32C, ctx->fx_q, ctx->d_cell_mean);
-    CU(cudaGetLastError());
+    {
+        LaunchTimer lt(ctx, M2M_TK_PRIOR);
+        k_prior_mean<<<nb, 256, 0, ctx->st>>>(ctx->d_cell_acc, ctx->d_cell_cnt, ctx->ncells,
+                                              ctx->prec == M2M_FP32C, ctx->fx_q, ctx->d_cell_mean);
+        CU(cudaGetLastError());
+    }
     int g = ctx->nsm * 8;
     long long need = (ctx->n + 255) / 256;
     if (g > need) g = (int)need;
-    k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->n);
-    CU(cudaGetLastError());
+    {
+        LaunchTimer lt(ctx, M2M_TK_PRIOR);
+        k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->n);
+        CU(cudaGetLastError());
+    }
     return M2M_OK;
 }
 
@@ -253,7 +318,15 @@ int check_err_word(m2m_ctx *ctx) {
     return M2M_OK;
 }
 
+void free_events(m2m_ctx *c) {
+    for (auto &e : c->evs) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    c->evs.clear();
+    c->ev_free.clear();
+}
+
 void free_all(m2m_ctx *c) {
+    free_events(c);
     void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
@@ -284,6 +357,8 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
             return set_err(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot[k].kind);
         }
     }
+    for (int k = 0; k < MAXPOT; ++k)
+        for (int j = 0; j < 6; ++j) tmp[k].cf[j] = (float)tmp[k].c[j];
     memcpy(ctx->pot, tmp, sizeof tmp);
     ctx->npot = npot;
     return M2M_OK;
@@ -343,6 +418,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
             delete ctx; return M2M_ERR_ARG;
         }
         d.nmom = o.quant == M2M_Q_GH ? 5 : 1;
+        d.gx_top = (float)(d.nx - 1);
+        d.gy_top = (float)(d.ny - 1);
         long long cells = (long long)d.nx * d.ny;
         d.obs_off = nobs;
         if (nobs + cells * d.nmom > MAXOBS) {
@@ -388,6 +465,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     }
     ctx->nsets = nsets;
     ctx->nobs = nobs;
+    ctx->layout = detect_layout(ctx);
     ctx->edge_len = (int)edges_d.size();
     ctx->gh_len = (int)gh_d.size();
 
@@ -480,11 +558,13 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
             }
     }
     // the pass kernels may use more than 48 KB of shared memory
-    void *kfns[] = {(void *)k_pass<float, 256, 2>, (void *)k_pass<float, 512, 2>, (void *)k_pass<float, 1024, 1>,
-                    (void *)k_pass<double, 256, 1>, (void *)k_pass<double, 512, 1>,
-                    (void *)k_cells<float>, (void *)k_cells<double>};
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64()};
+    for (int lay = 0; lay < 4; ++lay) {
+        for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
+        for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
+    }
     for (void *f : kfns) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, f);
@@ -644,7 +724,8 @@ int m2m_get_cells(m2m_ctx *ctx, int32_t *obs_cells, int32_t *prior_cells) {
     long long need = (ctx->n + 255) / 256;
     if (g > need) g = (int)need;
     void *args[] = {&a, &obs_cells, &prior_cells};
-    void *fn = ctx->prec == M2M_FP32C ? (void *)k_cells<float> : (void *)k_cells<double>;
+    void *fn = ctx->prec == M2M_FP32C ? cells_kernel_f32() : cells_kernel_f64();
+    LaunchTimer lt(ctx, M2M_TK_OTHER);
     CU(cudaLaunchKernel(fn, dim3(g), dim3(256), args, sm, ctx->st));
     return M2M_OK;
 }
@@ -660,6 +741,39 @@ int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm) {
         return set_err(ctx, M2M_ERR_ARG, "launch shape %d threads x %d blocks/SM not supported", threads, blocks_per_sm);
     ctx->threads = threads;
     ctx->bps_req = blocks_per_sm;
+    return M2M_OK;
+}
+
+int m2m_set_layout(m2m_ctx *ctx, int32_t layout) {
+    if (!ctx) return M2M_ERR_ARG;
+    if (layout < 0) { ctx->layout = detect_layout(ctx); return M2M_OK; }
+    if (layout != 0 && layout != detect_layout(ctx))
+        return set_err(ctx, M2M_ERR_ARG, "layout %d does not match the observable sets", layout);
+    ctx->layout = layout;
+    return M2M_OK;
+}
+
+int m2m_set_timing(m2m_ctx *ctx, int32_t enable) {
+    if (!ctx) return M2M_ERR_ARG;
+    ctx->timing = enable != 0;
+    return M2M_OK;
+}
+
+int m2m_get_timing(m2m_ctx *ctx, m2m_timing *out) {
+    if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    memset(out, 0, sizeof *out);
+    CU(cudaStreamSynchronize(ctx->st));
+    for (auto &e : ctx->evs) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e.a, e.b));
+        out->launches[e.kind]++;
+        out->ms[e.kind] += ms;
+        ctx->ev_free.push_back(e.a);
+        ctx->ev_free.push_back(e.b);
+    }
+    ctx->evs.clear();
+    out->kernels_total = ctx->kernels_total;
+    ctx->kernels_total = 0;
     return M2M_OK;
 }
 

@@ -29,11 +29,13 @@ struct SetDev {
     int gh_off;           // offset into the GH table (5 values per cell)
     int gx_mode, gy_mode; // index guess for the x / y edges
     float gx_a, gx_b, gy_a, gy_b;
+    float gx_top, gy_top; // nx - 1, ny - 1 as floats (clamp of the guess)
 };
 
 struct PotDev {
     int kind;             // 1 hernquist, 2 nfw, 3 log
     double c[6];          // hernquist: GM, a;  log: Rc2, iq2, v0sq, hv;  nfw: C=4 pi rho_s r_s^3, r_s, 1/r_s
+    float cf[6];          // the same rounded once to float (no per-particle conversions)
 };
 
 struct PassArgs {
@@ -45,6 +47,7 @@ struct PassArgs {
     SetDev sets[MAXSETS];
     PotDev pot[MAXPOT];
     double eps_dt, mu, ent_c, hdt, dt, sin_i, cos_i;
+    float f_eps_dt, f_mu, f_ent_c, f_hdt, f_dt, f_sin_i, f_cos_i, f_pk, f_pgma;
     const void *edge_tab; int edge_len;     // R
     const void *gh_tab;   int gh_len;       // R, 5 per GH cell: V, 1/S, c1, t2, norm
     const void *coef;                       // R[nobs]
@@ -60,6 +63,27 @@ struct PassArgs {
     unsigned *cell_cnt;                     // [ncells]
     int *err;
 };
+
+// Constants in the state precision: floats are rounded once on the host
+// (the FP64 pipe also executes the double->float conversion).
+__device__ __forceinline__ float kc(double, float f, float *) { return f; }
+__device__ __forceinline__ double kc(double d, float, double *) { return d; }
+#define KC(R, d, f) kc((d), (f), (R *)nullptr)
+
+// Sign/finiteness tests of a double with integer instructions.
+__device__ __forceinline__ bool d_pos(double d) {          // d > 0 (NaN false)
+    long long b = __double_as_longlong(d);
+    return b > 0 && b < 0x7ff0000000000001ll;
+}
+__device__ __forceinline__ bool d_bad(double d) {          // d < 0, NaN or +-inf
+    long long b = __double_as_longlong(d);
+    return b < 0 || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
+// round-to-nearest integer of a float in [-2^22, 2^22] without F2I
+__device__ __forceinline__ int rint_small(float x) {
+    return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
 
 // ------------------------------------------------------------ conversions
 // Positive doubles in [2^-126, 1) -> float by truncation with integer ops
@@ -147,7 +171,7 @@ template <class R> struct Acc3 { R x, y, z; };
 
 __device__ __forceinline__ float nfw_f(float r, const PotDev &p) {
     // M(r)/r^3, M = C [ln(1+u) - u/(1+u)], u = r/r_s
-    float u = r * (float)p.c[2];
+    float u = r * p.cf[2];
     float mu;
     if (u < 1e-2f) {
         mu = u * u * (0.5f - u * (0.6666667f - u * (0.75f - u * (0.8f - u * 0.8333333f))));
@@ -155,7 +179,7 @@ __device__ __forceinline__ float nfw_f(float r, const PotDev &p) {
         mu = log1pf(u) - u / (1.0f + u);
     }
     float r3 = r * r * r;
-    return r > 0.f ? (float)p.c[0] * mu / r3 : 0.f;
+    return r > 0.f ? p.cf[0] * mu / r3 : 0.f;
 }
 __device__ __forceinline__ double nfw_f(double r, const PotDev &p) {
     double u = r * p.c[2];
@@ -175,7 +199,7 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a) {
     for (int k = 0; k < a.npot; ++k) {
         const PotDev &p = a.pot[k];
         if (p.kind == 1) {            // Hernquist
-            R GM = (R)p.c[0], aa = (R)p.c[1];
+            R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
             R r2 = (x * x + y * y) + z * z;
             R r = sqrt(r2);
             R s = r + aa;
@@ -184,7 +208,7 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a) {
             g.y = g.y + (-(f * y));
             g.z = g.z + (-(f * z));
         } else if (p.kind == 3) {     // flattened logarithmic
-            R Rc2 = (R)p.c[0], iq2 = (R)p.c[1], v0sq = (R)p.c[2];
+            R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), v0sq = KC(R, p.c[2], p.cf[2]);
             R R2 = x * x + y * y;
             R D = (Rc2 + R2) + (z * z) * iq2;
             R f = v0sq / D;
@@ -211,11 +235,11 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a) {
     for (int k = 0; k < a.npot; ++k) {
         const PotDev &p = a.pot[k];
         if (p.kind == 1) {
-            R GM = (R)p.c[0], aa = (R)p.c[1];
+            R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
             R r2 = (x * x + y * y) + z * z;
             phi = phi + (-(GM / (sqrt(r2) + aa)));
         } else if (p.kind == 3) {
-            R Rc2 = (R)p.c[0], iq2 = (R)p.c[1], hv = (R)p.c[3];
+            R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), hv = KC(R, p.c[3], p.cf[3]);
             R R2 = x * x + y * y;
             R D = (Rc2 + R2) + (z * z) * iq2;
             phi = phi + hv * plog(D);
@@ -234,7 +258,7 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a) {
 
 template <class R>
 __device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a) {
-    R h = (R)a.hdt, d = (R)a.dt;
+    R h = KC(R, a.hdt, a.f_hdt), d = KC(R, a.dt, a.f_dt);
     Acc3<R> g = accel<R>(x, y, z, a);
     vx = vx + h * g.x;
     vy = vy + h * g.y;
@@ -336,6 +360,67 @@ __device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R 
         int iy = find_bin<R>(Ys, edges + s.ey_off, s.ny, s.gy_mode, s.gy_a, s.gy_b);
         if (iy < 0) return -1;
         return iy * s.nx + ix;
+    }
+}
+
+
+// Branch-free cell lookup for edge tables whose index guess (linear or
+// log2, fitted on the host) is within one cell of the true cell everywhere
+// in range: one correction step on each side, decided by the two edges of
+// the guessed cell.  Same membership as find_bin.
+template <class R>
+__device__ __forceinline__ int find_fast(R v, const R *e, int nb, int mode, float ga, float gb, float top) {
+    const R e0 = e[0], en = e[nb];
+    const bool in = (v >= e0) && (v < en);
+    const float fv = (float)v;
+    const float t = (mode == G_LOG) ? __log2f(fv) : fv;
+    // nearest integer to (guess - 1/2), clamped to the table: within one cell
+    // of the true cell, which the two edge tests below then pin down
+    const float gf = fminf(fmaxf(fmaf(ga, t, gb) - 0.5f, 0.0f), top);
+    int g = rint_small(gf);
+    const R lo = e[g], hi = e[g + 1];
+    g += (v >= hi ? 1 : 0) - (v < lo ? 1 : 0);
+    return in ? g : -1;
+}
+
+template <class R, int G>
+__device__ __forceinline__ int cell_t(const SetDev &s, const R *edges, R x, R y, R z, R X, R Ys) {
+    if constexpr (G == 1) {
+        R r2 = (x * x + y * y) + z * z;
+        return find_fast<R>(r2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
+    } else if constexpr (G == 2) {
+        R R2 = X * X + Ys * Ys;
+        return find_fast<R>(R2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
+    } else {
+        int ix = find_fast<R>(X, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
+        int iy = find_fast<R>(Ys, edges + s.ey_off, s.ny, s.gy_mode, s.gy_a, s.gy_b, s.gy_top);
+        return (ix < 0 || iy < 0) ? -1 : iy * s.nx + ix;
+    }
+}
+
+// Fixed-point add of a float term v: V = round(v * 2^sh) (half away from
+// zero) from the float's bits with integer instructions only.  When
+// |V| < 2^31 (the usual case) it is one 32-bit shared atomic on the low word
+// plus a rare carry/sign word; larger terms take the 64-bit path.
+__device__ __forceinline__ void fx_add(unsigned *lo, unsigned *hi, int b, float v, int sh, bool &ovf) {
+    const unsigned bits = __float_as_uint(v);
+    const int ex = (int)((bits >> 23) & 0xffu);
+    const int s = ex - 150 + sh;                 // v = m * 2^(ex-150)
+    if (ex == 0) return;                         // zero / subnormal: below resolution
+    if (s <= 7) {
+        const unsigned m = (bits & 0x7fffffu) | 0x800000u;
+        const int rs = max(min(-s, 31), 0);
+        unsigned mag = s >= 0 ? (m << s) : ((m + ((1u << rs) >> 1)) >> rs);
+        if (-s > 24) mag = 0u;
+        const int V = (bits >> 31) ? -(int)mag : (int)mag;
+        if (V == 0) return;
+        const unsigned vl = (unsigned)V;
+        const unsigned old = atomicAdd(lo + b, vl);
+        const unsigned inc = ((old + vl) < old ? 1u : 0u) + (V < 0 ? 0xffffffffu : 0u);
+        if (inc) atomicAdd(hi + b, inc);
+    } else {
+        long long q = f2fixed(v, sh, ovf);
+        if (q) fixed_add(lo, hi, b, q);
     }
 }
 

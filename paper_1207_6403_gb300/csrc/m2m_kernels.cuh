@@ -15,14 +15,11 @@
 // k_cells     cell export for tests.
 #pragma once
 #include <math.h>
+#include <type_traits>
 #include "m2m_device.cuh"
 #include "../../include/m2m.h"
 
 namespace m2m {
-
-template <class R> struct Vec;
-template <> struct Vec<float> { static constexpr int N = 4; using T = float4; };
-template <> struct Vec<double> { static constexpr int N = 2; using T = double2; };
 
 __device__ __forceinline__ float ceil_to(double e, float *) {
     float f = __double2float_rn(e);
@@ -124,11 +121,11 @@ __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const
     R Lx = y * vz - z * vy;
     R Ly = z * vx - x * vz;
     R L2 = (Lx * Lx + Ly * Ly) + Lz * Lz;
-    R ed = E * (R)a.pk;
+    R ed = E * KC(R, a.pk, a.f_pk);
     R sq = sqrt(R(1) - R(8) * ed);
     R s = (R(-1) - sq) / (R(4) * ed);
     R sm = s - R(1);
-    R Lc2 = (R)a.pgma * (((sm * sm) * sm) / (s * s));
+    R Lc2 = KC(R, a.pgma, a.f_pgma) * (((sm * sm) * sm) / (s * s));
     R X = L2 / Lc2;
     int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
     int iL = count_le<R>(X, pl, a.nL, gp[2], gp[3]);
@@ -147,56 +144,119 @@ struct PassSmem {
     double *c_d;                     // FP64 prior-cell sums
 };
 
+// Observable layouts compiled as straight-line code (set order, geometry,
+// quantity); layout 0 walks the set descriptors at run time.
+//   1: grid/mass + grid/GH            (pixels + IFU apertures)
+//   2: shell/mass + annulus/GH        (shells + kinematic annuli)
+//   3: shell/mass + annulus/mass + annulus/v_los^2
+template <int V> using IC = std::integral_constant<int, V>;
+template <int L, class F>
+__device__ __forceinline__ void for_each_set(F &&f) {
+    if constexpr (L == 1) {
+        f(IC<0>{}, IC<M2M_GEOM_GRID>{}, IC<M2M_Q_MASS>{});
+        f(IC<1>{}, IC<M2M_GEOM_GRID>{}, IC<M2M_Q_GH>{});
+    } else if constexpr (L == 2) {
+        f(IC<0>{}, IC<M2M_GEOM_SHELL>{}, IC<M2M_Q_MASS>{});
+        f(IC<1>{}, IC<M2M_GEOM_ANNULUS>{}, IC<M2M_Q_GH>{});
+    } else if constexpr (L == 3) {
+        f(IC<0>{}, IC<M2M_GEOM_SHELL>{}, IC<M2M_Q_MASS>{});
+        f(IC<1>{}, IC<M2M_GEOM_ANNULUS>{}, IC<M2M_Q_MASS>{});
+        f(IC<2>{}, IC<M2M_GEOM_ANNULUS>{}, IC<M2M_Q_VLOS2>{});
+    }
+}
+
 // dot = sum_j K_j coef_j over the particle's cells, in set and moment order
-template <class R>
+template <class R, int L>
 __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
                                      R X, R Ys, R vlos) {
     R dot = R(0);
-    for (int k = 0; k < a.nsets; ++k) {
-        const SetDev &s = a.sets[k];
-        int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
-        if (c < 0) continue;
-        int b = s.obs_off + c * s.nmom;
-        if (s.quant == M2M_Q_MASS) {
-            dot = dot + S.coef[b];
-        } else if (s.quant == M2M_Q_VLOS2) {
-            dot = dot + (vlos * vlos) * S.coef[b];
-        } else {
-            R u[5];
-            gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+    if constexpr (L == 0) {
+        for (int k = 0; k < a.nsets; ++k) {
+            const SetDev &s = a.sets[k];
+            int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+            if (c < 0) continue;
+            int b = s.obs_off + c * s.nmom;
+            if (s.quant == M2M_Q_MASS) {
+                dot = dot + S.coef[b];
+            } else if (s.quant == M2M_Q_VLOS2) {
+                dot = dot + (vlos * vlos) * S.coef[b];
+            } else {
+                R u[5];
+                gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
 #pragma unroll
-            for (int m = 0; m < 5; ++m) dot = dot + u[m] * S.coef[b + m];
+                for (int m = 0; m < 5; ++m) dot = dot + u[m] * S.coef[b + m];
+            }
         }
+    } else {
+        for_each_set<L>([&](auto K, auto G, auto Q) {
+            constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
+            const SetDev &s = a.sets[k];
+            const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
+            if (c >= 0) {
+                if constexpr (q == M2M_Q_MASS) {
+                    dot = dot + S.coef[s.obs_off + c];
+                } else if constexpr (q == M2M_Q_VLOS2) {
+                    dot = dot + (vlos * vlos) * S.coef[s.obs_off + c];
+                } else {
+                    R u[5];
+                    gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+                    const R *cf = S.coef + s.obs_off + 5 * c;
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) dot = dot + u[m] * cf[m];
+                }
+            }
+        });
     }
     return dot;
 }
 
-__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, int sh, bool &ovf) {
-    long long q = f2fixed(v, sh, ovf);
-    if (q) fixed_add(S.h_lo, S.h_hi, b, q);
+__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, float, int sh, bool &ovf) {
+    fx_add(S.h_lo, S.h_hi, b, v, sh, ovf);
 }
-__device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, int, bool &) {
+__device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, float, int, bool &) {
     atomicAdd(S.h_d + b, v);
 }
 
-template <class R>
+template <class R, int L>
 __device__ __forceinline__ void scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                        R X, R Ys, R vlos, R wv, bool &ovf) {
-    for (int k = 0; k < a.nsets; ++k) {
-        const SetDev &s = a.sets[k];
-        int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
-        if (c < 0) continue;
-        int b = s.obs_off + c * s.nmom;
-        if (s.quant == M2M_Q_MASS) {
-            hist_add(S, b, wv, a.fx_shift, ovf);
-        } else if (s.quant == M2M_Q_VLOS2) {
-            hist_add(S, b, wv * (vlos * vlos), a.fx_shift, ovf);
-        } else {
-            R u[5];
-            gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+                                        R X, R Ys, R vlos, R wv, float fs, bool &ovf) {
+    const int sh = a.fx_shift;
+    if constexpr (L == 0) {
+        for (int k = 0; k < a.nsets; ++k) {
+            const SetDev &s = a.sets[k];
+            int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+            if (c < 0) continue;
+            int b = s.obs_off + c * s.nmom;
+            if (s.quant == M2M_Q_MASS) {
+                hist_add(S, b, wv, fs, sh, ovf);
+            } else if (s.quant == M2M_Q_VLOS2) {
+                hist_add(S, b, wv * (vlos * vlos), fs, sh, ovf);
+            } else {
+                R u[5];
+                gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
 #pragma unroll
-            for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], a.fx_shift, ovf);
+                for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
+            }
         }
+    } else {
+        for_each_set<L>([&](auto K, auto G, auto Q) {
+            constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
+            const SetDev &s = a.sets[k];
+            const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
+            if (c >= 0) {
+                if constexpr (q == M2M_Q_MASS) {
+                    hist_add(S, s.obs_off + c, wv, fs, sh, ovf);
+                } else if constexpr (q == M2M_Q_VLOS2) {
+                    hist_add(S, s.obs_off + c, wv * (vlos * vlos), fs, sh, ovf);
+                } else {
+                    R u[5];
+                    gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+                    const int b = s.obs_off + 5 * c;
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
+                }
+            }
+        });
     }
 }
 
@@ -206,13 +266,26 @@ struct ThreadAcc {
     bool ovf, bad;
 };
 
+// expm1 for the small exponents of the weight update (|d| < 2^-7: Taylor
+// to d^5, relative error < 2^-40), the library routine otherwise.
+__device__ __forceinline__ float expm1_small(float d) {
+    if (fabsf(d) < 0.0078125f) {
+        float p = fmaf(d, 1.0f / 120.0f, 1.0f / 24.0f);
+        p = fmaf(d, p, 1.0f / 6.0f);
+        p = fmaf(d, p, 0.5f);
+        p = fmaf(d, p, 1.0f);
+        return d * p;
+    }
+    return expm1f(d);
+}
+
 // The weight update of one particle: returns the new weight; L1 = ln(w_new/w_hat)
 __device__ __forceinline__ double upd_weight(double w, double what, float dot, const PassArgs &a, float &wnf, float &L1) {
     float wf = d2f_fast(w), whf = d2f_fast(what);
     float L = logf(__fdividef(wf, whf));
-    float G = (float)a.mu * (-L - (float)a.ent_c) - dot;
-    float d = (float)a.eps_dt * G;
-    float e = expm1f(d);
+    float G = a.f_mu * (-L - a.f_ent_c) - dot;
+    float d = a.f_eps_dt * G;
+    float e = expm1_small(d);
     double wn = fma(w, f2d_fast(e), w);
     wnf = d2f_fast(wn);
     L1 = L + d;
@@ -229,7 +302,7 @@ __device__ __forceinline__ double upd_weight(double w, double what, double dot, 
 }
 
 __device__ __forceinline__ void acc_stats(ThreadAcc &t, float wnf, float L1) {
-    t.s_f += -wnf * L1;
+    t.s_f = fmaf(-wnf, L1, t.s_f);
     t.w_f += wnf;
 }
 __device__ __forceinline__ void acc_stats(ThreadAcc &t, double wnd, double L1) {
@@ -257,37 +330,36 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
     atomicAdd((unsigned *)(S.c_lo) + c, 1u);
 }
 
-template <class R>
+template <class R, int L>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, long long i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
-                                         ThreadAcc &t, R &emin, R &emax, R &lzm) {
+                                         ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
     const int fl = a.flags;
+    const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
     if (fl & (F_UPD | F_STATS)) {
-        if (w > 0.0) {
+        if (d_pos(w)) {
             R L1;
             R wr;
             if (fl & F_UPD) {
-                R s = (R)a.sin_i, c = (R)a.cos_i;
-                R X = x, Ys = z * s - y * c, vlos = vy * s + vz * c;
-                R dot = obs_dot<R>(a, S, x, y, z, X, Ys, vlos);
+                R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
+                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos);
                 wn = upd_weight(w, what, dot, a, wr, L1);
-                if (!(wn >= 0.0) || wn > 1e300) t.bad = true;
+                if (d_bad(wn)) t.bad = true;
             } else {
                 wr = to_r(w, (R *)nullptr);
                 L1 = rlog_ratio(w, what, (R *)nullptr);
             }
             if (fl & F_STATS) acc_stats(t, wr, L1);
-        } else if (!(w == 0.0)) {
-            t.bad = true;       // negative or NaN weight
+        } else if (__double_as_longlong(w) != 0ll) {
+            t.bad = true;       // negative, -0 or NaN weight
         }
     }
     if (fl & F_PUSH) kdk<R>(x, y, z, vx, vy, vz, a);
     if (fl & F_SCAT) {
-        R s = (R)a.sin_i, c = (R)a.cos_i;
-        R X = x, Ys = z * s - y * c, vlos = vy * s + vz * c;
+        R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         R wv = to_r(wn, (R *)nullptr);
-        if (wv != R(0)) scatter<R>(a, S, x, y, z, X, Ys, vlos, wv, t.ovf);
+        if (wv != R(0)) scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t.ovf);
     }
     if (fl & F_MINMAX) {
         R E, Lz;
@@ -304,10 +376,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     w = wn;
 }
 
-template <class R>
-__device__ __forceinline__ R ld(const void *p, long long i) { return ((const R *)p)[i]; }
-
-template <class R, int NT, int MINB>
+template <class R, int NT, int MINB, int L>
 __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -357,62 +426,34 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
 
     ThreadAcc t{0.0, 0.0, 0.f, 0.f, false, false};
     R emin = R(INFINITY), emax = R(-INFINITY), lzm = R(0);
-    constexpr int V = Vec<R>::N;
-    using VT = typename Vec<R>::T;
+    const float fs = a.fx_shift <= 127 ? __int_as_float((a.fx_shift + 127) << 23) : INFINITY;
     const long long n = a.n;
-    const long long nch = (n + V - 1) / V;
     R *px = (R *)a.x, *py = (R *)a.y, *pz = (R *)a.z, *pvx = (R *)a.vx, *pvy = (R *)a.vy, *pvz = (R *)a.vz;
     const bool wr_pos = (fl & F_PUSH) != 0;
     const bool wr_w = (fl & F_UPD) != 0;
-    for (long long ch = (long long)blockIdx.x * NT + threadIdx.x; ch < nch; ch += (long long)gridDim.x * NT) {
-        const long long i0 = ch * V;
-        if (i0 + V <= n) {
-            VT X4 = ((const VT *)px)[ch], Y4 = ((const VT *)py)[ch], Z4 = ((const VT *)pz)[ch];
-            VT U4 = ((const VT *)pvx)[ch], V4 = ((const VT *)pvy)[ch], W4 = ((const VT *)pvz)[ch];
-            double wv[V], wh[V];
-            if (V == 4) {
-                double2 w0 = ((const double2 *)a.w)[2 * ch], w1 = ((const double2 *)a.w)[2 * ch + 1];
-                double2 h0 = ((const double2 *)a.what)[2 * ch], h1 = ((const double2 *)a.what)[2 * ch + 1];
-                wv[0] = w0.x; wv[1] = w0.y; wv[V > 2 ? 2 : 0] = w1.x; wv[V > 3 ? 3 : 1] = w1.y;
-                wh[0] = h0.x; wh[1] = h0.y; wh[V > 2 ? 2 : 0] = h1.x; wh[V > 3 ? 3 : 1] = h1.y;
-            } else {
-                double2 w0 = ((const double2 *)a.w)[ch];
-                double2 h0 = ((const double2 *)a.what)[ch];
-                wv[0] = w0.x; wv[1] = w0.y; wh[0] = h0.x; wh[1] = h0.y;
-            }
-            R *xs = (R *)&X4, *ys = (R *)&Y4, *zs = (R *)&Z4, *us = (R *)&U4, *vs = (R *)&V4, *ws = (R *)&W4;
-#pragma unroll
-            for (int k = 0; k < V; ++k)
-                particle<R>(a, S, i0 + k, xs[k], ys[k], zs[k], us[k], vs[k], ws[k], wv[k], wh[k], t, emin, emax, lzm);
-            if (wr_pos) {
-                ((VT *)px)[ch] = X4; ((VT *)py)[ch] = Y4; ((VT *)pz)[ch] = Z4;
-                ((VT *)pvx)[ch] = U4; ((VT *)pvy)[ch] = V4; ((VT *)pvz)[ch] = W4;
-            }
-            if (wr_w) {
-                if (V == 4) {
-                    ((double2 *)a.w)[2 * ch] = make_double2(wv[0], wv[1]);
-                    ((double2 *)a.w)[2 * ch + 1] = make_double2(wv[V > 2 ? 2 : 0], wv[V > 3 ? 3 : 1]);
-                } else {
-                    ((double2 *)a.w)[ch] = make_double2(wv[0], wv[1]);
-                }
-            }
-        } else {
-            for (long long i = i0; i < n; ++i) {
-                R x = px[i], y = py[i], z = pz[i], vx = pvx[i], vy = pvy[i], vz = pvz[i];
-                double w = a.w[i];
-                particle<R>(a, S, i, x, y, z, vx, vy, vz, w, a.what[i], t, emin, emax, lzm);
-                if (wr_pos) { px[i] = x; py[i] = y; pz[i] = z; pvx[i] = vx; pvy[i] = vy; pvz[i] = vz; }
-                if (wr_w) a.w[i] = w;
-            }
+    const long long stride = (long long)gridDim.x * NT;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
+        R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
+        R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
+        double w = __ldcs(a.w + i);
+        const double wh = __ldcs(a.what + i);
+        particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, t, emin, emax, lzm, fs);
+        if (wr_pos) {
+            __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
+            __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
         }
+        if (wr_w) __stcs(a.w + i, w);
     }
     __syncthreads();
     // epilogue: flush the block-private histograms and partial sums
     if (fl & F_SCAT) {
         if (FX) {
             long long *sl = (long long *)a.slots + (long long)blockIdx.x * nobs;
-            for (int k = threadIdx.x; k < nobs; k += NT)
-                sl[k] = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
+            for (int k = threadIdx.x; k < nobs; k += NT) {
+                long long v = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
+                if (v >= (1ll << 53) || v <= -(1ll << 53)) t.ovf = true;
+                sl[k] = v;
+            }
         } else {
             double *sl = (double *)a.slots + (long long)blockIdx.x * nobs;
             for (int k = threadIdx.x; k < nobs; k += NT) sl[k] = S.h_d[k];
@@ -460,20 +501,19 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
         if (lane == 0) { mm[0][wp] = emin; mm[1][wp] = emax; mm[2][wp] = lzm; }
         __syncthreads();
         if (threadIdx.x == 0) {
+            R e0 = mm[0][0], e1 = mm[1][0], l2 = mm[2][0];
             for (int k = 1; k < NT / 32; ++k) {
-                emin = fmin(emin, mm[0][k]); emax = fmax(emax, mm[1][k]); lzm = fmax(lzm, mm[2][k]);
+                e0 = fmin(e0, mm[0][k]); e1 = fmax(e1, mm[1][k]); l2 = fmax(l2, mm[2][k]);
             }
             R *o = (R *)a.mm_slots + 4 * blockIdx.x;
-            o[0] = mm[0][0] < emin ? mm[0][0] : emin;
-            o[1] = mm[1][0] > emax ? mm[1][0] : emax;
-            o[2] = mm[2][0] > lzm ? mm[2][0] : lzm;
-            o[3] = R(0);
+            o[0] = e0; o[1] = e1; o[2] = l2; o[3] = R(0);
         }
     }
     if (t.ovf) atomicOr(a.err, ERR_OVERFLOW);
     if (t.bad) atomicOr(a.err, ERR_NONFINITE);
 }
 
+#ifdef M2M_COMMON_KERNELS
 // ------------------------------------------------------------- k_residual
 struct ResArgs {
     const void *slots; int nblk; int nobs; int fixed; double q;
@@ -494,28 +534,41 @@ __device__ __forceinline__ double block_sum_strided(const double *v, int stride,
     return block_sum(s, red);
 }
 
-__global__ void __launch_bounds__(256) k_residual(const __grid_constant__ ResArgs a) {
-    __shared__ unsigned long long si[8][32];
-    __shared__ double sd[8][32];
+// 32 observables per block (lane = observable); the 32 warps split the
+// per-block slots, each with four independent accumulators.  Integer slots
+// sum exactly; double slots in a fixed order.
+constexpr int RES_NT = 1024;
+__global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ ResArgs a) {
+    constexpr int NW = RES_NT / 32;
+    __shared__ unsigned long long si[NW][32];
+    __shared__ double sd[NW][32];
     __shared__ double red[32];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + lane;
     if (j < a.nobs) {
         if (a.fixed) {
-            unsigned long long acc = 0; double ap = 0.0;
-            const long long *sl = (const long long *)a.slots;
-            for (int b = wp; b < a.nblk; b += 8) {
-                long long v = sl[(long long)b * a.nobs + j];
-                acc += (unsigned long long)v;
-                ap += (double)v;
+            // each block slot is below 2^53 in magnitude (checked at the
+            // flush), so the sum of at most 1024 of them cannot wrap
+            const long long *sl = (const long long *)a.slots + j;
+            unsigned long long acc[4] = {0, 0, 0, 0};
+            int b = wp;
+            for (; b + 3 * NW < a.nblk; b += 4 * NW) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] += (unsigned long long)sl[(long long)(b + u * NW) * a.nobs];
             }
-            si[wp][lane] = acc; sd[wp][lane] = ap;
+            for (; b < a.nblk; b += NW) acc[0] += (unsigned long long)sl[(long long)b * a.nobs];
+            si[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         } else {
-            double acc = 0.0;
-            const double *sl = (const double *)a.slots;
-            for (int b = wp; b < a.nblk; b += 8) acc += sl[(long long)b * a.nobs + j];
-            sd[wp][lane] = acc;
+            const double *sl = (const double *)a.slots + j;
+            double acc[4] = {0, 0, 0, 0};
+            int b = wp;
+            for (; b + 3 * NW < a.nblk; b += 4 * NW) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] += sl[(long long)(b + u * NW) * a.nobs];
+            }
+            for (; b < a.nblk; b += NW) acc[0] += sl[(long long)b * a.nobs];
+            sd[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
     }
     __syncthreads();
@@ -524,14 +577,12 @@ __global__ void __launch_bounds__(256) k_residual(const __grid_constant__ ResArg
         if (j < a.nobs) {
             double yv;
             if (a.fixed) {
-                unsigned long long tot = 0; double ap = 0.0;
-                for (int k = 0; k < 8; ++k) { tot += si[k][lane]; ap += sd[k][lane]; }
-                double exact = (double)(long long)tot;
-                if (fabs(exact - ap) > 1e-6 * fabs(ap) + 1.0) atomicOr(a.err, ERR_OVERFLOW);
-                yv = exact * a.q;
+                unsigned long long tot = 0;
+                for (int k = 0; k < NW; ++k) tot += si[k][lane];
+                yv = (double)(long long)tot * a.q;
             } else {
                 yv = 0.0;
-                for (int k = 0; k < 8; ++k) yv += sd[k][lane];
+                for (int k = 0; k < NW; ++k) yv += sd[k][lane];
             }
             double s = a.sigma[j];
             bool valid = s > 0.0;
@@ -567,9 +618,15 @@ __global__ void __launch_bounds__(256) k_residual(const __grid_constant__ ResArg
     double c2r = block_sum_strided(a.chi_slots, 3, 1, gridDim.x, red);
     double S = block_sum_strided(a.stat_slots, 2, 0, a.stat_nblk, red);
     double W = block_sum_strided(a.stat_slots, 2, 1, a.stat_nblk, red);
+    double mx = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, a.chi_slots[3 * b + 2]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if (lane == 0) red[wp] = mx;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double mx = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) mx = fmax(mx, a.chi_slots[3 * b + 2]);
+        for (int k = 1; k < NW; ++k) mx = fmax(mx, red[k]);
         m2m_record r;
         r.step = a.rec_step;
         r.chi2 = c2; r.chi2_raw = c2r; r.S = S; r.sum_w = W;
@@ -597,6 +654,8 @@ __global__ void k_prior_gather(const int *cell, const double *mean, double *what
         what[i] = mean[cell[i]];
 }
 
+#endif  // M2M_COMMON_KERNELS
+
 // ------------------------------------------------------------- k_cells
 template <class R>
 __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int *prior_cells) {
@@ -609,7 +668,7 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
     for (int k = threadIdx.x; k < a.edge_len; k += blockDim.x) edges[k] = ((const R *)a.edge_tab)[k];
     if (prior_cells) prior_setup<R>(a, pe, pl, gp);
     __syncthreads();
-    R s = (R)a.sin_i, c = (R)a.cos_i;
+    R s = KC(R, a.sin_i, a.f_sin_i), c = KC(R, a.cos_i, a.f_cos_i);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
         R x = ((const R *)a.x)[i], y = ((const R *)a.y)[i], z = ((const R *)a.z)[i];
         R vx = ((const R *)a.vx)[i], vy = ((const R *)a.vy)[i], vz = ((const R *)a.vz)[i];
@@ -618,5 +677,11 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
         if (prior_cells) prior_cells[i] = prior_cell<R>(x, y, z, vx, vy, vz, a, pe, pl, gp);
     }
 }
+
+// Kernel tables, one per precision, each in its own translation unit.
+void *pass_kernel_f32(int threads, int layout);
+void *pass_kernel_f64(int threads, int layout);
+void *cells_kernel_f32();
+void *cells_kernel_f64();
 
 }  // namespace m2m

@@ -1,0 +1,27 @@
+// FP32-compensated instantiations of the particle pass (one translation
+// unit per precision so the library builds in parallel).
+#include "m2m_kernels.cuh"
+
+namespace m2m {
+
+template <int NT, int MINB>
+static void *pick_layout_f32(int layout) {
+    switch (layout) {
+        case 1: return (void *)k_pass<float, NT, MINB, 1>;
+        case 2: return (void *)k_pass<float, NT, MINB, 2>;
+        case 3: return (void *)k_pass<float, NT, MINB, 3>;
+        default: return (void *)k_pass<float, NT, MINB, 0>;
+    }
+}
+
+void *pass_kernel_f32(int threads, int layout) {
+    switch (threads) {
+        case 256: return pick_layout_f32<256, 2>(layout);
+        case 1024: return pick_layout_f32<1024, 1>(layout);
+        default: return pick_layout_f32<512, 2>(layout);
+    }
+}
+
+void *cells_kernel_f32() { return (void *)k_cells<float>; }
+
+}  // namespace m2m

@@ -46,6 +46,14 @@ class m2m_params(ctypes.Structure):
                 ("entropy_const", c_double), ("incl_sin", c_double), ("incl_cos", c_double)]
 
 
+TK_N = 6
+TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other")
+
+
+class m2m_timing(ctypes.Structure):
+    _fields_ = [("launches", c_int64 * TK_N), ("ms", c_double * TK_N), ("kernels_total", c_int64)]
+
+
 class m2m_record(ctypes.Structure):
     _fields_ = [("step", c_int64), ("chi2", c_double), ("chi2_raw", c_double), ("S", c_double),
                 ("sum_w", c_double), ("F", c_double), ("max_abs_dt", c_double)]
@@ -86,6 +94,9 @@ def library():
         "m2m_nobs": (c_int64, [P]),
         "m2m_steps_taken": (c_int64, [P]),
         "m2m_set_launch": (c_int32, [P, c_int32, c_int32]),
+        "m2m_set_layout": (c_int32, [P, c_int32]),
+        "m2m_set_timing": (c_int32, [P, c_int32]),
+        "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_last_error": (ctypes.c_char_p, [P]),
         "m2m_free": (c_int32, [P]),
     }
@@ -185,6 +196,19 @@ class Context:
 
     def m2m_set_launch(self, threads, blocks_per_sm=0):
         _check(library().m2m_set_launch(self.ptr, threads, blocks_per_sm), self.ptr)
+
+    def m2m_set_layout(self, layout=-1):
+        _check(library().m2m_set_layout(self.ptr, layout), self.ptr)
+
+    def m2m_set_timing(self, enable):
+        _check(library().m2m_set_timing(self.ptr, 1 if enable else 0), self.ptr)
+
+    def m2m_get_timing(self):
+        t = m2m_timing()
+        _check(library().m2m_get_timing(self.ptr, byref(t)), self.ptr)
+        return {"launches": {k: t.launches[i] for i, k in enumerate(TIMING_KINDS)},
+                "ms": {k: t.ms[i] for i, k in enumerate(TIMING_KINDS)},
+                "kernels_total": t.kernels_total}
 
     def m2m_free(self):
         if self.ptr:

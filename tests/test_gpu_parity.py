@@ -169,11 +169,16 @@ def test_prior_cells_log_potential_match_except_at_edges(prec):
 
 
 # --------------------------------------------------------- observe, update
+@pytest.mark.parametrize("layout", [-1, 0])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 1e-5)])
 @pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log"])
-def test_observe_residual_and_update_match(prec, tol, name):
+def test_observe_residual_and_update_match(prec, tol, name, layout):
+    """layout -1: the kernels compiled for the workload's observable sets;
+    0: the run-time walk over the set descriptors."""
     P = problem(name, 20011, prec)
     ctx = B.from_problem(P, prec)
+    ctx.m2m_set_layout(layout)
+    ctx.m2m_observe(2)
     st = O.init(P, prec)
     y, D, Dt = ctx.m2m_get_obs()
     assert_obs_close(y, st.y_obs, P.sigma, tol)
@@ -304,3 +309,33 @@ def test_full_size_flat_log_one_step_sampled():
     assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
     r = ctx.m2m_get_record()
     assert r["sum_w"] == pytest.approx(st.history[-1]["sum_w"], rel=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_compiled_and_generic_layouts_agree_over_a_run(prec):
+    """Both code paths for the same sets give the same trajectory, weights
+    and observables (the fixed-point histogram makes FP32C sums exact)."""
+    P = problem("moving-priors", 20000, prec)
+    out = []
+    for layout in (-1, 0):
+        ctx = B.from_problem(P, prec)
+        ctx.m2m_set_layout(layout)
+        ctx.m2m_step(60)
+        g = ctx.state()
+        y, _, _ = ctx.m2m_get_obs()
+        out.append((g, y))
+    (g1, y1), (g0, y0) = out
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g1[k], g0[k])
+    np.testing.assert_allclose(g1["w"], g0["w"], rtol=1e-13 if prec == "fp64" else 1e-7)
+    np.testing.assert_allclose(y1, y0, rtol=1e-12, atol=1e-18)
+
+
+def test_layout_override_is_checked():
+    P = problem("plain-fp64", 2000, "fp64")
+    ctx = B.from_problem(P, "fp64")
+    with pytest.raises(B.M2MError):
+        ctx.m2m_set_layout(1)        # pixels + apertures: not this workload's sets
+    ctx.m2m_set_layout(3)
+    ctx.m2m_set_layout(0)
+    ctx.m2m_set_layout(-1)
