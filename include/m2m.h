@@ -35,6 +35,10 @@
  *    allocated in m2m_init and freed by m2m_free.
  *  - Errors found by kernels (non-finite weights, fixed-point overflow) are
  *    sticky and reported by the next m2m_get_* call.
+ *  - Every scatter records each particle's cells (library-owned, 4 bytes per
+ *    particle) so that the next weight update need not look them up again.
+ *    A caller that changes x..vz itself (not through m2m_step/m2m_push)
+ *    must call m2m_observe before the next m2m_update_weights.
  */
 #ifndef M2M_H
 #define M2M_H

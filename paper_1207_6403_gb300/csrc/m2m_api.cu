@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/m2m.h"
+#include "m2m.h"
 #define M2M_COMMON_KERNELS
 #include "m2m_kernels.cuh"
 
@@ -72,6 +72,9 @@ struct m2m_ctx {
     bool pending;
     int last_grid;       // grid of the last scatter pass (slots to reduce)
     int layout;          // compiled observable layout of the pass kernel
+    int cache_bits;      // bits of the packed per-particle cell cache
+    unsigned *d_cell_cache;
+    bool cache_valid;    // cell cache holds the cells of the current positions
     // timing of the library's launches
     bool timing;
     long long kernels_total;
@@ -173,6 +176,7 @@ size_t pass_smem(const m2m_ctx *c, int flags) {
     if (flags & F_UPD) b += rs * (size_t)((c->nobs + 3) & ~3);
     b += rs * (size_t)((c->edge_len + 3) & ~3);
     b += rs * (size_t)((c->gh_len + 3) & ~3);
+    if (flags & F_UPD) b += rs * (size_t)((c->gh_len + 3) & ~3);
     if (flags & F_CELLS) {
         b += rs * (size_t)((c->prior.nE + 4) & ~3) + rs * (size_t)((c->prior.nL + 4) & ~3) + 16;
         if (c->prec == M2M_FP32C) b += 12 * (size_t)((c->ncells + 3) & ~3);
@@ -184,10 +188,13 @@ size_t pass_smem(const m2m_ctx *c, int flags) {
 // Compile-time observable layout matching the context's sets (see
 // for_each_set); 0 = generic.  Layouts need index guesses good to one cell.
 int detect_layout(const m2m_ctx *c) {
+    // radial sets need log-uniform edges, grids value-uniform edges
     for (int k = 0; k < c->nsets; ++k) {
         const SetDev &s = c->sets[k];
-        if (s.gx_mode == G_BIS || (s.geom == M2M_GEOM_GRID && s.gy_mode == G_BIS)) return 0;
+        if (s.geom == M2M_GEOM_GRID && (s.gx_mode != G_LIN || s.gy_mode != G_LIN)) return 0;
+        if (s.geom != M2M_GEOM_GRID && s.gx_mode != G_LOG) return 0;
     }
+    if (c->cache_bits > 32) return 0;
     auto is = [&](int k, int g, int q) { return c->sets[k].geom == g && c->sets[k].quant == q; };
     if (c->nsets == 2 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) && is(1, M2M_GEOM_GRID, M2M_Q_GH)) return 1;
     if (c->nsets == 2 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_GH)) return 2;
@@ -226,6 +233,9 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
     a.f_pk = (float)a.pk; a.f_pgma = (float)a.pgma;
     a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
+    a.cell_cache = c->d_cell_cache;
+    a.cache_read = (flags & F_UPD) && c->cache_valid && c->layout != 0;
+    a.cache_write = (flags & F_SCAT) && c->layout != 0;
     a.cell_ids = c->d_cell_ids; a.cell_acc = c->d_cell_acc; a.cell_cnt = c->d_cell_cnt;
     a.err = c->d_err;
 }
@@ -253,6 +263,8 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     }
     if (flags & F_SCAT) ctx->last_grid = (int)grid;
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
+    if (flags & F_SCAT) ctx->cache_valid = ctx->layout != 0;
+    else if (flags & F_PUSH) ctx->cache_valid = false;
     if (grid_out) *grid_out = (int)grid;
     return M2M_OK;
 }
@@ -330,7 +342,7 @@ void free_all(m2m_ctx *c) {
     void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
-                    c->d_cell_mean};
+                    c->d_cell_mean, c->d_cell_cache};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -465,6 +477,17 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     }
     ctx->nsets = nsets;
     ctx->nobs = nobs;
+    {
+        int bits = 0;
+        for (int k = 0; k < nsets; ++k) {
+            int cells = ctx->sets[k].nx * ctx->sets[k].ny, b = 1;
+            while ((1 << b) < cells + 1) ++b;
+            ctx->sets[k].cshift = bits < 32 ? bits : 0;
+            ctx->sets[k].cmask = (1 << b) - 1;
+            bits += b;
+        }
+        ctx->cache_bits = bits;
+    }
     ctx->layout = detect_layout(ctx);
     ctx->edge_len = (int)edges_d.size();
     ctx->gh_len = (int)gh_d.size();
@@ -518,6 +541,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_last, sizeof(m2m_record));
     ALLOC(ctx->d_err, 4);
     ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
+    ALLOC(ctx->d_cell_cache, 4 * (size_t)n);
     if (ctx->ncells) {
         ALLOC(ctx->d_cell_ids, 4 * (size_t)n);
         ALLOC(ctx->d_cell_acc, 8 * (size_t)ctx->ncells);
@@ -746,9 +770,10 @@ int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm) {
 
 int m2m_set_layout(m2m_ctx *ctx, int32_t layout) {
     if (!ctx) return M2M_ERR_ARG;
-    if (layout < 0) { ctx->layout = detect_layout(ctx); return M2M_OK; }
+    if (layout < 0) layout = detect_layout(ctx);
     if (layout != 0 && layout != detect_layout(ctx))
         return set_err(ctx, M2M_ERR_ARG, "layout %d does not match the observable sets", layout);
+    if (layout != ctx->layout) ctx->cache_valid = false;
     ctx->layout = layout;
     return M2M_OK;
 }

@@ -30,6 +30,7 @@ struct SetDev {
     int gx_mode, gy_mode; // index guess for the x / y edges
     float gx_a, gx_b, gy_a, gy_b;
     float gx_top, gy_top; // nx - 1, ny - 1 as floats (clamp of the guess)
+    int cshift, cmask;    // packed cell cache: ((cell + 1) & cmask) << cshift
 };
 
 struct PotDev {
@@ -58,6 +59,8 @@ struct PassArgs {
     int prior_kind, nE, nL, ncells;
     double pk, pgma;                        // e_lc: a/GM, GM*a
     void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
+    unsigned *cell_cache;                   // [n] packed cells of the last scatter
+    int cache_read, cache_write;
     int *cell_ids;                          // [n]
     void *cell_acc;                         // [ncells] int64 fixed point or double (global atomics)
     unsigned *cell_cnt;                     // [ncells]
@@ -86,27 +89,26 @@ __device__ __forceinline__ int rint_small(float x) {
 }
 
 // ------------------------------------------------------------ conversions
-// Positive doubles in [2^-126, 1) -> float by truncation with integer ops
-// (the FP64 pipe of this part is ~1.75 ops/clk/SM); anything else goes
-// through the hardware conversion.
+// Non-negative double -> float by truncation with integer instructions
+// only (no FP64-pipe fallback): below the float range -> 0, above -> inf.
 __device__ __forceinline__ float d2f_fast(double d) {
-    unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    unsigned e = hi >> 20;                        // sign bit lands at bit 11
-    if (e - 897u <= 125u)
-        return __uint_as_float(__funnelshift_l(lo, hi, 3) - (384u << 23));
-    return __double2float_rn(d);
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int e = (int)(hi >> 20) - 896;                     // float biased exponent
+    unsigned r = ((unsigned)e << 23) | (__funnelshift_l(lo, hi, 3) & 0x7fffffu);
+    r = e <= 0 ? 0u : r;
+    r = e >= 255 ? 0x7f800000u : r;
+    return __uint_as_float(r);
 }
 
-// Normal float -> double with integer ops; zero and subnormals via hardware.
+// Float -> double with integer instructions; zero and subnormals -> 0.
 __device__ __forceinline__ double f2d_fast(float f) {
-    unsigned b = __float_as_uint(f);
-    unsigned ex = (b >> 23) & 0xffu;
-    if (ex - 1u <= 253u) {
-        unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-        unsigned lo = b << 29;
-        return __hiloint2double((int)hi, (int)lo);
-    }
-    return (double)f;
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    unsigned lo = b << 29;
+    hi = ex == 0u ? (b & 0x80000000u) : hi;
+    lo = ex == 0u ? 0u : lo;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // round(f * 2^sh) as a 64-bit integer from the float's bits (round half away
@@ -345,6 +347,9 @@ __device__ __forceinline__ void gh_eval(double vlos, const double *g, double u[5
     u[4] = gs * ((4.0 * E4 - 12.0 * E2 + 3.0) / SQ24);
 }
 
+__device__ __forceinline__ float gh_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double gh_exp(double x) { return exp(x); }
+
 // Cell of particle in set s (-1 = none).  X = x, Ys = z*sin - y*cos.
 template <class R>
 __device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R y, R z, R X, R Ys) {
@@ -368,55 +373,55 @@ __device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R 
 // log2, fitted on the host) is within one cell of the true cell everywhere
 // in range: one correction step on each side, decided by the two edges of
 // the guessed cell.  Same membership as find_bin.
-template <class R>
-__device__ __forceinline__ int find_fast(R v, const R *e, int nb, int mode, float ga, float gb, float top) {
-    const R e0 = e[0], en = e[nb];
-    const bool in = (v >= e0) && (v < en);
+template <class R, int MODE>
+__device__ __forceinline__ int find_fast(R v, const R *e, int nb, float ga, float gb, float top) {
     const float fv = (float)v;
-    const float t = (mode == G_LOG) ? __log2f(fv) : fv;
+    const float t = MODE == G_LOG ? __log2f(fv) : fv;
     // nearest integer to (guess - 1/2), clamped to the table: within one cell
-    // of the true cell, which the two edge tests below then pin down
+    // of the true cell for any v in range, which the two edge tests pin down;
+    // a v outside the table (or NaN) ends outside [0, nb)
     const float gf = fminf(fmaxf(fmaf(ga, t, gb) - 0.5f, 0.0f), top);
     int g = rint_small(gf);
     const R lo = e[g], hi = e[g + 1];
     g += (v >= hi ? 1 : 0) - (v < lo ? 1 : 0);
-    return in ? g : -1;
+    return ((unsigned)g < (unsigned)nb && v == v) ? g : -1;
 }
 
+// Cell of a particle in a set of compile-time geometry G whose edge tables
+// are uniform in value (G_LIN: grids) or in log (G_LOG: shells, annuli).
 template <class R, int G>
 __device__ __forceinline__ int cell_t(const SetDev &s, const R *edges, R x, R y, R z, R X, R Ys) {
     if constexpr (G == 1) {
         R r2 = (x * x + y * y) + z * z;
-        return find_fast<R>(r2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
+        return find_fast<R, G_LOG>(r2, edges + s.ex_off, s.nx, s.gx_a, s.gx_b, s.gx_top);
     } else if constexpr (G == 2) {
         R R2 = X * X + Ys * Ys;
-        return find_fast<R>(R2, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
+        return find_fast<R, G_LOG>(R2, edges + s.ex_off, s.nx, s.gx_a, s.gx_b, s.gx_top);
     } else {
-        int ix = find_fast<R>(X, edges + s.ex_off, s.nx, s.gx_mode, s.gx_a, s.gx_b, s.gx_top);
-        int iy = find_fast<R>(Ys, edges + s.ey_off, s.ny, s.gy_mode, s.gy_a, s.gy_b, s.gy_top);
+        int ix = find_fast<R, G_LIN>(X, edges + s.ex_off, s.nx, s.gx_a, s.gx_b, s.gx_top);
+        int iy = find_fast<R, G_LIN>(Ys, edges + s.ey_off, s.ny, s.gy_a, s.gy_b, s.gy_top);
         return (ix < 0 || iy < 0) ? -1 : iy * s.nx + ix;
     }
 }
 
-// Fixed-point add of a float term v: V = round(v * 2^sh) (half away from
-// zero) from the float's bits with integer instructions only.  When
-// |V| < 2^31 (the usual case) it is one 32-bit shared atomic on the low word
-// plus a rare carry/sign word; larger terms take the 64-bit path.
-__device__ __forceinline__ void fx_add(unsigned *lo, unsigned *hi, int b, float v, int sh, bool &ovf) {
-    const unsigned bits = __float_as_uint(v);
-    const int ex = (int)((bits >> 23) & 0xffu);
-    const int s = ex - 150 + sh;                 // v = m * 2^(ex-150)
-    if (ex == 0) return;                         // zero / subnormal: below resolution
-    if (s <= 7) {
-        const unsigned m = (bits & 0x7fffffu) | 0x800000u;
-        const int rs = max(min(-s, 31), 0);
-        unsigned mag = s >= 0 ? (m << s) : ((m + ((1u << rs) >> 1)) >> rs);
-        if (-s > 24) mag = 0u;
-        const int V = (bits >> 31) ? -(int)mag : (int)mag;
-        if (V == 0) return;
-        const unsigned vl = (unsigned)V;
+// Fixed-point add of a float term v: V = round(v * 2^sh) as a 64-bit
+// two's-complement integer accumulated exactly in a shared (lo, hi) pair of
+// u32 words.  For |v * 2^sh| < 2^38 the rounding is done with two exact
+// float steps (1.5*2^23 "magic" rounding of S/2^16, then of the exact
+// remainder S - h*2^16), larger terms take the bit-level path.
+// fscale = 2^sh as a float (an exact power of two).
+__device__ __forceinline__ void fx_add(unsigned *lo, unsigned *hi, int b, float v, float fscale, int sh, bool &ovf) {
+    const float S = v * fscale;
+    if (fabsf(S) < 274877906944.0f) {                       // 2^38
+        const float M = 12582912.0f;                         // 1.5 * 2^23
+        const float t = fmaf(S, 1.52587890625e-05f, M);      // round(S / 2^16) + M
+        const int h = __float_as_int(t) - 0x4B400000;
+        const float r = fmaf(-(t - M), 65536.0f, S);         // S - h * 2^16, exact
+        const int l = __float_as_int(r + M) - 0x4B400000;    // round(r)
+        const long long V = ((long long)h << 16) + l;
+        const unsigned vl = (unsigned)V, vh = (unsigned)((unsigned long long)V >> 32);
         const unsigned old = atomicAdd(lo + b, vl);
-        const unsigned inc = ((old + vl) < old ? 1u : 0u) + (V < 0 ? 0xffffffffu : 0u);
+        const unsigned inc = vh + ((old + vl) < old ? 1u : 0u);
         if (inc) atomicAdd(hi + b, inc);
     } else {
         long long q = f2fixed(v, sh, ovf);

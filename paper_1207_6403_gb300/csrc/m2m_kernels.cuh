@@ -17,7 +17,7 @@
 #include <math.h>
 #include <type_traits>
 #include "m2m_device.cuh"
-#include "../../include/m2m.h"
+#include "m2m.h"
 
 namespace m2m {
 
@@ -138,6 +138,7 @@ struct PassSmem {
     unsigned *h_lo, *h_hi;   // FP32C histogram (exact fixed point)
     double *h_d;             // FP64 histogram
     const R *coef, *edges, *gh;
+    const R *gpoly;          // per GH cell: norm * sum_n coef_n E[H_n] as a quartic in m
     R *pe, *pl;
     float *gp;
     unsigned *c_lo, *c_hi, *c_cnt;   // FP32C prior-cell sums / counts
@@ -168,7 +169,7 @@ __device__ __forceinline__ void for_each_set(F &&f) {
 // dot = sum_j K_j coef_j over the particle's cells, in set and moment order
 template <class R, int L>
 __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                     R X, R Ys, R vlos) {
+                                     R X, R Ys, R vlos, bool cached, unsigned cc) {
     R dot = R(0);
     if constexpr (L == 0) {
         for (int k = 0; k < a.nsets; ++k) {
@@ -191,18 +192,26 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
-            const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
+            const int c = cached ? (int)((cc >> s.cshift) & (unsigned)s.cmask) - 1
+                                 : cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
             if (c >= 0) {
                 if constexpr (q == M2M_Q_MASS) {
                     dot = dot + S.coef[s.obs_off + c];
                 } else if constexpr (q == M2M_Q_VLOS2) {
                     dot = dot + (vlos * vlos) * S.coef[s.obs_off + c];
                 } else {
-                    R u[5];
-                    gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
-                    const R *cf = S.coef + s.obs_off + 5 * c;
-#pragma unroll
-                    for (int m = 0; m < 5; ++m) dot = dot + u[m] * cf[m];
+                    // sum_n coef_n u_n(nu) = exp(-nu m / 2) * P(m), m = nu c1,
+                    // with the quartic P of this cell built in the prologue
+                    const R *g = S.gh + s.gh_off + 5 * c;
+                    const R *P = S.gpoly + s.gh_off + 5 * c;
+                    const R nu = (vlos - g[0]) * g[1];
+                    const R m = nu * g[2];
+                    const R e = gh_exp(R(-0.5) * nu * m);
+                    R q = fma(P[4], m, P[3]);
+                    q = fma(q, m, P[2]);
+                    q = fma(q, m, P[1]);
+                    q = fma(q, m, P[0]);
+                    dot = dot + e * q;
                 }
             }
         });
@@ -210,17 +219,18 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
     return dot;
 }
 
-__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, float, int sh, bool &ovf) {
-    fx_add(S.h_lo, S.h_hi, b, v, sh, ovf);
+__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, float fs, int sh, bool &ovf) {
+    fx_add(S.h_lo, S.h_hi, b, v, fs, sh, ovf);
 }
 __device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, float, int, bool &) {
     atomicAdd(S.h_d + b, v);
 }
 
 template <class R, int L>
-__device__ __forceinline__ void scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                        R X, R Ys, R vlos, R wv, float fs, bool &ovf) {
+__device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
+                                            R X, R Ys, R vlos, R wv, float fs, bool &ovf) {
     const int sh = a.fx_shift;
+    unsigned packed = 0u;
     if constexpr (L == 0) {
         for (int k = 0; k < a.nsets; ++k) {
             const SetDev &s = a.sets[k];
@@ -243,7 +253,8 @@ __device__ __forceinline__ void scatter(const PassArgs &a, const PassSmem<R> &S,
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
             const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
-            if (c >= 0) {
+            packed |= (unsigned)(c + 1) << s.cshift;
+            if (c >= 0 && wv != R(0)) {
                 if constexpr (q == M2M_Q_MASS) {
                     hist_add(S, s.obs_off + c, wv, fs, sh, ovf);
                 } else if constexpr (q == M2M_Q_VLOS2) {
@@ -258,6 +269,7 @@ __device__ __forceinline__ void scatter(const PassArgs &a, const PassSmem<R> &S,
             }
         });
     }
+    return packed;
 }
 
 struct ThreadAcc {
@@ -282,7 +294,7 @@ __device__ __forceinline__ float expm1_small(float d) {
 // The weight update of one particle: returns the new weight; L1 = ln(w_new/w_hat)
 __device__ __forceinline__ double upd_weight(double w, double what, float dot, const PassArgs &a, float &wnf, float &L1) {
     float wf = d2f_fast(w), whf = d2f_fast(what);
-    float L = logf(__fdividef(wf, whf));
+    float L = __logf(__fdividef(wf, whf));
     float G = a.f_mu * (-L - a.f_ent_c) - dot;
     float d = a.f_eps_dt * G;
     float e = expm1_small(d);
@@ -312,7 +324,7 @@ __device__ __forceinline__ void acc_stats(ThreadAcc &t, double wnd, double L1) {
 __device__ __forceinline__ float to_r(double v, float *) { return d2f_fast(v); }
 __device__ __forceinline__ double to_r(double v, double *) { return v; }
 __device__ __forceinline__ float rlog_ratio(double w, double what, float *) {
-    return logf(__fdividef(d2f_fast(w), d2f_fast(what)));
+    return __logf(__fdividef(d2f_fast(w), d2f_fast(what)));
 }
 __device__ __forceinline__ double rlog_ratio(double w, double what, double *) { return log(w / what); }
 
@@ -331,7 +343,7 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
 }
 
 template <class R, int L>
-__device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, long long i,
+__device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
                                          ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
     const int fl = a.flags;
@@ -343,7 +355,9 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             R wr;
             if (fl & F_UPD) {
                 R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
-                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos);
+                const bool cached = L != 0 && a.cache_read;
+                const unsigned cc = cached ? a.cell_cache[i] : 0u;
+                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc);
                 wn = upd_weight(w, what, dot, a, wr, L1);
                 if (d_bad(wn)) t.bad = true;
             } else {
@@ -359,7 +373,8 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         R wv = to_r(wn, (R *)nullptr);
-        if (wv != R(0)) scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t.ovf);
+        const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t.ovf);
+        if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
     }
     if (fl & F_MINMAX) {
         R E, Lz;
@@ -393,6 +408,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
     if (fl & F_UPD) { S.coef = (const R *)p; p += sizeof(R) * ((nobs + 3) & ~3); }
     S.edges = (const R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
     S.gh = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3);
+    if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
     if (fl & F_CELLS) {
         S.pe = (R *)p; p += sizeof(R) * ((a.nE + 4) & ~3);
         S.pl = (R *)p; p += sizeof(R) * ((a.nL + 4) & ~3);
@@ -414,6 +430,28 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
         for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
     for (int k = threadIdx.x; k < a.edge_len; k += NT) ((R *)S.edges)[k] = ((const R *)a.edge_tab)[k];
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    if ((fl & F_UPD) && L != 0) {
+        // E[H_n] over N(m, t2) as polynomials in m (van der Marel & Franx
+        // H_0..H_4), weighted by this step's coefficients of the cell
+        for (int k = 0; k < a.nsets; ++k) {
+            const SetDev &st = a.sets[k];
+            if (st.quant != M2M_Q_GH) continue;
+            const int ncell = st.nx * st.ny;
+            for (int c = threadIdx.x; c < ncell; c += NT) {
+                const R *g = (const R *)a.gh_tab + st.gh_off + 5 * c;
+                const R *cf = (const R *)a.coef + st.obs_off + 5 * c;
+                const R t2 = g[3], nrm = g[4];
+                const R r2 = R(1.4142135623730951), r3 = R(1.7320508075688772), r24 = R(4.898979485566356);
+                R *P = (R *)S.gpoly + st.gh_off + 5 * c;
+                P[0] = nrm * (cf[0] + cf[2] * ((R(2) * t2 - R(1)) / r2) +
+                              cf[4] * ((R(12) * t2 * t2 - R(12) * t2 + R(3)) / r24));
+                P[1] = nrm * (cf[1] * r2 + cf[3] * ((R(6) * t2 - R(3)) / r3));
+                P[2] = nrm * (cf[2] * r2 + cf[4] * ((R(24) * t2 - R(12)) / r24));
+                P[3] = nrm * (cf[3] * (R(2) / r3));
+                P[4] = nrm * (cf[4] * (R(4) / r24));
+            }
+        }
+    }
     if (fl & F_CELLS) {
         if (FX) {
             for (int k = threadIdx.x; k < 3 * a.ncells; k += NT) S.c_lo[k] = 0u;   // lo, hi, cnt
@@ -431,8 +469,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
     R *px = (R *)a.x, *py = (R *)a.y, *pz = (R *)a.z, *pvx = (R *)a.vx, *pvy = (R *)a.vy, *pvz = (R *)a.vz;
     const bool wr_pos = (fl & F_PUSH) != 0;
     const bool wr_w = (fl & F_UPD) != 0;
-    const long long stride = (long long)gridDim.x * NT;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
+    const int stride = gridDim.x * NT;
+    for (int i = blockIdx.x * NT + threadIdx.x; i < (int)n; i += stride) {
         R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
         R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
         double w = __ldcs(a.w + i);

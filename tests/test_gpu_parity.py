@@ -327,8 +327,11 @@ def test_compiled_and_generic_layouts_agree_over_a_run(prec):
     (g1, y1), (g0, y0) = out
     for k in ("x", "y", "z", "vx", "vy", "vz"):
         assert np.array_equal(g1[k], g0[k])
-    np.testing.assert_allclose(g1["w"], g0["w"], rtol=1e-13 if prec == "fp64" else 1e-7)
-    np.testing.assert_allclose(y1, y0, rtol=1e-12, atol=1e-18)
+    # the compiled layouts evaluate the Gauss-Hermite part of the update as
+    # one quartic per cell, so the rounding (not the result) differs
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    np.testing.assert_allclose(g1["w"], g0["w"], rtol=tol)
+    assert_obs_close(y1, y0, P.sigma, tol)
 
 
 def test_layout_override_is_checked():
