@@ -55,6 +55,7 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
 #define M2M_ERR_ARG       -1   /* invalid argument, size or alignment */
 #define M2M_ERR_CUDA      -2   /* a CUDA runtime call failed */
 #define M2M_ERR_NONFINITE -3   /* a weight became non-finite or negative */
+#define M2M_ERR_TIMEOUT   -4   /* a bounded device-side wait ran out */
 #define M2M_ERR_STATE     -5   /* call not valid in the context's state */
 #define M2M_ERR_NOMEM     -6   /* device allocation failed */
 #define M2M_ERR_OVERFLOW  -7   /* fixed-point histogram range exceeded */
@@ -225,9 +226,10 @@ int m2m_get_cells(m2m_ctx *ctx, int32_t *obs_cells, int32_t *prior_cells);
 int64_t m2m_nobs(const m2m_ctx *ctx);
 int64_t m2m_steps_taken(const m2m_ctx *ctx);
 
-/* Launch shape of the particle kernels: threads per block (multiple of
- * 32, <= 1024) and blocks per SM (0 = as many as fit).  Takes effect on the
- * next launch. */
+/* Launch shape of the particle kernels: threads per block (FP32C: 256, 512
+ * or 1024 (default; the pipelined pass needs 1024); FP64: 256 (default) or
+ * 512) and blocks per SM (0 = as many as fit, at most 4).  Takes effect on
+ * the next launch. */
 int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
 
 /* Observable layout of the particle kernels: the common set combinations
@@ -237,6 +239,18 @@ int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
  * automatic (the default); 0: force the run-time walk; 1-3: the compiled
  * layout, only if it matches (else M2M_ERR_ARG).  Results are identical. */
 int m2m_set_layout(m2m_ctx *ctx, int32_t layout);
+
+/* Streaming and reduction options of the FP32C passes (bit flags):
+ *  1: stream the particles of the compiled layouts through a warp-level
+ *     pipeline: lane 0 of each warp stages the warp's next 32-particle
+ *     chunk into shared memory with bulk copies (TMA) completing on an
+ *     mbarrier while the warp computes the current chunk (default off:
+ *     plain loads);
+ *  2: flush each block's exact histogram to a per-block slot reduced by the
+ *     residual kernel;
+ *  4: flush it with 64-bit integer atomics into the totals (default).
+ * All combinations give bit-identical results. */
+int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable);
 
 /* Device timing of the library's own launches, by kernel class, with CUDA
  * events recorded on the context's stream around every launch while

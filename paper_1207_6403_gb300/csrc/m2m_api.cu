@@ -52,9 +52,10 @@ struct m2m_ctx {
     int ncells;
     int edge_len, gh_len;
     void *d_edges, *d_gh;
-    double *d_Y, *d_sigma, *d_Dt, *d_y, *d_Delta, *d_coef_d;
+    double *d_Y, *d_sigma, *d_isig, *d_Dt, *d_y, *d_Delta, *d_coef_d;
     void *d_coef_r;
     void *d_slots;
+    unsigned long long *d_y_acc;   // FP32C exact observable totals (int64)
     int slot_cap;
     double *d_stat_slots, *d_chi_slots;
     unsigned *d_ticket;
@@ -75,6 +76,8 @@ struct m2m_ctx {
     int cache_bits;      // bits of the packed per-particle cell cache
     unsigned *d_cell_cache;
     bool cache_valid;    // cell cache holds the cells of the current positions
+    bool pipe;           // use the bulk-copy pipelined pass where it applies
+    int fx_atomic;       // FP32C histogram flush: global integer atomics (1) or slots (0)
     // timing of the library's launches
     bool timing;
     long long kernels_total;
@@ -226,7 +229,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.edge_tab = c->d_edges; a.edge_len = c->edge_len;
     a.gh_tab = c->d_gh; a.gh_len = c->gh_len;
     a.coef = c->d_coef_r;
-    a.slots = c->d_slots; a.fx_shift = c->fx_shift;
+    a.slots = c->d_slots; a.fx_shift = c->fx_shift; a.y_acc = c->d_y_acc; a.fx_atomic = c->fx_atomic;
     a.stat_slots = c->d_stat_slots;
     a.prior_kind = c->prior.kind; a.nE = c->prior.nE; a.nL = c->prior.nL; a.ncells = c->ncells;
     a.pk = c->prior.hernquist_a / c->prior.hernquist_GM;
@@ -246,7 +249,14 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     LaunchShape ks = pick_kernel(ctx);
     size_t sm = pass_smem(ctx, flags);
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
+    if (ctx->pipe && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0) {
+        // warp-level bulk-copy pipeline when its stage buffers fit beside the tables
+        void *fp = pass_kernel_f32_pipe(ctx->layout);
+        size_t smp = sm + (size_t)32 * PIPE_STAGES * Chunk<float>::BYTES;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
+        if (occ >= 1) { ks = {fp, 1024}; sm = smp; }
+    }
+    if (occ < 1) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
     if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "pass needs %zu B shared memory: does not fit", sm);
     int bps = occ;
     if (ctx->bps_req > 0 && ctx->bps_req < bps) bps = ctx->bps_req;
@@ -272,19 +282,22 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
 int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, int stat_nblk) {
     ResArgs r;
     memset(&r, 0, sizeof r);
-    r.slots = ctx->d_slots; r.nblk = ctx->last_grid; r.nobs = ctx->nobs;
+    r.slots = ctx->d_slots; r.nblk = ctx->last_grid; r.nobs = ctx->nobs; r.y_acc = ctx->d_y_acc;
+    r.fx_atomic = ctx->fx_atomic;
     r.fixed = ctx->prec == M2M_FP32C; r.q = ctx->fx_q;
-    r.Y = ctx->d_Y; r.sigma = ctx->d_sigma; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
+    r.Y = ctx->d_Y; r.inv_sigma = ctx->d_isig; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
     r.coef_d = ctx->d_coef_d; r.coef_r = ctx->d_coef_r; r.r_float = ctx->prec == M2M_FP32C;
     r.mode = mode; r.alpha = ctx->par.alpha; r.mu = ctx->par.mu;
     r.stat_slots = ctx->d_stat_slots; r.stat_nblk = stat_nblk;
     r.chi_slots = ctx->d_chi_slots; r.ticket = ctx->d_ticket;
     r.ring = ctx->d_ring; r.last = ctx->d_last; r.rec_step = rec_step; r.write_ring = write_ring;
     r.err = ctx->d_err;
-    int nb = (ctx->nobs + 31) / 32;
+    const bool direct = r.fixed && r.fx_atomic;
+    int nt = direct ? RES_NT_FX : RES_NT;
+    int nb = direct ? (ctx->nobs + RES_NT_FX - 1) / RES_NT_FX : (ctx->nobs + 31) / 32;
     void *args[] = {&r};
     LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
-    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(RES_NT), args, 0, ctx->st));
+    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(nt), args, 0, ctx->st));
     return M2M_OK;
 }
 
@@ -327,6 +340,7 @@ int check_err_word(m2m_ctx *ctx) {
     CU(cudaStreamSynchronize(ctx->st));
     if (h & ERR_NONFINITE) return set_err(ctx, M2M_ERR_NONFINITE, "a weight or a reduction became non-finite");
     if (h & ERR_OVERFLOW) return set_err(ctx, M2M_ERR_OVERFLOW, "fixed-point histogram range exceeded");
+    if (h & ERR_TIMEOUT) return set_err(ctx, M2M_ERR_TIMEOUT, "a bulk-copy wait ran out (results invalid)");
     return M2M_OK;
 }
 
@@ -339,10 +353,10 @@ void free_events(m2m_ctx *c) {
 
 void free_all(m2m_ctx *c) {
     free_events(c);
-    void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
+    void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_isig, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
-                    c->d_cell_mean, c->d_cell_cache};
+                    c->d_cell_mean, c->d_cell_cache, c->d_y_acc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -409,8 +423,10 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ctx->w = w; ctx->what = what;
     ctx->st = (cudaStream_t)stream;
     ctx->par = *par;
-    ctx->threads = precision == M2M_FP32C ? 512 : 256;
+    ctx->threads = precision == M2M_FP32C ? 1024 : 256;
     ctx->bps_req = 0;
+    ctx->pipe = false;
+    ctx->fx_atomic = 1;
     int rc = build_potential(ctx, pot, npot);
     if (rc) { g_init_error = ctx->err; delete ctx; return rc; }
 
@@ -531,11 +547,13 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_edges, rs * ctx->edge_len);
     ALLOC(ctx->d_gh, rs * (ctx->gh_len + 1));
     ALLOC(ctx->d_Y, 8 * nobs); ALLOC(ctx->d_sigma, 8 * nobs); ALLOC(ctx->d_Dt, 8 * nobs);
+    ALLOC(ctx->d_isig, 8 * nobs);
     ALLOC(ctx->d_y, 8 * nobs); ALLOC(ctx->d_Delta, 8 * nobs); ALLOC(ctx->d_coef_d, 8 * nobs);
     ALLOC(ctx->d_coef_r, rs * nobs);
     ALLOC(ctx->d_slots, (size_t)8 * nobs * ctx->slot_cap);
+    ALLOC(ctx->d_y_acc, (size_t)8 * nobs);
     ALLOC(ctx->d_stat_slots, (size_t)16 * ctx->slot_cap);
-    ALLOC(ctx->d_chi_slots, (size_t)24 * ((nobs + 31) / 32));
+    ALLOC(ctx->d_chi_slots, (size_t)24 * ((nobs + 31) / 32 + 1));
     ALLOC(ctx->d_ticket, 4);
     ALLOC(ctx->d_ring, sizeof(m2m_record) * M2M_HISTORY);
     ALLOC(ctx->d_last, sizeof(m2m_record));
@@ -569,12 +587,16 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         std::vector<double> zero(nobs, 0.0);
         cudaError_t e3 = cudaMemcpy(ctx->d_Y, Y ? Y : zero.data(), 8 * nobs, cudaMemcpyHostToDevice);
         cudaError_t e4 = cudaMemcpy(ctx->d_sigma, sigma ? sigma : zero.data(), 8 * nobs, cudaMemcpyHostToDevice);
+        std::vector<double> isig(nobs, 0.0);
+        for (int j = 0; j < nobs && sigma; ++j) isig[j] = sigma[j] > 0 ? 1.0 / sigma[j] : 0.0;
+        if (e4 == cudaSuccess) e4 = cudaMemcpy(ctx->d_isig, isig.data(), 8 * nobs, cudaMemcpyHostToDevice);
         cudaError_t e5 = cudaMemset(ctx->d_Dt, 0, 8 * nobs);
         cudaError_t e6 = cudaMemset(ctx->d_ticket, 0, 4);
         cudaError_t e7 = cudaMemset(ctx->d_err, 0, 4);
         cudaError_t e8 = cudaMemset(ctx->d_coef_r, 0, rs * nobs);
         cudaError_t e9 = cudaMemset(ctx->d_ring, 0, sizeof(m2m_record) * M2M_HISTORY);
-        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9};
+        cudaError_t e10 = cudaMemset(ctx->d_y_acc, 0, 8 * (size_t)nobs);
+        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9, e10};
         for (cudaError_t e : es)
             if (e != cudaSuccess) {
                 set_err(nullptr, M2M_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
@@ -588,6 +610,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     for (int lay = 0; lay < 4; ++lay) {
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
+        if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
     }
     for (void *f : kfns) {
         cudaFuncAttributes fa;
@@ -637,6 +660,9 @@ int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma) {
     if (!ctx || !Y || !sigma) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
     CU(cudaMemcpyAsync(ctx->d_Y, Y, 8 * (size_t)ctx->nobs, cudaMemcpyHostToDevice, ctx->st));
     CU(cudaMemcpyAsync(ctx->d_sigma, sigma, 8 * (size_t)ctx->nobs, cudaMemcpyHostToDevice, ctx->st));
+    int nb = (ctx->nobs + 255) / 256;
+    k_inv_sigma<<<nb, 256, 0, ctx->st>>>(ctx->d_sigma, ctx->d_isig, ctx->nobs);
+    CU(cudaGetLastError());
     return M2M_OK;
 }
 
@@ -775,6 +801,14 @@ int m2m_set_layout(m2m_ctx *ctx, int32_t layout) {
         return set_err(ctx, M2M_ERR_ARG, "layout %d does not match the observable sets", layout);
     if (layout != ctx->layout) ctx->cache_valid = false;
     ctx->layout = layout;
+    return M2M_OK;
+}
+
+int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable) {
+    if (!ctx) return M2M_ERR_ARG;
+    ctx->pipe = (enable & 1) != 0;
+    if (enable & 2) ctx->fx_atomic = 0;      // FP32C: per-block slots instead of atomics
+    if (enable & 4) ctx->fx_atomic = 1;      // FP32C: global integer atomics (default)
     return M2M_OK;
 }
 

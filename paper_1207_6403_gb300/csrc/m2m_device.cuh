@@ -20,7 +20,7 @@ constexpr int MAXCELLS = 16385;
 
 enum { F_UPD = 1, F_PUSH = 2, F_SCAT = 4, F_STATS = 8, F_MINMAX = 16, F_CELLS = 32 };
 enum { G_LIN = 0, G_LOG = 1, G_BIS = 2 };
-enum { ERR_NONFINITE = 1, ERR_OVERFLOW = 2 };
+enum { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
 
 struct SetDev {
     int geom, quant, nx, ny, nmom;
@@ -52,7 +52,9 @@ struct PassArgs {
     const void *edge_tab; int edge_len;     // R
     const void *gh_tab;   int gh_len;       // R, 5 per GH cell: V, 1/S, c1, t2, norm
     const void *coef;                       // R[nobs]
-    void *slots;                            // [grid][nobs]: int64 (fixed point) or double
+    void *slots;                            // FP64: [grid][nobs] double per-block sums
+    unsigned long long *y_acc;              // FP32C: [nobs] int64 fixed-point totals
+    int fx_atomic;                          // FP32C: flush to y_acc with atomics (else slots)
     int fx_shift;                           // fixed point: value * 2^fx_shift
     double *stat_slots;                     // [grid][2]: S, sum w
     // priors
@@ -86,6 +88,47 @@ __device__ __forceinline__ bool d_bad(double d) {          // d < 0, NaN or +-in
 // round-to-nearest integer of a float in [-2^22, 2^22] without F2I
 __device__ __forceinline__ int rint_small(float x) {
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+
+// ------------------------------------------------------------ TMA / mbarrier
+// One-dimensional bulk copies global -> shared completing on an mbarrier
+// (each warp stages its next 32-particle chunk while it computes the
+// current one).  Waits are bounded: a wait that runs out returns false and
+// the kernel reports M2M_ERR_TIMEOUT instead of spinning forever.
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+constexpr int MBAR_MAX_TRIES = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (int it = 0; it < MBAR_MAX_TRIES; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // ------------------------------------------------------------ conversions

@@ -345,7 +345,7 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
 template <class R, int L>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
-                                         ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
+                                         unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
     const int fl = a.flags;
     const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
@@ -356,7 +356,6 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             if (fl & F_UPD) {
                 R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
                 const bool cached = L != 0 && a.cache_read;
-                const unsigned cc = cached ? a.cell_cache[i] : 0u;
                 R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc);
                 wn = upd_weight(w, what, dot, a, wr, L1);
                 if (d_bad(wn)) t.bad = true;
@@ -391,10 +390,20 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     w = wn;
 }
 
-template <class R, int NT, int MINB, int L>
+// Stage buffer of one warp chunk (32 particles): x,y,z,vx,vy,vz (R), w, w_hat
+// (double), cached cells (u32).
+template <class R> struct Chunk {
+    static constexpr int OX = 0, OY = 32 * sizeof(R), OZ = 64 * sizeof(R), OVX = 96 * sizeof(R),
+                         OVY = 128 * sizeof(R), OVZ = 160 * sizeof(R), OW = 192 * sizeof(R),
+                         OWH = OW + 256, OCC = OWH + 256, BYTES = OCC + 128;
+};
+constexpr int PIPE_STAGES = 2;
+
+template <class R, int NT, int MINB, int L, int PIPE>
 __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
+    __shared__ __align__(8) unsigned long long bars[PIPE ? (NT / 32) * PIPE_STAGES : 1];
     constexpr bool FX = sizeof(R) == 4;
     const int fl = a.flags;
     PassSmem<R> S{};
@@ -420,6 +429,12 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
             S.c_d = (double *)p; p += 8 * ((a.ncells + 1) & ~1);
             S.c_lo = (unsigned *)p; p += 4 * ((a.ncells + 3) & ~3);   // counts
         }
+    }
+    unsigned char *stages = p;        // PIPE: (NT/32) * PIPE_STAGES chunk buffers
+    if constexpr (PIPE) {
+        if ((threadIdx.x & 31) == 0)
+            for (int st = 0; st < PIPE_STAGES; ++st) mbar_init(&bars[(threadIdx.x >> 5) * PIPE_STAGES + st], 1);
+        fence_mbar_init();
     }
     // prologue: clear histograms, stage the tables
     if (fl & F_SCAT) {
@@ -469,28 +484,117 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
     R *px = (R *)a.x, *py = (R *)a.y, *pz = (R *)a.z, *pvx = (R *)a.vx, *pvy = (R *)a.vy, *pvz = (R *)a.vz;
     const bool wr_pos = (fl & F_PUSH) != 0;
     const bool wr_w = (fl & F_UPD) != 0;
-    const int stride = gridDim.x * NT;
-    for (int i = blockIdx.x * NT + threadIdx.x; i < (int)n; i += stride) {
-        R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
-        R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
-        double w = __ldcs(a.w + i);
-        const double wh = __ldcs(a.what + i);
-        particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, t, emin, emax, lzm, fs);
-        if (wr_pos) {
-            __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
-            __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
+    const bool need_what = (fl & (F_UPD | F_STATS)) != 0;
+    const bool need_cc = L != 0 && a.cache_read && (fl & F_UPD);
+    if constexpr (PIPE) {
+        // warp-level pipeline: lane 0 stages the warp's next chunk with bulk
+        // copies while the warp computes the current one
+        using C = Chunk<R>;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        unsigned char *wbuf = stages + (size_t)warp * PIPE_STAGES * C::BYTES;
+        unsigned long long *wbar = &bars[warp * PIPE_STAGES];
+        const int nfull = (int)(n >> 5), nch = (int)((n + 31) >> 5);
+        const int gw = blockIdx.x * (NT / 32) + warp, TW = gridDim.x * (NT / 32);
+        const unsigned bytes = 6 * 32 * sizeof(R) + 256 + (need_what ? 256 : 0) + (need_cc ? 128 : 0);
+        // per-stage bits: copies pending; parity of the next completion
+        unsigned pendm = 0u, parm = 0u;
+        auto issue = [&](int c, int st) {
+            if (c >= nfull) return;
+            pendm |= 1u << st;
+            if (lane != 0) return;
+            unsigned char *d = wbuf + st * C::BYTES;
+            unsigned long long *b = wbar + st;
+            mbar_expect_tx(b, bytes);
+            const size_t oR = (size_t)c * 32 * sizeof(R), oD = (size_t)c * 256;
+            bulk_g2s(d + C::OX, (const char *)px + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OY, (const char *)py + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OZ, (const char *)pz + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OVX, (const char *)pvx + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OVY, (const char *)pvy + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OVZ, (const char *)pvz + oR, 32 * sizeof(R), b);
+            bulk_g2s(d + C::OW, (const char *)a.w + oD, 256, b);
+            if (need_what) bulk_g2s(d + C::OWH, (const char *)a.what + oD, 256, b);
+            if (need_cc) bulk_g2s(d + C::OCC, (const char *)a.cell_cache + (size_t)c * 128, 128, b);
+        };
+        for (int st = 0; st < PIPE_STAGES; ++st) issue(gw + st * TW, st);
+        bool abort = false;
+        int k = 0;
+        for (int c = gw; c < nch; c += TW, ++k) {
+            const int st = k % PIPE_STAGES;
+            const int i = c * 32 + lane;
+            R x = R(0), y = R(0), z = R(0), vx = R(0), vy = R(0), vz = R(0);
+            double w = 0.0, wh = 0.0;
+            unsigned cc = 0u;
+            if (c < nfull) {
+                const bool ok = mbar_wait(wbar + st, (parm >> st) & 1u);
+                if (__any_sync(0xffffffffu, !ok)) { abort = true; break; }
+                pendm &= ~(1u << st);
+                parm ^= 1u << st;
+                const unsigned char *d = wbuf + st * C::BYTES;
+                x = ((const R *)(d + C::OX))[lane]; y = ((const R *)(d + C::OY))[lane];
+                z = ((const R *)(d + C::OZ))[lane]; vx = ((const R *)(d + C::OVX))[lane];
+                vy = ((const R *)(d + C::OVY))[lane]; vz = ((const R *)(d + C::OVZ))[lane];
+                w = ((const double *)(d + C::OW))[lane];
+                if (need_what) wh = ((const double *)(d + C::OWH))[lane];
+                if (need_cc) cc = ((const unsigned *)(d + C::OCC))[lane];
+            } else if (i < (int)n) {
+                x = px[i]; y = py[i]; z = pz[i]; vx = pvx[i]; vy = pvy[i]; vz = pvz[i];
+                w = a.w[i];
+                if (need_what) wh = a.what[i];
+                if (need_cc) cc = a.cell_cache[i];
+            }
+            if (i < (int)n) {
+                particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                if (wr_pos) {
+                    __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
+                    __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
+                }
+                if (wr_w) __stcs(a.w + i, w);
+            }
+            __syncwarp();
+            issue(c + PIPE_STAGES * TW, st);
         }
-        if (wr_w) __stcs(a.w + i, w);
+        if (abort) {
+            // let this warp's copies in flight land before the block exits
+            if (lane == 0) {
+                atomicOr(a.err, ERR_TIMEOUT);
+                for (int st = 0; st < PIPE_STAGES; ++st)
+                    if ((pendm >> st) & 1u) mbar_wait(wbar + st, (parm >> st) & 1u);
+            }
+            __syncwarp();
+        }
+    } else {
+        const int stride = gridDim.x * NT;
+        for (int i = blockIdx.x * NT + threadIdx.x; i < (int)n; i += stride) {
+            R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
+            R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
+            double w = __ldcs(a.w + i);
+            const double wh = need_what ? __ldcs(a.what + i) : 0.0;
+            const unsigned cc = need_cc ? a.cell_cache[i] : 0u;
+            particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+            if (wr_pos) {
+                __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
+                __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
+            }
+            if (wr_w) __stcs(a.w + i, w);
+        }
     }
     __syncthreads();
     // epilogue: flush the block-private histograms and partial sums
     if (fl & F_SCAT) {
         if (FX) {
+            // exact block totals, either into the global totals with 64-bit
+            // integer atomics or to this block's slot for the residual to sum;
+            // integer sums, so the result does not depend on the order
             long long *sl = (long long *)a.slots + (long long)blockIdx.x * nobs;
             for (int k = threadIdx.x; k < nobs; k += NT) {
-                long long v = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
+                const long long v = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
                 if (v >= (1ll << 53) || v <= -(1ll << 53)) t.ovf = true;
-                sl[k] = v;
+                if (a.fx_atomic) {
+                    if (v) atomicAdd(a.y_acc + k, (unsigned long long)v);
+                } else {
+                    sl[k] = v;
+                }
             }
         } else {
             double *sl = (double *)a.slots + (long long)blockIdx.x * nobs;
@@ -555,7 +659,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
 // ------------------------------------------------------------- k_residual
 struct ResArgs {
     const void *slots; int nblk; int nobs; int fixed; double q;
-    const double *Y, *sigma;
+    unsigned long long *y_acc; int fx_atomic;
+    const double *Y, *inv_sigma;    // 1/sigma_j, 0 where sigma_j <= 0 (masked)
     double *Dt, *y, *Delta, *coef_d; void *coef_r; int r_float;
     int mode; double alpha, mu;
     const double *stat_slots; int stat_nblk;
@@ -572,109 +677,150 @@ __device__ __forceinline__ double block_sum_strided(const double *v, int stride,
     return block_sum(s, red);
 }
 
-// 32 observables per block (lane = observable); the 32 warps split the
-// per-block slots, each with four independent accumulators.  Integer slots
-// sum exactly; double slots in a fixed order.
-constexpr int RES_NT = 1024;
+// FP32C (fx_atomic): one thread per observable in small blocks; the totals
+// are exact integers already summed by the pass's atomics (re-zeroed here
+// for the next scatter).  Slots (FP64, or FP32C without atomics): 32
+// observables per block (lane = observable), the warps split the per-block
+// slots with four independent accumulators each, in a fixed order.  The
+// per-observable arithmetic is FP64 (slow on this part), so it is spread
+// over many blocks; divisions by sigma are multiplications by its
+// reciprocal.  Chi^2 partials per block, then the last block to finish
+// writes the record.
+constexpr int RES_NT = 1024;      // slot reduction
+constexpr int RES_NT_FX = 128;    // FP32C atomic totals
 __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ ResArgs a) {
     constexpr int NW = RES_NT / 32;
     __shared__ unsigned long long si[NW][32];
     __shared__ double sd[NW][32];
-    __shared__ double red[32];
+    __shared__ double wred[3][NW];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + lane;
-    if (j < a.nobs) {
-        if (a.fixed) {
-            // each block slot is below 2^53 in magnitude (checked at the
-            // flush), so the sum of at most 1024 of them cannot wrap
-            const long long *sl = (const long long *)a.slots + j;
-            unsigned long long acc[4] = {0, 0, 0, 0};
-            int b = wp;
-            for (; b + 3 * NW < a.nblk; b += 4 * NW) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] += (unsigned long long)sl[(long long)(b + u * NW) * a.nobs];
-            }
-            for (; b < a.nblk; b += NW) acc[0] += (unsigned long long)sl[(long long)b * a.nobs];
-            si[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        } else {
-            const double *sl = (const double *)a.slots + j;
-            double acc[4] = {0, 0, 0, 0};
-            int b = wp;
-            for (; b + 3 * NW < a.nblk; b += 4 * NW) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] += sl[(long long)(b + u * NW) * a.nobs];
-            }
-            for (; b < a.nblk; b += NW) acc[0] += sl[(long long)b * a.nobs];
-            sd[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        }
-    }
-    __syncthreads();
-    if (wp == 0) {
-        double c2 = 0.0, c2r = 0.0, mx = 0.0;
+    const int nw = blockDim.x >> 5;
+    const bool direct = a.fixed && a.fx_atomic;
+    const int j = direct ? blockIdx.x * blockDim.x + threadIdx.x : blockIdx.x * 32 + lane;
+    bool have = false;
+    double yv = 0.0;
+    if (direct) {
         if (j < a.nobs) {
-            double yv;
+            const unsigned long long tot = a.y_acc[j];
+            a.y_acc[j] = 0ull;
+            yv = (double)(long long)tot * a.q;
+            have = true;
+        }
+    } else {
+        if (j < a.nobs) {
+            if (a.fixed) {
+                const long long *sl = (const long long *)a.slots + j;
+                unsigned long long acc[4] = {0, 0, 0, 0};
+                int b = wp;
+                for (; b + 3 * nw < a.nblk; b += 4 * nw) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[u] += (unsigned long long)sl[(long long)(b + u * nw) * a.nobs];
+                }
+                for (; b < a.nblk; b += nw) acc[0] += (unsigned long long)sl[(long long)b * a.nobs];
+                si[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            } else {
+                const double *sl = (const double *)a.slots + j;
+                double acc[4] = {0, 0, 0, 0};
+                int b = wp;
+                for (; b + 3 * nw < a.nblk; b += 4 * nw) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[u] += sl[(long long)(b + u * nw) * a.nobs];
+                }
+                for (; b < a.nblk; b += nw) acc[0] += sl[(long long)b * a.nobs];
+                sd[wp][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            }
+        }
+        __syncthreads();
+        if (wp == 0 && j < a.nobs) {
             if (a.fixed) {
                 unsigned long long tot = 0;
-                for (int k = 0; k < NW; ++k) tot += si[k][lane];
+                for (int k = 0; k < nw; ++k) tot += si[k][lane];
                 yv = (double)(long long)tot * a.q;
             } else {
-                yv = 0.0;
-                for (int k = 0; k < NW; ++k) yv += sd[k][lane];
+                for (int k = 0; k < nw; ++k) yv += sd[k][lane];
             }
-            double s = a.sigma[j];
-            bool valid = s > 0.0;
-            double D = valid ? (yv - a.Y[j]) / s : 0.0;
-            double dold = a.Dt[j];
-            double dn = (a.mode == 1) ? a.alpha * D + (1.0 - a.alpha) * dold : (a.mode == 2 ? D : dold);
-            double cf = valid ? dn / s : 0.0;
-            a.y[j] = yv;
-            a.Delta[j] = D;
-            if (a.mode != 0) a.Dt[j] = dn;
-            a.coef_d[j] = cf;
-            if (a.r_float) ((float *)a.coef_r)[j] = (float)cf;
-            else ((double *)a.coef_r)[j] = cf;
-            c2 = dn * dn; c2r = D * D; mx = fabs(dn);
-        }
-        c2 = warp_sum(c2);
-        c2r = warp_sum(c2r);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) {
-            a.chi_slots[3 * blockIdx.x] = c2;
-            a.chi_slots[3 * blockIdx.x + 1] = c2r;
-            a.chi_slots[3 * blockIdx.x + 2] = mx;
+            have = true;
         }
     }
-    __threadfence();
+    double c2 = 0.0, c2r = 0.0, mx = 0.0;
+    if (have) {
+        const double is = a.inv_sigma[j];
+        const bool valid = is > 0.0;
+        const double D = valid ? (yv - a.Y[j]) * is : 0.0;
+        const double dold = a.Dt[j];
+        const double dn = (a.mode == 1) ? a.alpha * D + (1.0 - a.alpha) * dold : (a.mode == 2 ? D : dold);
+        const double cf = valid ? dn * is : 0.0;
+        a.y[j] = yv;
+        a.Delta[j] = D;
+        if (a.mode != 0) a.Dt[j] = dn;
+        a.coef_d[j] = cf;
+        if (a.r_float) ((float *)a.coef_r)[j] = (float)cf;
+        else ((double *)a.coef_r)[j] = cf;
+        c2 = dn * dn; c2r = D * D; mx = fabs(dn);
+    }
+    c2 = warp_sum(c2);
+    c2r = warp_sum(c2r);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) { wred[0][wp] = c2; wred[1][wp] = c2r; wred[2][wp] = mx; }
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int k = 0; k < nw; ++k) { s0 += wred[0][k]; s1 += wred[1][k]; s2 = fmax(s2, wred[2][k]); }
+        a.chi_slots[3 * blockIdx.x] = s0;
+        a.chi_slots[3 * blockIdx.x + 1] = s1;
+        a.chi_slots[3 * blockIdx.x + 2] = s2;
+        __threadfence();
+        s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double c2 = block_sum_strided(a.chi_slots, 3, 0, gridDim.x, red);
-    double c2r = block_sum_strided(a.chi_slots, 3, 1, gridDim.x, red);
-    double S = block_sum_strided(a.stat_slots, 2, 0, a.stat_nblk, red);
-    double W = block_sum_strided(a.stat_slots, 2, 1, a.stat_nblk, red);
-    double mx = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) mx = fmax(mx, a.chi_slots[3 * b + 2]);
+    // one strided pass over the block partials, one fixed-shape reduction of
+    // the five totals (deterministic: the shape depends only on the sizes)
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        v0 += a.chi_slots[3 * b];
+        v1 += a.chi_slots[3 * b + 1];
+        v2 = fmax(v2, a.chi_slots[3 * b + 2]);
+    }
+    for (int b = threadIdx.x; b < a.stat_nblk; b += blockDim.x) {
+        v3 += a.stat_slots[2 * b];
+        v4 += a.stat_slots[2 * b + 1];
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __syncthreads();
-    if (lane == 0) red[wp] = mx;
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+        v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+        v4 += __shfl_xor_sync(0xffffffffu, v4, o);
+    }
+    __shared__ double fin[5][NW];
+    if (lane == 0) { fin[0][wp] = v0; fin[1][wp] = v1; fin[2][wp] = v2; fin[3][wp] = v3; fin[4][wp] = v4; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < NW; ++k) mx = fmax(mx, red[k]);
+        double C2 = 0.0, C2r = 0.0, M = 0.0, S = 0.0, W = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            C2 += fin[0][k]; C2r += fin[1][k]; M = fmax(M, fin[2][k]); S += fin[3][k]; W += fin[4][k];
+        }
         m2m_record r;
         r.step = a.rec_step;
-        r.chi2 = c2; r.chi2_raw = c2r; r.S = S; r.sum_w = W;
-        r.F = -0.5 * c2 + a.mu * S;
-        r.max_abs_dt = mx;
+        r.chi2 = C2; r.chi2_raw = C2r; r.S = S; r.sum_w = W;
+        r.F = -0.5 * C2 + a.mu * S;
+        r.max_abs_dt = M;
         *a.last = r;
         if (a.write_ring) a.ring[a.rec_step % M2M_HISTORY] = r;
-        if (!(isfinite(c2) && isfinite(S) && isfinite(W))) atomicOr(a.err, ERR_NONFINITE);
+        if (!(isfinite(C2) && isfinite(S) && isfinite(W))) atomicOr(a.err, ERR_NONFINITE);
         *a.ticket = 0u;
     }
+}
+
+// 1/sigma_j (0 where sigma_j <= 0: masked observable)
+__global__ void k_inv_sigma(const double *sigma, double *isig, int nobs) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nobs) isig[j] = sigma[j] > 0.0 ? 1.0 / sigma[j] : 0.0;
 }
 
 // ----------------------------------------------------------- prior means
@@ -718,6 +864,7 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
 
 // Kernel tables, one per precision, each in its own translation unit.
 void *pass_kernel_f32(int threads, int layout);
+void *pass_kernel_f32_pipe(int layout);
 void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();

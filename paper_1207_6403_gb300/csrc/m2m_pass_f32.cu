@@ -7,10 +7,10 @@ namespace m2m {
 template <int NT, int MINB>
 static void *pick_layout_f32(int layout) {
     switch (layout) {
-        case 1: return (void *)k_pass<float, NT, MINB, 1>;
-        case 2: return (void *)k_pass<float, NT, MINB, 2>;
-        case 3: return (void *)k_pass<float, NT, MINB, 3>;
-        default: return (void *)k_pass<float, NT, MINB, 0>;
+        case 1: return (void *)k_pass<float, NT, MINB, 1, 0>;
+        case 2: return (void *)k_pass<float, NT, MINB, 2, 0>;
+        case 3: return (void *)k_pass<float, NT, MINB, 3, 0>;
+        default: return (void *)k_pass<float, NT, MINB, 0, 0>;
     }
 }
 
@@ -19,6 +19,16 @@ void *pass_kernel_f32(int threads, int layout) {
         case 256: return pick_layout_f32<256, 2>(layout);
         case 1024: return pick_layout_f32<1024, 1>(layout);
         default: return pick_layout_f32<512, 2>(layout);
+    }
+}
+
+// The compiled layouts with the warp-level bulk-copy pipeline (1024 threads).
+void *pass_kernel_f32_pipe(int layout) {
+    switch (layout) {
+        case 1: return (void *)k_pass<float, 1024, 1, 1, 1>;
+        case 2: return (void *)k_pass<float, 1024, 1, 2, 1>;
+        case 3: return (void *)k_pass<float, 1024, 1, 3, 1>;
+        default: return nullptr;
     }
 }
 

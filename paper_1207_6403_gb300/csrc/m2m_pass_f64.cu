@@ -6,10 +6,10 @@ namespace m2m {
 template <int NT, int MINB>
 static void *pick_layout_f64(int layout) {
     switch (layout) {
-        case 1: return (void *)k_pass<double, NT, MINB, 1>;
-        case 2: return (void *)k_pass<double, NT, MINB, 2>;
-        case 3: return (void *)k_pass<double, NT, MINB, 3>;
-        default: return (void *)k_pass<double, NT, MINB, 0>;
+        case 1: return (void *)k_pass<double, NT, MINB, 1, 0>;
+        case 2: return (void *)k_pass<double, NT, MINB, 2, 0>;
+        case 3: return (void *)k_pass<double, NT, MINB, 3, 0>;
+        default: return (void *)k_pass<double, NT, MINB, 0, 0>;
     }
 }
 

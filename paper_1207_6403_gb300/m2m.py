@@ -15,7 +15,7 @@ import numpy as np
 from . import build as _build
 
 M2M_OK = 0
-ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE",
+ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE", -4: "M2M_ERR_TIMEOUT",
           -5: "M2M_ERR_STATE", -6: "M2M_ERR_NOMEM", -7: "M2M_ERR_OVERFLOW"}
 FP64, FP32C = 0, 1
 POT = {"hernquist": 1, "nfw": 2, "log": 3}
@@ -95,6 +95,7 @@ def library():
         "m2m_steps_taken": (c_int64, [P]),
         "m2m_set_launch": (c_int32, [P, c_int32, c_int32]),
         "m2m_set_layout": (c_int32, [P, c_int32]),
+        "m2m_set_pipeline": (c_int32, [P, c_int32]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_last_error": (ctypes.c_char_p, [P]),
@@ -199,6 +200,9 @@ class Context:
 
     def m2m_set_layout(self, layout=-1):
         _check(library().m2m_set_layout(self.ptr, layout), self.ptr)
+
+    def m2m_set_pipeline(self, enable=True):
+        _check(library().m2m_set_pipeline(self.ptr, int(enable)), self.ptr)
 
     def m2m_set_timing(self, enable):
         _check(library().m2m_set_timing(self.ptr, 1 if enable else 0), self.ptr)
