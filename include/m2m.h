@@ -275,8 +275,54 @@ int m2m_set_timing(m2m_ctx *ctx, int32_t enable);
 /* Synchronises, fills *out for the launches since the last call, resets. */
 int m2m_get_timing(m2m_ctx *ctx, m2m_timing *out);
 
+/* Observables of a particle set without any device allocation.
+ *
+ * The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory when they observe -- code running inside a CUDA
+ * graph capture, under an external allocator that owns all device memory,
+ * or in allocator-free real-time deployments, and callers that must not
+ * incur the implicit synchronisation of cudaMalloc/cudaFree.  It computes
+ * exactly what m2m_observe computes for an FP32C context over the same
+ * particles (the same scatter kernel, exact fixed-point sums), without a
+ * context.
+ *
+ * All scratch memory -- the integer totals, an error word and the edge and
+ * Gauss-Hermite tables -- is one fixed device array of
+ * M2M_STATIC_SCRATCH_BYTES inside the library, present on every GPU that
+ * loads the library until the process exits.  The call allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine).
+ *   n            particle count, 1 <= n < 2^31
+ *   x..vz        device float arrays (the FP32C state), w device double
+ *                array; all caller-owned, 16-byte aligned, only read
+ *   obs, nsets   observable sets as for m2m_init (host, copied); at most
+ *                M2M_STATIC_MAX_OBS observables, M2M_STATIC_MAX_EDGES edges
+ *                in total and M2M_STATIC_MAX_GH_CELLS Gauss-Hermite cells,
+ *                else M2M_ERR_ARG with the reason in m2m_last_error(NULL)
+ *   incl_sin, incl_cos  line of sight as for m2m_params
+ *   weight_scale a value of the order of sum(w) (> 0): the fixed-point
+ *                resolution is 2^-50 * 2^ceil(log2(weight_scale))
+ *   y_out        caller-owned device array of the observable count (double)
+ *   stream       cudaStream_t (NULL = default stream); the work is enqueued
+ *                on it and the call returns without synchronising
+ * The first call on a device (the current device) looks up the array's
+ * device address once (cudaGetSymbolAddress) and sets kernel attributes;
+ * make that first call before any stream capture.  Every call shares the
+ * one array, which keeps the previous call's contents (the totals are
+ * cleared at the start of each call): calls that overlap on the GPU -- on
+ * different streams or from different host threads -- race and give wrong
+ * results.  A fixed-point overflow or a non-finite weight makes every
+ * output NaN. */
+#define M2M_STATIC_MAX_OBS 8192
+#define M2M_STATIC_MAX_EDGES 2048
+#define M2M_STATIC_MAX_GH_CELLS 4096
+#define M2M_STATIC_SCRATCH_BYTES 163840
+int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, const void *vx,
+                       const void *vy, const void *vz, const double *w, const m2m_obs_desc *obs,
+                       int32_t nsets, double incl_sin, double incl_cos, double weight_scale,
+                       double *y_out, void *stream);
+
 /* Text of the last error on this context (or of the last failed m2m_init
- * when ctx is NULL). */
+ * or m2m_observe_static when ctx is NULL). */
 const char *m2m_last_error(const m2m_ctx *ctx);
 
 /* Release library-owned memory; particle arrays are not touched. */

@@ -392,6 +392,10 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
 
 }  // namespace
 
+namespace m2m {
+void note_context_free_error(const char *msg) { g_init_error = msg; }
+}  // namespace m2m
+
 extern "C" {
 
 int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, void *z, void *vx,

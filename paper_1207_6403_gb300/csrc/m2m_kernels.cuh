@@ -869,4 +869,7 @@ void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();
 
+// Text returned by m2m_last_error(NULL) (errors not tied to a context).
+void note_context_free_error(const char *msg);
+
 }  // namespace m2m

@@ -98,6 +98,8 @@ def library():
         "m2m_set_pipeline": (c_int32, [P, c_int32]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
+        "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
+                                         c_double, c_double, c_double, P, P]),
         "m2m_last_error": (ctypes.c_char_p, [P]),
         "m2m_free": (c_int32, [P]),
     }
@@ -338,3 +340,37 @@ def observe_targets(problem, precision=None, device="cuda:0"):
     y, _, _ = ctx.m2m_get_obs()
     ctx.m2m_free()
     return y
+
+
+def m2m_observe_static(pos, vel, w, obs, incl_sin, incl_cos, weight_scale, y_out, stream=None):
+    """Observables of a particle set without device allocation (see the C
+    declaration): pos, vel are (x, y, z) / (vx, vy, vz) float32 device
+    tensors, w a float64 device tensor, y_out a float64 device tensor of the
+    observable count.  The library keeps its scratch in one fixed device
+    array, so concurrent calls race; the call is enqueued on `stream` (the
+    current stream by default) and returns without synchronising."""
+    import torch
+    lib = library()
+    keep = []
+    od = (m2m_obs_desc * len(obs))()
+    for k, s in enumerate(obs):
+        ex = np.ascontiguousarray(s.edges_x, dtype=np.float64)
+        keep.append(ex)
+        od[k].geom, od[k].quant = GEOM[s.geom], QUANT[s.quant]
+        od[k].nx, od[k].ny = len(ex) - 1, (1 if s.edges_y is None else len(s.edges_y) - 1)
+        od[k].edges_x = _dptr(ex)
+        if s.edges_y is not None:
+            ey = np.ascontiguousarray(s.edges_y, dtype=np.float64)
+            keep.append(ey)
+            od[k].edges_y = _dptr(ey)
+        if s.quant == "gh":
+            V = np.ascontiguousarray(s.gh_V, dtype=np.float64)
+            S = np.ascontiguousarray(s.gh_S, dtype=np.float64)
+            keep += [V, S]
+            od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
+        od[k].sigma_kernel = float(s.sigma_kernel)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    ptrs = [c_void_p(t.data_ptr()) for t in (*pos, *vel, w)]
+    rc = lib.m2m_observe_static(int(w.shape[0]), *ptrs, od, len(obs), float(incl_sin), float(incl_cos),
+                                float(weight_scale), c_void_p(y_out.data_ptr()), c_void_p(st))
+    _check(rc, None)
