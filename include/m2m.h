@@ -275,6 +275,49 @@ int m2m_set_timing(m2m_ctx *ctx, int32_t enable);
 /* Synchronises, fills *out for the launches since the last call, resets. */
 int m2m_get_timing(m2m_ctx *ctx, m2m_timing *out);
 
+/* ---- many models in one launch (trial potentials, Section 4 of the paper:
+ * models fitted in a sequence of potentials) ----
+ * Each model is an independent M2M problem with its own particles,
+ * potential, observables, targets, priors and epsilon; all share the
+ * precision, the other step parameters and the stream.  When every model
+ * is FP32C with the same compiled observable layout and the same prior
+ * schedule, one kernel launch advances all models' particles per stage
+ * (blocks shared out in proportion to N) and, on a non-default stream, the
+ * launch sequence of m2m_batch_step is captured once into a CUDA graph and
+ * replayed; otherwise the models are stepped one after another.  Results
+ * are those of stepping each model alone. */
+typedef struct {
+    int64_t n;
+    void *x, *y, *z, *vx, *vy, *vz;   /* device, caller-owned (as m2m_init) */
+    double *w, *what;
+    const m2m_potential_desc *pot;
+    int32_t npot;
+    const m2m_obs_desc *obs;
+    int32_t nsets;
+    const double *Y, *sigma;          /* host, or NULL */
+    double eps;                       /* this model's epsilon */
+    const m2m_prior_desc *prior;      /* NULL = flat */
+} m2m_model_desc;
+typedef struct m2m_batch m2m_batch;
+
+/* par supplies mu, dt, alpha, entropy_const and the line of sight (its eps
+ * is ignored: each model brings its own).  1 <= nmodels <= 1024. */
+int m2m_batch_init(m2m_batch **batch_out, int32_t precision, int32_t nmodels, const m2m_model_desc *models,
+                   const m2m_params *par, void *stream);
+
+/* nsteps M2M steps of every model (see m2m_step). */
+int m2m_batch_step(m2m_batch *batch, int64_t nsteps);
+
+/* The context of model `model` (owned by the batch: valid until
+ * m2m_batch_free; use it for m2m_get_obs, m2m_get_record, ...). */
+int m2m_batch_context(m2m_batch *batch, int32_t model, m2m_ctx **ctx_out);
+
+/* 1 if the last m2m_batch_step used one launch per stage for all models
+ * (2 if also through a CUDA graph), 0 if it stepped them one by one. */
+int m2m_batch_fused(const m2m_batch *batch);
+
+int m2m_batch_free(m2m_batch *batch);
+
 /* Observables of a particle set without any device allocation.
  *
  * The paper has no counterpart to this call: it serves callers that cannot

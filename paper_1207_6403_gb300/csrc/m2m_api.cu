@@ -16,7 +16,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "m2m.h"
@@ -615,6 +617,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
+        kfns.push_back(pass_kernel_f32_batch(lay));
     }
     for (void *f : kfns) {
         cudaFuncAttributes fa;
@@ -847,6 +850,349 @@ int m2m_free(m2m_ctx *ctx) {
     cudaStreamSynchronize(ctx->st);
     free_all(ctx);
     delete ctx;
+    return M2M_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Batches of models
+// ======================================================================
+struct m2m_batch {
+    int prec = 0, nmodels = 0;
+    std::vector<m2m_ctx *> ctx;
+    cudaStream_t st = nullptr;
+    bool fusable = false;        // one launch per stage is possible
+    int layout = 0;
+    int period = 0;              // common moving-prior period (0: flat)
+    PassArgs *d_pass = nullptr;  // per-model arguments
+    ResArgs *d_res = nullptr;
+    int *d_tab = nullptr;        // pass: model, rank, count | residual: model, rank, count
+    int pgrid = 0, rgrid = 0;
+    std::vector<int> pcount, rcount;
+    long long *d_step = nullptr; // step counter read by the batched residual
+    long long t = 0;
+    int last_mode = 0;
+    std::map<std::tuple<long long, long long, int>, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+namespace {
+
+int berr(m2m_batch *b, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    g_init_error = buf;
+    return code;
+}
+
+__global__ void k_add_step(long long *step, long long n) { *step += n; }
+
+void batch_free_all(m2m_batch *b) {
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    for (m2m_ctx *c : b->ctx) m2m_free(c);
+    b->ctx.clear();
+    void *ptrs[] = {b->d_pass, b->d_res, b->d_tab, b->d_step};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+// Upload the models' current arguments (potentials may have changed).
+int batch_upload(m2m_batch *b) {
+    std::vector<PassArgs> pa(b->nmodels);
+    std::vector<ResArgs> ra(b->nmodels);
+    for (int m = 0; m < b->nmodels; ++m) {
+        m2m_ctx *c = b->ctx[m];
+        fill_args(c, pa[m], 0);
+        ResArgs &r = ra[m];
+        memset(&r, 0, sizeof r);
+        r.slots = c->d_slots; r.nblk = b->pcount[m]; r.nobs = c->nobs; r.y_acc = c->d_y_acc;
+        r.fx_atomic = 1; r.fixed = 1; r.q = c->fx_q;
+        r.Y = c->d_Y; r.inv_sigma = c->d_isig; r.Dt = c->d_Dt; r.y = c->d_y; r.Delta = c->d_Delta;
+        r.coef_d = c->d_coef_d; r.coef_r = c->d_coef_r; r.r_float = 1;
+        r.alpha = c->par.alpha; r.mu = c->par.mu;
+        r.stat_slots = c->d_stat_slots; r.stat_nblk = b->pcount[m];
+        r.chi_slots = c->d_chi_slots; r.ticket = c->d_ticket;
+        r.ring = c->d_ring; r.last = c->d_last;
+        r.err = c->d_err;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_pass, pa.data(), sizeof(PassArgs) * b->nmodels, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_res, ra.data(), sizeof(ResArgs) * b->nmodels, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);   // host staging buffers go out of scope
+    if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
+    return M2M_OK;
+}
+
+size_t batch_smem(const m2m_batch *b, int flags) {
+    size_t sm = 0;
+    for (m2m_ctx *c : b->ctx) sm = std::max(sm, pass_smem(c, flags));
+    return sm;
+}
+
+int batch_pass(m2m_batch *b, int flags, int cache_read) {
+    BatchPass bp;
+    bp.models = b->d_pass;
+    bp.blk_model = b->d_tab;
+    bp.blk_rank = b->d_tab + b->pgrid;
+    bp.blk_count = b->d_tab + 2 * b->pgrid;
+    bp.flags = flags;
+    bp.cache_read = cache_read;
+    bp.cache_write = 1;
+    void *args[] = {&bp};
+    cudaError_t e = cudaLaunchKernel(pass_kernel_f32_batch(b->layout), dim3(b->pgrid), dim3(1024), args,
+                                     batch_smem(b, flags), b->st);
+    if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "batched pass: %s", cudaGetErrorString(e));
+    return M2M_OK;
+}
+
+// One fused step sequence of nsteps steps starting at step t0 with the
+// models' update pending or not.  Records are numbered from *d_step.
+int batch_sequence(m2m_batch *b, long long nsteps, long long t0, bool pending) {
+    const int *rtab = b->d_tab + 2 * b->pgrid + b->nmodels;   // see the table layout in m2m_batch_init
+    for (long long k = 0; k < nsteps; ++k) {
+        const long long t1 = t0 + k + 1;
+        const bool prior_due = b->period > 0 && (t1 % b->period == 0);
+        int fl = F_PUSH | F_SCAT | F_STATS | (pending ? F_UPD : 0) | (prior_due ? F_MINMAX : 0);
+        int rc = batch_pass(b, fl, pending ? 1 : 0);
+        if (rc) return rc;
+        BatchRes br;
+        br.models = b->d_res;
+        br.blk_model = rtab;
+        br.blk_rank = rtab + b->rgrid;
+        br.blk_count = rtab + 2 * b->rgrid;
+        br.mode = 1;
+        br.write_ring = 1;
+        br.rec_step = (long long)(k + 1);     // relative: k_residual_batch adds *d_step
+        br.step = b->d_step;
+        void *args[] = {&br};
+        cudaError_t e = cudaLaunchKernel((void *)k_residual_batch, dim3(b->rgrid), dim3(RES_NT_FX), args, 0, b->st);
+        if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "batched residual: %s", cudaGetErrorString(e));
+        pending = true;
+        if (prior_due) {
+            for (int m = 0; m < b->nmodels; ++m) {
+                m2m_ctx *c = b->ctx[m];
+                c->mm_nblocks = b->pcount[m];
+                rc = prior_recompute(c, F_UPD);
+                if (rc) return berr(b, rc, "model %d priors: %s", m, c->err.c_str());
+            }
+            pending = false;
+        }
+    }
+    if (pending) {
+        int rc = batch_pass(b, F_UPD, 1);
+        if (rc) return rc;
+    }
+    k_add_step<<<1, 1, 0, b->st>>>(b->d_step, nsteps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "step counter: %s", cudaGetErrorString(e));
+    return M2M_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int m2m_batch_init(m2m_batch **out, int32_t precision, int32_t nmodels, const m2m_model_desc *models,
+                   const m2m_params *par, void *stream) {
+    if (!out) return berr(nullptr, M2M_ERR_ARG, "batch_out is NULL");
+    *out = nullptr;
+    if (nmodels < 1 || nmodels > 1024 || !models || !par)
+        return berr(nullptr, M2M_ERR_ARG, "nmodels=%d out of [1,1024] or NULL argument", nmodels);
+    m2m_batch *b = new m2m_batch();
+    b->prec = precision;
+    b->nmodels = nmodels;
+    b->st = (cudaStream_t)stream;
+    for (int m = 0; m < nmodels; ++m) {
+        const m2m_model_desc &d = models[m];
+        m2m_params pm = *par;
+        pm.eps = d.eps;
+        m2m_ctx *c = nullptr;
+        int rc = m2m_init(&c, precision, d.n, d.x, d.y, d.z, d.vx, d.vy, d.vz, d.w, d.what, d.pot, d.npot, d.obs,
+                          d.nsets, d.Y, d.sigma, &pm, d.prior, stream);
+        if (rc) {
+            std::string msg = g_init_error;
+            batch_free_all(b);
+            delete b;
+            return berr(nullptr, rc, "model %d: %s", m, msg.c_str());
+        }
+        b->ctx.push_back(c);
+    }
+    // one launch per stage needs FP32C, one compiled layout and one prior schedule
+    m2m_ctx *c0 = b->ctx[0];
+    b->fusable = precision == M2M_FP32C && c0->layout != 0;
+    b->layout = c0->layout;
+    b->period = c0->prior.kind == M2M_PRIOR_FLAT ? 0 : c0->prior.period;
+    for (m2m_ctx *c : b->ctx) {
+        const int per = c->prior.kind == M2M_PRIOR_FLAT ? 0 : c->prior.period;
+        if (c->layout != b->layout || per != b->period) b->fusable = false;
+    }
+    if (b->fusable) {
+        // blocks in proportion to N (at least one per model)
+        size_t sm = batch_smem(b, F_UPD | F_PUSH | F_SCAT | F_STATS | F_MINMAX);
+        int occ = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel_f32_batch(b->layout), 1024, sm);
+        if (e != cudaSuccess || occ < 1) b->fusable = false;
+        long long G = (long long)c0->nsm * std::max(occ, 1);
+        double tot = 0;
+        for (m2m_ctx *c : b->ctx) tot += (double)c->n;
+        std::vector<double> share(nmodels);
+        int used = 0;
+        b->pcount.assign(nmodels, 1);
+        for (int m = 0; m < nmodels; ++m) {
+            share[m] = G * (double)b->ctx[m]->n / tot;
+            b->pcount[m] = std::max(1, (int)share[m]);
+            long long need = (b->ctx[m]->n + 1023) / 1024;
+            b->pcount[m] = (int)std::min<long long>(std::min<long long>(b->pcount[m], need), b->ctx[m]->slot_cap);
+            used += b->pcount[m];
+        }
+        for (int extra = (int)G - used; extra > 0; --extra) {     // largest remainders first
+            int best = -1;
+            double bestr = 0;
+            for (int m = 0; m < nmodels; ++m) {
+                long long need = (b->ctx[m]->n + 1023) / 1024;
+                if (b->pcount[m] >= need || b->pcount[m] >= b->ctx[m]->slot_cap) continue;
+                double r = share[m] - b->pcount[m];
+                if (best < 0 || r > bestr) { best = m; bestr = r; }
+            }
+            if (best < 0) break;
+            ++b->pcount[best];
+        }
+        b->rcount.assign(nmodels, 1);
+        for (int m = 0; m < nmodels; ++m) b->rcount[m] = (b->ctx[m]->nobs + RES_NT_FX - 1) / RES_NT_FX;
+        std::vector<int> tab;
+        b->pgrid = 0;
+        for (int m = 0; m < nmodels; ++m) b->pgrid += b->pcount[m];
+        b->rgrid = 0;
+        for (int m = 0; m < nmodels; ++m) b->rgrid += b->rcount[m];
+        std::vector<int> pm_, pr_, rm_, rr_;
+        for (int m = 0; m < nmodels; ++m)
+            for (int k = 0; k < b->pcount[m]; ++k) { pm_.push_back(m); pr_.push_back(k); }
+        for (int m = 0; m < nmodels; ++m)
+            for (int k = 0; k < b->rcount[m]; ++k) { rm_.push_back(m); rr_.push_back(k); }
+        tab.insert(tab.end(), pm_.begin(), pm_.end());
+        tab.insert(tab.end(), pr_.begin(), pr_.end());
+        tab.insert(tab.end(), b->pcount.begin(), b->pcount.end());
+        tab.insert(tab.end(), rm_.begin(), rm_.end());
+        tab.insert(tab.end(), rr_.begin(), rr_.end());
+        tab.insert(tab.end(), b->rcount.begin(), b->rcount.end());
+        // table layout: pass [model(pgrid) | rank(pgrid) | count(nmodels)],
+        // then residual [model(rgrid) | rank(rgrid) | count(nmodels)]
+        e = cudaMalloc(&b->d_tab, sizeof(int) * tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_pass, sizeof(PassArgs) * nmodels);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_res, sizeof(ResArgs) * nmodels);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(long long));
+        if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(long long));
+        if (e != cudaSuccess) {
+            batch_free_all(b);
+            delete b;
+            return berr(nullptr, M2M_ERR_NOMEM, "batch tables: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = b;
+    return M2M_OK;
+}
+
+int m2m_batch_step(m2m_batch *b, int64_t nsteps) {
+    if (!b || nsteps < 0) return berr(b, M2M_ERR_ARG, "bad argument");
+    if (nsteps == 0) return M2M_OK;
+    bool pending = false;
+    for (m2m_ctx *c : b->ctx) pending |= c->pending;
+    if (!b->fusable || pending) {
+        for (int m = 0; m < b->nmodels; ++m) {
+            int rc = m2m_step(b->ctx[m], nsteps);
+            if (rc) return berr(b, rc, "model %d: %s", m, b->ctx[m]->err.c_str());
+        }
+        b->t += nsteps;
+        b->last_mode = 0;
+        return M2M_OK;
+    }
+    // cell caches valid for every model (their last pass scattered)?
+    bool cache_ok = true;
+    for (m2m_ctx *c : b->ctx) cache_ok &= c->cache_valid;
+    if (!cache_ok) {
+        for (m2m_ctx *c : b->ctx) {     // one scatter at the current state refreshes the caches
+            int rc = m2m_observe(c, 0);
+            if (rc) return berr(b, rc, "cache refresh: %s", c->err.c_str());
+        }
+    }
+    int rc = batch_upload(b);
+    if (rc) return rc;
+    // step counter of the records: the models' common step count
+    long long t0 = b->ctx[0]->t;
+    cudaError_t e = cudaMemcpyAsync(b->d_step, &t0, sizeof t0, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "step counter: %s", cudaGetErrorString(e));
+    const bool graphable = b->st != nullptr && b->st != cudaStreamLegacy && b->st != cudaStreamPerThread;
+    const auto key = std::make_tuple((long long)nsteps, b->period ? t0 % b->period : 0ll, 0);
+    bool launched = false;
+    if (graphable) {
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            for (m2m_ctx *c : b->ctx) c->timing = false;   // events are not captured
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = batch_sequence(b, nsteps, t0, false);
+                cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+                if (rc) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) {
+                b->graphs[key] = ge;
+                it = b->graphs.find(key);
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (it != b->graphs.end()) {
+            e = cudaGraphLaunch(it->second, b->st);
+            if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+            launched = true;
+            b->last_mode = 2;
+        }
+    }
+    if (!launched) {
+        rc = batch_sequence(b, nsteps, t0, false);
+        if (rc) return rc;
+        b->last_mode = 1;
+    }
+    for (int m = 0; m < b->nmodels; ++m) {
+        m2m_ctx *c = b->ctx[m];
+        c->t = t0 + nsteps;
+        c->pending = false;
+        c->cache_valid = true;
+        c->last_grid = b->pcount[m];
+    }
+    b->t += nsteps;
+    return M2M_OK;
+}
+
+int m2m_batch_context(m2m_batch *b, int32_t model, m2m_ctx **ctx_out) {
+    if (!b || !ctx_out || model < 0 || model >= b->nmodels) return berr(b, M2M_ERR_ARG, "bad model index");
+    *ctx_out = b->ctx[model];
+    return M2M_OK;
+}
+
+int m2m_batch_fused(const m2m_batch *b) { return b ? b->last_mode : -1; }
+
+int m2m_batch_free(m2m_batch *b) {
+    if (!b) return M2M_OK;
+    cudaStreamSynchronize(b->st);
+    batch_free_all(b);
+    delete b;
     return M2M_OK;
 }
 

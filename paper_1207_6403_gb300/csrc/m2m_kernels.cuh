@@ -399,8 +399,10 @@ template <class R> struct Chunk {
 };
 constexpr int PIPE_STAGES = 2;
 
-template <class R, int NT, int MINB, int L, int PIPE>
-__global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
+// One block's share of a pass over the particles of one model: block `bid`
+// of `nblk` blocks that share the model's particles (grid-stride).
+template <class R, int NT, int L, int PIPE>
+__device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, const int nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ __align__(8) unsigned long long bars[PIPE ? (NT / 32) * PIPE_STAGES : 1];
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
         unsigned char *wbuf = stages + (size_t)warp * PIPE_STAGES * C::BYTES;
         unsigned long long *wbar = &bars[warp * PIPE_STAGES];
         const int nfull = (int)(n >> 5), nch = (int)((n + 31) >> 5);
-        const int gw = blockIdx.x * (NT / 32) + warp, TW = gridDim.x * (NT / 32);
+        const int gw = bid * (NT / 32) + warp, TW = nblk * (NT / 32);
         const unsigned bytes = 6 * 32 * sizeof(R) + 256 + (need_what ? 256 : 0) + (need_cc ? 128 : 0);
         // per-stage bits: copies pending; parity of the next completion
         unsigned pendm = 0u, parm = 0u;
@@ -564,8 +566,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
             __syncwarp();
         }
     } else {
-        const int stride = gridDim.x * NT;
-        for (int i = blockIdx.x * NT + threadIdx.x; i < (int)n; i += stride) {
+        const int stride = nblk * NT;
+        for (int i = bid * NT + threadIdx.x; i < (int)n; i += stride) {
             R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
             R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
             double w = __ldcs(a.w + i);
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
             // exact block totals, either into the global totals with 64-bit
             // integer atomics or to this block's slot for the residual to sum;
             // integer sums, so the result does not depend on the order
-            long long *sl = (long long *)a.slots + (long long)blockIdx.x * nobs;
+            long long *sl = (long long *)a.slots + (long long)bid * nobs;
             for (int k = threadIdx.x; k < nobs; k += NT) {
                 const long long v = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
                 if (v >= (1ll << 53) || v <= -(1ll << 53)) t.ovf = true;
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
                 }
             }
         } else {
-            double *sl = (double *)a.slots + (long long)blockIdx.x * nobs;
+            double *sl = (double *)a.slots + (long long)bid * nobs;
             for (int k = threadIdx.x; k < nobs; k += NT) sl[k] = S.h_d[k];
         }
     }
@@ -627,8 +629,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
         double s_tot = block_sum(sv, red);
         double w_tot = block_sum(wv, red);
         if (threadIdx.x == 0) {
-            a.stat_slots[2 * blockIdx.x] = s_tot;
-            a.stat_slots[2 * blockIdx.x + 1] = w_tot;
+            a.stat_slots[2 * bid] = s_tot;
+            a.stat_slots[2 * bid + 1] = w_tot;
         }
     }
     if (fl & F_MINMAX) {
@@ -647,12 +649,42 @@ __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassA
             for (int k = 1; k < NT / 32; ++k) {
                 e0 = fmin(e0, mm[0][k]); e1 = fmax(e1, mm[1][k]); l2 = fmax(l2, mm[2][k]);
             }
-            R *o = (R *)a.mm_slots + 4 * blockIdx.x;
+            R *o = (R *)a.mm_slots + 4 * bid;
             o[0] = e0; o[1] = e1; o[2] = l2; o[3] = R(0);
         }
     }
     if (t.ovf) atomicOr(a.err, ERR_OVERFLOW);
     if (t.bad) atomicOr(a.err, ERR_NONFINITE);
+}
+
+template <class R, int NT, int MINB, int L, int PIPE>
+__global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
+    pass_body<R, NT, L, PIPE>(a, blockIdx.x, gridDim.x);
+}
+
+// Many models in one launch: block b runs block blk_rank[b] of
+// blk_count[m] blocks of model m = blk_model[b]; each model's arguments are
+// its own PassArgs (device array), the flags and cache use are shared.
+struct BatchPass {
+    const PassArgs *models;
+    const int *blk_model, *blk_rank, *blk_count;
+    int flags, cache_read, cache_write;
+};
+template <class R, int NT, int MINB, int L>
+__global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__ BatchPass b) {
+    const int m = b.blk_model[blockIdx.x];
+    __shared__ __align__(16) PassArgs a;
+    static_assert(sizeof(PassArgs) % 4 == 0, "PassArgs copied as words");
+    const unsigned *src = (const unsigned *)(b.models + m);
+    for (int k = threadIdx.x; k < (int)(sizeof(PassArgs) / 4); k += NT) ((unsigned *)&a)[k] = src[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.flags = b.flags;
+        a.cache_read = b.cache_read;
+        a.cache_write = b.cache_write;
+    }
+    __syncthreads();
+    pass_body<R, NT, L, 0>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
 #ifdef M2M_COMMON_KERNELS
@@ -688,7 +720,7 @@ __device__ __forceinline__ double block_sum_strided(const double *v, int stride,
 // writes the record.
 constexpr int RES_NT = 1024;      // slot reduction
 constexpr int RES_NT_FX = 128;    // FP32C atomic totals
-__global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ ResArgs a) {
+__device__ __forceinline__ void residual_body(const ResArgs &a, const int bid, const int nblk) {
     constexpr int NW = RES_NT / 32;
     __shared__ unsigned long long si[NW][32];
     __shared__ double sd[NW][32];
@@ -697,7 +729,7 @@ __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ Res
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const bool direct = a.fixed && a.fx_atomic;
-    const int j = direct ? blockIdx.x * blockDim.x + threadIdx.x : blockIdx.x * 32 + lane;
+    const int j = direct ? bid * blockDim.x + threadIdx.x : bid * 32 + lane;
     bool have = false;
     double yv = 0.0;
     if (direct) {
@@ -768,11 +800,11 @@ __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ Res
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         for (int k = 0; k < nw; ++k) { s0 += wred[0][k]; s1 += wred[1][k]; s2 = fmax(s2, wred[2][k]); }
-        a.chi_slots[3 * blockIdx.x] = s0;
-        a.chi_slots[3 * blockIdx.x + 1] = s1;
-        a.chi_slots[3 * blockIdx.x + 2] = s2;
+        a.chi_slots[3 * bid] = s0;
+        a.chi_slots[3 * bid + 1] = s1;
+        a.chi_slots[3 * bid + 2] = s2;
         __threadfence();
-        s_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+        s_last = (atomicAdd(a.ticket, 1u) == (unsigned)nblk - 1u);
     }
     __syncthreads();
     if (!s_last) return;
@@ -780,7 +812,7 @@ __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ Res
     // one strided pass over the block partials, one fixed-shape reduction of
     // the five totals (deterministic: the shape depends only on the sizes)
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
         v0 += a.chi_slots[3 * b];
         v1 += a.chi_slots[3 * b + 1];
         v2 = fmax(v2, a.chi_slots[3 * b + 2]);
@@ -815,6 +847,35 @@ __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ Res
         if (!(isfinite(C2) && isfinite(S) && isfinite(W))) atomicOr(a.err, ERR_NONFINITE);
         *a.ticket = 0u;
     }
+}
+
+__global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ ResArgs a) {
+    residual_body(a, blockIdx.x, gridDim.x);
+}
+
+// Residuals of many models in one launch (FP32C totals: one thread per
+// observable); per-model arguments in a device array, step fields shared.
+struct BatchRes {
+    const ResArgs *models;
+    const int *blk_model, *blk_rank, *blk_count;
+    int mode, write_ring;
+    long long rec_step;           // added to *step (records stay right when a graph replays)
+    const long long *step;
+};
+__global__ void __launch_bounds__(RES_NT_FX) k_residual_batch(const __grid_constant__ BatchRes b) {
+    const int m = b.blk_model[blockIdx.x];
+    __shared__ __align__(16) ResArgs a;
+    static_assert(sizeof(ResArgs) % 4 == 0, "ResArgs copied as words");
+    const unsigned *src = (const unsigned *)(b.models + m);
+    for (int k = threadIdx.x; k < (int)(sizeof(ResArgs) / 4); k += blockDim.x) ((unsigned *)&a)[k] = src[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.mode = b.mode;
+        a.write_ring = b.write_ring;
+        a.rec_step = b.rec_step + *b.step;
+    }
+    __syncthreads();
+    residual_body(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
 // 1/sigma_j (0 where sigma_j <= 0: masked observable)
@@ -865,6 +926,7 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
 // Kernel tables, one per precision, each in its own translation unit.
 void *pass_kernel_f32(int threads, int layout);
 void *pass_kernel_f32_pipe(int layout);
+void *pass_kernel_f32_batch(int layout);
 void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();

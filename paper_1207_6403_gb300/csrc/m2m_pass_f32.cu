@@ -32,6 +32,16 @@ void *pass_kernel_f32_pipe(int layout) {
     }
 }
 
+// All models of a batch in one launch (compiled layouts, plain loads).
+void *pass_kernel_f32_batch(int layout) {
+    switch (layout) {
+        case 1: return (void *)k_pass_batch<float, 1024, 1, 1>;
+        case 2: return (void *)k_pass_batch<float, 1024, 1, 2>;
+        case 3: return (void *)k_pass_batch<float, 1024, 1, 3>;
+        default: return (void *)k_pass_batch<float, 1024, 1, 0>;
+    }
+}
+
 void *cells_kernel_f32() { return (void *)k_cells<float>; }
 
 }  // namespace m2m

@@ -25,7 +25,8 @@ in integral-of-motion space) at the sizes of the five benchmark workloads:
   moving-priors N=1,000,000 Hernquist, 100 shells + 60 annuli x h0..h4, (E, L^2/Lc^2) priors
   flat-log      N=4,000,000 flattened logarithmic potential at 60 deg, 64x64 pixels +
                 20x20 apertures x h0..h4, (E, L_z) priors
-  batched       48 Hernquist+NFW models of uneven N (not built by this module yet)
+  batched       48 Hernquist+NFW models, N log-uniform in [1e5, 2e6], halo grid
+                (M_h/M_*, r_s/a) of 6 x 8, each with its own targets (make_batch)
   sh-selfcons   8,000,000-particle disc+bulge with a spherical-harmonic potential
                 (not built by this module yet)
 """
@@ -41,7 +42,7 @@ __all__ = [
     "PotentialComponent", "ObservableSet", "PriorSpec", "Problem",
     "rng", "hernquist_positions", "hernquist_isotropic", "hernquist_om_target",
     "log_flattened_realisation", "log_shell_edges", "uniform_edges",
-    "error_model", "make_problem", "WORKLOADS",
+    "error_model", "make_problem", "make_batch", "WORKLOADS",
 ]
 
 
@@ -475,3 +476,74 @@ def make_problem(name, n=None, precision=None, seed_model=None,
                    eps=0.05 / nominal, mu=1e-3, dt=0.01, alpha=0.02, prior=prior,
                    nsteps=steps, precision=prec, target_pos=tp, target_vel=tv,
                    target_w=tw)
+
+
+# --------------------------------------------------------------------------
+# Batched trial potentials: Hernquist stars in Hernquist + NFW potentials
+# --------------------------------------------------------------------------
+def nfw_rho_s(mass_ratio, r_s, M_star=1.0):
+    """rho_s of an NFW halo whose mass inside 10 r_s is mass_ratio * M_star."""
+    c = 10.0
+    return mass_ratio * M_star / (4 * math.pi * r_s ** 3 * (math.log1p(c) - c / (1 + c)))
+
+
+def _nfw_mass(r, rho_s, r_s):
+    u = r / r_s
+    return 4 * math.pi * rho_s * r_s ** 3 * (np.log1p(u) - u / (1 + u))
+
+
+def hernquist_in_halo(n, seed, rho_s, r_s, ra=None, GM=1.0, a=1.0, rmax=100.0):
+    """Hernquist tracer (positions by inverse CDF) with Gaussian velocities
+    from the Jeans equation in the Hernquist + NFW potential (isotropic, or
+    Osipkov-Merritt-like beta = r^2/(r^2 + ra^2))."""
+    pos, r, g = hernquist_positions(n, seed, GM, a, rmax)
+    rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x, GM, a),
+                                   lambda x: _hernquist_mass(x, GM, a) + _nfw_mass(x, rho_s, r_s), ra=ra)
+    sr = np.sqrt(_Interp(rr, s2)(r))
+    if ra is None:
+        st = sr
+    else:
+        st = np.sqrt(1.0 - r * r / (r * r + ra * ra)) * sr
+    vel = _spherical_gaussian_velocities(g, pos, r, sr, st)
+    return pos, vel
+
+
+HALO_MASS_RATIOS = (0.5, 1.0, 2.0, 4.0, 8.0, 16.0)
+HALO_RS = tuple(float(v) for v in np.geomspace(1.0, 20.0, 8))
+
+
+def make_batch(nmodels=48, n_lo=100_000, n_hi=2_000_000, seed=7, n_scale=1.0, precision="fp32c",
+               with_target=True):
+    """The batched workload: model m uses halo (HALO_MASS_RATIOS[m // 8],
+    HALO_RS[m % 8]) (the 6 x 8 grid for 48 models), N_m = floor(exp(U(ln
+    n_lo, ln n_hi))) from one seeded stream (times n_scale for reduced
+    tests), model seed 1000 + m and target seed 2000 + m (Osipkov-Merritt-
+    like r_a = 1), observables as the moving-prior workload (100 shells +
+    60 annuli x h0..h4), flat priors, eps = 0.05 / N_m (nominal N)."""
+    g = rng(seed)
+    Ns = np.floor(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), nmodels))).astype(np.int64)
+    out = []
+    for m in range(nmodels):
+        ratio = HALO_MASS_RATIOS[(m // 8) % len(HALO_MASS_RATIOS)]
+        r_s = HALO_RS[m % 8]
+        rho_s = nfw_rho_s(ratio, r_s)
+        n = max(1, int(Ns[m] * n_scale))
+        pos, vel = hernquist_in_halo(n, 1000 + m, rho_s, r_s)
+        tp = tv = tw = None
+        if with_target:
+            tp, tv = hernquist_in_halo(n, 2000 + m, rho_s, r_s, ra=1.0)
+            tw = np.full(n, 1.0 / n)
+        e = log_shell_edges(60, 0.05, 20.0)
+        rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+        rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x), lambda x: _hernquist_mass(x) + _nfw_mass(x, rho_s, r_s))
+        S = np.sqrt(_Interp(rr, s2)(rmid))
+        obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+               ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
+        pot = [PotentialComponent("hernquist", (1.0, 1.0)), PotentialComponent("nfw", (rho_s, r_s))]
+        w0 = np.full(n, 1.0 / n)
+        out.append(Problem(name=f"batched-{m}", n=n, pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel),
+                           w0=w0, what0=w0.copy(), potential=pot, obs=obs, incl_sin=0.0, incl_cos=1.0,
+                           eps=0.05 / int(Ns[m]), mu=1e-3, dt=0.01, alpha=0.02, prior=PriorSpec("flat"),
+                           nsteps=1000, precision=precision, target_pos=tp, target_vel=tv, target_w=tw,
+                           meta={"mass_ratio": ratio, "r_s": r_s, "rho_s": rho_s, "N_nominal": int(Ns[m])}))
+    return out

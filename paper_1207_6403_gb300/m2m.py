@@ -54,6 +54,15 @@ class m2m_timing(ctypes.Structure):
     _fields_ = [("launches", c_int64 * TK_N), ("ms", c_double * TK_N), ("kernels_total", c_int64)]
 
 
+class m2m_model_desc(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("x", c_void_p), ("y", c_void_p), ("z", c_void_p), ("vx", c_void_p),
+                ("vy", c_void_p), ("vz", c_void_p), ("w", c_void_p), ("what", c_void_p),
+                ("pot", POINTER(m2m_potential_desc)), ("npot", c_int32),
+                ("obs", POINTER(m2m_obs_desc)), ("nsets", c_int32),
+                ("Y", POINTER(c_double)), ("sigma", POINTER(c_double)), ("eps", c_double),
+                ("prior", POINTER(m2m_prior_desc))]
+
+
 class m2m_record(ctypes.Structure):
     _fields_ = [("step", c_int64), ("chi2", c_double), ("chi2_raw", c_double), ("S", c_double),
                 ("sum_w", c_double), ("F", c_double), ("max_abs_dt", c_double)]
@@ -100,6 +109,12 @@ def library():
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
                                          c_double, c_double, c_double, P, P]),
+        "m2m_batch_init": (c_int32, [POINTER(P), c_int32, c_int32, POINTER(m2m_model_desc),
+                                     POINTER(m2m_params), P]),
+        "m2m_batch_step": (c_int32, [P, c_int64]),
+        "m2m_batch_context": (c_int32, [P, c_int32, POINTER(P)]),
+        "m2m_batch_fused": (c_int32, [P]),
+        "m2m_batch_free": (c_int32, [P]),
         "m2m_last_error": (ctypes.c_char_p, [P]),
         "m2m_free": (c_int32, [P]),
     }
@@ -130,7 +145,8 @@ def _dptr(a):
 class Context:
     """A library context plus the tensors and host tables it borrows."""
 
-    def __init__(self, ptr, tensors, keep, nobs, precision):
+    def __init__(self, ptr, tensors, keep, nobs, precision, owned=True):
+        self.owned = owned
         self.ptr = ptr
         self.t = tensors          # dict name -> torch tensor (device)
         self._keep = keep
@@ -217,9 +233,9 @@ class Context:
                 "kernels_total": t.kernels_total}
 
     def m2m_free(self):
-        if self.ptr:
+        if self.ptr and self.owned:
             library().m2m_free(self.ptr)
-            self.ptr = None
+        self.ptr = None
 
     def __del__(self):
         try:
@@ -374,3 +390,112 @@ def m2m_observe_static(pos, vel, w, obs, incl_sin, incl_cos, weight_scale, y_out
     rc = lib.m2m_observe_static(int(w.shape[0]), *ptrs, od, len(obs), float(incl_sin), float(incl_cos),
                                 float(weight_scale), c_void_p(y_out.data_ptr()), c_void_p(st))
     _check(rc, None)
+
+
+def _obs_array(obs, keep):
+    od = (m2m_obs_desc * len(obs))()
+    for k, s in enumerate(obs):
+        ex = np.ascontiguousarray(s.edges_x, dtype=np.float64)
+        keep.append(ex)
+        od[k].geom, od[k].quant = GEOM[s.geom], QUANT[s.quant]
+        od[k].nx, od[k].ny = len(ex) - 1, (1 if s.edges_y is None else len(s.edges_y) - 1)
+        od[k].edges_x = _dptr(ex)
+        if s.edges_y is not None:
+            ey = np.ascontiguousarray(s.edges_y, dtype=np.float64)
+            keep.append(ey)
+            od[k].edges_y = _dptr(ey)
+        if s.quant == "gh":
+            V = np.ascontiguousarray(s.gh_V, dtype=np.float64)
+            S = np.ascontiguousarray(s.gh_S, dtype=np.float64)
+            keep += [V, S]
+            od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
+        od[k].sigma_kernel = float(s.sigma_kernel)
+    keep.append(od)
+    return od
+
+
+class Batch:
+    """Several models advanced together (m2m_batch_*)."""
+
+    def __init__(self, ptr, tensors, keep, problems, precision, stream):
+        self.ptr = ptr
+        self.t = tensors
+        self._keep = keep
+        self.problems = problems
+        self.precision = precision
+        self.stream = stream
+
+    def m2m_batch_step(self, nsteps=1):
+        _check(library().m2m_batch_step(self.ptr, nsteps), None)
+
+    def m2m_batch_fused(self):
+        return library().m2m_batch_fused(self.ptr)
+
+    def m2m_batch_context(self, m):
+        cp = c_void_p()
+        _check(library().m2m_batch_context(self.ptr, m, byref(cp)), None)
+        P = self.problems[m]
+        return Context(cp, self.t[m], {"nsets": len(P.obs)}, P.nobs, self.precision, owned=False)
+
+    def m2m_batch_free(self):
+        if self.ptr:
+            library().m2m_batch_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.m2m_batch_free()
+        except Exception:
+            pass
+
+
+def m2m_batch_init(precision, problems, device="cuda:0", stream=None, targets=True):
+    """A batch over inputs.Problem models (their own potentials, observables,
+    targets, priors and eps).  Uses a dedicated non-default stream by default
+    so that the step sequence can be captured in a CUDA graph."""
+    import torch
+    lib = library()
+    prec = {"fp64": FP64, "fp32c": FP32C}[precision] if isinstance(precision, str) else precision
+    dt = torch.float64 if prec == FP64 else torch.float32
+    dev = torch.device(device)
+    stream = stream or torch.cuda.Stream(device=dev)
+    keep, tensors = [], []
+    md = (m2m_model_desc * len(problems))()
+    for m, P in enumerate(problems):
+        t = {}
+        for k, name in enumerate(("x", "y", "z")):
+            t[name] = torch.as_tensor(np.asarray(P.pos[k])).to(device=dev, dtype=dt).contiguous().clone()
+        for k, name in enumerate(("vx", "vy", "vz")):
+            t[name] = torch.as_tensor(np.asarray(P.vel[k])).to(device=dev, dtype=dt).contiguous().clone()
+        t["w"] = torch.as_tensor(P.w0).to(device=dev, dtype=torch.float64).contiguous().clone()
+        t["what"] = torch.as_tensor(P.what0).to(device=dev, dtype=torch.float64).contiguous().clone()
+        tensors.append(t)
+        pot, npot = _pot_array(P.potential)
+        keep.append(pot)
+        od = _obs_array(P.obs, keep)
+        d = md[m]
+        d.n = P.n
+        d.x, d.y, d.z = t["x"].data_ptr(), t["y"].data_ptr(), t["z"].data_ptr()
+        d.vx, d.vy, d.vz = t["vx"].data_ptr(), t["vy"].data_ptr(), t["vz"].data_ptr()
+        d.w, d.what = t["w"].data_ptr(), t["what"].data_ptr()
+        d.pot, d.npot = pot, npot
+        d.obs, d.nsets = od, len(P.obs)
+        if targets and P.Y is not None:
+            Y = np.ascontiguousarray(P.Y, dtype=np.float64)
+            sg = np.ascontiguousarray(P.sigma, dtype=np.float64)
+            keep += [Y, sg]
+            d.Y, d.sigma = _dptr(Y), _dptr(sg)
+        d.eps = float(P.eps)
+        if P.prior is not None and P.prior.kind != "flat":
+            pd = m2m_prior_desc(PRIOR[P.prior.kind], P.prior.nE, P.prior.nL, P.prior.period,
+                                float(P.prior.hernquist[0]), float(P.prior.hernquist[1]))
+            keep.append(pd)
+            d.prior = ctypes.pointer(pd)
+    P0 = problems[0]
+    par = m2m_params(eps=0.0, mu=P0.mu, dt=P0.dt, alpha=P0.alpha, entropy_const=P0.entropy_const,
+                     incl_sin=P0.incl_sin, incl_cos=P0.incl_cos)
+    keep += [md, par]
+    torch.cuda.synchronize(dev)
+    ptr = c_void_p()
+    _check(lib.m2m_batch_init(byref(ptr), prec, len(problems), md, byref(par), c_void_p(stream.cuda_stream)), None)
+    return Batch(ptr, tensors, keep, problems, prec, stream)
