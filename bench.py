@@ -9,6 +9,11 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload flat-log|batched]
+
+--workload batched times the 48 trial-potential models (Hernquist stars in
+Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
+3e7 particles in all) advanced together by m2m_batch_step.
 
 Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
 FP64 GPU path is measured on the same box and reported under "fp64_gpu".
@@ -365,6 +370,66 @@ def run_ours(args, D):
         print(json.dumps(line), flush=True)
 
 
+def run_batched(args, D):
+    import torch
+    from paper_1207_6403_gb300 import inputs as I
+    from paper_1207_6403_gb300 import m2m as B
+    dev = f"cuda:{D.local}"
+    torch.cuda.set_device(dev)
+    problems = I.make_batch(nmodels=48, seed=7 + 1000 * D.rank)
+    for k, P in enumerate(problems):
+        Y = B.observe_targets(P, "fp32c", dev)
+        problems[k] = P.with_targets(Y)
+    ntot = sum(P.n for P in problems)
+    bt = B.m2m_batch_init("fp32c", problems, device=dev)
+    st = bt.stream
+    steps = args.steps if args.steps_given else 2000
+    with torch.cuda.stream(st):
+        bt.m2m_batch_step(args.warmup)
+        torch.cuda.synchronize()
+        clocks = Clocks(D.local)
+        clocks.start()
+        D.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.time()
+        e0.record(st)
+        bt.m2m_batch_step(steps)
+        e1.record(st)
+        torch.cuda.synchronize()
+        w1 = time.time()
+        clocks.stop()
+    fused = bt.m2m_batch_fused()
+    ms = D.max(e0.elapsed_time(e1))
+    value = D.world * ntot * steps / (ms * 1e-3)
+    peak, peak_kind = peaks()
+    # the step's algorithmic traffic: 72 B per particle-step over all models
+    achieved = BYTES_PER_PARTICLE_FP32C * ntot * steps / (ms * 1e-3) / 1e9
+    cpu = None
+    if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
+        rate, ns, secs = time_oracle(problems[0], 3, 4)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"every 4th particle of model 0 ({ns:,} of {problems[0].n:,}), 3 oracle steps "
+                         f"({secs:.1f} s)"}
+    if D.rank == 0:
+        line = {"metric": "M2M particle-steps/s, 48 batched trial-potential models", "value": value,
+                "unit": "particle-steps/s", "n_gpus": D.world, "steps": steps, "warmup": args.warmup,
+                "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (FP32-compensated; f64 weights)", "data": "synthetic",
+                "config": {"workload": "batched: 48 models, Hernquist stars in Hernquist + NFW halos "
+                                       "(M_h/M_* x r_s/a = 6 x 8 grid), N log-uniform in [1e5, 2e6], "
+                                       "100 shells + 60 annuli x h0..h4 each, flat priors",
+                           "models": len(problems), "global_particles": ntot * D.world,
+                           "launch": {2: "one launch per stage, CUDA graph", 1: "one launch per stage",
+                                      0: "model by model"}[fused]},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "whole step (batched k_pass + batched residual), 72 B/particle",
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+                "cpu_baseline": cpu, "clocks": clocks.summary(w0, w1)}
+        print(json.dumps(line), flush=True)
+    bt.m2m_batch_free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,13 +438,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched"])
     args = ap.parse_args()
+    args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
     if args.warmup < 3:
         args.warmup = 3
     D = Dist()
     try:
         if args.impl == "reference":
             run_reference(args, D)
+        elif args.workload == "batched":
+            run_batched(args, D)
         else:
             run_ours(args, D)
     finally:
