@@ -9,7 +9,9 @@ integral-of-motion space.
 
 One step t -> t+1, in this order:
 
-1. push      KDK leapfrog: v += dt/2 a(x); x += dt v; v += dt/2 a(x)
+1. push      KDK leapfrog: v += dt/2 a(x); x += dt v; v += dt/2 a(x) (a from
+             analytic components and, optionally, a spherical-harmonic
+             expansion of the particles themselves, see :mod:`oracle.sh`)
 2. observe   y_j = sum_i w_i K_j(x_i, v_i) at the new positions, old weights
 3. residual  Delta_j = (y_j - Y_j)/sigma_j (0 where sigma_j <= 0);
              Delta~_j <- alpha Delta_j + (1-alpha) Delta~_j;
@@ -18,7 +20,9 @@ One step t -> t+1, in this order:
              w_i <- w_i exp(eps dt G_i)   (c = 1: the derivative of Eq. 2)
 5. priors    if moving and (t+1) % period == 0: w_hat_i = mean w over the
              cell of i, cells from (x_{t+1}, v_{t+1}), weights w_{t+1}
-6. record    S_t, sum w_t (the weights that produced y), F_t = -chi2/2 + mu S_t
+6. potential if it has a spherical-harmonic part and (t+1) % its period == 0:
+             recompute its tables from (x_{t+1}, w_{t+1})
+7. record    S_t, sum w_t (the weights that produced y), F_t = -chi2/2 + mu S_t
 
 At initialisation Delta~ := Delta of an observe at (x_0, w_0).
 
@@ -33,7 +37,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import gh as _gh
-from .potentials import acceleration, potential
+from . import sh as _sh
+from .potentials import acceleration as _analytic_acceleration
+from .potentials import potential as _analytic_potential
 
 
 def state_dtype(precision):
@@ -41,23 +47,61 @@ def state_dtype(precision):
 
 
 # --------------------------------------------------------------------------
+# potential: analytic components plus, optionally, a self-consistent
+# spherical-harmonic component (kind 'sh', params (K, rmin, rmax, period),
+# last in the list) whose tables are part of the state
+# --------------------------------------------------------------------------
+def _split(comps):
+    an = [c for c in comps if c.kind != "sh"]
+    sh = [c for c in comps if c.kind == "sh"]
+    return an, (sh[0] if sh else None)
+
+
+def sh_tables(x, y, z, w, comp):
+    """(F, D, nodes) of the expansion of the weighted particles."""
+    K, rmin, rmax = int(comp.params[0]), comp.params[1], comp.params[2]
+    rn = _sh.nodes(rmin, rmax, K)
+    A, B = _sh.coefficients(x, y, z, w, rn)
+    F, D = _sh.tables(A, B, rn)
+    return F, D, rn
+
+
+def acceleration(x, y, z, comps, sh=None):
+    """Analytic components in order, then the expansion (float64, rounded
+    to the state precision) if the potential has one."""
+    ax, ay, az = _analytic_acceleration(x, y, z, _split(comps)[0])
+    if sh is not None:
+        T = x.dtype.type
+        bx, by, bz = _sh.acceleration(x, y, z, *sh)
+        ax, ay, az = ax + bx.astype(T), ay + by.astype(T), az + bz.astype(T)
+    return ax, ay, az
+
+
+def potential(x, y, z, comps, sh=None):
+    phi = _analytic_potential(x, y, z, _split(comps)[0])
+    if sh is not None:
+        phi = phi + _sh.potential(x, y, z, *sh).astype(x.dtype)
+    return phi
+
+
+# --------------------------------------------------------------------------
 # 1. push
 # --------------------------------------------------------------------------
-def kdk(x, y, z, vx, vy, vz, comps, dt):
+def kdk(x, y, z, vx, vy, vz, comps, dt, sh=None):
     """One kick-drift-kick step in the dtype of the arrays; returns new arrays.
 
     dt/2 and dt are rounded once from float64 to the state precision."""
     T = x.dtype.type
     h = T(np.float64(0.5) * np.float64(dt))
     d = T(dt)
-    ax, ay, az = acceleration(x, y, z, comps)
+    ax, ay, az = acceleration(x, y, z, comps, sh)
     vx = vx + h * ax
     vy = vy + h * ay
     vz = vz + h * az
     x = x + d * vx
     y = y + d * vy
     z = z + d * vz
-    ax, ay, az = acceleration(x, y, z, comps)
+    ax, ay, az = acceleration(x, y, z, comps, sh)
     vx = vx + h * ax
     vy = vy + h * ay
     vz = vz + h * az
@@ -202,7 +246,7 @@ def _count_edges_le(v, lo, hi, ncell):
     return np.where(np.isnan(vd), 0, cnt).astype(np.int64)
 
 
-def prior_cells(x, y, z, vx, vy, vz, prior, comps):
+def prior_cells(x, y, z, vx, vy, vz, prior, comps, sh=None):
     """Cell of every particle in integral-of-motion space (Section 2.1).
 
     Computed in the state precision, in this order:
@@ -220,7 +264,7 @@ def prior_cells(x, y, z, vx, vy, vz, prior, comps):
     T = x.dtype.type
     v2 = (vx * vx + vy * vy) + vz * vz
     with np.errstate(divide="ignore", invalid="ignore"):
-        E = T(0.5) * v2 + potential(x, y, z, comps)
+        E = T(0.5) * v2 + potential(x, y, z, comps, sh)
         if prior.kind == "e_lz":
             Lz = x * vy - y * vx
             lo, hi = np.float64(E.min()), np.float64(E.max())
@@ -276,6 +320,7 @@ class State:
     y_obs: np.ndarray = None
     Delta: np.ndarray = None
     history: list = field(default_factory=list)
+    sh: tuple = None
 
     @property
     def pos(self):
@@ -298,7 +343,11 @@ def init(problem, precision=None):
                  problem.incl_cos)
     Delta, Dt, coef, _, _ = residual(yv, problem.Y, problem.sigma, None,
                                      problem.alpha, True)
-    return State(x, y, z, vx, vy, vz, w, what, Dt, coef, 0, yv, Delta)
+    st = State(x, y, z, vx, vy, vz, w, what, Dt, coef, 0, yv, Delta)
+    shc = _split(problem.potential)[1]
+    if shc is not None:
+        st.sh = sh_tables(x, y, z, w, shc)
+    return st
 
 
 def step(st, problem, push=True):
@@ -309,7 +358,7 @@ def step(st, problem, push=True):
     sumw_t = float(np.sum(st.w))
     if push:
         st.x, st.y, st.z, st.vx, st.vy, st.vz = kdk(
-            st.x, st.y, st.z, st.vx, st.vy, st.vz, P.potential, P.dt)
+            st.x, st.y, st.z, st.vx, st.vy, st.vz, P.potential, P.dt, st.sh)
     kern = cells_and_kernels(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.obs,
                              P.incl_sin, P.incl_cos)
     yv = observe_from(kern, w_used, P.obs)
@@ -321,8 +370,11 @@ def step(st, problem, push=True):
     st.t += 1
     if P.prior.kind != "flat" and st.t % P.prior.period == 0:
         cells = prior_cells(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.prior,
-                            P.potential)
+                            P.potential, st.sh)
         st.what = prior_means(st.w, cells, P.prior.ncells)
+    shc = _split(P.potential)[1]
+    if shc is not None and st.t % int(shc.params[3]) == 0:
+        st.sh = sh_tables(st.x, st.y, st.z, st.w, shc)
     st.Dt, st.coef, st.y_obs, st.Delta = Dt, coef, yv, Delta
     rec = dict(t=st.t, chi2=chi2, chi2_raw=chi2_raw, S=S_t, sum_w=sumw_t,
                F=merit(chi2, S_t, P.mu))

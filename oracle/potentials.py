@@ -86,6 +86,8 @@ def acceleration(x, y, z, comps):
                 ax = ax + (-(f * x))
                 ay = ay + (-(f * y))
                 az = az + (-(f * z))
+            elif c.kind == "sh":
+                raise ValueError("the spherical-harmonic component needs the particles: use oracle.m2m")
             else:
                 raise ValueError(f"unknown potential kind {c.kind!r}")
     return ax, ay, az

@@ -27,8 +27,9 @@ in integral-of-motion space) at the sizes of the five benchmark workloads:
                 20x20 apertures x h0..h4, (E, L_z) priors
   batched       48 Hernquist+NFW models, N log-uniform in [1e5, 2e6], halo grid
                 (M_h/M_*, r_s/a) of 6 x 8, each with its own targets (make_batch)
-  sh-selfcons   8,000,000-particle disc+bulge with a spherical-harmonic potential
-                (not built by this module yet)
+  sh-selfcons   N=8,000,000 Miyamoto-Nagai disc + Hernquist bulge (1:3) moving in
+                the spherical-harmonic expansion of their own weighted mass,
+                recomputed every 50 steps; observables as moving-priors, flat priors
 """
 from __future__ import annotations
 
@@ -42,7 +43,7 @@ __all__ = [
     "PotentialComponent", "ObservableSet", "PriorSpec", "Problem",
     "rng", "hernquist_positions", "hernquist_isotropic", "hernquist_om_target",
     "log_flattened_realisation", "log_shell_edges", "uniform_edges",
-    "error_model", "make_problem", "make_batch", "WORKLOADS",
+    "error_model", "make_problem", "make_batch", "WORKLOADS", "disc_bulge_realisation",
 ]
 
 
@@ -56,6 +57,11 @@ class PotentialComponent:
     kind 'hernquist': params (GM, a)           Phi = -GM/(r+a)
     kind 'nfw':       params (rho_s, r_s)      Phi = -4 pi rho_s r_s^3 ln(1+r/r_s)/r
     kind 'log':       params (v0, Rc, q)       Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)
+    kind 'sh':        params (K, rmin, rmax, period)
+                      the potential of the weighted particles themselves,
+                      expanded in even Legendre multipoles l <= 8 on K
+                      log-spaced radial nodes in [rmin, rmax] and recomputed
+                      every `period` steps (at most one, listed last)
     """
     kind: str
     params: tuple
@@ -362,6 +368,68 @@ def log_flattened_realisation(n, seed, v0=1.0, Rc=0.1, q=0.8, mmax=5.0,
 # --------------------------------------------------------------------------
 # Edge tables and the error model
 # --------------------------------------------------------------------------
+# --------------------------------------------------------------------------
+# Disc + bulge: Miyamoto & Nagai (1975) disc and a Hernquist bulge, G = 1
+# --------------------------------------------------------------------------
+def miyamoto_nagai_rho(R, z, M=1.0, a=1.0, b=0.2):
+    zeta = np.sqrt(z * z + b * b)
+    s = a + zeta
+    return (b * b * M / (4 * math.pi)) * (a * R * R + (a + 3 * zeta) * s * s) / (
+        (R * R + s * s) ** 2.5 * zeta ** 3)
+
+
+def _mn_positions(g, n, M, a, b, Rmax=30.0, zmax=30.0, nR=600, nz=400):
+    """Positions drawn from the Miyamoto-Nagai density truncated at R < Rmax,
+    |z| < zmax: a cell of a (log R, asinh(z/b)) grid by the cumulative mass
+    of the grid, then uniform in area and height inside the cell."""
+    Re = np.concatenate([[0.0], np.geomspace(1e-3, Rmax, nR)])
+    ze = b * np.sinh(np.linspace(0.0, math.asinh(zmax / b), nz + 1))
+    Rm = 0.5 * (Re[1:] + Re[:-1])
+    zm = 0.5 * (ze[1:] + ze[:-1])
+    area = math.pi * (Re[1:] ** 2 - Re[:-1] ** 2)
+    mass = miyamoto_nagai_rho(Rm[:, None], zm[None, :], M, a, b) * area[:, None] * np.diff(ze)[None, :]
+    cdf = np.cumsum(mass.ravel())
+    cdf /= cdf[-1]
+    cell = np.minimum(np.searchsorted(cdf, g.uniform(0.0, 1.0, n), side="right"), cdf.size - 1)
+    iR, iz = np.divmod(cell, nz)
+    R = np.sqrt(Re[iR] ** 2 + g.uniform(0.0, 1.0, n) * (Re[iR + 1] ** 2 - Re[iR] ** 2))
+    z = (ze[iz] + g.uniform(0.0, 1.0, n) * (ze[iz + 1] - ze[iz])) * np.where(g.uniform(0.0, 1.0, n) < 0.5, -1.0, 1.0)
+    phi = g.uniform(0.0, 2 * math.pi, n)
+    return R, phi, z
+
+
+def disc_bulge_realisation(n, seed, disc_frac=0.25, Md_a=1.0, Md_b=0.2, bulge_a=0.3, rmax=30.0):
+    """Disc + bulge of total mass 1 (disc : bulge = 1 : 3 by default), sorted
+    by radius.  Disc: Miyamoto-Nagai (a, b), v = v_c(R) e_phi + N(0, (0.1
+    v_c)^2) per component, v_c from the midplane forces of both components.
+    Bulge: Hernquist (a) with isotropic Gaussian velocities from the Jeans
+    equation in the bulge mass plus the disc mass taken as spherical,
+    M_d r^3 / (r^2 + (a+b)^2)^(3/2)."""
+    Md = disc_frac
+    Mb = 1.0 - Md
+    nd = int(round(n * disc_frac))
+    nb = n - nd
+    g = rng(seed)
+    R, phi, z = _mn_positions(g, nd, Md, Md_a, Md_b, Rmax=rmax, zmax=rmax)
+    vc = np.sqrt(Md * R * R / (R * R + (Md_a + Md_b) ** 2) ** 1.5 + Mb * R / (R + bulge_a) ** 2)
+    cp, sp = np.cos(phi), np.sin(phi)
+    vR = 0.1 * vc * g.standard_normal(nd)
+    vp = vc + 0.1 * vc * g.standard_normal(nd)
+    vz = 0.1 * vc * g.standard_normal(nd)
+    dpos = np.stack([R * cp, R * sp, z])
+    dvel = np.stack([vR * cp - vp * sp, vR * sp + vp * cp, vz])
+    bpos, rb, gb = hernquist_positions(nb, seed + 7919, Mb, bulge_a, rmax)
+    ab = Md_a + Md_b
+    rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x, Mb, bulge_a),
+                                   lambda x: _hernquist_mass(x, Mb, bulge_a) + Md * x ** 3 / (x * x + ab * ab) ** 1.5)
+    sb = np.sqrt(_Interp(rr, s2)(rb))
+    bvel = _spherical_gaussian_velocities(gb, bpos, rb, sb, sb)
+    pos = np.concatenate([dpos, bpos], axis=1)
+    vel = np.concatenate([dvel, bvel], axis=1)
+    order = np.argsort((pos * pos).sum(0), kind="stable")
+    return np.ascontiguousarray(pos[:, order]), np.ascontiguousarray(vel[:, order])
+
+
 def log_shell_edges(nbins, rmin, rmax):
     """Squared edges r_k^2 of nbins log-spaced radial bins in [rmin, rmax]."""
     k = np.arange(nbins + 1, dtype=np.float64)
@@ -395,9 +463,9 @@ def error_model(Y, obs_sets, frac=0.02):
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
-WORKLOADS = ("plain-fp64", "moving-priors", "flat-log")
+WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons")
 
-_DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000,
+_DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000, "sh-selfcons": 8_000_000,
               "flat-log": 4_000_000}
 
 
@@ -466,6 +534,22 @@ def make_problem(name, n=None, precision=None, seed_model=None,
         sin_i, cos_i = math.sin(inc), math.cos(inc)
         prec = precision or "fp32c"
         steps = nsteps or 5000
+    elif name == "sh-selfcons":
+        sm, st = seed_model or 9, seed_target or 10
+        pos, vel = disc_bulge_realisation(n, sm)
+        tp = tv = None
+        if with_target:
+            tp, tv = disc_bulge_realisation(n, st)
+        e = log_shell_edges(60, 0.05, 20.0)
+        rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+        S = np.maximum(np.sqrt(hernquist_sigma_iso(0.75, 0.3)(rmid)), 0.05)
+        obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+               ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
+        pot = [PotentialComponent("sh", (256, 1e-3, 100.0, 50))]
+        prior = PriorSpec("flat")
+        sin_i, cos_i = 0.0, 1.0
+        prec = precision or "fp32c"
+        steps = nsteps or 10000
     else:
         raise ValueError(f"unknown workload {name!r}")
     w0 = np.full(n, 1.0 / n)
