@@ -9,11 +9,14 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched]
+                  [--workload flat-log|batched|sh]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
 3e7 particles in all) advanced together by m2m_batch_step.
+--workload sh times the self-consistent disc + bulge (N = 8,000,000) in the
+spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
+recomputed every 50 steps).
 
 Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
 FP64 GPU path is measured on the same box and reported under "fp64_gpu".
@@ -430,6 +433,80 @@ def run_batched(args, D):
     bt.m2m_batch_free()
 
 
+def run_sh(args, D):
+    import torch
+    from paper_1207_6403_gb300 import inputs as I
+    from paper_1207_6403_gb300 import m2m as B
+    dev = f"cuda:{D.local}"
+    torch.cuda.set_device(dev)
+    n = args.n if args.n != N_DEFAULT else 8_000_000
+    P = I.make_problem("sh-selfcons", n=n, precision="fp32c", seed_model=9 + 1000 * D.rank,
+                       seed_target=10 + 1000 * D.rank)
+    P = P.with_targets(B.observe_targets(P, "fp32c", dev))
+    steps = args.steps if args.steps_given else 1000
+    stream = torch.cuda.current_stream()
+    ctx = B.from_problem(P, "fp32c", device=dev)
+    ctx.m2m_step(args.warmup)
+    torch.cuda.synchronize()
+    ctx.m2m_get_timing()
+    clocks = Clocks(D.local)
+    clocks.start()
+    D.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    e0.record(stream)
+    ctx.m2m_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    D.barrier()
+    clocks.stop()
+    launches = ctx.m2m_get_timing()["kernels_total"]
+    ms = D.max(e0.elapsed_time(e1))
+    value = D.world * n * steps / (ms * 1e-3)
+    k_roof = min(steps, 500)
+    ctx.m2m_set_timing(True)
+    ctx.m2m_step(k_roof)
+    tm = ctx.m2m_get_timing()
+    ctx.m2m_set_timing(False)
+    tot_ms = sum(tm["ms"].values())
+    shares = {k: round(v / tot_ms, 4) for k, v in tm["ms"].items() if v > 0}
+    pass_ms = tm["ms"]["step_upd"] / max(1, tm["launches"]["step_upd"])
+    sh_ms = tm["ms"]["sh"] / max(1, tm["launches"]["sh"] // 2)
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_PARTICLE_FP32C * n / (pass_ms * 1e-3) / 1e9
+    rec = ctx.m2m_get_record()
+    ctx.m2m_free()
+    cpu = None
+    if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
+        rate, ns, secs = time_oracle(P, 3, 64)
+        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"every 64th particle ({ns:,} of {n:,}) of the workload, 3 oracle steps "
+                         f"({secs:.1f} s, numpy, one thread)"}
+    if D.rank == 0:
+        line = {"metric": "M2M particle-steps/s, self-consistent SH potential (N=8M)", "value": value,
+                "unit": "particle-steps/s", "n_gpus": D.world, "steps": steps, "warmup": args.warmup,
+                "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (FP32-compensated; f64 weights, exact fixed-point SH sums)", "data": "synthetic",
+                "config": {"workload": f"sh-selfcons: N={n:,} Miyamoto-Nagai disc (a=1, b=0.2) + Hernquist "
+                                       "bulge (a=0.3), 1:3, in the even-l <= 8 multipole expansion of its own "
+                                       "weighted particles on 256 log nodes in [1e-3, 100], recomputed every "
+                                       "50 steps; 100 shells + 60 annuli x h0..h4, flat priors, dt=0.01",
+                           "n_particles": n, "global_particles": n * D.world,
+                           "l2": "particle arrays (576 MB/step) exceed the 129 MB L2; no flush needed"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "k_pass (step pass: update + push in the expansion + scatter)",
+                             "bytes_per_particle": BYTES_PER_PARTICLE_FP32C, "launch_ms": pass_ms,
+                             "sh_recompute_ms": sh_ms,
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                             "kernel_time_shares": shares},
+                "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks.summary(w0, w1),
+                "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -438,7 +515,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched"])
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh"])
     args = ap.parse_args()
     args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
     if args.warmup < 3:
@@ -449,6 +526,8 @@ def main():
             run_reference(args, D)
         elif args.workload == "batched":
             run_batched(args, D)
+        elif args.workload == "sh":
+            run_sh(args, D)
         else:
             run_ours(args, D)
     finally:

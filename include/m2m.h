@@ -72,11 +72,32 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
 /* ---- potential: Phi = sum of up to M2M_MAX_POT components (G = 1) ----
  * HERNQUIST p = {GM, a}:        Phi = -GM/(r+a)
  * NFW       p = {rho_s, r_s}:   Phi = -4 pi rho_s r_s^3 ln(1+r/r_s)/r
- * LOG       p = {v0, Rc, q}:    Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)   */
+ * LOG       p = {v0, Rc, q}:    Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)
+ * SH        p = {K, rmin, rmax, period}: the potential of the weighted
+ *           particles themselves (Section 1 and 2: the potential may be
+ *           evolved self-consistently from the particles), as the
+ *           axisymmetric multipole expansion with even l = 0..8,
+ *             Phi = -sum_l P_l(cos theta) [A_l(r)/r^(l+1) + B_l(r) r^l],
+ *             A_l(r) = sum_{r_i < r} w_i P_l r_i^l,
+ *             B_l(r) = sum_{r <= r_i < rmax} w_i P_l r_i^-(l+1),
+ *           tabulated at K (4..512, integer) nodes r_k = rmin
+ *           (rmax/rmin)^(k/(K-1)) and interpolated linearly in r between
+ *           them (exterior multipole law beyond rmax, interior solution
+ *           inside rmin).  Which side of node k a particle is on is decided
+ *           by its r^2 against r_k^2, like the shells.  Side sums: FP32C
+ *           exact 64-bit fixed point of the float terms (resolution 2^-56
+ *           of the initial total weight), FP64 double sums; the tables are
+ *           built in double.  Recomputed from
+ *           (x_{t+1}, w_{t+1}) after the update of every step t+1 that is a
+ *           multiple of `period` (integer >= 1), at m2m_init and by
+ *           m2m_potential.  At most one SH component, listed last; added
+ *           after the analytic ones.  Errors: M2M_ERR_ARG for bad p. */
 #define M2M_MAX_POT 4
 #define M2M_POT_HERNQUIST 1
 #define M2M_POT_NFW       2
 #define M2M_POT_LOG       3
+#define M2M_POT_SH        4
+#define M2M_SH_ROW        21   /* values per node in m2m_get_sh_table */
 typedef struct {
     int32_t kind;
     int32_t reserved;
@@ -178,8 +199,17 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n,
  * <= 0 masks).  Cites Section 2 (observables with errors). */
 int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma);
 
-/* Replace the potential (fixed, known potential of Section 2). */
+/* Replace the potential (fixed, known potential of Section 2; an SH
+ * component is expanded at once from the current positions and weights).
+ * M2M_ERR_STATE while an update is pending. */
 int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot);
+
+/* Copy the SH node table to host memory as doubles, K rows of M2M_SH_ROW:
+ * F_l(r_k) for l = 0,2,4,6,8; the slopes of F_l to node k+1; D_l(r_k) =
+ * dF_l/dr; the slopes of D_l; r_k (last row: zero slopes).  Phi =
+ * -sum P_l F_l.  out must hold K * M2M_SH_ROW doubles.  Synchronises.
+ * M2M_ERR_STATE if the potential has no SH component. */
+int m2m_get_sh_table(m2m_ctx *ctx, double *out);
 
 /* Scatter + residual at the current state, no push and no weight change.
  * mode 0: compute y and Delta only (Delta~ untouched);
@@ -261,7 +291,8 @@ int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable);
 #define M2M_TK_UPDATE    3   /* update-only pass (end of a call, m2m_update_weights) */
 #define M2M_TK_PRIOR     4   /* update + prior-cell pass, cell means, gather */
 #define M2M_TK_OTHER     5   /* observe, push, range and cell-export passes */
-#define M2M_TK_N         6
+#define M2M_TK_SH        6   /* spherical-harmonic side sums and node table */
+#define M2M_TK_N         7
 typedef struct {
     int64_t launches[M2M_TK_N];  /* launches timed since the last read */
     double ms[M2M_TK_N];         /* summed device milliseconds */

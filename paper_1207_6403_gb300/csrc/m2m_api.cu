@@ -26,6 +26,7 @@
 #include "m2m_kernels.cuh"
 
 using namespace m2m;
+static_assert(SH_ROW == M2M_SH_ROW, "node table row");
 
 namespace {
 
@@ -80,6 +81,15 @@ struct m2m_ctx {
     bool cache_valid;    // cell cache holds the cells of the current positions
     bool pipe;           // use the bulk-copy pipelined pass where it applies
     int fx_atomic;       // FP32C histogram flush: global integer atomics (1) or slots (0)
+    // self-consistent spherical-harmonic potential (kind M2M_POT_SH)
+    bool sh_on;
+    int sh_K, sh_period;
+    double sh_rmin, sh_rmax;
+    int sh_gmode;
+    float sh_ga, sh_gb;
+    void *d_sh_e2, *d_sh_rn, *d_sh_irn, *d_sh_tab;
+    double *d_sh_rnd;
+    unsigned long long *d_sh_sum;
     // timing of the library's launches
     bool timing;
     long long kernels_total;
@@ -182,6 +192,7 @@ size_t pass_smem(const m2m_ctx *c, int flags) {
     b += rs * (size_t)((c->edge_len + 3) & ~3);
     b += rs * (size_t)((c->gh_len + 3) & ~3);
     if (flags & F_UPD) b += rs * (size_t)((c->gh_len + 3) & ~3);
+    if (c->sh_on && (flags & (F_PUSH | F_MINMAX | F_CELLS))) b += rs * (size_t)((SH_ROW * c->sh_K + 3) & ~3);
     if (flags & F_CELLS) {
         b += rs * (size_t)((c->prior.nE + 4) & ~3) + rs * (size_t)((c->prior.nL + 4) & ~3) + 16;
         if (c->prec == M2M_FP32C) b += 12 * (size_t)((c->ncells + 3) & ~3);
@@ -238,6 +249,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
     a.f_pk = (float)a.pk; a.f_pgma = (float)a.pgma;
     a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
+    a.sh_tab = c->sh_on ? c->d_sh_tab : nullptr; a.sh_K = c->sh_K;
     a.cell_cache = c->d_cell_cache;
     a.cache_read = (flags & F_UPD) && c->cache_valid && c->layout != 0;
     a.cache_write = (flags & F_SCAT) && c->layout != 0;
@@ -358,7 +370,8 @@ void free_all(m2m_ctx *c) {
     void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_isig, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
-                    c->d_cell_mean, c->d_cell_cache, c->d_y_acc};
+                    c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -381,6 +394,16 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         } else if (pot[k].kind == M2M_POT_NFW) {
             if (!(p[0] > 0 && p[1] > 0)) return set_err(ctx, M2M_ERR_ARG, "nfw needs rho_s>0, r_s>0");
             d.c[0] = 4.0 * M_PI * p[0] * p[1] * p[1] * p[1]; d.c[1] = p[1]; d.c[2] = 1.0 / p[1];
+        } else if (pot[k].kind == M2M_POT_SH) {
+            const int K = (int)p[0];
+            if (k != npot - 1) return set_err(ctx, M2M_ERR_ARG, "the spherical-harmonic component must be last");
+            if (!((double)K == p[0] && K >= 4 && K <= SH_MAXK && p[1] > 0 && p[2] > p[1] && isfinite(p[2]) &&
+                  p[3] >= 1 && p[3] == floor(p[3]) && p[3] < 2147483648.0))
+                return set_err(ctx, M2M_ERR_ARG, "sh needs integer K in [4,%d], 0 < rmin < rmax, integer period >= 1",
+                               SH_MAXK);
+            d.ik = K;
+            const double lgc = (K - 1) / log2(p[2] / p[1]);
+            d.c[0] = K; d.c[1] = p[1]; d.c[2] = p[2]; d.c[3] = lgc; d.c[4] = -lgc * log2(p[1]); d.c[5] = 1.0 / p[1];
         } else {
             return set_err(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot[k].kind);
         }
@@ -389,6 +412,97 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         for (int j = 0; j < 6; ++j) tmp[k].cf[j] = (float)tmp[k].c[j];
     memcpy(ctx->pot, tmp, sizeof tmp);
     ctx->npot = npot;
+    ctx->sh_on = npot > 0 && pot[npot - 1].kind == M2M_POT_SH;
+    if (ctx->sh_on) {
+        const double *p = pot[npot - 1].p;
+        ctx->sh_K = (int)p[0];
+        ctx->sh_rmin = p[1];
+        ctx->sh_rmax = p[2];
+        ctx->sh_period = (int)p[3];
+    }
+    return M2M_OK;
+}
+
+// Node tables of the expansion: r_k = rmin (rmax/rmin)^(k/(K-1)), r_(K-1) =
+// rmax, and r_k^2 (for R = float the smallest float >= the double square).
+int sh_setup(m2m_ctx *ctx) {
+    const int K = ctx->sh_K;
+    const size_t rs = ctx->prec == M2M_FP32C ? 4 : 8;
+    void **bufs[] = {&ctx->d_sh_e2, &ctx->d_sh_rn, &ctx->d_sh_irn, &ctx->d_sh_tab, (void **)&ctx->d_sh_rnd,
+                     (void **)&ctx->d_sh_sum};
+    for (void **b : bufs)
+        if (*b) { cudaFree(*b); *b = nullptr; }
+    CU(cudaMalloc(&ctx->d_sh_e2, rs * K));
+    CU(cudaMalloc(&ctx->d_sh_rn, rs * K));
+    CU(cudaMalloc(&ctx->d_sh_irn, rs * K));
+    CU(cudaMalloc(&ctx->d_sh_tab, rs * SH_ROW * K));
+    CU(cudaMalloc((void **)&ctx->d_sh_rnd, 8 * (size_t)K));
+    CU(cudaMalloc((void **)&ctx->d_sh_sum, 80 * (size_t)K));
+    std::vector<double> rn(K), e2(K), irn(K);
+    const double ratio = ctx->sh_rmax / ctx->sh_rmin;
+    for (int k = 0; k < K; ++k) rn[k] = ctx->sh_rmin * pow(ratio, (double)k / (double)(K - 1));
+    rn[K - 1] = ctx->sh_rmax;
+    for (int k = 0; k < K; ++k) { e2[k] = rn[k] * rn[k]; irn[k] = 1.0 / rn[k]; }
+    for (int k = 1; k < K; ++k)
+        if (!(e2[k] > e2[k - 1])) return set_err(ctx, M2M_ERR_ARG, "sh nodes not strictly increasing");
+    guess_params(e2.data(), K - 1, &ctx->sh_gmode, &ctx->sh_ga, &ctx->sh_gb);
+    std::vector<unsigned char> buf(rs * 3 * K);
+    if (rs == 4) {
+        float *f = (float *)buf.data();
+        for (int k = 0; k < K; ++k) { f[k] = ceil_float(e2[k]); f[K + k] = (float)rn[k]; f[2 * K + k] = (float)irn[k]; }
+    } else {
+        double *d = (double *)buf.data();
+        for (int k = 0; k < K; ++k) { d[k] = e2[k]; d[K + k] = rn[k]; d[2 * K + k] = irn[k]; }
+    }
+    CU(cudaMemcpy(ctx->d_sh_e2, buf.data(), rs * K, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->d_sh_rn, buf.data() + rs * K, rs * K, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->d_sh_irn, buf.data() + 2 * rs * K, rs * K, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->d_sh_rnd, rn.data(), 8 * (size_t)K, cudaMemcpyHostToDevice));
+    return M2M_OK;
+}
+
+size_t sh_coef_smem(const m2m_ctx *c) {
+    const size_t NS = 10 * (size_t)c->sh_K;
+    return 8 * NS + (c->prec == M2M_FP32C ? 4 : 8) * 3 * (size_t)c->sh_K;
+}
+
+// The expansion from the current positions and weights: side sums, then
+// the node table the push reads.
+int sh_recompute(m2m_ctx *ctx) {
+    const int K = ctx->sh_K;
+    CU(cudaMemsetAsync(ctx->d_sh_sum, 0, 80 * (size_t)K, ctx->st));
+    ShArgs a;
+    memset(&a, 0, sizeof a);
+    a.x = ctx->x; a.y = ctx->y; a.z = ctx->z; a.w = ctx->w; a.n = ctx->n;
+    a.K = K; a.e2 = ctx->d_sh_e2; a.rn = ctx->d_sh_rn; a.irn = ctx->d_sh_irn;
+    a.gmode = ctx->sh_gmode; a.ga = ctx->sh_ga; a.gb = ctx->sh_gb;
+    a.sh = ctx->fx_shift + 6;
+    a.sum = ctx->d_sh_sum; a.err = ctx->d_err;
+    const bool f32 = ctx->prec == M2M_FP32C;
+    void *fn = f32 ? (void *)k_sh_coef<float> : (void *)k_sh_coef<double>;
+    const size_t sm = sh_coef_smem(ctx);
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, sm));
+    if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "sh coefficient pass needs %zu B shared memory", sm);
+    long long grid = (long long)ctx->nsm * occ, need = (ctx->n + 511) / 512;
+    if (grid > need) grid = need;
+    {
+        void *args[] = {&a};
+        LaunchTimer lt(ctx, M2M_TK_SH);
+        CU(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, sm, ctx->st));
+    }
+    const double q = ldexp(1.0, -a.sh);
+    const size_t tsm = 160 * (size_t)K;
+    {
+        LaunchTimer lt(ctx, M2M_TK_SH);
+        if (f32)
+            k_sh_tables<float><<<1, 256, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
+                                                         (float *)ctx->d_sh_tab, ctx->d_err);
+        else
+            k_sh_tables<double><<<1, 256, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
+                                                          (double *)ctx->d_sh_tab, ctx->d_err);
+        CU(cudaGetLastError());
+    }
     return M2M_OK;
 }
 
@@ -612,7 +726,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     // the pass kernels may use more than 48 KB of shared memory
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64()};
+    std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64(), (void *)k_sh_coef<float>,
+                                (void *)k_sh_coef<double>, (void *)k_sh_tables<float>, (void *)k_sh_tables<double>};
     for (int lay = 0; lay < 4; ++lay) {
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
@@ -651,6 +766,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
             ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
         }
     }
+    if (rc == M2M_OK && ctx->sh_on) rc = sh_setup(ctx);
+    if (rc == M2M_OK && ctx->sh_on) rc = sh_recompute(ctx);
     if (rc == M2M_OK) rc = observe_now(ctx, 0, 2, 0, 0);
     if (rc == M2M_OK) rc = check_err_word(ctx);
     if (rc != M2M_OK) {
@@ -675,7 +792,32 @@ int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma) {
 
 int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
     if (!ctx) return M2M_ERR_ARG;
-    return build_potential(ctx, pot, npot);
+    if (ctx->pending) return set_err(ctx, M2M_ERR_STATE, "update pending");
+    const int oldK = ctx->sh_on ? ctx->sh_K : 0;
+    const double oldr0 = ctx->sh_rmin, oldr1 = ctx->sh_rmax;
+    int rc = build_potential(ctx, pot, npot);
+    if (rc || !ctx->sh_on) return rc;
+    if (ctx->sh_K != oldK || ctx->sh_rmin != oldr0 || ctx->sh_rmax != oldr1) {
+        rc = sh_setup(ctx);
+        if (rc) { ctx->sh_on = false; ctx->npot = 0; return rc; }
+    }
+    return sh_recompute(ctx);
+}
+
+int m2m_get_sh_table(m2m_ctx *ctx, double *out) {
+    if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    if (!ctx->sh_on) return set_err(ctx, M2M_ERR_STATE, "the potential has no SH component");
+    const size_t cnt = (size_t)SH_ROW * ctx->sh_K;
+    if (ctx->prec == M2M_FP32C) {
+        std::vector<float> f(cnt);
+        CU(cudaMemcpyAsync(f.data(), ctx->d_sh_tab, 4 * cnt, cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+        for (size_t k = 0; k < cnt; ++k) out[k] = f[k];
+    } else {
+        CU(cudaMemcpyAsync(out, ctx->d_sh_tab, 8 * cnt, cudaMemcpyDeviceToHost, ctx->st));
+        CU(cudaStreamSynchronize(ctx->st));
+    }
+    return M2M_OK;
 }
 
 int m2m_observe(m2m_ctx *ctx, int32_t mode) {
@@ -724,6 +866,16 @@ int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
             rc = prior_recompute(ctx, F_UPD);
             if (rc) return rc;
             ctx->pending = false;
+        }
+        if (ctx->sh_on && t1 % ctx->sh_period == 0) {
+            // the expansion of (x_{t+1}, w_{t+1}): apply the update first
+            if (ctx->pending) {
+                rc = launch_pass(ctx, F_UPD);
+                if (rc) return rc;
+                ctx->pending = false;
+            }
+            rc = sh_recompute(ctx);
+            if (rc) return rc;
         }
     }
     if (ctx->pending) {
@@ -1030,7 +1182,7 @@ int m2m_batch_init(m2m_batch **out, int32_t precision, int32_t nmodels, const m2
     b->period = c0->prior.kind == M2M_PRIOR_FLAT ? 0 : c0->prior.period;
     for (m2m_ctx *c : b->ctx) {
         const int per = c->prior.kind == M2M_PRIOR_FLAT ? 0 : c->prior.period;
-        if (c->layout != b->layout || per != b->period) b->fusable = false;
+        if (c->layout != b->layout || per != b->period || c->sh_on) b->fusable = false;
     }
     if (b->fusable) {
         // blocks in proportion to N (at least one per model)

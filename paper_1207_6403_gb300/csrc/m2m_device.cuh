@@ -34,10 +34,23 @@ struct SetDev {
 };
 
 struct PotDev {
-    int kind;             // 1 hernquist, 2 nfw, 3 log
+    int kind;             // 1 hernquist, 2 nfw, 3 log, 4 spherical harmonics
+    int ik;               // sh: number of radial nodes K
     double c[6];          // hernquist: GM, a;  log: Rc2, iq2, v0sq, hv;  nfw: C=4 pi rho_s r_s^3, r_s, 1/r_s
+                          // sh: -, r_0, r_(K-1), lgc = (K-1)/log2(r_(K-1)/r_0), -lgc log2(r_0), 1/r_0
     float cf[6];          // the same rounded once to float (no per-particle conversions)
 };
+
+// Spherical-harmonic node table: one row of SH_ROW values per radial node k
+// (0..K-1), in the state precision:
+//   [0..4]   F_l(r_k)          l = 0, 2, 4, 6, 8
+//   [5..9]   dF_l per unit r to node k+1 (slope of the linear interpolant)
+//   [10..14] D_l(r_k)  (= dF_l/dr at the node)
+//   [15..19] slope of D_l to node k+1
+//   [20]     r_k
+// The last row has zero slopes.
+constexpr int SH_ROW = 21;
+constexpr int SH_MAXK = 512;
 
 struct PassArgs {
     void *x, *y, *z, *vx, *vy, *vz;
@@ -61,6 +74,7 @@ struct PassArgs {
     int prior_kind, nE, nL, ncells;
     double pk, pgma;                        // e_lc: a/GM, GM*a
     void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
+    const void *sh_tab; int sh_K;           // spherical-harmonic node table (R, SH_ROW per node) or NULL
     unsigned *cell_cache;                   // [n] packed cells of the last scatter
     int cache_read, cache_write;
     int *cell_ids;                          // [n]
@@ -238,8 +252,113 @@ __device__ __forceinline__ double nfw_f(double r, const PotDev &p) {
     return r > 0. ? p.c[0] * mu / r3 : 0.;
 }
 
+// ------------------------------------------------------------ multipoles
+// Even Legendre polynomials P_0..P_8 (as P[0..4]) and their derivatives by
+// Bonnet's recurrence (l+1) P_(l+1) = (2l+1) mu P_l - l P_(l-1) and
+// P'_(l+1) = P'_(l-1) + (2l+1) P_l.
 template <class R>
-__device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a) {
+__device__ __forceinline__ void legendre_even(R mu, R P[5], R dP[5]) {
+    const R p1 = mu;
+    const R p2 = (R(3) * mu * p1 - R(1)) * R(0.5);
+    const R p3 = (R(5) * mu * p2 - R(2) * p1) * R(1.0 / 3.0);
+    const R p4 = (R(7) * mu * p3 - R(3) * p2) * R(0.25);
+    const R p5 = (R(9) * mu * p4 - R(4) * p3) * R(0.2);
+    const R p6 = (R(11) * mu * p5 - R(5) * p4) * R(1.0 / 6.0);
+    const R p7 = (R(13) * mu * p6 - R(6) * p5) * R(1.0 / 7.0);
+    const R p8 = (R(15) * mu * p7 - R(7) * p6) * R(0.125);
+    P[0] = R(1); P[1] = p2; P[2] = p4; P[3] = p6; P[4] = p8;
+    dP[0] = R(0);
+    dP[1] = R(3) * p1;
+    dP[2] = dP[1] + R(7) * p3;
+    dP[3] = dP[2] + R(11) * p5;
+    dP[4] = dP[3] + R(15) * p7;
+}
+
+// F_l(r), D_l(r) from the node table: linear between nodes, the exterior law
+// F_l(K-1) (r_(K-1)/r)^(l+1) beyond the last node, and inside the first
+// F_l(0) (r/r_0)^l, D_l(0) (r/r_0)^max(l-1, 1).
+template <class R>
+__device__ __forceinline__ void sh_radial(R r, R ir, const R *T, const PotDev &p, R F[5], R D[5]) {
+    const int K = p.ik;
+    const R r0 = KC(R, p.c[1], p.cf[1]), rK = KC(R, p.c[2], p.cf[2]);
+    if (r >= rK) {
+        const R *row = T + (K - 1) * SH_ROW;
+        const R q = rK * ir, q2 = q * q;
+        R qq = q;
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+            F[n] = row[n] * qq;
+            D[n] = -(R(2 * n + 1) * F[n]) * ir;
+            qq = qq * q2;
+        }
+    } else if (r < r0) {
+        const R q = r * KC(R, p.c[5], p.cf[5]), q2 = q * q;
+        F[0] = T[0];
+        D[0] = T[10] * q;
+        R ql = q2, qd = q;
+#pragma unroll
+        for (int n = 1; n < 5; ++n) {
+            F[n] = T[n] * ql;
+            D[n] = T[10 + n] * qd;
+            ql = ql * q2;
+            qd = qd * q2;
+        }
+    } else {
+        // segment guess from log2 r, then fixed by the node radii
+        const float lg = fmaf(__log2f((float)r), p.cf[3], p.cf[4]) - 0.5f;
+        int k = rint_small(fminf(fmaxf(lg, 0.0f), (float)(K - 2)));
+        while (k > 0 && r < T[k * SH_ROW + 20]) --k;
+        while (k < K - 2 && r >= T[(k + 1) * SH_ROW + 20]) ++k;
+        const R *row = T + k * SH_ROW;
+        const R dr = r - row[20];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+            F[n] = row[n] + dr * row[5 + n];
+            D[n] = row[10 + n] + dr * row[15 + n];
+        }
+    }
+}
+
+// a = -grad Phi, Phi = -sum_l P_l(mu) F_l(r):
+// a = (sum P_l D_l) r_hat + (sum P_l' F_l) grad mu,
+// grad mu = (-z x, -z y, x^2 + y^2) / r^3; nothing at r = 0.
+template <class R>
+__device__ __forceinline__ void sh_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
+    const R r2 = (x * x + y * y) + z * z;
+    if (!(r2 > R(0))) return;
+    const R r = sqrt(r2), ir = R(1) / r, mu = z * ir;
+    R P[5], dP[5], F[5], D[5];
+    legendre_even<R>(mu, P, dP);
+    sh_radial<R>(r, ir, T, p, F, D);
+    R gr = P[0] * D[0], gm = R(0);
+#pragma unroll
+    for (int n = 1; n < 5; ++n) {
+        gr = gr + P[n] * D[n];
+        gm = gm + dP[n] * F[n];
+    }
+    const R t = gr * ir, u = gm * ((ir * ir) * ir);
+    const R c = t - u * z;
+    g.x = g.x + x * c;
+    g.y = g.y + y * c;
+    g.z = g.z + (z * t + u * (x * x + y * y));
+}
+
+template <class R>
+__device__ __forceinline__ R sh_phi(R x, R y, R z, const R *T, const PotDev &p) {
+    const R r2 = (x * x + y * y) + z * z;
+    if (!(r2 > R(0))) return -T[0];
+    const R r = sqrt(r2), ir = R(1) / r, mu = z * ir;
+    R P[5], dP[5], F[5], D[5];
+    legendre_even<R>(mu, P, dP);
+    sh_radial<R>(r, ir, T, p, F, D);
+    R s = F[0];
+#pragma unroll
+    for (int n = 1; n < 5; ++n) s = s + P[n] * F[n];
+    return -s;
+}
+
+template <class R>
+__device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const R *sh = nullptr) {
     Acc3<R> g{R(0), R(0), R(0)};
     for (int k = 0; k < a.npot; ++k) {
         const PotDev &p = a.pot[k];
@@ -266,6 +385,8 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a) {
             g.x = g.x + (-(f * x));
             g.y = g.y + (-(f * y));
             g.z = g.z + (-(f * z));
+        } else if (p.kind == 4) {     // spherical harmonics of the particles
+            sh_accel<R>(x, y, z, sh, p, g);
         }
     }
     return g;
@@ -275,7 +396,7 @@ __device__ __forceinline__ float plog(float v) { return logf(v); }
 __device__ __forceinline__ double plog(double v) { return log(v); }
 
 template <class R>
-__device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a) {
+__device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R *sh = nullptr) {
     R phi = R(0);
     for (int k = 0; k < a.npot; ++k) {
         const PotDev &p = a.pot[k];
@@ -296,22 +417,25 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a) {
             double u = r * p.c[2];
             double v = r > 0 ? -p.c[0] * log1p(u) / r : -p.c[0] * p.c[2];
             phi = phi + (R)v;
+        } else if (p.kind == 4) {
+            phi = phi + sh_phi<R>(x, y, z, sh, p);
         }
     }
     return phi;
 }
 
 template <class R>
-__device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a) {
+__device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a,
+                                    const R *sh = nullptr) {
     R h = KC(R, a.hdt, a.f_hdt), d = KC(R, a.dt, a.f_dt);
-    Acc3<R> g = accel<R>(x, y, z, a);
+    Acc3<R> g = accel<R>(x, y, z, a, sh);
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;
     x = x + d * vx;
     y = y + d * vy;
     z = z + d * vz;
-    g = accel<R>(x, y, z, a);
+    g = accel<R>(x, y, z, a, sh);
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;

@@ -100,17 +100,18 @@ __device__ void prior_setup(const PassArgs &a, R *pe, R *pl, float *gp) {
 }
 
 template <class R>
-__device__ __forceinline__ void energy_lz(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a, R &E, R &Lz) {
+__device__ __forceinline__ void energy_lz(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a, const R *sh,
+                                          R &E, R &Lz) {
     R v2 = (vx * vx + vy * vy) + vz * vz;
-    E = R(0.5) * v2 + potential<R>(x, y, z, a);
+    E = R(0.5) * v2 + potential<R>(x, y, z, a, sh);
     Lz = x * vy - y * vx;
 }
 
 template <class R>
 __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a,
-                                          const R *pe, const R *pl, const float *gp) {
+                                          const R *pe, const R *pl, const float *gp, const R *sh) {
     R E, Lz;
-    energy_lz<R>(x, y, z, vx, vy, vz, a, E, Lz);
+    energy_lz<R>(x, y, z, vx, vy, vz, a, sh, E, Lz);
     if (a.prior_kind == M2M_PRIOR_E_LZ) {
         int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
         int iL = count_le<R>(Lz, pl, a.nL, gp[2], gp[3]);
@@ -141,6 +142,7 @@ struct PassSmem {
     const R *gpoly;          // per GH cell: norm * sum_n coef_n E[H_n] as a quartic in m
     R *pe, *pl;
     float *gp;
+    const R *sh;             // spherical-harmonic node table
     unsigned *c_lo, *c_hi, *c_cnt;   // FP32C prior-cell sums / counts
     double *c_d;                     // FP64 prior-cell sums
 };
@@ -368,7 +370,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             t.bad = true;       // negative, -0 or NaN weight
         }
     }
-    if (fl & F_PUSH) kdk<R>(x, y, z, vx, vy, vz, a);
+    if (fl & F_PUSH) kdk<R>(x, y, z, vx, vy, vz, a, S.sh);
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         R wv = to_r(wn, (R *)nullptr);
@@ -377,13 +379,13 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     }
     if (fl & F_MINMAX) {
         R E, Lz;
-        energy_lz<R>(x, y, z, vx, vy, vz, a, E, Lz);
+        energy_lz<R>(x, y, z, vx, vy, vz, a, S.sh, E, Lz);
         emin = fmin(emin, E);
         emax = fmax(emax, E);
         lzm = fmax(lzm, fabs(Lz));
     }
     if (fl & F_CELLS) {
-        int c = prior_cell<R>(x, y, z, vx, vy, vz, a, S.pe, S.pl, S.gp);
+        int c = prior_cell<R>(x, y, z, vx, vy, vz, a, S.pe, S.pl, S.gp, S.sh);
         a.cell_ids[i] = c;
         cell_add<R>(a, S, c, wn, t.ovf);
     }
@@ -420,6 +422,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     S.edges = (const R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
     S.gh = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3);
     if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
+    const int sh_len = (a.sh_tab && (fl & (F_PUSH | F_MINMAX | F_CELLS))) ? SH_ROW * a.sh_K : 0;
+    if (sh_len) { S.sh = (const R *)p; p += sizeof(R) * ((sh_len + 3) & ~3); }
     if (fl & F_CELLS) {
         S.pe = (R *)p; p += sizeof(R) * ((a.nE + 4) & ~3);
         S.pl = (R *)p; p += sizeof(R) * ((a.nL + 4) & ~3);
@@ -447,6 +451,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
     for (int k = threadIdx.x; k < a.edge_len; k += NT) ((R *)S.edges)[k] = ((const R *)a.edge_tab)[k];
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    for (int k = threadIdx.x; k < sh_len; k += NT) ((R *)S.sh)[k] = ((const R *)a.sh_tab)[k];
     if ((fl & F_UPD) && L != 0) {
         // E[H_n] over N(m, t2) as polynomials in m (van der Marel & Franx
         // H_0..H_4), weighted by this step's coefficients of the cell
@@ -899,6 +904,202 @@ __global__ void k_prior_gather(const int *cell, const double *mean, double *what
         what[i] = mean[cell[i]];
 }
 
+// ------------------------------------------------------ spherical harmonics
+// The expansion of the weighted particles (kind 4): per radial side j (side
+// 0: r < r_0; side j: r_(j-1) <= r < r_j; r >= r_(K-1) left out), sums of
+//   A terms  w P_l(mu) (r/r_j)^l             (j = 0..K-1)
+//   B terms  w P_l(mu) (r_(j-1)/r)^(l+1)     (j = 1..K-1)
+// each at most w in size; the table kernel multiplies back r_j^l and
+// r_(j-1)^-(l+1) in double.  FP32C: the float terms are summed exactly in
+// 64-bit fixed point (one scale serves every side; its resolution, 2^-56 of
+// the total weight, is far below a float term's rounding).  FP64: double
+// sums (block-private, then global atomics), since a 64-bit fixed point
+// would round double terms of large N far above their own precision.
+struct ShArgs {
+    const void *x, *y, *z;
+    const double *w;
+    long long n;
+    int K;
+    const void *e2;                 // R[K] squared node radii (float: smallest float >= the double)
+    const void *rn, *irn;           // R[K] node radii and their reciprocals
+    int gmode; float ga, gb;        // index guess for e2
+    int sh;                         // fixed point: value * 2^sh
+    unsigned long long *sum;        // [10][K]: A_l sides (l = 0..8 even), then B_l sides
+    int *err;
+};
+
+__device__ __forceinline__ long long to_fixed(float v, int sh, bool &ovf) { return f2fixed(v, sh, ovf); }
+__device__ __forceinline__ long long to_fixed(double v, int sh, bool &ovf) { return d2fixed(v, sh, ovf); }
+
+template <class R>
+__global__ void __launch_bounds__(512) k_sh_coef(const __grid_constant__ ShArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool FX = sizeof(R) == 4;
+    const int K = a.K, NS = 10 * K;
+    unsigned *lo = (unsigned *)smem, *hi = lo + NS;     // FX: (lo, hi) pairs; else NS doubles
+    double *acc = (double *)smem;
+    R *e2 = (R *)(hi + NS), *rn = e2 + K, *irn = rn + K;
+    for (int k = threadIdx.x; k < 2 * NS; k += blockDim.x) lo[k] = 0u;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        e2[k] = ((const R *)a.e2)[k];
+        rn[k] = ((const R *)a.rn)[k];
+        irn[k] = ((const R *)a.irn)[k];
+    }
+    __syncthreads();
+    bool ovf = false, bad = false;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (shuffles)
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        const long long i = base + threadIdx.x;
+        int j = K;
+        long long q[10];           // FX: fixed-point terms
+        R v[10];                   // double terms
+#pragma unroll
+        for (int m = 0; m < 10; ++m) { q[m] = 0; v[m] = R(0); }
+        if (i < a.n) {
+            const R x = ((const R *)a.x)[i], y = ((const R *)a.y)[i], z = ((const R *)a.z)[i];
+            const double wd = a.w[i];
+            const R r2 = (x * x + y * y) + z * z;
+            if (r2 < e2[0]) {
+                j = 0;
+            } else {
+                const int c = find_bin<R>(r2, e2, K - 1, a.gmode, a.ga, a.gb);
+                j = c < 0 ? K : c + 1;                  // NaN or r >= r_(K-1): left out
+            }
+            if (d_bad(wd) && __double_as_longlong(wd) != 0ll) bad = true;
+            if (j < K && d_pos(wd)) {
+                const R wr = to_r(wd, (R *)nullptr);
+                const R r = sqrt(r2);
+                const R mu = r2 > R(0) ? z / r : R(0);
+                R P[5], dP[5];
+                legendre_even<R>(mu, P, dP);
+                const R rho = r * irn[j], rho2 = rho * rho;
+                R t = wr;
+#pragma unroll
+                for (int n = 0; n < 5; ++n) {
+                    v[n] = t * P[n];
+                    t = t * rho2;
+                }
+                if (j > 0) {
+                    const R sg = rn[j - 1] / r, sg2 = sg * sg;
+                    R u = wr * sg;
+#pragma unroll
+                    for (int n = 0; n < 5; ++n) {
+                        v[5 + n] = u * P[n];
+                        u = u * sg2;
+                    }
+                }
+                if (FX)
+#pragma unroll
+                    for (int m = 0; m < 10; ++m) q[m] = to_fixed(v[m], a.sh, ovf);
+            }
+        }
+        const int j0 = __shfl_sync(0xffffffffu, j, 0);
+        if (__all_sync(0xffffffffu, j == j0)) {
+            if (j0 < K) {
+                // one side for the whole warp: warp sums, then one update
+#pragma unroll
+                for (int m = 0; m < 10; ++m) {
+                    if (FX) {
+                        long long u = q[m];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                        q[m] = u;
+                    } else {
+                        v[m] = warp_sum(v[m]);
+                    }
+                }
+                if (lane == 0)
+#pragma unroll
+                    for (int m = 0; m < 10; ++m) {
+                        if (FX) { if (q[m]) fixed_add(lo, hi, m * K + j0, q[m]); }
+                        else if (v[m] != R(0)) atomicAdd(acc + m * K + j0, (double)v[m]);
+                    }
+            }
+        } else if (j < K) {
+#pragma unroll
+            for (int m = 0; m < 10; ++m) {
+                if (FX) { if (q[m]) fixed_add(lo, hi, m * K + j, q[m]); }
+                else if (v[m] != R(0)) atomicAdd(acc + m * K + j, (double)v[m]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) {
+        if (FX) {
+            const unsigned long long u = ((unsigned long long)hi[k] << 32) | lo[k];
+            if (u) atomicAdd(a.sum + k, u);
+        } else if (acc[k] != 0.0) {
+            atomicAdd((double *)a.sum + k, acc[k]);
+        }
+    }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (bad) atomicOr(a.err, ERR_NONFINITE);
+}
+
+// Node tables from the side sums (one block): scale back, prefix sums for
+// A_l(r_k) = sum_{j <= k}, suffix sums (outside in) for B_l(r_k) =
+// sum_{j > k}, then F_l, D_l and the slopes to the next node, in double.
+template <class R>
+__global__ void k_sh_tables(const long long *sum, int K, const double *rn, double q, R *tab, int *err) {
+    extern __shared__ __align__(16) double sd[];
+    double *S = sd;                // [10][K] side sums, then A, B at the nodes
+    double *FD = sd + 10 * K;      // [10][K] F_l, D_l at the nodes
+    for (int k = threadIdx.x; k < 10 * K; k += blockDim.x) {
+        const int m = k / K, j = k - m * K, n = m % 5, l = 2 * n;
+        const double v = sizeof(R) == 4 ? (double)sum[k] * q : ((const double *)sum)[k];
+        double s = 1.0;
+        if (m < 5) {
+            for (int e = 0; e < l; ++e) s *= rn[j];                       // r_j^l
+        } else if (j > 0) {
+            for (int e = 0; e <= l; ++e) s *= rn[j - 1];                  // r_(j-1)^(l+1)
+            s = 1.0 / s;
+        } else {
+            s = 0.0;
+        }
+        S[k] = v * s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double *row = S + threadIdx.x * K;
+        double acc = 0.0;
+        if (threadIdx.x < 5) {
+            for (int k = 0; k < K; ++k) { acc += row[k]; row[k] = acc; }
+        } else {
+            for (int k = K - 1; k >= 0; --k) { const double b = row[k]; row[k] = acc; acc += b; }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double r = rn[k], ir = 1.0 / r;
+        double rl = 1.0;           // r^l
+        for (int n = 0; n < 5; ++n) {
+            const int l = 2 * n;
+            const double A = S[n * K + k], B = S[(5 + n) * K + k];
+            const double irl1 = ir / rl;                  // r^-(l+1)
+            FD[n * K + k] = A * irl1 + B * rl;
+            FD[(5 + n) * K + k] = -(double)(l + 1) * A * (irl1 * ir) + (l > 0 ? (double)l * B * (rl * ir) : 0.0);
+            rl = rl * r * r;
+        }
+        if (!isfinite(FD[k])) atomicOr(err, ERR_NONFINITE);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        R *row = tab + (size_t)k * SH_ROW;
+        const bool last = k == K - 1;
+        const double h = last ? 1.0 : 1.0 / (rn[k + 1] - rn[k]);
+        for (int n = 0; n < 5; ++n) {
+            const double F = FD[n * K + k], D = FD[(5 + n) * K + k];
+            row[n] = (R)F;
+            row[10 + n] = (R)D;
+            row[5 + n] = last ? R(0) : (R)((FD[n * K + k + 1] - F) * h);
+            row[15 + n] = last ? R(0) : (R)((FD[(5 + n) * K + k + 1] - D) * h);
+        }
+        row[20] = (R)rn[k];
+    }
+}
+
 #endif  // M2M_COMMON_KERNELS
 
 // ------------------------------------------------------------- k_cells
@@ -919,7 +1120,7 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
         R vx = ((const R *)a.vx)[i], vy = ((const R *)a.vy)[i], vz = ((const R *)a.vz)[i];
         R X = x, Ys = z * s - y * c;
         for (int k = 0; k < a.nsets; ++k) obs_cells[(long long)k * a.n + i] = set_cell<R>(a.sets[k], edges, x, y, z, X, Ys);
-        if (prior_cells) prior_cells[i] = prior_cell<R>(x, y, z, vx, vy, vz, a, pe, pl, gp);
+        if (prior_cells) prior_cells[i] = prior_cell<R>(x, y, z, vx, vy, vz, a, pe, pl, gp, (const R *)a.sh_tab);
     }
 }
 

@@ -18,7 +18,8 @@ M2M_OK = 0
 ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE", -4: "M2M_ERR_TIMEOUT",
           -5: "M2M_ERR_STATE", -6: "M2M_ERR_NOMEM", -7: "M2M_ERR_OVERFLOW"}
 FP64, FP32C = 0, 1
-POT = {"hernquist": 1, "nfw": 2, "log": 3}
+POT = {"hernquist": 1, "nfw": 2, "log": 3, "sh": 4}
+SH_ROW = 21
 GEOM = {"shell": 1, "annulus": 2, "grid": 3}
 QUANT = {"mass": 1, "vlos2": 2, "gh": 3}
 PRIOR = {"flat": 0, "e_lc": 1, "e_lz": 2}
@@ -46,8 +47,8 @@ class m2m_params(ctypes.Structure):
                 ("entropy_const", c_double), ("incl_sin", c_double), ("incl_cos", c_double)]
 
 
-TK_N = 6
-TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other")
+TK_N = 7
+TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other", "sh")
 
 
 class m2m_timing(ctypes.Structure):
@@ -107,6 +108,7 @@ def library():
         "m2m_set_pipeline": (c_int32, [P, c_int32]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
+        "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
         "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
                                          c_double, c_double, c_double, P, P]),
         "m2m_batch_init": (c_int32, [POINTER(P), c_int32, c_int32, POINTER(m2m_model_desc),
@@ -231,6 +233,13 @@ class Context:
         return {"launches": {k: t.launches[i] for i, k in enumerate(TIMING_KINDS)},
                 "ms": {k: t.ms[i] for i, k in enumerate(TIMING_KINDS)},
                 "kernels_total": t.kernels_total}
+
+    def m2m_get_sh_table(self, K):
+        """(K, 21) node table of the spherical-harmonic component (float64)."""
+        import numpy as np
+        out = np.zeros((K, SH_ROW), dtype=np.float64)
+        _check(library().m2m_get_sh_table(self.ptr, out.ctypes.data_as(POINTER(c_double))), self.ptr)
+        return out
 
     def m2m_free(self):
         if self.ptr and self.owned:

@@ -48,7 +48,13 @@ def _init(**kw):
     od[0].geom, od[0].quant, od[0].nx, od[0].ny = 1, 1, 2, 1
     od[0].edges_x = ctypes.cast(ex, ctypes.POINTER(ctypes.c_double))
     ctx = P()
-    rc = L.m2m_init(ctypes.byref(ctx), args["prec"], args["n"], *args["ptrs"], None, 0, od,
+    pots = args.get("pots", [])
+    pd = (B.m2m_potential_desc * max(1, len(pots)))()
+    for k, (kind, prm) in enumerate(pots):
+        pd[k].kind = kind
+        for j, v in enumerate(prm):
+            pd[k].p[j] = v
+    rc = L.m2m_init(ctypes.byref(ctx), args["prec"], args["n"], *args["ptrs"], pd if pots else None, len(pots), od,
                     args["nsets"], None, None, ctypes.byref(args["par"]), None, None)
     return rc, ctx, L.m2m_last_error(None).decode()
 
@@ -61,6 +67,13 @@ def _init(**kw):
     (dict(nsets=0), "nsets"),
     (dict(par=B.m2m_params(0, 0, 0.01, 0.0, 1, 0, 1)), "alpha"),
     (dict(par=B.m2m_params(float("nan"), 0, 0.01, 0.5, 1, 0, 1)), "non-finite"),
+    (dict(pots=[(4, (2, 1e-3, 100.0, 50))]), "sh needs"),
+    (dict(pots=[(4, (256.5, 1e-3, 100.0, 50))]), "sh needs"),
+    (dict(pots=[(4, (256, 1.0, 0.5, 50))]), "sh needs"),
+    (dict(pots=[(4, (256, 1e-3, 100.0, 0))]), "sh needs"),
+    (dict(pots=[(4, (1024, 1e-3, 100.0, 50))]), "sh needs"),
+    (dict(pots=[(4, (256, 1e-3, 100.0, 50)), (1, (1.0, 1.0))]), "must be last"),
+    (dict(pots=[(9, (1.0, 1.0))]), "unknown potential"),
 ])
 def test_init_rejects_bad_arguments_without_touching_memory(kw, needle):
     rc, ctx, msg = _init(**kw)

@@ -1,0 +1,203 @@
+"""GPU parity of the self-consistent spherical-harmonic potential: node
+tables, pushes, the recompute schedule inside m2m_step, the edge cases of
+the radial laws, and the full-size disc + bulge workload on samples.
+
+Tolerances:
+* FP64: double side sums in another order than the oracle's, so the tables
+  agree to 1e-12 of the monopole scale; positions and weights after a run
+  to 1e-10 relative.
+* FP32C: the per-particle terms are float (and the weights enter truncated
+  to float), so the tables agree to 2e-6 of the monopole scale; the force is
+  evaluated in float, so positions agree to 2e-5 of their range after a
+  few tens of steps, weights to 1e-5 (99th percentile) and observables to
+  1e-4 of their scale.
+
+Orbits that pass close to the centre of the disc + bulge (the bulge has a
+density cusp) are not resolved by dt = 0.01 and, in a force built from the
+few particles there, amplify any rounding difference by orders of magnitude
+within tens of steps.  Trajectories are therefore compared for the particles
+whose oracle orbit stays outside r = 0.05 (more than 90% of them), and the
+tables of a run are compared with the oracle's expansion of the GPU's own
+state, which checks the arithmetic without the divergence.
+"""
+import numpy as np
+import pytest
+
+from oracle import m2m as O
+from oracle import sh as SH
+from paper_1207_6403_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1207_6403_gb300 import m2m as B  # noqa: E402
+
+_CACHE = {}
+
+
+def sh_problem(n, prec, K=64, period=5, seed=9, targets=True):
+    key = (n, prec, K, period, seed, targets)
+    if key not in _CACHE:
+        P = I.make_problem("sh-selfcons", n=n, precision=prec, seed_model=seed, seed_target=seed + 1,
+                           with_target=targets)
+        P.potential = [I.PotentialComponent("sh", (K, 1e-3, 100.0, period))]
+        if targets:
+            Y = O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos)
+            P = P.with_targets(Y)
+        _CACHE[key] = P
+    return _CACHE[key]
+
+
+def split_table(T):
+    return T[:, 0:5].T, T[:, 5:10].T, T[:, 10:15].T, T[:, 15:20].T, T[:, 20]
+
+
+def assert_tables_close(T, ref, tol):
+    F, SF, D, SD, rk = split_table(T)
+    Fo, Do, rn = ref
+    np.testing.assert_array_equal(rk, rn.astype(T.dtype) if tol < 1e-9 else rn.astype(np.float32))
+    sF, sD = np.abs(Fo[0]).max(), np.abs(Do[0]).max()
+    assert np.abs(F - Fo).max() <= tol * sF, np.abs(F - Fo).max() / sF
+    assert np.abs(D - Do).max() <= tol * sD, np.abs(D - Do).max() / sD
+    # slopes of the linear interpolant to the next node
+    h = np.diff(rn)
+    np.testing.assert_allclose(SF[:, :-1] * h, np.diff(Fo, axis=1), rtol=0, atol=4 * tol * sF)
+    np.testing.assert_allclose(SD[:, :-1] * h, np.diff(Do, axis=1), rtol=0, atol=4 * tol * sD)
+    assert np.all(SF[:, -1] == 0) and np.all(SD[:, -1] == 0)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 2e-6)])
+def test_initial_tables_match_the_oracle(prec, tol):
+    P = sh_problem(5003, prec)
+    ctx = B.from_problem(P, prec)
+    T = ctx.m2m_get_sh_table(64)
+    st = O.init(P, prec)
+    assert_tables_close(T, st.sh, tol)
+
+
+def resolved(rmin_traj):
+    keep = rmin_traj > 0.05
+    assert keep.mean() > 0.9
+    return keep
+
+
+def assert_positions_close(g, s, keep, prec, keys=("x", "y", "z", "vx", "vy", "vz")):
+    for a, k in zip(s, keys):
+        if prec == "fp64":
+            np.testing.assert_allclose(g[k][keep], a[keep], rtol=1e-10, atol=1e-12 * np.abs(a).max())
+        else:
+            np.testing.assert_allclose(g[k][keep], a[keep], rtol=0, atol=2e-5 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_push_in_the_expansion(prec):
+    P = sh_problem(4097, prec, K=128)
+    ctx = B.from_problem(P, prec)
+    ctx.m2m_push(40)
+    g = ctx.state()
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    rmin = np.full(P.n, np.inf)
+    for _ in range(40):
+        s = O.kdk(*s, P.potential, P.dt, st.sh)
+        rmin = np.minimum(rmin, np.sqrt(s[0].astype(np.float64) ** 2 + s[1] ** 2 + s[2] ** 2))
+    assert_positions_close(g, s, resolved(rmin), prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_step_recomputes_the_expansion_on_schedule(prec):
+    P = sh_problem(6001, prec, K=64, period=5)
+    comp = P.potential[0]
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    ctx = B.from_problem(P, prec)
+    # after step 20 the table is the expansion of (x_20, w_20) of the GPU run
+    ctx.m2m_step(20)
+    g20 = ctx.state()
+    T = ctx.m2m_get_sh_table(64)
+    assert_tables_close(T, O.sh_tables(g20["x"], g20["y"], g20["z"], g20["w"], comp), tol)
+    ctx.m2m_step(3)
+    g = ctx.state()
+    y, _, _ = ctx.m2m_get_obs()
+    # ... and stays so until the recompute after step 25
+    assert np.array_equal(ctx.m2m_get_sh_table(64), T)
+    st = O.init(P, prec)
+    rmin = np.full(P.n, np.inf)
+    for _ in range(23):
+        O.step(st, P)
+        rmin = np.minimum(rmin, np.sqrt(st.x.astype(np.float64) ** 2 + st.y ** 2 + st.z ** 2))
+    keep = resolved(rmin)
+    assert_positions_close(g, (st.x, st.y, st.z, st.vx, st.vy, st.vz), keep, prec)
+    rel = np.abs(g["w"] / st.w - 1)
+    scale = np.maximum(np.maximum(np.abs(st.y_obs), P.sigma / 0.02), 1e-300)
+    if prec == "fp64":
+        assert np.quantile(rel[keep], 0.999) < 1e-10
+        assert np.quantile(np.abs(y - st.y_obs) / scale, 0.99) < 1e-10
+    else:
+        assert np.quantile(rel[keep], 0.99) < 1e-5
+        assert np.quantile(np.abs(y - st.y_obs) / scale, 0.99) < 1e-4
+    ctx.m2m_step(2)
+    assert not np.array_equal(ctx.m2m_get_sh_table(64), T)
+
+
+def test_edge_cases_origin_outside_inside_and_on_a_node():
+    P = sh_problem(2000, "fp64", K=32, targets=False)
+    rn = SH.nodes(1e-3, 100.0, 32)
+    x, y, z = (a.copy() for a in P.pos)
+    # r = 0; beyond rmax (excluded from the sums, exterior law); inside r_0
+    # (interior law); exactly on nodes 0, 5 and K-1 (upper side)
+    x[0] = y[0] = z[0] = 0.0
+    x[1], y[1], z[1] = 150.0, 20.0, -40.0
+    x[2], y[2], z[2] = 2e-4, -3e-4, 1e-4
+    x[3], y[3], z[3] = rn[0], 0.0, 0.0
+    x[4], y[4], z[4] = 0.0, 0.0, -rn[5]
+    x[5], y[5], z[5] = 0.0, rn[31], 0.0
+    P2 = I.Problem(**{**P.__dict__, "pos": np.stack([x, y, z])})
+    P2 = P2.with_targets(np.ones(P2.nobs))
+    ctx = B.from_problem(P2, "fp64")
+    st = O.init(P2, "fp64")
+    assert_tables_close(ctx.m2m_get_sh_table(32), st.sh, 1e-12)
+    ctx.m2m_push(3)
+    g = ctx.state()
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for _ in range(3):
+        s = O.kdk(*s, P2.potential, P2.dt, st.sh)
+    for a, k in zip(s, ("x", "y", "z", "vx", "vy", "vz")):
+        np.testing.assert_allclose(g[k][:6], a[:6], rtol=1e-12, atol=1e-15)
+
+
+def test_potential_call_recomputes_and_rejects_a_bad_descriptor():
+    P = sh_problem(3000, "fp64", K=32, targets=False)
+    P = P.with_targets(np.ones(P.nobs))
+    ctx = B.from_problem(P, "fp64")
+    ctx.m2m_push(7)
+    comp = I.PotentialComponent("sh", (48, 1e-3, 50.0, 9))
+    ctx.m2m_potential([comp])
+    g = ctx.state()
+    ref = O.sh_tables(g["x"], g["y"], g["z"], g["w"], comp)
+    assert_tables_close(ctx.m2m_get_sh_table(48), ref, 1e-12)
+    with pytest.raises(B.M2MError) as e:
+        ctx.m2m_potential([I.PotentialComponent("sh", (48, 1e-3, 50.0, 0))])
+    assert e.value.code == -1
+
+
+def test_full_size_disc_bulge_tables_and_push_sampled():
+    """The self-consistent workload at its full size (N = 8,000,000, K = 256,
+    recompute every 50 steps) through one recompute inside m2m_step: the
+    table against the oracle's expansion of the same state, then one push
+    of a sample of particles."""
+    P = I.make_problem("sh-selfcons", precision="fp32c", with_target=False)
+    P = P.with_targets(np.ones(P.nobs))
+    comp = P.potential[0]
+    ctx = B.from_problem(P, "fp32c")
+    ctx.m2m_step(50)
+    g = ctx.state()
+    ref = O.sh_tables(g["x"], g["y"], g["z"], g["w"], comp)
+    T = ctx.m2m_get_sh_table(256)
+    assert_tables_close(T, ref, 2e-6)
+    idx = np.random.default_rng(0).choice(P.n, 8192, replace=False)
+    s0 = tuple(g[k][idx] for k in ("x", "y", "z", "vx", "vy", "vz"))
+    ctx.m2m_push(1)
+    g1 = ctx.state()
+    s1 = O.kdk(*s0, P.potential, P.dt, ref)
+    for a, k in zip(s1, ("x", "y", "z", "vx", "vy", "vz")):
+        np.testing.assert_allclose(g1[k][idx], a, rtol=0, atol=2e-6 * np.abs(a).max())
