@@ -187,7 +187,7 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
 size_t pass_smem(const m2m_ctx *c, int flags) {
     size_t rs = c->prec == M2M_FP32C ? 4 : 8;
     size_t b = 0;
-    if (flags & F_SCAT) b += 8 * (size_t)((c->nobs + 1) & ~1);
+    if (flags & F_SCAT) b += c->prec == M2M_FP32C ? 12 * (size_t)((c->nobs + 3) & ~3) : 8 * (size_t)((c->nobs + 1) & ~1);
     if (flags & F_UPD) b += rs * (size_t)((c->nobs + 3) & ~3);
     b += rs * (size_t)((c->edge_len + 3) & ~3);
     b += rs * (size_t)((c->gh_len + 3) & ~3);
@@ -263,13 +263,17 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     LaunchShape ks = pick_kernel(ctx);
     size_t sm = pass_smem(ctx, flags);
     int occ = 0;
-    if (ctx->pipe && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0) {
+    const long long pipe_grid = std::min<long long>((long long)ctx->nsm, ctx->slot_cap);
+    if (ctx->pipe && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0 &&
+        (ctx->n + pipe_grid * FX_SEG - 1) / (pipe_grid * FX_SEG) <= 1) {
         // warp-level bulk-copy pipeline when its stage buffers fit beside the tables
         void *fp = pass_kernel_f32_pipe(ctx->layout);
         size_t smp = sm + (size_t)32 * PIPE_STAGES * Chunk<float>::BYTES;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
         if (occ >= 1) { ks = {fp, 1024}; sm = smp; }
     }
+    if (occ < 1 && flags == F_STEADY && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0)
+        ks = {pass_kernel_f32_steady(ctx->layout), 1024};
     if (occ < 1) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
     if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "pass needs %zu B shared memory: does not fit", sm);
     int bps = occ;
@@ -732,7 +736,9 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
+        if (lay) kfns.push_back(pass_kernel_f32_steady(lay));
         kfns.push_back(pass_kernel_f32_batch(lay));
+        if (lay) kfns.push_back(pass_kernel_f32_batch(lay, true));
     }
     for (void *f : kfns) {
         cudaFuncAttributes fa;
@@ -1097,7 +1103,8 @@ int batch_pass(m2m_batch *b, int flags, int cache_read) {
     bp.cache_read = cache_read;
     bp.cache_write = 1;
     void *args[] = {&bp};
-    cudaError_t e = cudaLaunchKernel(pass_kernel_f32_batch(b->layout), dim3(b->pgrid), dim3(1024), args,
+    const bool steady = flags == F_STEADY && cache_read;
+    cudaError_t e = cudaLaunchKernel(pass_kernel_f32_batch(b->layout, steady), dim3(b->pgrid), dim3(1024), args,
                                      batch_smem(b, flags), b->st);
     if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "batched pass: %s", cudaGetErrorString(e));
     return M2M_OK;

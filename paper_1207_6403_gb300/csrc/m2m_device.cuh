@@ -571,28 +571,39 @@ __device__ __forceinline__ int cell_t(const SetDev &s, const R *edges, R x, R y,
     }
 }
 
-// Fixed-point add of a float term v: V = round(v * 2^sh) as a 64-bit
-// two's-complement integer accumulated exactly in a shared (lo, hi) pair of
-// u32 words.  For |v * 2^sh| < 2^38 the rounding is done with two exact
-// float steps (1.5*2^23 "magic" rounding of S/2^16, then of the exact
-// remainder S - h*2^16), larger terms take the bit-level path.
+// Fixed-point histogram add of a float term v, V = round(v * 2^sh) (a
+// 64-bit integer), kept as three int32 sums per bin in shared memory:
+// V = A * 2^32 + B * 2^16 + L with B and L in [-2^15, 2^15].  Every part
+// goes in with a plain reduction (no returned value, no carry), and the bin
+// total is A_sum * 2^32 + B_sum * 2^16 + L_sum.  It is exact while at most
+// 2^15 terms reach a bin between two flushes (the pass flushes every
+// 32768 particles of a block), which keeps |B_sum|, |L_sum| < 2^31; A_sum
+// stays in range for any |V| < 2^62.  A is 0 for the usual terms (|V| <
+// 2^31) and its reduction is skipped.  For |V| < 2^38 the split takes two
+// exact float steps (1.5*2^23 "magic" rounding of V/2^16, then of the exact
+// remainder V - h*2^16), larger terms take the bit-level path.
 // fscale = 2^sh as a float (an exact power of two).
-__device__ __forceinline__ void fx_add(unsigned *lo, unsigned *hi, int b, float v, float fscale, int sh, bool &ovf) {
+constexpr float FX_MAGIC = 12582912.0f;            // 1.5 * 2^23
+__device__ __forceinline__ void fx_red(int *Lo, int *Mid, int *Hi, int b, float v, float fscale, int sh,
+                                       bool &ovf) {
     const float S = v * fscale;
-    if (fabsf(S) < 274877906944.0f) {                       // 2^38
-        const float M = 12582912.0f;                         // 1.5 * 2^23
-        const float t = fmaf(S, 1.52587890625e-05f, M);      // round(S / 2^16) + M
-        const int h = __float_as_int(t) - 0x4B400000;
-        const float r = fmaf(-(t - M), 65536.0f, S);         // S - h * 2^16, exact
-        const int l = __float_as_int(r + M) - 0x4B400000;    // round(r)
-        const long long V = ((long long)h << 16) + l;
-        const unsigned vl = (unsigned)V, vh = (unsigned)((unsigned long long)V >> 32);
-        const unsigned old = atomicAdd(lo + b, vl);
-        const unsigned inc = vh + ((old + vl) < old ? 1u : 0u);
-        if (inc) atomicAdd(hi + b, inc);
+    int h, l;
+    if (fabsf(S) < 274877906944.0f) {                          // 2^38
+        const float t = fmaf(S, 1.52587890625e-05f, FX_MAGIC); // round(S / 2^16) + M
+        h = __float_as_int(t) - 0x4B400000;
+        const float r = fmaf(-(t - FX_MAGIC), 65536.0f, S);    // S - h * 2^16, exact
+        l = __float_as_int(r + FX_MAGIC) - 0x4B400000;
+        const int A = (h + 32768) >> 16;
+        atomicAdd(Lo + b, l);
+        atomicAdd(Mid + b, h - (A << 16));
+        if (A) atomicAdd(Hi + b, A);
     } else {
-        long long q = f2fixed(v, sh, ovf);
-        if (q) fixed_add(lo, hi, b, q);
+        const long long q = f2fixed(v, sh, ovf);
+        const long long hh = (q + 32768) >> 16;
+        const long long A = (hh + 32768) >> 16;
+        atomicAdd(Lo + b, (int)(q - (hh << 16)));
+        atomicAdd(Mid + b, (int)(hh - (A << 16)));
+        atomicAdd(Hi + b, (int)A);
     }
 }
 

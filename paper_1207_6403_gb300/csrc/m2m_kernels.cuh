@@ -136,7 +136,7 @@ __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const
 // ----------------------------------------------------------------- k_pass
 template <class R>
 struct PassSmem {
-    unsigned *h_lo, *h_hi;   // FP32C histogram (exact fixed point)
+    int *hL, *hM, *hH;       // FP32C histogram: V = H * 2^32 + M * 2^16 + L per bin (exact fixed point)
     double *h_d;             // FP64 histogram
     const R *coef, *edges, *gh;
     const R *gpoly;          // per GH cell: norm * sum_n coef_n E[H_n] as a quartic in m
@@ -221,16 +221,22 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
     return dot;
 }
 
-__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, float fs, int sh, bool &ovf) {
-    fx_add(S.h_lo, S.h_hi, b, v, fs, sh, ovf);
+struct ThreadAcc {
+    double s_d, w_d;     // FP64 path
+    float s_f, w_f;      // FP32C path
+    bool ovf, bad;
+};
+
+__device__ __forceinline__ void hist_add(const PassSmem<float> &S, int b, float v, float fs, int sh, ThreadAcc &t) {
+    fx_red(S.hL, S.hM, S.hH, b, v, fs, sh, t.ovf);
 }
-__device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, float, int, bool &) {
+__device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, double v, float, int, ThreadAcc &) {
     atomicAdd(S.h_d + b, v);
 }
 
 template <class R, int L>
 __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                            R X, R Ys, R vlos, R wv, float fs, bool &ovf) {
+                                            R X, R Ys, R vlos, R wv, float fs, ThreadAcc &ovf) {
     const int sh = a.fx_shift;
     unsigned packed = 0u;
     if constexpr (L == 0) {
@@ -273,12 +279,6 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
     }
     return packed;
 }
-
-struct ThreadAcc {
-    double s_d, w_d;     // FP64 path
-    float s_f, w_f;      // FP32C path
-    bool ovf, bad;
-};
 
 // expm1 for the small exponents of the weight update (|d| < 2^-7: Taylor
 // to d^5, relative error < 2^-40), the library routine otherwise.
@@ -344,11 +344,13 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
     atomicAdd((unsigned *)(S.c_lo) + c, 1u);
 }
 
-template <class R, int L>
+// FL != 0: the flags are that compile-time constant (specialised kernels of
+// the steady-state step), else they come from the arguments.
+template <class R, int L, int FL>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
                                          unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
-    const int fl = a.flags;
+    const int fl = FL ? FL : a.flags;
     const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
     if (fl & (F_UPD | F_STATS)) {
@@ -374,7 +376,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         R wv = to_r(wn, (R *)nullptr);
-        const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t.ovf);
+        const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t);
         if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
     }
     if (fl & F_MINMAX) {
@@ -400,23 +402,25 @@ template <class R> struct Chunk {
                          OWH = OW + 256, OCC = OWH + 256, BYTES = OCC + 128;
 };
 constexpr int PIPE_STAGES = 2;
+// particles a block scatters between two flushes of its FP32C histogram
+// (keeps every int32 part-sum of fx_red exact)
+constexpr int FX_SEG = 32768;
 
 // One block's share of a pass over the particles of one model: block `bid`
 // of `nblk` blocks that share the model's particles (grid-stride).
-template <class R, int NT, int L, int PIPE>
+template <class R, int NT, int L, int PIPE, int FL = 0>
 __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, const int nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ __align__(8) unsigned long long bars[PIPE ? (NT / 32) * PIPE_STAGES : 1];
     constexpr bool FX = sizeof(R) == 4;
-    const int fl = a.flags;
+    const int fl = FL ? FL : a.flags;
     PassSmem<R> S{};
     unsigned char *p = smem;
     const int nobs = a.nobs;
     if (fl & F_SCAT) {
-        if (FX) { S.h_lo = (unsigned *)p; S.h_hi = S.h_lo + nobs; }
-        else { S.h_d = (double *)p; }
-        p += 8 * ((nobs + 1) & ~1);
+        if (FX) { S.hL = (int *)p; S.hM = S.hL + nobs; S.hH = S.hM + nobs; p += 12 * ((nobs + 3) & ~3); }
+        else { S.h_d = (double *)p; p += 8 * ((nobs + 1) & ~1); }
     }
     if (fl & F_UPD) { S.coef = (const R *)p; p += sizeof(R) * ((nobs + 3) & ~3); }
     S.edges = (const R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
@@ -444,8 +448,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     }
     // prologue: clear histograms, stage the tables
     if (fl & F_SCAT) {
-        unsigned *hz = FX ? S.h_lo : (unsigned *)S.h_d;
-        for (int k = threadIdx.x; k < 2 * nobs; k += NT) hz[k] = 0u;
+        unsigned *hz = FX ? (unsigned *)S.hL : (unsigned *)S.h_d;
+        for (int k = threadIdx.x; k < (FX ? 3 : 2) * nobs; k += NT) hz[k] = 0u;
     }
     if (fl & F_UPD)
         for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
@@ -493,6 +497,26 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     const bool wr_w = (fl & F_UPD) != 0;
     const bool need_what = (fl & (F_UPD | F_STATS)) != 0;
     const bool need_cc = L != 0 && a.cache_read && (fl & F_UPD);
+    // FP32C histogram flush (all threads, after a barrier): the exact totals
+    // H * 2^32 + M * 2^16 + L of this segment go into the global totals with
+    // 64-bit integer atomics, or into this block's slot for the residual to
+    // sum (integer sums: the result does not depend on the order).
+    int nseg = 0;
+    auto flush_hist = [&](bool last) {
+        long long *sl = (long long *)a.slots + (long long)bid * nobs;
+        for (int k = threadIdx.x; k < nobs; k += NT) {
+            const long long v = (long long)(((unsigned long long)(long long)S.hH[k] << 32) +
+                                            ((unsigned long long)(long long)S.hM[k] << 16) +
+                                            (unsigned long long)(long long)S.hL[k]);
+            if (!last) { S.hL[k] = 0; S.hM[k] = 0; S.hH[k] = 0; }
+            if (a.fx_atomic) {
+                if (v) atomicAdd(a.y_acc + k, (unsigned long long)v);
+            } else {
+                sl[k] = nseg ? sl[k] + v : v;
+            }
+        }
+        ++nseg;
+    };
     if constexpr (PIPE) {
         // warp-level pipeline: lane 0 stages the warp's next chunk with bulk
         // copies while the warp computes the current one
@@ -503,6 +527,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         const int nfull = (int)(n >> 5), nch = (int)((n + 31) >> 5);
         const int gw = bid * (NT / 32) + warp, TW = nblk * (NT / 32);
         const unsigned bytes = 6 * 32 * sizeof(R) + 256 + (need_what ? 256 : 0) + (need_cc ? 128 : 0);
+        // no mid-pass flush here: a block may scatter at most FX_SEG particles
+        if (FX && (fl & F_SCAT) && (long long)((nch + TW - 1) / TW) * NT > FX_SEG) t.ovf = true;
         // per-stage bits: copies pending; parity of the next completion
         unsigned pendm = 0u, parm = 0u;
         auto issue = [&](int c, int st) {
@@ -551,7 +577,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 if (need_cc) cc = a.cell_cache[i];
             }
             if (i < (int)n) {
-                particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                particle<R, L, FL>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
                 if (wr_pos) {
                     __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
                     __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
@@ -571,38 +597,57 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             __syncwarp();
         }
     } else {
+        // grid-stride over the particles with the next particle's state
+        // loaded before the current one is processed; the trip count is the
+        // same for every thread of the block, so the histograms can be
+        // flushed (block-wide) every FX_SEG iterations
         const int stride = nblk * NT;
-        for (int i = bid * NT + threadIdx.x; i < (int)n; i += stride) {
-            R x = __ldcs(px + i), y = __ldcs(py + i), z = __ldcs(pz + i);
-            R vx = __ldcs(pvx + i), vy = __ldcs(pvy + i), vz = __ldcs(pvz + i);
-            double w = __ldcs(a.w + i);
-            const double wh = need_what ? __ldcs(a.what + i) : 0.0;
-            const unsigned cc = need_cc ? a.cell_cache[i] : 0u;
-            particle<R, L>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
-            if (wr_pos) {
-                __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
-                __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
+        int i = bid * NT + threadIdx.x;
+        R x = R(0), y = R(0), z = R(0), vx = R(0), vy = R(0), vz = R(0);
+        double w = 0.0, wh = 0.0;
+        unsigned cc = 0u;
+        if (i < (int)n) {
+            x = __ldcs(px + i); y = __ldcs(py + i); z = __ldcs(pz + i);
+            vx = __ldcs(pvx + i); vy = __ldcs(pvy + i); vz = __ldcs(pvz + i);
+            w = __ldcs(a.w + i);
+            if (need_what) wh = __ldcs(a.what + i);
+            if (need_cc) cc = a.cell_cache[i];
+        }
+        int it = 0;
+        for (int base = bid * NT; base < (int)n; base += stride, i += stride) {
+            const int j = i + stride;
+            R nx = R(0), ny = R(0), nz = R(0), nvx = R(0), nvy = R(0), nvz = R(0);
+            double nw = 0.0, nwh = 0.0;
+            unsigned ncc = 0u;
+            if (j < (int)n) {
+                nx = __ldcs(px + j); ny = __ldcs(py + j); nz = __ldcs(pz + j);
+                nvx = __ldcs(pvx + j); nvy = __ldcs(pvy + j); nvz = __ldcs(pvz + j);
+                nw = __ldcs(a.w + j);
+                if (need_what) nwh = __ldcs(a.what + j);
+                if (need_cc) ncc = a.cell_cache[j];
             }
-            if (wr_w) __stcs(a.w + i, w);
+            if (i < (int)n) {
+                particle<R, L, FL>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                if (wr_pos) {
+                    __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
+                    __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
+                }
+                if (wr_w) __stcs(a.w + i, w);
+            }
+            x = nx; y = ny; z = nz; vx = nvx; vy = nvy; vz = nvz; w = nw; wh = nwh; cc = ncc;
+            if (FX && (fl & F_SCAT) && ++it == FX_SEG / NT && base + stride < (int)n) {
+                __syncthreads();
+                flush_hist(false);
+                __syncthreads();
+                it = 0;
+            }
         }
     }
     __syncthreads();
     // epilogue: flush the block-private histograms and partial sums
     if (fl & F_SCAT) {
         if (FX) {
-            // exact block totals, either into the global totals with 64-bit
-            // integer atomics or to this block's slot for the residual to sum;
-            // integer sums, so the result does not depend on the order
-            long long *sl = (long long *)a.slots + (long long)bid * nobs;
-            for (int k = threadIdx.x; k < nobs; k += NT) {
-                const long long v = (long long)(((unsigned long long)S.h_hi[k] << 32) | (unsigned long long)S.h_lo[k]);
-                if (v >= (1ll << 53) || v <= -(1ll << 53)) t.ovf = true;
-                if (a.fx_atomic) {
-                    if (v) atomicAdd(a.y_acc + k, (unsigned long long)v);
-                } else {
-                    sl[k] = v;
-                }
-            }
+            flush_hist(true);
         } else {
             double *sl = (double *)a.slots + (long long)bid * nobs;
             for (int k = threadIdx.x; k < nobs; k += NT) sl[k] = S.h_d[k];
@@ -662,10 +707,13 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     if (t.bad) atomicOr(a.err, ERR_NONFINITE);
 }
 
-template <class R, int NT, int MINB, int L, int PIPE>
+template <class R, int NT, int MINB, int L, int PIPE, int FL = 0>
 __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
-    pass_body<R, NT, L, PIPE>(a, blockIdx.x, gridDim.x);
+    pass_body<R, NT, L, PIPE, FL>(a, blockIdx.x, gridDim.x);
 }
+
+// flags of the steady-state step pass: pending update, push, scatter, stats
+constexpr int F_STEADY = F_UPD | F_PUSH | F_SCAT | F_STATS;
 
 // Many models in one launch: block b runs block blk_rank[b] of
 // blk_count[m] blocks of model m = blk_model[b]; each model's arguments are
@@ -675,7 +723,7 @@ struct BatchPass {
     const int *blk_model, *blk_rank, *blk_count;
     int flags, cache_read, cache_write;
 };
-template <class R, int NT, int MINB, int L>
+template <class R, int NT, int MINB, int L, int FL = 0>
 __global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__ BatchPass b) {
     const int m = b.blk_model[blockIdx.x];
     __shared__ __align__(16) PassArgs a;
@@ -689,7 +737,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__
         a.cache_write = b.cache_write;
     }
     __syncthreads();
-    pass_body<R, NT, L, 0>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
+    pass_body<R, NT, L, 0, FL>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
 #ifdef M2M_COMMON_KERNELS
@@ -1127,7 +1175,8 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
 // Kernel tables, one per precision, each in its own translation unit.
 void *pass_kernel_f32(int threads, int layout);
 void *pass_kernel_f32_pipe(int layout);
-void *pass_kernel_f32_batch(int layout);
+void *pass_kernel_f32_steady(int layout);
+void *pass_kernel_f32_batch(int layout, bool steady = false);
 void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();

@@ -32,8 +32,28 @@ void *pass_kernel_f32_pipe(int layout) {
     }
 }
 
-// All models of a batch in one launch (compiled layouts, plain loads).
-void *pass_kernel_f32_batch(int layout) {
+// The steady-state step (pending update + push + scatter + stats) with its
+// flags compiled in (1024 threads, plain loads).
+void *pass_kernel_f32_steady(int layout) {
+    switch (layout) {
+        case 1: return (void *)k_pass<float, 1024, 1, 1, 0, F_STEADY>;
+        case 2: return (void *)k_pass<float, 1024, 1, 2, 0, F_STEADY>;
+        case 3: return (void *)k_pass<float, 1024, 1, 3, 0, F_STEADY>;
+        default: return nullptr;
+    }
+}
+
+// All models of a batch in one launch (compiled layouts, plain loads); the
+// steady-state step with its flags compiled in.
+void *pass_kernel_f32_batch(int layout, bool steady) {
+    if (steady) {
+        switch (layout) {
+            case 1: return (void *)k_pass_batch<float, 1024, 1, 1, F_STEADY>;
+            case 2: return (void *)k_pass_batch<float, 1024, 1, 2, F_STEADY>;
+            case 3: return (void *)k_pass_batch<float, 1024, 1, 3, F_STEADY>;
+            default: break;
+        }
+    }
     switch (layout) {
         case 1: return (void *)k_pass_batch<float, 1024, 1, 1>;
         case 2: return (void *)k_pass_batch<float, 1024, 1, 2>;

@@ -246,7 +246,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
     a.prior_kind = M2M_PRIOR_FLAT; a.nE = 1; a.nL = 1;
     const int layout = layout_of(a.sets, nsets);
     void *fn = pass_kernel_f32(1024, layout);
-    const size_t sm = 8 * (size_t)((nobs + 1) & ~1) + 4 * (size_t)((a.edge_len + 3) & ~3) +
+    const size_t sm = 12 * (size_t)((nobs + 3) & ~3) + 4 * (size_t)((a.edge_len + 3) & ~3) +
                       4 * (size_t)((a.gh_len + 3) & ~3);
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, sm);
