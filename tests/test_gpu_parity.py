@@ -128,6 +128,70 @@ def test_cells_on_edges_nan_and_out_of_range(prec):
         assert np.array_equal(oc[k], cell)
 
 
+def _edge_neighbours(edges, T):
+    """Every edge and its two neighbouring values in the state precision."""
+    e = edges.astype(T)
+    lo = np.nextafter(e, T(-np.inf))
+    hi = np.nextafter(e, T(np.inf))
+    ce = np.array([np.float32(v) if np.float32(v) >= v else np.nextafter(np.float32(v), np.float32(np.inf))
+                   for v in edges], T) if T == np.float32 else e
+    return np.unique(np.concatenate([e, lo, hi, ce, np.nextafter(ce, T(-np.inf))]))
+
+
+@pytest.mark.parametrize("name", ["flat-log", "moving-priors", "plain-fp64"])
+def test_scatter_cells_at_edge_neighbours(name):
+    """The compiled scatter decides most cells from the float index guess
+    alone; particles on every edge and one ulp either side of it must land
+    in the same cells as the oracle's (distinct weights: a particle in the
+    wrong cell moves a sum by far more than the tolerance)."""
+    T = np.float32
+    P = problem(name, 2000, "fp32c")
+    rng = np.random.default_rng(5)
+    xs, ys, zs = [], [], []
+    for s in P.obs:
+        if s.geom == "grid":
+            vx = _edge_neighbours(s.edges_x, T)
+            vy = _edge_neighbours(s.edges_y, T)
+            # X = x, Y = z sin i - y cos i: with z = 0 and cos i rounding
+            # to 1 or 1/2 in float, y = -Y / cos i is exact; the other axis
+            # at random
+            c = float(np.float32(P.incl_cos))
+            assert c in (1.0, 0.5)
+            ry = rng.uniform(s.edges_y[0], s.edges_y[-1], vx.size).astype(T)
+            rx = rng.uniform(s.edges_x[0], s.edges_x[-1], vy.size).astype(T)
+            xs += [vx, rx]
+            ys += [(-ry / T(c)).astype(T), (-vy / T(c)).astype(T)]
+            zs += [np.zeros(vx.size, T), np.zeros(vy.size, T)]
+        else:
+            # shells and annuli: edges of r^2 (R^2); a particle on the x axis
+            # with x^2 landing next to each squared edge
+            r = np.sqrt(_edge_neighbours(s.edges_x, np.float64))
+            v = np.unique(np.concatenate([r.astype(T), np.nextafter(r.astype(T), T(0)),
+                                          np.nextafter(r.astype(T), T(np.inf))]))
+            xs.append(v)
+            ys.append(np.zeros(v.size, T))
+            zs.append(np.zeros(v.size, T))
+    x, y, z = (np.concatenate(a).astype(T) for a in (xs, ys, zs))
+    n = x.size
+    pos = np.stack([x, y, z]).astype(np.float64)
+    vel = np.stack([rng.normal(0, 0.3, n) for _ in range(3)])
+    w = 1.0 + np.arange(n) / 4096.0
+    ctx = B.m2m_init("fp32c", pos.astype(T), vel.astype(T), w, w, P.potential, P.obs,
+                     dict(eps=0, mu=0, dt=0.01, alpha=1, entropy_const=1, incl_sin=P.incl_sin,
+                          incl_cos=P.incl_cos))
+    ctx.m2m_observe(0)
+    yg, _, _ = ctx.m2m_get_obs()
+    yo = O.observe(x, y, z, *vel.astype(T), w, P.obs, P.incl_sin, P.incl_cos)
+    off = 0
+    for s in P.obs:
+        blk = slice(off, off + s.nobs)
+        if s.quant == "mass":
+            np.testing.assert_allclose(yg[blk], yo[blk], rtol=1e-12, atol=1e-9)
+        else:
+            np.testing.assert_allclose(yg[blk], yo[blk], rtol=1e-4, atol=1e-4)
+        off += s.nobs
+
+
 def _prior_cells_oracle(P, prec, nsteps):
     st = O.init(P, prec)
     s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
