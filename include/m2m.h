@@ -271,11 +271,12 @@ int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
 int m2m_set_layout(m2m_ctx *ctx, int32_t layout);
 
 /* Streaming and reduction options of the FP32C passes (bit flags):
- *  1: stream the particles of the compiled layouts through a warp-level
- *     pipeline: lane 0 of each warp stages the warp's next 32-particle
- *     chunk into shared memory with bulk copies (TMA) completing on an
- *     mbarrier while the warp computes the current chunk (default off:
- *     plain loads);
+ *  1: stream the particles of the compiled layouts through a block-level
+ *     pipeline: one thread of each block stages the block's next chunk of
+ *     1024 consecutive particles into shared memory with one bulk copy
+ *     (TMA) per array, completing on an mbarrier, while the block computes
+ *     the current chunk (default off: plain loads with a one-particle
+ *     register prefetch);
  *  2: flush each block's exact histogram to a per-block slot reduced by the
  *     residual kernel;
  *  4: flush it with 64-bit integer atomics into the totals (default).

@@ -257,23 +257,31 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.err = c->d_err;
 }
 
+// The potential signature a steady-state kernel is compiled for (PK_ANY:
+// the run-time walk over the components).
+int potential_signature(const m2m_ctx *c) {
+    if (c->npot == 1 && c->pot[0].kind == M2M_POT_HERNQUIST) return PK_HERNQUIST;
+    if (c->npot == 1 && c->pot[0].kind == M2M_POT_LOG) return PK_LOG;
+    if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH) return PK_SH;
+    if (c->npot == 2 && c->pot[0].kind == M2M_POT_HERNQUIST && c->pot[1].kind == M2M_POT_NFW) return PK_HERNQUIST_NFW;
+    return PK_ANY;
+}
+
 int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     PassArgs a;
     fill_args(ctx, a, flags);
     LaunchShape ks = pick_kernel(ctx);
     size_t sm = pass_smem(ctx, flags);
     int occ = 0;
-    const long long pipe_grid = std::min<long long>((long long)ctx->nsm, ctx->slot_cap);
-    if (ctx->pipe && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0 &&
-        (ctx->n + pipe_grid * FX_SEG - 1) / (pipe_grid * FX_SEG) <= 1) {
-        // warp-level bulk-copy pipeline when its stage buffers fit beside the tables
-        void *fp = pass_kernel_f32_pipe(ctx->layout);
-        size_t smp = sm + (size_t)32 * PIPE_STAGES * Chunk<float>::BYTES;
+    if (ctx->pipe && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0) {
+        // block-level bulk-copy pipeline when its stage buffers fit beside the tables
+        void *fp = flags == F_STEADY ? pass_kernel_f32_pipe_steady(ctx->layout) : pass_kernel_f32_pipe(ctx->layout);
+        size_t smp = sm + (size_t)PIPE_STAGES * Chunk<float, 1024>::BYTES;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
         if (occ >= 1) { ks = {fp, 1024}; sm = smp; }
     }
     if (occ < 1 && flags == F_STEADY && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0)
-        ks = {pass_kernel_f32_steady(ctx->layout), 1024};
+        ks = {pass_kernel_f32_steady(ctx->layout, potential_signature(ctx)), 1024};
     if (occ < 1) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
     if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "pass needs %zu B shared memory: does not fit", sm);
     int bps = occ;
@@ -736,9 +744,13 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
-        if (lay) kfns.push_back(pass_kernel_f32_steady(lay));
+        if (lay)
+            for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW})
+                kfns.push_back(pass_kernel_f32_steady(lay, pk));
+        if (lay) kfns.push_back(pass_kernel_f32_pipe_steady(lay));
         kfns.push_back(pass_kernel_f32_batch(lay));
         if (lay) kfns.push_back(pass_kernel_f32_batch(lay, true));
+        if (lay == 2) kfns.push_back(pass_kernel_f32_batch(lay, true, PK_HERNQUIST_NFW));
     }
     for (void *f : kfns) {
         cudaFuncAttributes fa;
@@ -1022,6 +1034,7 @@ struct m2m_batch {
     cudaStream_t st = nullptr;
     bool fusable = false;        // one launch per stage is possible
     int layout = 0;
+    int pk = 0;                  // common potential signature (PK_ANY if they differ)
     int period = 0;              // common moving-prior period (0: flat)
     PassArgs *d_pass = nullptr;  // per-model arguments
     ResArgs *d_res = nullptr;
@@ -1104,7 +1117,7 @@ int batch_pass(m2m_batch *b, int flags, int cache_read) {
     bp.cache_write = 1;
     void *args[] = {&bp};
     const bool steady = flags == F_STEADY && cache_read;
-    cudaError_t e = cudaLaunchKernel(pass_kernel_f32_batch(b->layout, steady), dim3(b->pgrid), dim3(1024), args,
+    cudaError_t e = cudaLaunchKernel(pass_kernel_f32_batch(b->layout, steady, b->pk), dim3(b->pgrid), dim3(1024), args,
                                      batch_smem(b, flags), b->st);
     if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "batched pass: %s", cudaGetErrorString(e));
     return M2M_OK;
@@ -1186,7 +1199,10 @@ int m2m_batch_init(m2m_batch **out, int32_t precision, int32_t nmodels, const m2
     m2m_ctx *c0 = b->ctx[0];
     b->fusable = precision == M2M_FP32C && c0->layout != 0;
     b->layout = c0->layout;
+    b->pk = potential_signature(c0);
     b->period = c0->prior.kind == M2M_PRIOR_FLAT ? 0 : c0->prior.period;
+    for (m2m_ctx *c : b->ctx)
+        if (potential_signature(c) != b->pk) b->pk = PK_ANY;
     for (m2m_ctx *c : b->ctx) {
         const int per = c->prior.kind == M2M_PRIOR_FLAT ? 0 : c->prior.period;
         if (c->layout != b->layout || per != b->period || c->sh_on) b->fusable = false;

@@ -122,6 +122,9 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -357,34 +360,65 @@ __device__ __forceinline__ R sh_phi(R x, R y, R z, const R *T, const PotDev &p) 
     return -s;
 }
 
+// Potential signatures compiled into the steady-state kernels (the generic
+// form walks the component list at run time):
+enum { PK_ANY = 0, PK_HERNQUIST = 1, PK_LOG = 3, PK_SH = 4, PK_HERNQUIST_NFW = 5 };
+
 template <class R>
+__device__ __forceinline__ void acc_hernquist(R x, R y, R z, const PotDev &p, Acc3<R> &g) {
+    R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
+    R r2 = (x * x + y * y) + z * z;
+    R r = sqrt(r2);
+    R s = r + aa;
+    R f = r2 > R(0) ? GM / ((r * s) * s) : R(0);
+    g.x = g.x + (-(f * x));
+    g.y = g.y + (-(f * y));
+    g.z = g.z + (-(f * z));
+}
+template <class R>
+__device__ __forceinline__ void acc_log(R x, R y, R z, const PotDev &p, Acc3<R> &g) {
+    R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), v0sq = KC(R, p.c[2], p.cf[2]);
+    R R2 = x * x + y * y;
+    R D = (Rc2 + R2) + (z * z) * iq2;
+    R f = v0sq / D;
+    g.x = g.x + (-(f * x));
+    g.y = g.y + (-(f * y));
+    g.z = g.z + (-((f * iq2) * z));
+}
+template <class R>
+__device__ __forceinline__ void acc_nfw(R x, R y, R z, const PotDev &p, Acc3<R> &g) {
+    R r2 = (x * x + y * y) + z * z;
+    R f = nfw_f(sqrt(r2), p);
+    g.x = g.x + (-(f * x));
+    g.y = g.y + (-(f * y));
+    g.z = g.z + (-(f * z));
+}
+
+template <class R, int PK = PK_ANY>
 __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const R *sh = nullptr) {
     Acc3<R> g{R(0), R(0), R(0)};
+    if constexpr (PK == PK_HERNQUIST) {
+        acc_hernquist<R>(x, y, z, a.pot[0], g);
+        return g;
+    } else if constexpr (PK == PK_LOG) {
+        acc_log<R>(x, y, z, a.pot[0], g);
+        return g;
+    } else if constexpr (PK == PK_SH) {
+        sh_accel<R>(x, y, z, sh, a.pot[0], g);
+        return g;
+    } else if constexpr (PK == PK_HERNQUIST_NFW) {
+        acc_hernquist<R>(x, y, z, a.pot[0], g);
+        acc_nfw<R>(x, y, z, a.pot[1], g);
+        return g;
+    }
     for (int k = 0; k < a.npot; ++k) {
         const PotDev &p = a.pot[k];
         if (p.kind == 1) {            // Hernquist
-            R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
-            R r2 = (x * x + y * y) + z * z;
-            R r = sqrt(r2);
-            R s = r + aa;
-            R f = r2 > R(0) ? GM / ((r * s) * s) : R(0);
-            g.x = g.x + (-(f * x));
-            g.y = g.y + (-(f * y));
-            g.z = g.z + (-(f * z));
+            acc_hernquist<R>(x, y, z, p, g);
         } else if (p.kind == 3) {     // flattened logarithmic
-            R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), v0sq = KC(R, p.c[2], p.cf[2]);
-            R R2 = x * x + y * y;
-            R D = (Rc2 + R2) + (z * z) * iq2;
-            R f = v0sq / D;
-            g.x = g.x + (-(f * x));
-            g.y = g.y + (-(f * y));
-            g.z = g.z + (-((f * iq2) * z));
+            acc_log<R>(x, y, z, p, g);
         } else if (p.kind == 2) {     // NFW
-            R r2 = (x * x + y * y) + z * z;
-            R f = nfw_f(sqrt(r2), p);
-            g.x = g.x + (-(f * x));
-            g.y = g.y + (-(f * y));
-            g.z = g.z + (-(f * z));
+            acc_nfw<R>(x, y, z, p, g);
         } else if (p.kind == 4) {     // spherical harmonics of the particles
             sh_accel<R>(x, y, z, sh, p, g);
         }
@@ -424,18 +458,18 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R
     return phi;
 }
 
-template <class R>
+template <class R, int PK = PK_ANY>
 __device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a,
                                     const R *sh = nullptr) {
     R h = KC(R, a.hdt, a.f_hdt), d = KC(R, a.dt, a.f_dt);
-    Acc3<R> g = accel<R>(x, y, z, a, sh);
+    Acc3<R> g = accel<R, PK>(x, y, z, a, sh);
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;
     x = x + d * vx;
     y = y + d * vy;
     z = z + d * vz;
-    g = accel<R>(x, y, z, a, sh);
+    g = accel<R, PK>(x, y, z, a, sh);
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;

@@ -346,7 +346,7 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
 
 // FL != 0: the flags are that compile-time constant (specialised kernels of
 // the steady-state step), else they come from the arguments.
-template <class R, int L, int FL>
+template <class R, int L, int FL, int PK>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
                                          unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
@@ -372,7 +372,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             t.bad = true;       // negative, -0 or NaN weight
         }
     }
-    if (fl & F_PUSH) kdk<R>(x, y, z, vx, vy, vz, a, S.sh);
+    if (fl & F_PUSH) kdk<R, PK>(x, y, z, vx, vy, vz, a, S.sh);
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         R wv = to_r(wn, (R *)nullptr);
@@ -394,25 +394,25 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     w = wn;
 }
 
-// Stage buffer of one warp chunk (32 particles): x,y,z,vx,vy,vz (R), w, w_hat
-// (double), cached cells (u32).
-template <class R> struct Chunk {
-    static constexpr int OX = 0, OY = 32 * sizeof(R), OZ = 64 * sizeof(R), OVX = 96 * sizeof(R),
-                         OVY = 128 * sizeof(R), OVZ = 160 * sizeof(R), OW = 192 * sizeof(R),
-                         OWH = OW + 256, OCC = OWH + 256, BYTES = OCC + 128;
+// Stage buffer of one block chunk (NT consecutive particles): x,y,z,vx,vy,vz
+// (R), w, w_hat (double), cached cells (u32), each array contiguous.
+template <class R, int NT> struct Chunk {
+    static constexpr int OX = 0, OY = NT * sizeof(R), OZ = 2 * NT * sizeof(R), OVX = 3 * NT * sizeof(R),
+                         OVY = 4 * NT * sizeof(R), OVZ = 5 * NT * sizeof(R), OW = 6 * NT * sizeof(R),
+                         OWH = OW + 8 * NT, OCC = OWH + 8 * NT, BYTES = OCC + 4 * NT;
 };
-constexpr int PIPE_STAGES = 2;
+constexpr int PIPE_STAGES = 2;    // the pipeline below is written for two stages
 // particles a block scatters between two flushes of its FP32C histogram
 // (keeps every int32 part-sum of fx_red exact)
 constexpr int FX_SEG = 32768;
 
 // One block's share of a pass over the particles of one model: block `bid`
 // of `nblk` blocks that share the model's particles (grid-stride).
-template <class R, int NT, int L, int PIPE, int FL = 0>
+template <class R, int NT, int L, int PIPE, int FL = 0, int PK = PK_ANY>
 __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, const int nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
-    __shared__ __align__(8) unsigned long long bars[PIPE ? (NT / 32) * PIPE_STAGES : 1];
+    __shared__ __align__(8) unsigned long long bars[PIPE ? 2 * PIPE_STAGES : 1];   // full[], empty[]
     constexpr bool FX = sizeof(R) == 4;
     const int fl = FL ? FL : a.flags;
     PassSmem<R> S{};
@@ -440,11 +440,15 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             S.c_lo = (unsigned *)p; p += 4 * ((a.ncells + 3) & ~3);   // counts
         }
     }
-    unsigned char *stages = p;        // PIPE: (NT/32) * PIPE_STAGES chunk buffers
+    unsigned char *stages = p;        // PIPE: PIPE_STAGES chunk buffers of NT particles
     if constexpr (PIPE) {
-        if ((threadIdx.x & 31) == 0)
-            for (int st = 0; st < PIPE_STAGES; ++st) mbar_init(&bars[(threadIdx.x >> 5) * PIPE_STAGES + st], 1);
-        fence_mbar_init();
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < PIPE_STAGES; ++st) {
+                mbar_init(&bars[st], 1);                          // full: the producer's expect_tx
+                mbar_init(&bars[PIPE_STAGES + st], NT / 32);      // empty: one arrival per warp
+            }
+            fence_mbar_init();
+        }
     }
     // prologue: clear histograms, stage the tables
     if (fl & F_SCAT) {
@@ -518,58 +522,75 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         ++nseg;
     };
     if constexpr (PIPE) {
-        // warp-level pipeline: lane 0 stages the warp's next chunk with bulk
-        // copies while the warp computes the current one
-        using C = Chunk<R>;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        unsigned char *wbuf = stages + (size_t)warp * PIPE_STAGES * C::BYTES;
-        unsigned long long *wbar = &bars[warp * PIPE_STAGES];
-        const int nfull = (int)(n >> 5), nch = (int)((n + 31) >> 5);
-        const int gw = bid * (NT / 32) + warp, TW = nblk * (NT / 32);
-        const unsigned bytes = 6 * 32 * sizeof(R) + 256 + (need_what ? 256 : 0) + (need_cc ? 128 : 0);
-        // no mid-pass flush here: a block may scatter at most FX_SEG particles
-        if (FX && (fl & F_SCAT) && (long long)((nch + TW - 1) / TW) * NT > FX_SEG) t.ovf = true;
-        // per-stage bits: copies pending; parity of the next completion
-        unsigned pendm = 0u, parm = 0u;
-        auto issue = [&](int c, int st) {
+        // block-level pipeline over chunks of NT consecutive particles
+        // (chunk c of this block's grid stride): thread 0 stages the chunk
+        // of the next iteration into the other stage with one bulk copy per
+        // array (>= 4 KB each) once every warp has read that stage's
+        // previous chunk (empty barrier); each thread takes its particle of
+        // the current chunk from shared memory.  Every wait is bounded; a
+        // wait that runs out records M2M_ERR_TIMEOUT and the loop goes on
+        // (results invalid) so that the block's barriers stay matched.
+        using C = Chunk<R, NT>;
+        unsigned long long *full = bars, *empty = bars + PIPE_STAGES;
+        const int lane = threadIdx.x & 31;
+        const int nfull = (int)(n / NT), nch = (int)((n + NT - 1) / NT);
+        const unsigned bytes = 6 * NT * sizeof(R) + 8 * NT + (need_what ? 8 * NT : 0) + (need_cc ? 4 * NT : 0);
+        // thread 0: copies issued to / seen complete in stage 0 and 1 (scalars:
+        // no local-memory array)
+        int iss0 = 0, iss1 = 0, seen0 = 0, seen1 = 0;
+        bool late = false;
+        auto issue = [&](int c, int st) {    // thread 0 only
             if (c >= nfull) return;
-            pendm |= 1u << st;
-            if (lane != 0) return;
-            unsigned char *d = wbuf + st * C::BYTES;
-            unsigned long long *b = wbar + st;
+            unsigned char *d = stages + st * C::BYTES;
+            unsigned long long *b = full + st;
+            if (st) ++iss1; else ++iss0;
             mbar_expect_tx(b, bytes);
-            const size_t oR = (size_t)c * 32 * sizeof(R), oD = (size_t)c * 256;
-            bulk_g2s(d + C::OX, (const char *)px + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OY, (const char *)py + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OZ, (const char *)pz + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OVX, (const char *)pvx + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OVY, (const char *)pvy + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OVZ, (const char *)pvz + oR, 32 * sizeof(R), b);
-            bulk_g2s(d + C::OW, (const char *)a.w + oD, 256, b);
-            if (need_what) bulk_g2s(d + C::OWH, (const char *)a.what + oD, 256, b);
-            if (need_cc) bulk_g2s(d + C::OCC, (const char *)a.cell_cache + (size_t)c * 128, 128, b);
+            const size_t oR = (size_t)c * NT * sizeof(R), oD = (size_t)c * NT * 8, oC = (size_t)c * NT * 4;
+            bulk_g2s(d + C::OX, (const char *)px + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OY, (const char *)py + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OZ, (const char *)pz + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OVX, (const char *)pvx + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OVY, (const char *)pvy + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OVZ, (const char *)pvz + oR, NT * sizeof(R), b);
+            bulk_g2s(d + C::OW, (const char *)a.w + oD, NT * 8, b);
+            if (need_what) bulk_g2s(d + C::OWH, (const char *)a.what + oD, NT * 8, b);
+            if (need_cc) bulk_g2s(d + C::OCC, (const char *)a.cell_cache + oC, NT * 4, b);
         };
-        for (int st = 0; st < PIPE_STAGES; ++st) issue(gw + st * TW, st);
-        bool abort = false;
-        int k = 0;
-        for (int c = gw; c < nch; c += TW, ++k) {
-            const int st = k % PIPE_STAGES;
-            const int i = c * 32 + lane;
+        __syncthreads();                     // barrier initialisation visible to all
+        if (threadIdx.x == 0) {
+            issue(bid, 0);
+            issue(bid + nblk, 1);
+        }
+        int it = 0, k = 0;
+        for (int c = bid; c < nch; c += nblk, ++k) {
+            const int st = k & 1;
+            const unsigned par = (unsigned)(k >> 1) & 1u;
+            if (threadIdx.x == 0 && k >= 1 && c + nblk < nfull) {
+                // the next iteration's chunk goes where the previous one was
+                const int sp = (k + 1) & 1;
+                if (mbar_wait(empty + sp, (unsigned)((k - 1) >> 1) & 1u)) issue(c + nblk, sp);
+                else late = true;
+            }
+            const int i = c * NT + threadIdx.x;
             R x = R(0), y = R(0), z = R(0), vx = R(0), vy = R(0), vz = R(0);
             double w = 0.0, wh = 0.0;
             unsigned cc = 0u;
             if (c < nfull) {
-                const bool ok = mbar_wait(wbar + st, (parm >> st) & 1u);
-                if (__any_sync(0xffffffffu, !ok)) { abort = true; break; }
-                pendm &= ~(1u << st);
-                parm ^= 1u << st;
-                const unsigned char *d = wbuf + st * C::BYTES;
-                x = ((const R *)(d + C::OX))[lane]; y = ((const R *)(d + C::OY))[lane];
-                z = ((const R *)(d + C::OZ))[lane]; vx = ((const R *)(d + C::OVX))[lane];
-                vy = ((const R *)(d + C::OVY))[lane]; vz = ((const R *)(d + C::OVZ))[lane];
-                w = ((const double *)(d + C::OW))[lane];
-                if (need_what) wh = ((const double *)(d + C::OWH))[lane];
-                if (need_cc) cc = ((const unsigned *)(d + C::OCC))[lane];
+                if (mbar_wait(full + st, par)) {
+                    if (threadIdx.x == 0) { if (st) ++seen1; else ++seen0; }
+                } else {
+                    late = true;
+                }
+                const unsigned char *d = stages + st * C::BYTES;
+                const int q = threadIdx.x;
+                x = ((const R *)(d + C::OX))[q]; y = ((const R *)(d + C::OY))[q];
+                z = ((const R *)(d + C::OZ))[q]; vx = ((const R *)(d + C::OVX))[q];
+                vy = ((const R *)(d + C::OVY))[q]; vz = ((const R *)(d + C::OVZ))[q];
+                w = ((const double *)(d + C::OW))[q];
+                if (need_what) wh = ((const double *)(d + C::OWH))[q];
+                if (need_cc) cc = ((const unsigned *)(d + C::OCC))[q];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty + st);
             } else if (i < (int)n) {
                 x = px[i]; y = py[i]; z = pz[i]; vx = pvx[i]; vy = pvy[i]; vz = pvz[i];
                 w = a.w[i];
@@ -577,24 +598,29 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 if (need_cc) cc = a.cell_cache[i];
             }
             if (i < (int)n) {
-                particle<R, L, FL>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
                 if (wr_pos) {
                     __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
                     __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
                 }
                 if (wr_w) __stcs(a.w + i, w);
             }
-            __syncwarp();
-            issue(c + PIPE_STAGES * TW, st);
-        }
-        if (abort) {
-            // let this warp's copies in flight land before the block exits
-            if (lane == 0) {
-                atomicOr(a.err, ERR_TIMEOUT);
-                for (int st = 0; st < PIPE_STAGES; ++st)
-                    if ((pendm >> st) & 1u) mbar_wait(wbar + st, (parm >> st) & 1u);
+            if (FX && (fl & F_SCAT) && ++it == FX_SEG / NT && c + nblk < nch) {
+                __syncthreads();
+                flush_hist(false);
+                __syncthreads();
+                it = 0;
             }
-            __syncwarp();
+        }
+        if (late) {
+            atomicOr(a.err, ERR_TIMEOUT);
+            // let copies still in flight land before the block exits
+            if (threadIdx.x == 0) {
+                for (int u = seen0; u < iss0; ++u)
+                    if (!mbar_wait(full, (unsigned)u & 1u)) break;
+                for (int u = seen1; u < iss1; ++u)
+                    if (!mbar_wait(full + 1, (unsigned)u & 1u)) break;
+            }
         }
     } else {
         // grid-stride over the particles with the next particle's state
@@ -627,7 +653,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 if (need_cc) ncc = a.cell_cache[j];
             }
             if (i < (int)n) {
-                particle<R, L, FL>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
                 if (wr_pos) {
                     __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
                     __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
@@ -707,9 +733,9 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     if (t.bad) atomicOr(a.err, ERR_NONFINITE);
 }
 
-template <class R, int NT, int MINB, int L, int PIPE, int FL = 0>
+template <class R, int NT, int MINB, int L, int PIPE, int FL = 0, int PK = PK_ANY>
 __global__ void __launch_bounds__(NT, MINB) k_pass(const __grid_constant__ PassArgs a) {
-    pass_body<R, NT, L, PIPE, FL>(a, blockIdx.x, gridDim.x);
+    pass_body<R, NT, L, PIPE, FL, PK>(a, blockIdx.x, gridDim.x);
 }
 
 // flags of the steady-state step pass: pending update, push, scatter, stats
@@ -723,7 +749,7 @@ struct BatchPass {
     const int *blk_model, *blk_rank, *blk_count;
     int flags, cache_read, cache_write;
 };
-template <class R, int NT, int MINB, int L, int FL = 0>
+template <class R, int NT, int MINB, int L, int FL = 0, int PK = PK_ANY>
 __global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__ BatchPass b) {
     const int m = b.blk_model[blockIdx.x];
     __shared__ __align__(16) PassArgs a;
@@ -737,7 +763,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__
         a.cache_write = b.cache_write;
     }
     __syncthreads();
-    pass_body<R, NT, L, 0, FL>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
+    pass_body<R, NT, L, 0, FL, PK>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
 #ifdef M2M_COMMON_KERNELS
@@ -1175,8 +1201,9 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
 // Kernel tables, one per precision, each in its own translation unit.
 void *pass_kernel_f32(int threads, int layout);
 void *pass_kernel_f32_pipe(int layout);
-void *pass_kernel_f32_steady(int layout);
-void *pass_kernel_f32_batch(int layout, bool steady = false);
+void *pass_kernel_f32_steady(int layout, int pk = PK_ANY);
+void *pass_kernel_f32_pipe_steady(int layout);
+void *pass_kernel_f32_batch(int layout, bool steady = false, int pk = PK_ANY);
 void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();
