@@ -64,7 +64,8 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
  * M2M_FP64:  positions, push, bins and kernels in double; double sums.
  * M2M_FP32C: positions, push, bins and kernels in float; weights stored and
  *   updated in double; histogram sums exact in 64-bit fixed point
- *   (resolution 2^-50 of the initial total weight); chi^2, entropy and the
+ *   (resolution 2^-25 of the initial average weight, i.e. 2^-25 *
+ *   2^ceil(log2 sum w) / 2^ceil(log2 n)); chi^2, entropy and the
  *   prior-cell means reduced in double. */
 #define M2M_FP64  0
 #define M2M_FP32C 1
@@ -85,9 +86,9 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
  *           them (exterior multipole law beyond rmax, interior solution
  *           inside rmin).  Which side of node k a particle is on is decided
  *           by its r^2 against r_k^2, like the shells.  Side sums: FP32C
- *           exact 64-bit fixed point of the float terms (resolution 2^-56
- *           of the initial total weight), FP64 double sums; the tables are
- *           built in double.  Recomputed from
+ *           exact 64-bit fixed point of the float terms (resolution 2^-31
+ *           of the initial average weight), FP64 double sums; the tables
+ *           are built in double.  Recomputed from
  *           (x_{t+1}, w_{t+1}) after the update of every step t+1 that is a
  *           multiple of `period` (integer >= 1), at m2m_init and by
  *           m2m_potential.  At most one SH component, listed last; added

@@ -72,6 +72,7 @@ struct m2m_ctx {
     double *d_cell_mean;
     int fx_shift;
     double fx_q;
+    int cell_shift;      // FP32C prior-cell sums: weight * 2^cell_shift (2^-60 of the initial total)
     long long t;
     bool pending;
     int last_grid;       // grid of the last scatter pass (slots to reduce)
@@ -243,6 +244,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.gh_tab = c->d_gh; a.gh_len = c->gh_len;
     a.coef = c->d_coef_r;
     a.slots = c->d_slots; a.fx_shift = c->fx_shift; a.y_acc = c->d_y_acc; a.fx_atomic = c->fx_atomic;
+    a.cell_shift = c->cell_shift;
     a.stat_slots = c->d_stat_slots;
     a.prior_kind = c->prior.kind; a.nE = c->prior.nE; a.nL = c->prior.nL; a.ncells = c->ncells;
     a.pk = c->prior.hernquist_a / c->prior.hernquist_GM;
@@ -346,7 +348,8 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
     {
         LaunchTimer lt(ctx, M2M_TK_PRIOR);
         k_prior_mean<<<nb, 256, 0, ctx->st>>>(ctx->d_cell_acc, ctx->d_cell_cnt, ctx->ncells,
-                                              ctx->prec == M2M_FP32C, ctx->fx_q, ctx->d_cell_mean);
+                                              ctx->prec == M2M_FP32C, ldexp(1.0, -ctx->cell_shift),
+                                              ctx->d_cell_mean);
         CU(cudaGetLastError());
     }
     int g = ctx->nsm * 8;
@@ -764,10 +767,15 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         }
     }
 
-    // fixed-point scale from the initial total weight: resolution
-    // 2^-50 * 2^ceil(log2 sum w), range 2^13 times that total
-    ctx->fx_shift = 50;
-    ctx->fx_q = ldexp(1.0, -50);
+    // fixed-point scale from the particle count and the initial total
+    // weight: resolution 2^-25 of the average weight (2^-25 * 2^ceil(log2
+    // sum w) / 2^ceil(log2 n)), so that the usual terms w K stay below the
+    // 2^31 of the fast histogram path (terms up to ~64 times the average)
+    int nbits = 0;
+    while ((1ll << nbits) < n) ++nbits;
+    ctx->fx_shift = FX_AVG_BITS + nbits;
+    ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
+    ctx->cell_shift = 60;
     int g = 0;
     rc = launch_pass(ctx, F_STATS, &g);
     if (rc == M2M_OK) {
@@ -780,8 +788,9 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         if (rc == M2M_OK && !(W >= 0 && isfinite(W))) rc = set_err(ctx, M2M_ERR_NONFINITE, "sum of weights not finite");
         if (rc == M2M_OK && W > 0) {
             int e2 = (int)ceil(log2(W));
-            ctx->fx_shift = 50 - e2;
+            ctx->fx_shift = FX_AVG_BITS + nbits - e2;
             ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
+            ctx->cell_shift = 60 - e2;
         }
     }
     if (rc == M2M_OK && ctx->sh_on) rc = sh_setup(ctx);

@@ -69,6 +69,7 @@ struct PassArgs {
     unsigned long long *y_acc;              // FP32C: [nobs] int64 fixed-point totals
     int fx_atomic;                          // FP32C: flush to y_acc with atomics (else slots)
     int fx_shift;                           // fixed point: value * 2^fx_shift
+    int cell_shift;                         // FP32C prior-cell sums: weight * 2^cell_shift
     double *stat_slots;                     // [grid][2]: S, sum w
     // priors
     int prior_kind, nE, nL, ncells;
@@ -618,6 +619,17 @@ __device__ __forceinline__ int cell_t(const SetDev &s, const R *edges, R x, R y,
 // remainder V - h*2^16), larger terms take the bit-level path.
 // fscale = 2^sh as a float (an exact power of two).
 constexpr float FX_MAGIC = 12582912.0f;            // 1.5 * 2^23
+// The common case of fx_red, for |S| = |v * 2^sh| < 2^31 (A = 0): the two
+// lower parts only, no range test; the caller checks the range once for all
+// of a particle's terms of one observable set.
+constexpr float FX_FAST = 2147483648.0f;           // 2^31
+__device__ __forceinline__ void fx_red_fast(int *Lo, int *Mid, int b, float S) {
+    const float t = fmaf(S, 1.52587890625e-05f, FX_MAGIC);     // round(S / 2^16) + M
+    const float r = fmaf(-(t - FX_MAGIC), 65536.0f, S);        // S - h * 2^16, exact
+    atomicAdd(Lo + b, __float_as_int(r + FX_MAGIC) - 0x4B400000);
+    atomicAdd(Mid + b, __float_as_int(t) - 0x4B400000);
+}
+
 __device__ __forceinline__ void fx_red(int *Lo, int *Mid, int *Hi, int b, float v, float fscale, int sh,
                                        bool &ovf) {
     const float S = v * fscale;

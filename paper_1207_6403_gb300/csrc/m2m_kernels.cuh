@@ -263,16 +263,37 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
             const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
             packed |= (unsigned)(c + 1) << s.cshift;
             if (c >= 0 && wv != R(0)) {
-                if constexpr (q == M2M_Q_MASS) {
-                    hist_add(S, s.obs_off + c, wv, fs, sh, ovf);
-                } else if constexpr (q == M2M_Q_VLOS2) {
-                    hist_add(S, s.obs_off + c, wv * (vlos * vlos), fs, sh, ovf);
+                if constexpr (q == M2M_Q_MASS || q == M2M_Q_VLOS2) {
+                    const R v = q == M2M_Q_MASS ? wv : wv * (vlos * vlos);
+                    if constexpr (sizeof(R) == 4) {
+                        const float Sv = v * fs;
+                        if (fabsf(Sv) < FX_FAST) fx_red_fast(S.hL, S.hM, s.obs_off + c, Sv);
+                        else hist_add(S, s.obs_off + c, v, fs, sh, ovf);
+                    } else {
+                        hist_add(S, s.obs_off + c, v, fs, sh, ovf);
+                    }
                 } else {
                     R u[5];
                     gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
                     const int b = s.obs_off + 5 * c;
+                    if constexpr (sizeof(R) == 4) {
+                        // one range test for the cell's five terms
+                        float Sv[5];
 #pragma unroll
-                    for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
+                        for (int m = 0; m < 5; ++m) Sv[m] = (wv * u[m]) * fs;
+                        const float big = fmaxf(fmaxf(fmaxf(fabsf(Sv[0]), fabsf(Sv[1])), fmaxf(fabsf(Sv[2]), fabsf(Sv[3]))),
+                                                fabsf(Sv[4]));
+                        if (big < FX_FAST) {
+#pragma unroll
+                            for (int m = 0; m < 5; ++m) fx_red_fast(S.hL, S.hM, b + m, Sv[m]);
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
+                    }
                 }
             }
         });
@@ -334,7 +355,7 @@ template <class R>
 __device__ __forceinline__ void cell_add(const PassArgs &a, const PassSmem<R> &S, int c, double wv, bool &ovf);
 template <>
 __device__ __forceinline__ void cell_add<float>(const PassArgs &a, const PassSmem<float> &S, int c, double wv, bool &ovf) {
-    long long q = d2fixed(wv, a.fx_shift, ovf);
+    long long q = d2fixed(wv, a.cell_shift, ovf);
     if (q) fixed_add(S.c_lo, S.c_hi, c, q);
     atomicAdd(S.c_cnt + c, 1u);
 }
@@ -405,6 +426,8 @@ constexpr int PIPE_STAGES = 2;    // the pipeline below is written for two stage
 // particles a block scatters between two flushes of its FP32C histogram
 // (keeps every int32 part-sum of fx_red exact)
 constexpr int FX_SEG = 32768;
+// FP32C fixed-point resolution: 2^-FX_AVG_BITS of the average weight
+constexpr int FX_AVG_BITS = 25;
 
 // One block's share of a pass over the particles of one model: block `bid`
 // of `nblk` blocks that share the model's particles (grid-stride).
