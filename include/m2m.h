@@ -39,6 +39,11 @@
  *    particle) so that the next weight update need not look them up again.
  *    A caller that changes x..vz itself (not through m2m_step/m2m_push)
  *    must call m2m_observe before the next m2m_update_weights.
+ *  - M2M_FP32C keeps ln w_hat_i per particle in float (library-owned, 4
+ *    bytes per particle) for the weight update; it is taken from w_hat at
+ *    m2m_init and rewritten with w_hat at every prior recompute.  A caller
+ *    that writes w_hat itself must do so before m2m_init (or call
+ *    m2m_priors, which overwrites both).
  */
 #ifndef M2M_H
 #define M2M_H

@@ -79,6 +79,7 @@ struct m2m_ctx {
     int layout;          // compiled observable layout of the pass kernel
     int cache_bits;      // bits of the packed per-particle cell cache
     unsigned *d_cell_cache;
+    float *d_lnwhat;     // FP32C: ln w_hat per particle, refreshed at init and at every prior recompute
     bool cache_valid;    // cell cache holds the cells of the current positions
     bool pipe;           // use the bulk-copy pipelined pass where it applies
     int fx_atomic;       // FP32C histogram flush: global integer atomics (1) or slots (0)
@@ -230,7 +231,7 @@ LaunchShape pick_kernel(const m2m_ctx *c) {
 void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     memset(&a, 0, sizeof a);
     a.x = c->x; a.y = c->y; a.z = c->z; a.vx = c->vx; a.vy = c->vy; a.vz = c->vz;
-    a.w = c->w; a.what = c->what; a.n = c->n; a.flags = flags;
+    a.w = c->w; a.what = c->what; a.lnwhat = c->d_lnwhat; a.n = c->n; a.flags = flags;
     a.nsets = c->nsets; a.nobs = c->nobs; a.npot = c->npot;
     memcpy(a.sets, c->sets, sizeof a.sets);
     memcpy(a.pot, c->pot, sizeof a.pot);
@@ -357,7 +358,7 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
     if (g > need) g = (int)need;
     {
         LaunchTimer lt(ctx, M2M_TK_PRIOR);
-        k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->n);
+        k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->d_lnwhat, ctx->n);
         CU(cudaGetLastError());
     }
     return M2M_OK;
@@ -386,7 +387,7 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum};
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -695,6 +696,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_err, 4);
     ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
     ALLOC(ctx->d_cell_cache, 4 * (size_t)n);
+    if (f32) ALLOC(ctx->d_lnwhat, 4 * (size_t)n);
     if (ctx->ncells) {
         ALLOC(ctx->d_cell_ids, 4 * (size_t)n);
         ALLOC(ctx->d_cell_acc, 8 * (size_t)ctx->ncells);
@@ -767,6 +769,16 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         }
     }
 
+    if (f32) {
+        int gl = ctx->nsm * 8;
+        const long long needl = (n + 255) / 256;
+        if (gl > needl) gl = (int)needl;
+        k_lnwhat<<<gl, 256, 0, ctx->st>>>(what, ctx->d_lnwhat, n);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_err(nullptr, M2M_ERR_CUDA, "ln w_hat launch failed");
+            free_all(ctx); delete ctx; return M2M_ERR_CUDA;
+        }
+    }
     // fixed-point scale from the particle count and the initial total
     // weight: resolution 2^-25 of the average weight (2^-25 * 2^ceil(log2
     // sum w) / 2^ceil(log2 n)), so that the usual terms w K stay below the

@@ -55,6 +55,7 @@ constexpr int SH_MAXK = 512;
 struct PassArgs {
     void *x, *y, *z, *vx, *vy, *vz;
     double *w, *what;
+    const float *lnwhat;                    // FP32C: ln w_hat per particle (library-owned)
     long long n;
     int flags;
     int nsets, nobs, npot;

@@ -314,15 +314,18 @@ __device__ __forceinline__ float expm1_small(float d) {
     return expm1f(d);
 }
 
-// The weight update of one particle: returns the new weight; L1 = ln(w_new/w_hat)
-__device__ __forceinline__ double upd_weight(double w, double what, float dot, const PassArgs &a, float &wnf, float &L1) {
-    float wf = d2f_fast(w), whf = d2f_fast(what);
-    float L = __logf(__fdividef(wf, whf));
-    float G = a.f_mu * (-L - a.f_ent_c) - dot;
-    float d = a.f_eps_dt * G;
-    float e = expm1_small(d);
-    double wn = fma(w, f2d_fast(e), w);
-    wnf = d2f_fast(wn);
+// The weight update of one particle: returns the new weight; wnf = the new
+// weight in the state precision (for the entropy and weight sums), L1 =
+// ln(w_new/w_hat).  FP32C takes ln w_hat
+// (kept per particle in float by the library), FP64 w_hat itself.
+__device__ __forceinline__ double upd_weight(double w, float lnwh, float dot, const PassArgs &a, float &wnf, float &L1) {
+    const float wf = d2f_fast(w);
+    const float L = __logf(wf) - lnwh;
+    const float G = a.f_mu * (-L - a.f_ent_c) - dot;
+    const float d = a.f_eps_dt * G;
+    const float e = expm1_small(d);
+    const double wn = fma(w, f2d_fast(e), w);
+    wnf = fmaf(wf, e, wf);
     L1 = L + d;
     return wn;
 }
@@ -346,9 +349,7 @@ __device__ __forceinline__ void acc_stats(ThreadAcc &t, double wnd, double L1) {
 }
 __device__ __forceinline__ float to_r(double v, float *) { return d2f_fast(v); }
 __device__ __forceinline__ double to_r(double v, double *) { return v; }
-__device__ __forceinline__ float rlog_ratio(double w, double what, float *) {
-    return __logf(__fdividef(d2f_fast(w), d2f_fast(what)));
-}
+__device__ __forceinline__ float rlog_ratio(double w, float lnwh, float *) { return __logf(d2f_fast(w)) - lnwh; }
 __device__ __forceinline__ double rlog_ratio(double w, double what, double *) { return log(w / what); }
 
 template <class R>
@@ -369,8 +370,9 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
 // the steady-state step), else they come from the arguments.
 template <class R, int L, int FL, int PK>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
-                                         R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, double what,
+                                         R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, R what,
                                          unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
+    // what: FP32C ln w_hat, FP64 w_hat
     const int fl = FL ? FL : a.flags;
     const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
@@ -396,7 +398,9 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     if (fl & F_PUSH) kdk<R, PK>(x, y, z, vx, vy, vz, a, S.sh);
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
-        R wv = to_r(wn, (R *)nullptr);
+        // the scattered weight is a function of the stored (double) weight
+        // alone, whichever pass applied the update
+        const R wv = to_r(wn, (R *)nullptr);
         const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t);
         if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
     }
@@ -523,6 +527,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     const bool wr_pos = (fl & F_PUSH) != 0;
     const bool wr_w = (fl & F_UPD) != 0;
     const bool need_what = (fl & (F_UPD | F_STATS)) != 0;
+    // FP32C reads ln w_hat (float, kept by the library), FP64 w_hat
+    const R *pwh = FX ? (const R *)a.lnwhat : (const R *)a.what;
     const bool need_cc = L != 0 && a.cache_read && (fl & F_UPD);
     // FP32C histogram flush (all threads, after a barrier): the exact totals
     // H * 2^32 + M * 2^16 + L of this segment go into the global totals with
@@ -557,7 +563,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         unsigned long long *full = bars, *empty = bars + PIPE_STAGES;
         const int lane = threadIdx.x & 31;
         const int nfull = (int)(n / NT), nch = (int)((n + NT - 1) / NT);
-        const unsigned bytes = 6 * NT * sizeof(R) + 8 * NT + (need_what ? 8 * NT : 0) + (need_cc ? 4 * NT : 0);
+        const unsigned bytes = 6 * NT * sizeof(R) + 8 * NT + (need_what ? NT * sizeof(R) : 0) + (need_cc ? 4 * NT : 0);
         // thread 0: copies issued to / seen complete in stage 0 and 1 (scalars:
         // no local-memory array)
         int iss0 = 0, iss1 = 0, seen0 = 0, seen1 = 0;
@@ -576,7 +582,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             bulk_g2s(d + C::OVY, (const char *)pvy + oR, NT * sizeof(R), b);
             bulk_g2s(d + C::OVZ, (const char *)pvz + oR, NT * sizeof(R), b);
             bulk_g2s(d + C::OW, (const char *)a.w + oD, NT * 8, b);
-            if (need_what) bulk_g2s(d + C::OWH, (const char *)a.what + oD, NT * 8, b);
+            if (need_what) bulk_g2s(d + C::OWH, (const char *)pwh + oR, NT * sizeof(R), b);
             if (need_cc) bulk_g2s(d + C::OCC, (const char *)a.cell_cache + oC, NT * 4, b);
         };
         __syncthreads();                     // barrier initialisation visible to all
@@ -596,7 +602,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             }
             const int i = c * NT + threadIdx.x;
             R x = R(0), y = R(0), z = R(0), vx = R(0), vy = R(0), vz = R(0);
-            double w = 0.0, wh = 0.0;
+            double w = 0.0;
+            R wh = R(0);
             unsigned cc = 0u;
             if (c < nfull) {
                 if (mbar_wait(full + st, par)) {
@@ -610,14 +617,14 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 z = ((const R *)(d + C::OZ))[q]; vx = ((const R *)(d + C::OVX))[q];
                 vy = ((const R *)(d + C::OVY))[q]; vz = ((const R *)(d + C::OVZ))[q];
                 w = ((const double *)(d + C::OW))[q];
-                if (need_what) wh = ((const double *)(d + C::OWH))[q];
+                if (need_what) wh = ((const R *)(d + C::OWH))[q];
                 if (need_cc) cc = ((const unsigned *)(d + C::OCC))[q];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty + st);
             } else if (i < (int)n) {
                 x = px[i]; y = py[i]; z = pz[i]; vx = pvx[i]; vy = pvy[i]; vz = pvz[i];
                 w = a.w[i];
-                if (need_what) wh = a.what[i];
+                if (need_what) wh = pwh[i];
                 if (need_cc) cc = a.cell_cache[i];
             }
             if (i < (int)n) {
@@ -653,26 +660,28 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         const int stride = nblk * NT;
         int i = bid * NT + threadIdx.x;
         R x = R(0), y = R(0), z = R(0), vx = R(0), vy = R(0), vz = R(0);
-        double w = 0.0, wh = 0.0;
+        double w = 0.0;
+        R wh = R(0);
         unsigned cc = 0u;
         if (i < (int)n) {
             x = __ldcs(px + i); y = __ldcs(py + i); z = __ldcs(pz + i);
             vx = __ldcs(pvx + i); vy = __ldcs(pvy + i); vz = __ldcs(pvz + i);
             w = __ldcs(a.w + i);
-            if (need_what) wh = __ldcs(a.what + i);
+            if (need_what) wh = __ldcs(pwh + i);
             if (need_cc) cc = a.cell_cache[i];
         }
         int it = 0;
         for (int base = bid * NT; base < (int)n; base += stride, i += stride) {
             const int j = i + stride;
             R nx = R(0), ny = R(0), nz = R(0), nvx = R(0), nvy = R(0), nvz = R(0);
-            double nw = 0.0, nwh = 0.0;
+            double nw = 0.0;
+            R nwh = R(0);
             unsigned ncc = 0u;
             if (j < (int)n) {
                 nx = __ldcs(px + j); ny = __ldcs(py + j); nz = __ldcs(pz + j);
                 nvx = __ldcs(pvx + j); nvy = __ldcs(pvy + j); nvz = __ldcs(pvz + j);
                 nw = __ldcs(a.w + j);
-                if (need_what) nwh = __ldcs(a.what + j);
+                if (need_what) nwh = __ldcs(pwh + j);
                 if (need_cc) ncc = a.cell_cache[j];
             }
             if (i < (int)n) {
@@ -996,9 +1005,18 @@ __global__ void k_prior_mean(const void *acc, const unsigned *cnt, int ncells, i
     mean[c] = k ? s / (double)k : 0.0;
 }
 
-__global__ void k_prior_gather(const int *cell, const double *mean, double *what, long long n) {
+__global__ void k_prior_gather(const int *cell, const double *mean, double *what, float *lnwhat, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double m = mean[cell[i]];
+        what[i] = m;
+        if (lnwhat) lnwhat[i] = logf(__double2float_rn(m));
+    }
+}
+
+// ln w_hat in float from w_hat (FP32C: read by the weight update).
+__global__ void k_lnwhat(const double *what, float *lnwhat, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        what[i] = mean[cell[i]];
+        lnwhat[i] = logf(__double2float_rn(what[i]));
 }
 
 // ------------------------------------------------------ spherical harmonics
