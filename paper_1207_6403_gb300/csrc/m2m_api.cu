@@ -260,6 +260,24 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.err = c->d_err;
 }
 
+// A launch that may overlap the end of the preceding kernel of the stream
+// (programmatic dependent launch); the pass and residual kernels wait for
+// their inputs with griddep_wait.
+cudaError_t launch_dependent(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // The potential signature a steady-state kernel is compiled for (PK_ANY:
 // the run-time walk over the components).
 int potential_signature(const m2m_ctx *c) {
@@ -298,7 +316,7 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     void *args[] = {&a};
     {
         LaunchTimer lt(ctx, pass_kind(flags));
-        CU(cudaLaunchKernel(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
+        CU(launch_dependent(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
     }
     if (flags & F_SCAT) ctx->last_grid = (int)grid;
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
@@ -326,7 +344,7 @@ int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, 
     int nb = direct ? (ctx->nobs + RES_NT_FX - 1) / RES_NT_FX : (ctx->nobs + 31) / 32;
     void *args[] = {&r};
     LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
-    CU(cudaLaunchKernel((void *)k_residual, dim3(nb), dim3(nt), args, 0, ctx->st));
+    CU(launch_dependent((void *)k_residual, dim3(nb), dim3(nt), args, 0, ctx->st));
     return M2M_OK;
 }
 

@@ -150,6 +150,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     return false;
 }
 
+// ------------------------------------------------------------ dependent launch
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start before the preceding kernel of its stream has
+// finished; griddep_wait() returns once that kernel has completed and its
+// memory is visible, so everything a kernel reads that the preceding one may
+// write comes after it.  griddep_launch() lets the next kernel start early.
+// Both are no-ops for kernels launched the ordinary way.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ conversions
 // Non-negative double -> float by truncation with integer instructions
 // only (no FP64-pipe fallback): below the float range -> 0, above -> inf.

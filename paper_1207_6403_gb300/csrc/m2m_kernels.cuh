@@ -477,15 +477,18 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             fence_mbar_init();
         }
     }
-    // prologue: clear histograms, stage the tables
+    // prologue: clear histograms, stage the tables (the edge and GH tables
+    // are fixed at m2m_init; everything else a preceding kernel may write,
+    // so it is read after griddep_wait)
     if (fl & F_SCAT) {
         unsigned *hz = FX ? (unsigned *)S.hL : (unsigned *)S.h_d;
         for (int k = threadIdx.x; k < (FX ? 3 : 2) * nobs; k += NT) hz[k] = 0u;
     }
-    if (fl & F_UPD)
-        for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
     for (int k = threadIdx.x; k < a.edge_len; k += NT) ((R *)S.edges)[k] = ((const R *)a.edge_tab)[k];
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    griddep_wait();
+    if (fl & F_UPD)
+        for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
     for (int k = threadIdx.x; k < sh_len; k += NT) ((R *)S.sh)[k] = ((const R *)a.sh_tab)[k];
     if ((fl & F_UPD) && L != 0) {
         // E[H_n] over N(m, t2) as polynomials in m (van der Marel & Franx
@@ -701,6 +704,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             }
         }
     }
+    griddep_launch();
     __syncthreads();
     // epilogue: flush the block-private histograms and partial sums
     if (fl & F_SCAT) {
@@ -832,6 +836,8 @@ __device__ __forceinline__ double block_sum_strided(const double *v, int stride,
 constexpr int RES_NT = 1024;      // slot reduction
 constexpr int RES_NT_FX = 128;    // FP32C atomic totals
 __device__ __forceinline__ void residual_body(const ResArgs &a, const int bid, const int nblk) {
+    griddep_wait();            // the totals of the preceding pass
+    griddep_launch();          // the next pass may stage its fixed tables meanwhile
     constexpr int NW = RES_NT / 32;
     __shared__ unsigned long long si[NW][32];
     __shared__ double sd[NW][32];
