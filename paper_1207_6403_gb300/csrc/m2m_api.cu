@@ -187,20 +187,8 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
 }
 
 size_t pass_smem(const m2m_ctx *c, int flags) {
-    size_t rs = c->prec == M2M_FP32C ? 4 : 8;
-    size_t b = 0;
-    if (flags & F_SCAT) b += c->prec == M2M_FP32C ? 12 * (size_t)((c->nobs + 3) & ~3) : 8 * (size_t)((c->nobs + 1) & ~1);
-    if (flags & F_UPD) b += rs * (size_t)((c->nobs + 3) & ~3);
-    b += rs * (size_t)((c->edge_len + 3) & ~3);
-    b += rs * (size_t)((c->gh_len + 3) & ~3);
-    if (flags & F_UPD) b += rs * (size_t)((c->gh_len + 3) & ~3);
-    if (c->sh_on && (flags & (F_PUSH | F_MINMAX | F_CELLS))) b += rs * (size_t)((SH_ROW * c->sh_K + 3) & ~3);
-    if (flags & F_CELLS) {
-        b += rs * (size_t)((c->prior.nE + 4) & ~3) + rs * (size_t)((c->prior.nL + 4) & ~3) + 16;
-        if (c->prec == M2M_FP32C) b += 12 * (size_t)((c->ncells + 3) & ~3);
-        else b += 8 * (size_t)((c->ncells + 1) & ~1) + 4 * (size_t)((c->ncells + 3) & ~3);
-    }
-    return b;
+    return pass_smem_bytes(c->prec == M2M_FP32C, c->layout, flags, c->nobs, c->edge_len, c->gh_len,
+                           c->sh_on ? SH_ROW * c->sh_K : 0, c->prior.nE, c->prior.nL, c->ncells);
 }
 
 // Compile-time observable layout matching the context's sets (see
@@ -629,6 +617,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
                 delete ctx; return M2M_ERR_ARG;
             }
             d.gh_off = (int)gh_d.size();
+            d.ghc_off = d.gh_off / 5;
             for (long long c = 0; c < cells; ++c) {
                 double S = o.gh_S[c];
                 if (!(S > 0) || !isfinite(o.gh_V[c])) {

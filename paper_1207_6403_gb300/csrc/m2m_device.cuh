@@ -27,6 +27,7 @@ struct SetDev {
     int obs_off;          // first observable of this set
     int ex_off, ey_off;   // offsets into the edge table
     int gh_off;           // offset into the GH table (5 values per cell)
+    int ghc_off;          // the same in cells (gh_off / 5)
     int gx_mode, gy_mode; // index guess for the x / y edges
     float gx_a, gx_b, gy_a, gy_b;
     float gx_top, gy_top; // nx - 1, ny - 1 as floats (clamp of the guess)
@@ -560,6 +561,14 @@ __device__ __forceinline__ void gh_eval(double vlos, const double *g, double u[5
     u[4] = gs * ((4.0 * E4 - 12.0 * E2 + 3.0) / SQ24);
 }
 
+// gh_eval from the combined per-cell record of the compiled layouts:
+// r[0] = (V, 1/S, c1, P0), r[1] = (P1..P4), r[2] = (t2, norm, 0, 0).
+__device__ __forceinline__ void gh_eval_rec(float vlos, const float4 *r, float u[5]) {
+    const float4 a = r[0], c = r[2];
+    const float g[5] = {a.x, a.y, a.z, c.x, c.y};
+    gh_eval(vlos, g, u);
+}
+
 __device__ __forceinline__ float gh_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double gh_exp(double x) { return exp(x); }
 
@@ -586,8 +595,14 @@ __device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R 
 // log2, fitted on the host) is within one cell of the true cell everywhere
 // in range: one correction step on each side, decided by the two edges of
 // the guessed cell.  Same membership as find_bin.
+// Both edges of cell k as one shared-memory load: (e[k], e[k+1]).
+template <class R> struct EdgePair;
+template <> struct EdgePair<float> { using T = float2; };
+template <> struct EdgePair<double> { using T = double2; };
+template <class R> using Pair = typename EdgePair<R>::T;
+
 template <class R, int MODE>
-__device__ __forceinline__ int find_fast(R v, const R *e, int nb, float ga, float gb, float top) {
+__device__ __forceinline__ int find_fast(R v, const Pair<R> *e, int nb, float ga, float gb, float top) {
     const float fv = (float)v;
     const float t = MODE == G_LOG ? __log2f(fv) : fv;
     // nearest integer to (guess - 1/2), clamped to the table: within one cell
@@ -595,15 +610,15 @@ __device__ __forceinline__ int find_fast(R v, const R *e, int nb, float ga, floa
     // a v outside the table (or NaN) ends outside [0, nb)
     const float gf = fminf(fmaxf(fmaf(ga, t, gb) - 0.5f, 0.0f), top);
     int g = rint_small(gf);
-    const R lo = e[g], hi = e[g + 1];
-    g += (v >= hi ? 1 : 0) - (v < lo ? 1 : 0);
+    const Pair<R> ed = e[g];
+    g += (v >= ed.y ? 1 : 0) - (v < ed.x ? 1 : 0);
     return ((unsigned)g < (unsigned)nb && v == v) ? g : -1;
 }
 
 // Cell of a particle in a set of compile-time geometry G whose edge tables
 // are uniform in value (G_LIN: grids) or in log (G_LOG: shells, annuli).
 template <class R, int G>
-__device__ __forceinline__ int cell_t(const SetDev &s, const R *edges, R x, R y, R z, R X, R Ys) {
+__device__ __forceinline__ int cell_t(const SetDev &s, const Pair<R> *edges, R x, R y, R z, R X, R Ys) {
     if constexpr (G == 1) {
         R r2 = (x * x + y * y) + z * z;
         return find_fast<R, G_LOG>(r2, edges + s.ex_off, s.nx, s.gx_a, s.gx_b, s.gx_top);

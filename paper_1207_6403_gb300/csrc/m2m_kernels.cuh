@@ -134,12 +134,37 @@ __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const
 }
 
 // ----------------------------------------------------------------- k_pass
+// Dynamic shared memory of pass_body (host side; the same order and
+// rounding as the carve-up at the top of pass_body, without the pipeline's
+// stage buffers).  sh_len: SH node-table values staged when the pass pushes.
+inline size_t pass_smem_bytes(bool f32, int layout, int flags, int nobs, int edge_len, int gh_len, int sh_len,
+                              int nE, int nL, int ncells) {
+    const size_t rs = f32 ? 4 : 8;
+    size_t b = 0;
+    if (flags & F_SCAT) b += f32 ? 12 * (size_t)((nobs + 3) & ~3) : 8 * (size_t)((nobs + 1) & ~1);
+    if (flags & F_UPD) b += rs * (size_t)((nobs + 3) & ~3);
+    b += rs * (size_t)((edge_len + 3) & ~3);
+    b += 2 * rs * (size_t)((edge_len + 1) & ~1);                     // edge pairs
+    b += rs * (size_t)((gh_len + 3) & ~3);
+    if (f32 && layout != 0) b += 48 * (size_t)(gh_len / 5);          // combined GH records
+    else if (flags & F_UPD) b += rs * (size_t)((gh_len + 3) & ~3);
+    if (sh_len && (flags & (F_PUSH | F_MINMAX | F_CELLS))) b += rs * (size_t)((sh_len + 3) & ~3);
+    if (flags & F_CELLS) {
+        b += rs * (size_t)((nE + 4) & ~3) + rs * (size_t)((nL + 4) & ~3) + 16;
+        if (f32) b += 12 * (size_t)((ncells + 3) & ~3);
+        else b += 8 * (size_t)((ncells + 1) & ~1) + 4 * (size_t)((ncells + 3) & ~3);
+    }
+    return b;
+}
+
 template <class R>
 struct PassSmem {
     int *hL, *hM, *hH;       // FP32C histogram: V = H * 2^32 + M * 2^16 + L per bin (exact fixed point)
     double *h_d;             // FP64 histogram
     const R *coef, *edges, *gh;
+    const Pair<R> *epair;    // (e[k], e[k+1]) for every edge-table index k
     const R *gpoly;          // per GH cell: norm * sum_n coef_n E[H_n] as a quartic in m
+    const float4 *ghc;       // FP32C compiled layouts: per GH cell (V, 1/S, c1, P0), (P1..P4), (t2, norm)
     R *pe, *pl;
     float *gp;
     const R *sh;             // spherical-harmonic node table
@@ -195,7 +220,7 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
             const int c = cached ? (int)((cc >> s.cshift) & (unsigned)s.cmask) - 1
-                                 : cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
+                                 : cell_t<R, g>(s, S.epair, x, y, z, X, Ys);
             if (c >= 0) {
                 if constexpr (q == M2M_Q_MASS) {
                     dot = dot + S.coef[s.obs_off + c];
@@ -204,16 +229,29 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
                 } else {
                     // sum_n coef_n u_n(nu) = exp(-nu m / 2) * P(m), m = nu c1,
                     // with the quartic P of this cell built in the prologue
-                    const R *g = S.gh + s.gh_off + 5 * c;
-                    const R *P = S.gpoly + s.gh_off + 5 * c;
-                    const R nu = (vlos - g[0]) * g[1];
-                    const R m = nu * g[2];
-                    const R e = gh_exp(R(-0.5) * nu * m);
-                    R q = fma(P[4], m, P[3]);
-                    q = fma(q, m, P[2]);
-                    q = fma(q, m, P[1]);
-                    q = fma(q, m, P[0]);
-                    dot = dot + e * q;
+                    if constexpr (sizeof(R) == 4) {
+                        const float4 *r = S.ghc + 3 * (s.ghc_off + c);
+                        const float4 g0 = r[0], g1 = r[1];
+                        const float nu = (vlos - g0.x) * g0.y;
+                        const float m = nu * g0.z;
+                        const float e = gh_exp(-0.5f * nu * m);
+                        float q = fmaf(g1.w, m, g1.z);
+                        q = fmaf(q, m, g1.y);
+                        q = fmaf(q, m, g1.x);
+                        q = fmaf(q, m, g0.w);
+                        dot = dot + e * q;
+                    } else {
+                        const R *g = S.gh + s.gh_off + 5 * c;
+                        const R *P = S.gpoly + s.gh_off + 5 * c;
+                        const R nu = (vlos - g[0]) * g[1];
+                        const R m = nu * g[2];
+                        const R e = gh_exp(R(-0.5) * nu * m);
+                        R q = fma(P[4], m, P[3]);
+                        q = fma(q, m, P[2]);
+                        q = fma(q, m, P[1]);
+                        q = fma(q, m, P[0]);
+                        dot = dot + e * q;
+                    }
                 }
             }
         });
@@ -260,7 +298,7 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
-            const int c = cell_t<R, g>(s, S.edges, x, y, z, X, Ys);
+            const int c = cell_t<R, g>(s, S.epair, x, y, z, X, Ys);
             packed |= (unsigned)(c + 1) << s.cshift;
             if (c >= 0 && wv != R(0)) {
                 if constexpr (q == M2M_Q_MASS || q == M2M_Q_VLOS2) {
@@ -274,7 +312,8 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
                     }
                 } else {
                     R u[5];
-                    gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
+                    if constexpr (sizeof(R) == 4) gh_eval_rec(vlos, S.ghc + 3 * (s.ghc_off + c), u);
+                    else gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
                     const int b = s.obs_off + 5 * c;
                     if constexpr (sizeof(R) == 4) {
                         // one range test for the cell's five terms
@@ -451,8 +490,11 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     }
     if (fl & F_UPD) { S.coef = (const R *)p; p += sizeof(R) * ((nobs + 3) & ~3); }
     S.edges = (const R *)p; p += sizeof(R) * ((a.edge_len + 3) & ~3);
+    S.epair = (const Pair<R> *)p; p += 2 * sizeof(R) * ((a.edge_len + 1) & ~1);
     S.gh = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3);
-    if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
+    constexpr bool GHC = FX && L != 0;      // combined GH records instead of gh + gpoly
+    if (GHC) { S.ghc = (const float4 *)p; p += 48 * (a.gh_len / 5); }
+    else if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
     const int sh_len = (a.sh_tab && (fl & (F_PUSH | F_MINMAX | F_CELLS))) ? SH_ROW * a.sh_K : 0;
     if (sh_len) { S.sh = (const R *)p; p += sizeof(R) * ((sh_len + 3) & ~3); }
     if (fl & F_CELLS) {
@@ -484,31 +526,51 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         unsigned *hz = FX ? (unsigned *)S.hL : (unsigned *)S.h_d;
         for (int k = threadIdx.x; k < (FX ? 3 : 2) * nobs; k += NT) hz[k] = 0u;
     }
-    for (int k = threadIdx.x; k < a.edge_len; k += NT) ((R *)S.edges)[k] = ((const R *)a.edge_tab)[k];
+    for (int k = threadIdx.x; k < a.edge_len; k += NT) {
+        const R *et = (const R *)a.edge_tab;
+        ((R *)S.edges)[k] = et[k];
+        Pair<R> pr;
+        pr.x = et[k];
+        pr.y = k + 1 < a.edge_len ? et[k + 1] : R(INFINITY);
+        ((Pair<R> *)S.epair)[k] = pr;
+    }
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
     griddep_wait();
     if (fl & F_UPD)
         for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
     for (int k = threadIdx.x; k < sh_len; k += NT) ((R *)S.sh)[k] = ((const R *)a.sh_tab)[k];
-    if ((fl & F_UPD) && L != 0) {
+    if (L != 0 && (GHC || (fl & F_UPD))) {
         // E[H_n] over N(m, t2) as polynomials in m (van der Marel & Franx
-        // H_0..H_4), weighted by this step's coefficients of the cell
+        // H_0..H_4), weighted by this step's coefficients of the cell (0
+        // in a pass without an update; FP32C keeps them with the cell's GH
+        // parameters in one record)
         for (int k = 0; k < a.nsets; ++k) {
             const SetDev &st = a.sets[k];
             if (st.quant != M2M_Q_GH) continue;
             const int ncell = st.nx * st.ny;
             for (int c = threadIdx.x; c < ncell; c += NT) {
                 const R *g = (const R *)a.gh_tab + st.gh_off + 5 * c;
-                const R *cf = (const R *)a.coef + st.obs_off + 5 * c;
                 const R t2 = g[3], nrm = g[4];
-                const R r2 = R(1.4142135623730951), r3 = R(1.7320508075688772), r24 = R(4.898979485566356);
-                R *P = (R *)S.gpoly + st.gh_off + 5 * c;
-                P[0] = nrm * (cf[0] + cf[2] * ((R(2) * t2 - R(1)) / r2) +
-                              cf[4] * ((R(12) * t2 * t2 - R(12) * t2 + R(3)) / r24));
-                P[1] = nrm * (cf[1] * r2 + cf[3] * ((R(6) * t2 - R(3)) / r3));
-                P[2] = nrm * (cf[2] * r2 + cf[4] * ((R(24) * t2 - R(12)) / r24));
-                P[3] = nrm * (cf[3] * (R(2) / r3));
-                P[4] = nrm * (cf[4] * (R(4) / r24));
+                R P[5] = {R(0), R(0), R(0), R(0), R(0)};
+                if (fl & F_UPD) {
+                    const R *cf = (const R *)a.coef + st.obs_off + 5 * c;
+                    const R r2 = R(1.4142135623730951), r3 = R(1.7320508075688772), r24 = R(4.898979485566356);
+                    P[0] = nrm * (cf[0] + cf[2] * ((R(2) * t2 - R(1)) / r2) +
+                                  cf[4] * ((R(12) * t2 * t2 - R(12) * t2 + R(3)) / r24));
+                    P[1] = nrm * (cf[1] * r2 + cf[3] * ((R(6) * t2 - R(3)) / r3));
+                    P[2] = nrm * (cf[2] * r2 + cf[4] * ((R(24) * t2 - R(12)) / r24));
+                    P[3] = nrm * (cf[3] * (R(2) / r3));
+                    P[4] = nrm * (cf[4] * (R(4) / r24));
+                }
+                if constexpr (GHC) {
+                    float4 *rc = (float4 *)S.ghc + 3 * (st.ghc_off + c);
+                    rc[0] = make_float4(g[0], g[1], g[2], P[0]);
+                    rc[1] = make_float4(P[1], P[2], P[3], P[4]);
+                    rc[2] = make_float4(t2, nrm, 0.f, 0.f);
+                } else {
+                    R *Pd = (R *)S.gpoly + st.gh_off + 5 * c;
+                    for (int q = 0; q < 5; ++q) Pd[q] = P[q];
+                }
             }
         }
     }
@@ -674,6 +736,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             if (need_cc) cc = a.cell_cache[i];
         }
         int it = 0;
+#pragma unroll 2
         for (int base = bid * NT; base < (int)n; base += stride, i += stride) {
             const int j = i + stride;
             R nx = R(0), ny = R(0), nz = R(0), nvx = R(0), nvy = R(0), nvz = R(0);

@@ -200,6 +200,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
                 return fail(M2M_ERR_ARG, "more than %d Gauss-Hermite cells (the static scratch capacity)",
                             M2M_STATIC_MAX_GH_CELLS);
             d.gh_off = (int)gh.size();
+            d.ghc_off = d.gh_off / 5;
             for (long long c = 0; c < cells; ++c) {
                 const double S = o.gh_S[c];
                 if (!(S > 0) || !isfinite(o.gh_V[c])) return fail(M2M_ERR_ARG, "observable set %d: gh_S must be > 0", s);
@@ -246,8 +247,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
     a.prior_kind = M2M_PRIOR_FLAT; a.nE = 1; a.nL = 1;
     const int layout = layout_of(a.sets, nsets);
     void *fn = pass_kernel_f32(1024, layout);
-    const size_t sm = 12 * (size_t)((nobs + 3) & ~3) + 4 * (size_t)((a.edge_len + 3) & ~3) +
-                      4 * (size_t)((a.gh_len + 3) & ~3);
+    const size_t sm = pass_smem_bytes(true, layout, F_SCAT, nobs, a.edge_len, a.gh_len, 0, 1, 1, 0);
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, sm);
     if (e != cudaSuccess || occ < 1) return fail(M2M_ERR_CUDA, "scatter does not fit: %s", cudaGetErrorString(e));
