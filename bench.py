@@ -248,8 +248,10 @@ def run_ours(args, D):
     n = P.n
     stream = torch.cuda.current_stream()
 
-    # ---- FP32-compensated path: the headline number
+    # ---- FP32-compensated path: the headline number (launch shape and
+    # histogram privatisation autotuned on warm-up steps)
     ctx = B.from_problem(P, "fp32c", device=dev)
+    tuning = ctx.m2m_autotune(max(2, args.warmup // 4))
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()                     # reset the launch counter
@@ -364,6 +366,7 @@ def run_ours(args, D):
                                "m2m_get_record (host)"},
                 "gpu_launches": int(launches),
                 "clocks": clocks.summary(w0, w1),
+                "tuning": tuning,
                 "fp64_gpu": {"value": value64, "unit": "particle-steps/s", "steps": k64,
                              "ms_per_step": ms64 / k64,
                              "hbm_frac_at_120B": BYTES_PER_PARTICLE_FP64 * n * k64 / (ms64 * 1e-3) / 1e9 / peak},
@@ -388,6 +391,7 @@ def run_batched(args, D):
     st = bt.stream
     steps = args.steps if args.steps_given else 2000
     with torch.cuda.stream(st):
+        tuning = bt.m2m_batch_autotune(max(2, args.warmup // 6))
         bt.m2m_batch_step(args.warmup)
         torch.cuda.synchronize()
         clocks = Clocks(D.local)
@@ -428,7 +432,7 @@ def run_batched(args, D):
                              "frac": achieved / peak, "traffic": None,
                              "kernel": "whole step (batched k_pass + batched residual), 72 B/particle",
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
-                "cpu_baseline": cpu, "clocks": clocks.summary(w0, w1)}
+                "cpu_baseline": cpu, "clocks": clocks.summary(w0, w1), "tuning": tuning}
         print(json.dumps(line), flush=True)
     bt.m2m_batch_free()
 
@@ -446,6 +450,7 @@ def run_sh(args, D):
     steps = args.steps if args.steps_given else 1000
     stream = torch.cuda.current_stream()
     ctx = B.from_problem(P, "fp32c", device=dev)
+    tuning = ctx.m2m_autotune(max(2, args.warmup // 4))
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()
@@ -503,7 +508,7 @@ def run_sh(args, D):
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                              "kernel_time_shares": shares},
                 "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks.summary(w0, w1),
-                "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
+                "tuning": tuning, "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
         print(json.dumps(line), flush=True)
 
 

@@ -289,6 +289,32 @@ int m2m_set_layout(m2m_ctx *ctx, int32_t layout);
  * All combinations give bit-identical results. */
 int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable);
 
+/* ---- autotuning (no counterpart in the paper: a property of this
+ * implementation) ----
+ * Chooses the pass launch shape (1024, 512 or 256 threads; FP64: 512, 256)
+ * and the histogram privatisation (per-block shared-memory histograms
+ * flushed by global integer atomics, or to per-block slots reduced by the
+ * residual) and, FP32C with a compiled layout, the bulk-copy pipeline, by
+ * timing real steps of the live model: each candidate advances the model
+ * by steps_per_trial steps (1..10000), so the call advances it by
+ * out->candidates * steps_per_trial steps in all.  FP32C: every candidate
+ * yields the same positions, weights and observables (exact histogram
+ * sums); only S and sum w in the records, reduced in float per thread,
+ * move at rounding level.  FP64: results move at rounding level.
+ * cache_path (may be NULL): a JSON-lines file; an entry with this
+ * device's name and the model's configuration key is applied without
+ * timing (out->from_cache = 1, nothing is advanced), a new choice is
+ * appended.  Synchronises. */
+typedef struct {
+    int32_t threads;          /* chosen pass block size */
+    int32_t pipeline;         /* chosen m2m_set_pipeline flags */
+    double us_per_step;       /* its measured time per step (0 from the cache) */
+    int32_t candidates;       /* configurations timed */
+    int32_t from_cache;       /* 1: taken from cache_path */
+    char key[64];             /* the configuration key */
+} m2m_tuning;
+int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, m2m_tuning *out);
+
 /* Device timing of the library's own launches, by kernel class, with CUDA
  * events recorded on the context's stream around every launch while
  * enabled.  Classes: */
@@ -348,6 +374,14 @@ int m2m_batch_step(m2m_batch *batch, int64_t nsteps);
 
 /* The context of model `model` (owned by the batch: valid until
  * m2m_batch_free; use it for m2m_get_obs, m2m_get_record, ...). */
+/* Autotune a fused batch: the number of pass blocks (1, 2 or 4 times the
+ * SMs x resident blocks, shared in proportion to N_m), each timed on
+ * 2 * steps_per_trial real steps of all models (the models advance; their
+ * results do not depend on the choice).  out->key names the choice; a
+ * batch that steps model by model has nothing to tune (out->candidates =
+ * 0).  Synchronises. */
+int m2m_batch_autotune(m2m_batch *b, int32_t steps_per_trial, m2m_tuning *out);
+
 int m2m_batch_context(m2m_batch *batch, int32_t model, m2m_ctx **ctx_out);
 
 /* 1 if the last m2m_batch_step used one launch per stage for all models

@@ -999,6 +999,103 @@ int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm) {
     return M2M_OK;
 }
 
+int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, m2m_tuning *out) {
+    if (!ctx || !out || steps_per_trial < 1 || steps_per_trial > 10000)
+        return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    memset(out, 0, sizeof *out);
+    // configuration key: what the best launch depends on
+    int dev = 0;
+    cudaDeviceProp prop;
+    CU(cudaGetDevice(&dev));
+    CU(cudaGetDeviceProperties(&prop, dev));
+    unsigned long long h = 1469598103934665603ull;      // FNV-1a over the shape of the model
+    auto mix = [&](long long v) {
+        for (int k = 0; k < 8; ++k) { h ^= (unsigned long long)((v >> (8 * k)) & 0xff); h *= 1099511628211ull; }
+    };
+    mix(ctx->prec); mix(ctx->n); mix(ctx->layout); mix(potential_signature(ctx)); mix(ctx->nobs);
+    mix(ctx->prior.kind); mix(ctx->sh_on ? ctx->sh_K : 0); mix(ctx->edge_len); mix(ctx->gh_len);
+    snprintf(out->key, sizeof out->key, "%016llx", h);
+    std::string devname(prop.name);
+    for (char &ch : devname)
+        if (ch == '"' || ch == '\\' || ch == '\n') ch = ' ';
+    auto valid = [&](int nt, int pl) {
+        if (ctx->prec != M2M_FP32C && (nt == 1024 || (pl & 1) || (pl & 2))) return false;
+        if ((pl & 1) && !(nt == 1024 && ctx->layout != 0)) return false;
+        return true;
+    };
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof line, f)) {
+                if (!strstr(line, out->key)) continue;
+                std::string dn = "\"device\": \"" + devname + "\"";
+                if (!strstr(line, dn.c_str())) continue;
+                const char *pt = strstr(line, "\"threads\": "), *pp = strstr(line, "\"pipeline\": ");
+                int nt = 0, pl = 0;
+                if (pt && pp && sscanf(pt + 11, "%d", &nt) == 1 && sscanf(pp + 12, "%d", &pl) == 1 && valid(nt, pl)) {
+                    ctx->threads = nt;
+                    ctx->bps_req = 0;
+                    ctx->pipe = (pl & 1) != 0;
+                    ctx->fx_atomic = (pl & 2) ? 0 : 1;
+                    out->threads = nt; out->pipeline = pl; out->from_cache = 1;
+                }
+            }
+            fclose(f);
+            if (out->from_cache) return M2M_OK;
+        }
+    }
+    const int shapes[] = {1024, 512, 256};
+    const int flushes[] = {4, 2, 4 | 1, 2 | 1};
+    const bool was_timing = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return set_err(ctx, M2M_ERR_CUDA, "event"); }
+    double best = 1e300;
+    int bt = ctx->threads, bp = (ctx->pipe ? 1 : 0) | (ctx->fx_atomic ? 4 : 2);
+    int rc = M2M_OK;
+    for (int nt : shapes) {
+        for (int pl : flushes) {
+            if (!valid(nt, pl)) continue;
+            ctx->threads = nt;
+            ctx->bps_req = 0;
+            ctx->pipe = (pl & 1) != 0;
+            ctx->fx_atomic = (pl & 2) ? 0 : 1;
+            rc = m2m_step(ctx, 1);                      // warm-up in this shape
+            if (!rc && cudaEventRecord(e0, ctx->st) != cudaSuccess) rc = set_err(ctx, M2M_ERR_CUDA, "event");
+            if (!rc) rc = m2m_step(ctx, steps_per_trial);
+            if (!rc && cudaEventRecord(e1, ctx->st) != cudaSuccess) rc = set_err(ctx, M2M_ERR_CUDA, "event");
+            float ms = 0.f;
+            if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = set_err(ctx, M2M_ERR_CUDA, "event timing");
+            if (rc) break;
+            ++out->candidates;
+            const double us = 1e3 * ms / steps_per_trial;
+            if (us < best) { best = us; bt = nt; bp = pl; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = was_timing;
+    ctx->threads = bt;
+    ctx->bps_req = 0;
+    ctx->pipe = (bp & 1) != 0;
+    ctx->fx_atomic = (bp & 2) ? 0 : 1;
+    if (rc) return rc;
+    out->threads = bt; out->pipeline = bp; out->us_per_step = best;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "{\"device\": \"%s\", \"key\": \"%s\", \"threads\": %d, \"pipeline\": %d, \"us_per_step\": %.3f}\n",
+                    devname.c_str(), out->key, bt, bp, best);
+            fclose(f);
+        }
+    }
+    return check_err_word(ctx);
+}
+
 int m2m_set_layout(m2m_ctx *ctx, int32_t layout) {
     if (!ctx) return M2M_ERR_ARG;
     if (layout < 0) layout = detect_layout(ctx);
@@ -1068,6 +1165,7 @@ struct m2m_batch {
     ResArgs *d_res = nullptr;
     int *d_tab = nullptr;        // pass: model, rank, count | residual: model, rank, count
     int pgrid = 0, rgrid = 0;
+    int mult = 1;                // pass blocks = mult * SMs * resident blocks (autotuned)
     std::vector<int> pcount, rcount;
     long long *d_step = nullptr; // step counter read by the batched residual
     long long t = 0;
@@ -1194,6 +1292,85 @@ int batch_sequence(m2m_batch *b, long long nsteps, long long t0, bool pending) {
     return M2M_OK;
 }
 
+// Block plan of the fused batch: mult * (SMs x resident blocks) pass blocks
+// in proportion to N_m (at least one per model, largest remainders first),
+// one residual block per 128 observables of each model; device tables
+// [model | rank | count] for the pass, then for the residual.  Drops the
+// captured graphs (their launch shapes change).
+int batch_plan(m2m_batch *b, int mult) {
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    b->graphs.clear();
+    m2m_ctx *c0 = b->ctx[0];
+    const int nmodels = b->nmodels;
+    size_t sm = batch_smem(b, F_UPD | F_PUSH | F_SCAT | F_STATS | F_MINMAX);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel_f32_batch(b->layout), 1024, sm);
+    if (e != cudaSuccess || occ < 1) {
+        b->fusable = false;
+        g_init_error = "batched pass does not fit";
+        return M2M_OK;
+    }
+    long long G = (long long)c0->nsm * occ * mult;
+    double tot = 0;
+    for (m2m_ctx *c : b->ctx) tot += (double)c->n;
+    std::vector<double> share(nmodels);
+    int used = 0;
+    b->pcount.assign(nmodels, 1);
+    for (int m = 0; m < nmodels; ++m) {
+        share[m] = G * (double)b->ctx[m]->n / tot;
+        b->pcount[m] = std::max(1, (int)share[m]);
+        long long need = (b->ctx[m]->n + 1023) / 1024;
+        b->pcount[m] = (int)std::min<long long>(std::min<long long>(b->pcount[m], need), b->ctx[m]->slot_cap);
+        used += b->pcount[m];
+    }
+    for (int extra = (int)G - used; extra > 0; --extra) {     // largest remainders first
+        int best = -1;
+        double bestr = 0;
+        for (int m = 0; m < nmodels; ++m) {
+            long long need = (b->ctx[m]->n + 1023) / 1024;
+            if (b->pcount[m] >= need || b->pcount[m] >= b->ctx[m]->slot_cap) continue;
+            double r = share[m] - b->pcount[m];
+            if (best < 0 || r > bestr) { best = m; bestr = r; }
+        }
+        if (best < 0) break;
+        ++b->pcount[best];
+    }
+    b->rcount.assign(nmodels, 1);
+    for (int m = 0; m < nmodels; ++m) b->rcount[m] = (b->ctx[m]->nobs + RES_NT_FX - 1) / RES_NT_FX;
+    b->pgrid = 0;
+    for (int m = 0; m < nmodels; ++m) b->pgrid += b->pcount[m];
+    b->rgrid = 0;
+    for (int m = 0; m < nmodels; ++m) b->rgrid += b->rcount[m];
+    std::vector<int> tab, pm_, pr_, rm_, rr_;
+    for (int m = 0; m < nmodels; ++m)
+        for (int k = 0; k < b->pcount[m]; ++k) { pm_.push_back(m); pr_.push_back(k); }
+    for (int m = 0; m < nmodels; ++m)
+        for (int k = 0; k < b->rcount[m]; ++k) { rm_.push_back(m); rr_.push_back(k); }
+    tab.insert(tab.end(), pm_.begin(), pm_.end());
+    tab.insert(tab.end(), pr_.begin(), pr_.end());
+    tab.insert(tab.end(), b->pcount.begin(), b->pcount.end());
+    tab.insert(tab.end(), rm_.begin(), rm_.end());
+    tab.insert(tab.end(), rr_.begin(), rr_.end());
+    tab.insert(tab.end(), b->rcount.begin(), b->rcount.end());
+    // table layout: pass [model(pgrid) | rank(pgrid) | count(nmodels)],
+    // then residual [model(rgrid) | rank(rgrid) | count(nmodels)]
+    if (b->d_tab) { cudaFree(b->d_tab); b->d_tab = nullptr; }
+    e = cudaMalloc(&b->d_tab, sizeof(int) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !b->d_pass) e = cudaMalloc(&b->d_pass, sizeof(PassArgs) * nmodels);
+    if (e == cudaSuccess && !b->d_res) e = cudaMalloc(&b->d_res, sizeof(ResArgs) * nmodels);
+    if (e == cudaSuccess && !b->d_step) {
+        e = cudaMalloc(&b->d_step, sizeof(long long));
+        if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(long long));
+    }
+    if (e != cudaSuccess) {
+        g_init_error = cudaGetErrorString(e);
+        return M2M_ERR_NOMEM;
+    }
+    b->mult = mult;
+    return M2M_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1236,66 +1413,11 @@ int m2m_batch_init(m2m_batch **out, int32_t precision, int32_t nmodels, const m2
         if (c->layout != b->layout || per != b->period || c->sh_on) b->fusable = false;
     }
     if (b->fusable) {
-        // blocks in proportion to N (at least one per model)
-        size_t sm = batch_smem(b, F_UPD | F_PUSH | F_SCAT | F_STATS | F_MINMAX);
-        int occ = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel_f32_batch(b->layout), 1024, sm);
-        if (e != cudaSuccess || occ < 1) b->fusable = false;
-        long long G = (long long)c0->nsm * std::max(occ, 1);
-        double tot = 0;
-        for (m2m_ctx *c : b->ctx) tot += (double)c->n;
-        std::vector<double> share(nmodels);
-        int used = 0;
-        b->pcount.assign(nmodels, 1);
-        for (int m = 0; m < nmodels; ++m) {
-            share[m] = G * (double)b->ctx[m]->n / tot;
-            b->pcount[m] = std::max(1, (int)share[m]);
-            long long need = (b->ctx[m]->n + 1023) / 1024;
-            b->pcount[m] = (int)std::min<long long>(std::min<long long>(b->pcount[m], need), b->ctx[m]->slot_cap);
-            used += b->pcount[m];
-        }
-        for (int extra = (int)G - used; extra > 0; --extra) {     // largest remainders first
-            int best = -1;
-            double bestr = 0;
-            for (int m = 0; m < nmodels; ++m) {
-                long long need = (b->ctx[m]->n + 1023) / 1024;
-                if (b->pcount[m] >= need || b->pcount[m] >= b->ctx[m]->slot_cap) continue;
-                double r = share[m] - b->pcount[m];
-                if (best < 0 || r > bestr) { best = m; bestr = r; }
-            }
-            if (best < 0) break;
-            ++b->pcount[best];
-        }
-        b->rcount.assign(nmodels, 1);
-        for (int m = 0; m < nmodels; ++m) b->rcount[m] = (b->ctx[m]->nobs + RES_NT_FX - 1) / RES_NT_FX;
-        std::vector<int> tab;
-        b->pgrid = 0;
-        for (int m = 0; m < nmodels; ++m) b->pgrid += b->pcount[m];
-        b->rgrid = 0;
-        for (int m = 0; m < nmodels; ++m) b->rgrid += b->rcount[m];
-        std::vector<int> pm_, pr_, rm_, rr_;
-        for (int m = 0; m < nmodels; ++m)
-            for (int k = 0; k < b->pcount[m]; ++k) { pm_.push_back(m); pr_.push_back(k); }
-        for (int m = 0; m < nmodels; ++m)
-            for (int k = 0; k < b->rcount[m]; ++k) { rm_.push_back(m); rr_.push_back(k); }
-        tab.insert(tab.end(), pm_.begin(), pm_.end());
-        tab.insert(tab.end(), pr_.begin(), pr_.end());
-        tab.insert(tab.end(), b->pcount.begin(), b->pcount.end());
-        tab.insert(tab.end(), rm_.begin(), rm_.end());
-        tab.insert(tab.end(), rr_.begin(), rr_.end());
-        tab.insert(tab.end(), b->rcount.begin(), b->rcount.end());
-        // table layout: pass [model(pgrid) | rank(pgrid) | count(nmodels)],
-        // then residual [model(rgrid) | rank(rgrid) | count(nmodels)]
-        e = cudaMalloc(&b->d_tab, sizeof(int) * tab.size());
-        if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_pass, sizeof(PassArgs) * nmodels);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_res, sizeof(ResArgs) * nmodels);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_step, sizeof(long long));
-        if (e == cudaSuccess) e = cudaMemset(b->d_step, 0, sizeof(long long));
-        if (e != cudaSuccess) {
+        int rc = batch_plan(b, 1);
+        if (rc) {
             batch_free_all(b);
             delete b;
-            return berr(nullptr, M2M_ERR_NOMEM, "batch tables: %s", cudaGetErrorString(e));
+            return berr(nullptr, rc, "batch tables: %s", g_init_error.c_str());
         }
     }
     *out = b;
@@ -1380,6 +1502,45 @@ int m2m_batch_step(m2m_batch *b, int64_t nsteps) {
         c->last_grid = b->pcount[m];
     }
     b->t += nsteps;
+    return M2M_OK;
+}
+
+int m2m_batch_autotune(m2m_batch *b, int32_t steps_per_trial, m2m_tuning *out) {
+    if (!b || !out || steps_per_trial < 1 || steps_per_trial > 10000) return berr(b, M2M_ERR_ARG, "bad argument");
+    memset(out, 0, sizeof *out);
+    out->threads = 1024;
+    out->pipeline = 4;
+    if (!b->fusable) return M2M_OK;           // stepped model by model: nothing to tune here
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return berr(b, M2M_ERR_CUDA, "event");
+    }
+    double best = 1e300;
+    int bm = b->mult, rc = M2M_OK;
+    for (int mult : {1, 2, 4}) {
+        rc = batch_plan(b, mult);
+        if (rc || !b->fusable) break;
+        rc = m2m_batch_step(b, steps_per_trial);        // warm-up: captures this plan's graph
+        if (!rc && cudaEventRecord(e0, b->st) != cudaSuccess) rc = berr(b, M2M_ERR_CUDA, "event");
+        if (!rc) rc = m2m_batch_step(b, steps_per_trial);
+        if (!rc && cudaEventRecord(e1, b->st) != cudaSuccess) rc = berr(b, M2M_ERR_CUDA, "event");
+        float ms = 0.f;
+        if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = berr(b, M2M_ERR_CUDA, "event timing");
+        if (rc) break;
+        ++out->candidates;
+        const double us = 1e3 * ms / steps_per_trial;
+        if (us < best) { best = us; bm = mult; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = batch_plan(b, bm);
+    if (rc) return berr(b, rc, "batch tables: %s", g_init_error.c_str());
+    out->us_per_step = best;
+    out->threads = 1024;
+    snprintf(out->key, sizeof out->key, "pass blocks x%d", bm);
     return M2M_OK;
 }
 

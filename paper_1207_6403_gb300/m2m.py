@@ -51,6 +51,11 @@ TK_N = 7
 TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other", "sh")
 
 
+class m2m_tuning(ctypes.Structure):
+    _fields_ = [("threads", c_int32), ("pipeline", c_int32), ("us_per_step", c_double),
+                ("candidates", c_int32), ("from_cache", c_int32), ("key", ctypes.c_char * 64)]
+
+
 class m2m_timing(ctypes.Structure):
     _fields_ = [("launches", c_int64 * TK_N), ("ms", c_double * TK_N), ("kernels_total", c_int64)]
 
@@ -109,11 +114,13 @@ def library():
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
+        "m2m_autotune": (c_int32, [P, c_int32, ctypes.c_char_p, POINTER(m2m_tuning)]),
         "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
                                          c_double, c_double, c_double, P, P]),
         "m2m_batch_init": (c_int32, [POINTER(P), c_int32, c_int32, POINTER(m2m_model_desc),
                                      POINTER(m2m_params), P]),
         "m2m_batch_step": (c_int32, [P, c_int64]),
+        "m2m_batch_autotune": (c_int32, [P, c_int32, POINTER(m2m_tuning)]),
         "m2m_batch_context": (c_int32, [P, c_int32, POINTER(P)]),
         "m2m_batch_fused": (c_int32, [P]),
         "m2m_batch_free": (c_int32, [P]),
@@ -233,6 +240,15 @@ class Context:
         return {"launches": {k: t.launches[i] for i, k in enumerate(TIMING_KINDS)},
                 "ms": {k: t.ms[i] for i, k in enumerate(TIMING_KINDS)},
                 "kernels_total": t.kernels_total}
+
+    def m2m_autotune(self, steps_per_trial=20, cache_path=None):
+        """Choose launch shape and histogram privatisation by timing real
+        steps (advances the model unless the cache has an entry)."""
+        t = m2m_tuning()
+        cp = None if cache_path is None else os.fsencode(cache_path)
+        _check(library().m2m_autotune(self.ptr, int(steps_per_trial), cp, byref(t)), self.ptr)
+        return {"threads": t.threads, "pipeline": t.pipeline, "us_per_step": t.us_per_step,
+                "candidates": t.candidates, "from_cache": bool(t.from_cache), "key": t.key.decode()}
 
     def m2m_get_sh_table(self, K):
         """(K, 21) node table of the spherical-harmonic component (float64)."""
@@ -436,6 +452,12 @@ class Batch:
 
     def m2m_batch_step(self, nsteps=1):
         _check(library().m2m_batch_step(self.ptr, nsteps), None)
+
+    def m2m_batch_autotune(self, steps_per_trial=10):
+        """Time 1x, 2x and 4x pass blocks on real steps and keep the fastest."""
+        t = m2m_tuning()
+        _check(library().m2m_batch_autotune(self.ptr, int(steps_per_trial), byref(t)), None)
+        return {"us_per_step": t.us_per_step, "candidates": t.candidates, "choice": t.key.decode()}
 
     def m2m_batch_fused(self):
         return library().m2m_batch_fused(self.ptr)
