@@ -60,8 +60,16 @@ struct m2m_ctx {
     void *d_slots;
     unsigned long long *d_y_acc;   // FP32C exact observable totals (int64)
     int slot_cap;
-    double *d_stat_slots, *d_chi_slots;
+    double *d_stat_slots, *d_chi_slots;   // stats: two halves of 2*slot_cap doubles (by stat_par)
     unsigned *d_ticket;
+    int stat_par;        // half of d_stat_slots the next pass with F_STATS writes
+    int stat_prev_nblk;  // blocks of the last pass with F_STATS (its half: stat_par ^ 1)
+    // record of the last step, left to the next pass by its residual
+    bool rec_pending;
+    long long rec_step;
+    int rec_chi_nblk, rec_stat_par, rec_stat_nblk;
+    unsigned long long *d_rec_ticket;
+    unsigned long long rec_base;
     m2m_record *d_ring, *d_last;
     int *d_err;
     void *d_mm_slots;
@@ -234,7 +242,12 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.coef = c->d_coef_r;
     a.slots = c->d_slots; a.fx_shift = c->fx_shift; a.y_acc = c->d_y_acc; a.fx_atomic = c->fx_atomic;
     a.cell_shift = c->cell_shift;
-    a.stat_slots = c->d_stat_slots;
+    a.stat_slots = c->d_stat_slots + (size_t)2 * c->slot_cap * c->stat_par;
+    a.rec_pending = c->rec_pending; a.rec_write_ring = 1; a.rec_step = c->rec_step;
+    a.rec_chi = c->d_chi_slots; a.rec_chi_nblk = c->rec_chi_nblk;
+    a.rec_stat = c->d_stat_slots + (size_t)2 * c->slot_cap * c->rec_stat_par; a.rec_stat_nblk = c->rec_stat_nblk;
+    a.rec_ticket = c->d_rec_ticket; a.rec_base = c->rec_base;
+    a.ring = c->d_ring; a.last = c->d_last;
     a.prior_kind = c->prior.kind; a.nE = c->prior.nE; a.nL = c->prior.nL; a.ncells = c->ncells;
     a.pk = c->prior.hernquist_a / c->prior.hernquist_GM;
     a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
@@ -307,6 +320,8 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
         CU(launch_dependent(ks.fn, dim3((unsigned)grid), dim3(ks.nt), args, sm, ctx->st));
     }
     if (flags & F_SCAT) ctx->last_grid = (int)grid;
+    if (flags & F_STATS) { ctx->stat_prev_nblk = (int)grid; ctx->stat_par ^= 1; }
+    if (a.rec_pending) { ctx->rec_pending = false; ctx->rec_base += (unsigned long long)grid; }
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
     if (flags & F_SCAT) ctx->cache_valid = ctx->layout != 0;
     else if (flags & F_PUSH) ctx->cache_valid = false;
@@ -314,7 +329,13 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     return M2M_OK;
 }
 
-int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, int stat_nblk) {
+// tail 1: the residual's last block writes the step record; 0: the next
+// pass (or finish_record) does, from the partials left in place.
+int finish_record(m2m_ctx *ctx);
+
+int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, int stat_nblk, int tail = 1) {
+    int rc0 = finish_record(ctx);          // its partials are about to be overwritten
+    if (rc0) return rc0;
     ResArgs r;
     memset(&r, 0, sizeof r);
     r.slots = ctx->d_slots; r.nblk = ctx->last_grid; r.nobs = ctx->nobs; r.y_acc = ctx->d_y_acc;
@@ -323,7 +344,8 @@ int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, 
     r.Y = ctx->d_Y; r.inv_sigma = ctx->d_isig; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
     r.coef_d = ctx->d_coef_d; r.coef_r = ctx->d_coef_r; r.r_float = ctx->prec == M2M_FP32C;
     r.mode = mode; r.alpha = ctx->par.alpha; r.mu = ctx->par.mu;
-    r.stat_slots = ctx->d_stat_slots; r.stat_nblk = stat_nblk;
+    r.stat_slots = ctx->d_stat_slots + (size_t)2 * ctx->slot_cap * (ctx->stat_par ^ 1); r.stat_nblk = stat_nblk;
+    r.tail = tail;
     r.chi_slots = ctx->d_chi_slots; r.ticket = ctx->d_ticket;
     r.ring = ctx->d_ring; r.last = ctx->d_last; r.rec_step = rec_step; r.write_ring = write_ring;
     r.err = ctx->d_err;
@@ -331,6 +353,7 @@ int launch_residual(m2m_ctx *ctx, int mode, long long rec_step, int write_ring, 
     int nt = direct ? RES_NT_FX : RES_NT;
     int nb = direct ? (ctx->nobs + RES_NT_FX - 1) / RES_NT_FX : (ctx->nobs + 31) / 32;
     void *args[] = {&r};
+    ctx->rec_chi_nblk = nb;
     LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
     CU(launch_dependent((void *)k_residual, dim3(nb), dim3(nt), args, 0, ctx->st));
     return M2M_OK;
@@ -370,6 +393,19 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
     return M2M_OK;
 }
 
+// Writes a record still left to a next pass (when no pass follows).
+int finish_record(m2m_ctx *ctx) {
+    if (!ctx->rec_pending) return M2M_OK;
+    LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
+    k_record<<<1, 32, 0, ctx->st>>>(ctx->d_chi_slots, ctx->rec_chi_nblk,
+                                    ctx->d_stat_slots + (size_t)2 * ctx->slot_cap * ctx->rec_stat_par,
+                                    ctx->rec_stat_nblk, ctx->par.mu, ctx->rec_step, 1, ctx->d_ring, ctx->d_last,
+                                    ctx->d_err);
+    CU(cudaGetLastError());
+    ctx->rec_pending = false;
+    return M2M_OK;
+}
+
 int check_err_word(m2m_ctx *ctx) {
     int h = 0;
     CU(cudaMemcpyAsync(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost, ctx->st));
@@ -390,7 +426,7 @@ void free_events(m2m_ctx *c) {
 void free_all(m2m_ctx *c) {
     free_events(c);
     void *ptrs[] = {c->d_edges, c->d_gh, c->d_Y, c->d_sigma, c->d_isig, c->d_Dt, c->d_y, c->d_Delta, c->d_coef_d,
-                    c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_ring,
+                    c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
                     c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat};
@@ -695,7 +731,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_coef_r, rs * nobs);
     ALLOC(ctx->d_slots, (size_t)8 * nobs * ctx->slot_cap);
     ALLOC(ctx->d_y_acc, (size_t)8 * nobs);
-    ALLOC(ctx->d_stat_slots, (size_t)16 * ctx->slot_cap);
+    ALLOC(ctx->d_stat_slots, (size_t)32 * ctx->slot_cap);
+    ALLOC(ctx->d_rec_ticket, 8);
     ALLOC(ctx->d_chi_slots, (size_t)24 * ((nobs + 31) / 32 + 1));
     ALLOC(ctx->d_ticket, 4);
     ALLOC(ctx->d_ring, sizeof(m2m_record) * M2M_HISTORY);
@@ -736,6 +773,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         if (e4 == cudaSuccess) e4 = cudaMemcpy(ctx->d_isig, isig.data(), 8 * nobs, cudaMemcpyHostToDevice);
         cudaError_t e5 = cudaMemset(ctx->d_Dt, 0, 8 * nobs);
         cudaError_t e6 = cudaMemset(ctx->d_ticket, 0, 4);
+        if (e6 == cudaSuccess) e6 = cudaMemset(ctx->d_rec_ticket, 0, 8);
         cudaError_t e7 = cudaMemset(ctx->d_err, 0, 4);
         cudaError_t e8 = cudaMemset(ctx->d_coef_r, 0, rs * nobs);
         cudaError_t e9 = cudaMemset(ctx->d_ring, 0, sizeof(m2m_record) * M2M_HISTORY);
@@ -799,7 +837,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     rc = launch_pass(ctx, F_STATS, &g);
     if (rc == M2M_OK) {
         std::vector<double> st(2 * g);
-        cudaError_t e = cudaMemcpyAsync(st.data(), ctx->d_stat_slots, 16 * g, cudaMemcpyDeviceToHost, ctx->st);
+        cudaError_t e = cudaMemcpyAsync(st.data(), ctx->d_stat_slots + (size_t)2 * ctx->slot_cap * (ctx->stat_par ^ 1),
+                                        16 * g, cudaMemcpyDeviceToHost, ctx->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
         if (e != cudaSuccess) rc = set_err(ctx, M2M_ERR_CUDA, "init reduction: %s", cudaGetErrorString(e));
         double W = 0.0;
@@ -904,8 +943,12 @@ int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
         int g = 0;
         int rc = launch_pass(ctx, fl, &g);
         if (rc) return rc;
-        rc = launch_residual(ctx, 1, t1, 1, g);
+        rc = launch_residual(ctx, 1, t1, 1, g, 0);
         if (rc) return rc;
+        ctx->rec_pending = true;
+        ctx->rec_step = t1;
+        ctx->rec_stat_par = ctx->stat_par ^ 1;
+        ctx->rec_stat_nblk = ctx->stat_prev_nblk;
         ctx->t = t1;
         ctx->pending = true;
         if (prior_due) {
@@ -943,6 +986,8 @@ int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt) {
 
 int m2m_get_record(m2m_ctx *ctx, m2m_record *out) {
     if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    int rc = finish_record(ctx);
+    if (rc) return rc;
     CU(cudaMemcpyAsync(out, ctx->d_last, sizeof *out, cudaMemcpyDeviceToHost, ctx->st));
     return check_err_word(ctx);
 }
@@ -954,6 +999,8 @@ int m2m_get_history(m2m_ctx *ctx, int64_t first, int64_t count, m2m_record *out)
     if (first < lo || first + count - 1 > ctx->t)
         return set_err(ctx, M2M_ERR_ARG, "records [%lld, %lld) not in the ring [%lld, %lld]", (long long)first,
                        (long long)(first + count), lo, ctx->t);
+    int rc = finish_record(ctx);
+    if (rc) return rc;
     for (int64_t k = 0; k < count;) {
         long long idx = (first + k) % M2M_HISTORY;
         long long run = M2M_HISTORY - idx;
@@ -1205,6 +1252,11 @@ int batch_upload(m2m_batch *b) {
     std::vector<ResArgs> ra(b->nmodels);
     for (int m = 0; m < b->nmodels; ++m) {
         m2m_ctx *c = b->ctx[m];
+        // a fused batch writes and reads the first half of the stat slots
+        // and leaves no record to a next pass
+        int rc = finish_record(c);
+        if (rc) return berr(b, rc, "model %d record: %s", m, c->err.c_str());
+        c->stat_par = 0;
         fill_args(c, pa[m], 0);
         ResArgs &r = ra[m];
         memset(&r, 0, sizeof r);
@@ -1216,6 +1268,7 @@ int batch_upload(m2m_batch *b) {
         r.stat_slots = c->d_stat_slots; r.stat_nblk = b->pcount[m];
         r.chi_slots = c->d_chi_slots; r.ticket = c->d_ticket;
         r.ring = c->d_ring; r.last = c->d_last;
+        r.tail = 1;
         r.err = c->d_err;
     }
     cudaError_t e = cudaMemcpyAsync(b->d_pass, pa.data(), sizeof(PassArgs) * b->nmodels, cudaMemcpyHostToDevice, b->st);

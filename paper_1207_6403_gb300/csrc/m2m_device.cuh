@@ -78,6 +78,14 @@ struct PassArgs {
     double pk, pgma;                        // e_lc: a/GM, GM*a
     void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
     const void *sh_tab; int sh_K;           // spherical-harmonic node table (R, SH_ROW per node) or NULL
+    // record of the preceding step, left by its residual to this pass (the
+    // first block to finish its particles writes it; see record_warp)
+    int rec_pending, rec_write_ring, rec_chi_nblk, rec_stat_nblk;
+    long long rec_step;
+    unsigned long long rec_base;            // rec_ticket value the first block sees
+    unsigned long long *rec_ticket;
+    const double *rec_chi, *rec_stat;
+    void *ring, *last;                      // m2m_record
     unsigned *cell_cache;                   // [n] packed cells of the last scatter
     int cache_read, cache_write;
     int *cell_ids;                          // [n]

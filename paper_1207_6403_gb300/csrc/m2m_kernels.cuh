@@ -133,6 +133,65 @@ __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const
     return iE * a.nL + iL;
 }
 
+// ----------------------------------------------------------------- record
+// The step record from the residual's per-block partials (chi^2, sum of
+// Delta^2, max |Delta~|: 3 doubles per block) and the pass's per-block
+// partials (S, sum w: 2 doubles per block), reduced by one warp in a fixed
+// order (lane k takes blocks k, k+32, ... in turn, then a fixed shuffle
+// tree): the same record whichever kernel computes it.  Lane 0 writes it.
+__device__ __forceinline__ void record_warp(const double *chi, int nch, const double *st, int nst, double mu,
+                                            long long step, int write_ring, m2m_record *ring, m2m_record *last,
+                                            int *err) {
+    const int lane = threadIdx.x & 31;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
+    // up to 8 partials per lane loaded before any is added (one memory
+    // latency instead of eight), then added in block order
+    constexpr int U = 8;
+    for (int b0 = lane; b0 < nch; b0 += 32 * U) {
+        double t0[U], t1[U], t2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + 32 * u;
+            const bool ok = b < nch;
+            t0[u] = ok ? chi[3 * b] : 0.0;
+            t1[u] = ok ? chi[3 * b + 1] : 0.0;
+            t2[u] = ok ? chi[3 * b + 2] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) { v0 += t0[u]; v1 += t1[u]; v2 = fmax(v2, t2[u]); }
+    }
+    for (int b0 = lane; b0 < nst; b0 += 32 * U) {
+        double t3[U], t4[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + 32 * u;
+            const bool ok = b < nst;
+            t3[u] = ok ? st[2 * b] : 0.0;
+            t4[u] = ok ? st[2 * b + 1] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) { v3 += t3[u]; v4 += t4[u]; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, o));
+        v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+        v4 += __shfl_xor_sync(0xffffffffu, v4, o);
+    }
+    if (lane == 0) {
+        m2m_record r;
+        r.step = step;
+        r.chi2 = v0; r.chi2_raw = v1; r.S = v3; r.sum_w = v4;
+        r.F = -0.5 * v0 + mu * v3;
+        r.max_abs_dt = v2;
+        *last = r;
+        if (write_ring) ring[step % M2M_HISTORY] = r;
+        if (!(isfinite(v0) && isfinite(v3) && isfinite(v4))) atomicOr(err, ERR_NONFINITE);
+    }
+}
+
 // ----------------------------------------------------------------- k_pass
 // Dynamic shared memory of pass_body (host side; the same order and
 // rounding as the carve-up at the top of pass_body, without the pipeline's
@@ -767,6 +826,15 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             }
         }
     }
+    if (a.rec_pending) {
+        // the record of the preceding step, by the first block to get here
+        __shared__ int s_rec;
+        if (threadIdx.x == 0) s_rec = atomicAdd(a.rec_ticket, 1ull) == a.rec_base;
+        __syncthreads();
+        if (s_rec && threadIdx.x < 32)
+            record_warp(a.rec_chi, a.rec_chi_nblk, a.rec_stat, a.rec_stat_nblk, a.mu, a.rec_step, a.rec_write_ring,
+                        (m2m_record *)a.ring, (m2m_record *)a.last, a.err);
+    }
     griddep_launch();
     __syncthreads();
     // epilogue: flush the block-private histograms and partial sums
@@ -876,6 +944,7 @@ struct ResArgs {
     const double *stat_slots; int stat_nblk;
     double *chi_slots; unsigned *ticket;
     m2m_record *ring, *last; long long rec_step; int write_ring;
+    int tail;                       // 1: the last block writes the record; 0: the next pass does
     int *err;
 };
 
@@ -983,50 +1052,26 @@ __device__ __forceinline__ void residual_body(const ResArgs &a, const int bid, c
         a.chi_slots[3 * bid] = s0;
         a.chi_slots[3 * bid + 1] = s1;
         a.chi_slots[3 * bid + 2] = s2;
-        __threadfence();
-        s_last = (atomicAdd(a.ticket, 1u) == (unsigned)nblk - 1u);
+        if (a.tail) {
+            __threadfence();
+            s_last = (atomicAdd(a.ticket, 1u) == (unsigned)nblk - 1u);
+        }
     }
+    if (!a.tail) return;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // one strided pass over the block partials, one fixed-shape reduction of
-    // the five totals (deterministic: the shape depends only on the sizes)
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        v0 += a.chi_slots[3 * b];
-        v1 += a.chi_slots[3 * b + 1];
-        v2 = fmax(v2, a.chi_slots[3 * b + 2]);
-    }
-    for (int b = threadIdx.x; b < a.stat_nblk; b += blockDim.x) {
-        v3 += a.stat_slots[2 * b];
-        v4 += a.stat_slots[2 * b + 1];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-        v2 = fmax(v2, __shfl_xor_sync(0xffffffffu, v2, o));
-        v3 += __shfl_xor_sync(0xffffffffu, v3, o);
-        v4 += __shfl_xor_sync(0xffffffffu, v4, o);
-    }
-    __shared__ double fin[5][NW];
-    if (lane == 0) { fin[0][wp] = v0; fin[1][wp] = v1; fin[2][wp] = v2; fin[3][wp] = v3; fin[4][wp] = v4; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double C2 = 0.0, C2r = 0.0, M = 0.0, S = 0.0, W = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            C2 += fin[0][k]; C2r += fin[1][k]; M = fmax(M, fin[2][k]); S += fin[3][k]; W += fin[4][k];
-        }
-        m2m_record r;
-        r.step = a.rec_step;
-        r.chi2 = C2; r.chi2_raw = C2r; r.S = S; r.sum_w = W;
-        r.F = -0.5 * C2 + a.mu * S;
-        r.max_abs_dt = M;
-        *a.last = r;
-        if (a.write_ring) a.ring[a.rec_step % M2M_HISTORY] = r;
-        if (!(isfinite(C2) && isfinite(S) && isfinite(W))) atomicOr(a.err, ERR_NONFINITE);
-        *a.ticket = 0u;
-    }
+    if (threadIdx.x < 32)
+        record_warp(a.chi_slots, nblk, a.stat_slots, a.stat_nblk, a.mu, a.rec_step, a.write_ring, a.ring, a.last, a.err);
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+// The record of a step whose residual left it to the next pass, when no
+// pass follows (one warp).
+__global__ void k_record(const double *chi, int nch, const double *st, int nst, double mu, long long step,
+                         int write_ring, m2m_record *ring, m2m_record *last, int *err) {
+    griddep_wait();
+    record_warp(chi, nch, st, nst, mu, step, write_ring, ring, last, err);
 }
 
 __global__ void __launch_bounds__(RES_NT) k_residual(const __grid_constant__ ResArgs a) {
