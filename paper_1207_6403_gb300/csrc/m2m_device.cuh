@@ -664,6 +664,26 @@ __device__ __forceinline__ void fx_red_fast(int *Lo, int *Mid, int b, float S) {
     atomicAdd(Mid + b, __float_as_int(t) - 0x4B400000);
 }
 
+// The five Gauss-Hermite terms of one particle (the arithmetic of gh_eval),
+// each scaled by W = w 2^sh and added to the histogram as soon as it is
+// formed (|W u_n| < 2^31 is the caller's test), to keep few values live.
+__device__ __forceinline__ void gh_red_stream(float vlos, const float4 *r, float W, int *Lo, int *Mid, int b) {
+    const float SQ2 = 1.41421356237f, ISQ2 = 0.707106781187f, ISQ3 = 0.57735026919f, ISQ24 = 0.204124145232f;
+    const float4 a = r[0], c = r[2];
+    const float nu = (vlos - a.x) * a.y;
+    const float c1 = a.z, t2 = c.x;
+    const float gs = c.y * __expf(-0.5f * nu * nu * c1);
+    const float m = nu * c1, m2 = m * m;
+    fx_red_fast(Lo, Mid, b, W * gs);
+    fx_red_fast(Lo, Mid, b + 1, W * (gs * (SQ2 * m)));
+    const float E2 = m2 + t2;
+    fx_red_fast(Lo, Mid, b + 2, W * (gs * (fmaf(2.f, E2, -1.f) * ISQ2)));
+    const float E3 = m * fmaf(3.f, t2, m2);
+    fx_red_fast(Lo, Mid, b + 3, W * (gs * (fmaf(2.f, E3, -3.f * m) * ISQ3)));
+    const float E4 = fmaf(m2, m2, fmaf(6.f * m2, t2, 3.f * t2 * t2));
+    fx_red_fast(Lo, Mid, b + 4, W * (gs * (fmaf(4.f, E4, fmaf(-12.f, E2, 3.f)) * ISQ24)));
+}
+
 __device__ __forceinline__ void fx_red(int *Lo, int *Mid, int *Hi, int b, float v, float fscale, int sh,
                                        bool &ovf) {
     const float S = v * fscale;

@@ -370,25 +370,26 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
                         hist_add(S, s.obs_off + c, v, fs, sh, ovf);
                     }
                 } else {
-                    R u[5];
-                    if constexpr (sizeof(R) == 4) gh_eval_rec(vlos, S.ghc + 3 * (s.ghc_off + c), u);
-                    else gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
                     const int b = s.obs_off + 5 * c;
                     if constexpr (sizeof(R) == 4) {
-                        // one range test for the cell's five terms
-                        float Sv[5];
-#pragma unroll
-                        for (int m = 0; m < 5; ++m) Sv[m] = (wv * u[m]) * fs;
-                        const float big = fmaxf(fmaxf(fmaxf(fabsf(Sv[0]), fabsf(Sv[1])), fmaxf(fabsf(Sv[2]), fabsf(Sv[3]))),
-                                                fabsf(Sv[4]));
-                        if (big < FX_FAST) {
-#pragma unroll
-                            for (int m = 0; m < 5; ++m) fx_red_fast(S.hL, S.hM, b + m, Sv[m]);
+                        // |u_n| <= sqrt 2 for every n and nu (a Gaussian average
+                        // of Hermite functions, Cramer's bound), so one test of
+                        // the weight decides the fast path for all five terms,
+                        // each added as soon as it is formed: (w 2^sh) u_n =
+                        // (w u_n) 2^sh exactly
+                        const float4 *rc = S.ghc + 3 * (s.ghc_off + c);
+                        const float W = wv * fs;
+                        if (fabsf(W) < 0.5f * FX_FAST) {
+                            gh_red_stream(vlos, rc, W, S.hL, S.hM, b);
                         } else {
+                            R u[5];
+                            gh_eval_rec(vlos, rc, u);
 #pragma unroll
                             for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
                         }
                     } else {
+                        R u[5];
+                        gh_eval(vlos, S.gh + s.gh_off + 5 * c, u);
 #pragma unroll
                         for (int m = 0; m < 5; ++m) hist_add(S, b + m, wv * u[m], fs, sh, ovf);
                     }
