@@ -251,7 +251,7 @@ def run_ours(args, D):
     # ---- FP32-compensated path: the headline number (launch shape and
     # histogram privatisation autotuned on warm-up steps)
     ctx = B.from_problem(P, "fp32c", device=dev)
-    tuning = ctx.m2m_autotune(max(2, args.warmup // 4))
+    tuning = ctx.m2m_autotune(max(2, args.warmup // 4), args.tune_cache)
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()                     # reset the launch counter
@@ -310,11 +310,26 @@ def run_ours(args, D):
     c64.m2m_free()
 
     # ---- equal weight accuracy: both GPU forms from the same state, 50 steps
+    # (their orbits are FP32 and FP64 orbits, so particles near cell edges
+    # part ways), and 50 observe + update rounds at the initial positions
+    # (the weight arithmetic alone: same cells for both forms)
     ca, cb = B.from_problem(P, "fp32c", device=dev), B.from_problem(P, "fp64", device=dev)
     ca.m2m_step(50)
     cb.m2m_step(50)
     torch.cuda.synchronize()
     wrel = float(((ca.t["w"] - cb.t["w"]).abs() / cb.t["w"].abs().clamp_min(1e-300)).max().item())
+    ca.m2m_free()
+    cb.m2m_free()
+    ca, cb = B.from_problem(P, "fp32c", device=dev), B.from_problem(P, "fp64", device=dev)
+    for _ in range(50):
+        for c in (ca, cb):
+            c.m2m_observe(1)
+            c.m2m_update_weights()
+    torch.cuda.synchronize()
+    wdiff = ((ca.t["w"] - cb.t["w"]).abs() / cb.t["w"].abs().clamp_min(1e-300))
+    wrel_fixed = {"max": float(wdiff.max().item()), "median": float(wdiff.median().item()),
+                  "w_change_median": float(((cb.t["w"] - torch.as_tensor(P.w0, device=dev)).abs()
+                                            / torch.as_tensor(P.w0, device=dev)).median().item())}
     ca.m2m_free()
     cb.m2m_free()
 
@@ -372,6 +387,7 @@ def run_ours(args, D):
                              "hbm_frac_at_120B": BYTES_PER_PARTICLE_FP64 * n * k64 / (ms64 * 1e-3) / 1e9 / peak},
                 "fp32c_over_fp64": value / value64,
                 "w_max_rel_diff_fp32c_vs_fp64_50_steps": wrel,
+                "w_rel_diff_fp32c_vs_fp64_50_updates_fixed_positions": wrel_fixed,
                 "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
         print(json.dumps(line), flush=True)
 
@@ -450,7 +466,7 @@ def run_sh(args, D):
     steps = args.steps if args.steps_given else 1000
     stream = torch.cuda.current_stream()
     ctx = B.from_problem(P, "fp32c", device=dev)
-    tuning = ctx.m2m_autotune(max(2, args.warmup // 4))
+    tuning = ctx.m2m_autotune(max(2, args.warmup // 4), args.tune_cache)
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()
@@ -521,6 +537,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh"])
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()
     args.steps_given = any(a.startswith("--steps") for a in sys.argv[1:])
     if args.warmup < 3:
