@@ -302,8 +302,10 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
         if (occ >= 1) { ks = {fp, 1024}; sm = smp; }
     }
-    if (occ < 1 && flags == F_STEADY && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0)
-        ks = {pass_kernel_f32_steady(ctx->layout, potential_signature(ctx)), 1024};
+    if (occ < 1 && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0) {
+        void *f = pass_kernel_f32_compiled(flags, ctx->layout, potential_signature(ctx));
+        if (f) ks = {f, 1024};
+    }
     if (occ < 1) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks.fn, ks.nt, sm));
     if (occ < 1) return set_err(ctx, M2M_ERR_ARG, "pass needs %zu B shared memory: does not fit", sm);
     int bps = occ;
@@ -796,7 +798,9 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
         if (lay)
             for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW})
-                kfns.push_back(pass_kernel_f32_steady(lay, pk));
+                for (int fl : {F_STEADY, F_STEADY | F_MINMAX, F_PUSH | F_SCAT | F_STATS,
+                               F_PUSH | F_SCAT | F_STATS | F_MINMAX, F_CELLS | F_UPD})
+                    if (void *f = pass_kernel_f32_compiled(fl, lay, pk)) kfns.push_back(f);
         if (lay) kfns.push_back(pass_kernel_f32_pipe_steady(lay));
         kfns.push_back(pass_kernel_f32_batch(lay));
         if (lay) kfns.push_back(pass_kernel_f32_batch(lay, true));

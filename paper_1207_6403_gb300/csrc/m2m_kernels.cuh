@@ -1358,6 +1358,7 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
 void *pass_kernel_f32(int threads, int layout);
 void *pass_kernel_f32_pipe(int layout);
 void *pass_kernel_f32_steady(int layout, int pk = PK_ANY);
+void *pass_kernel_f32_compiled(int flags, int layout, int pk);   // NULL if not compiled
 void *pass_kernel_f32_pipe_steady(int layout);
 void *pass_kernel_f32_batch(int layout, bool steady = false, int pk = PK_ANY);
 void *pass_kernel_f64(int threads, int layout);
