@@ -450,32 +450,49 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
 __device__ __forceinline__ float plog(float v) { return logf(v); }
 __device__ __forceinline__ double plog(double v) { return log(v); }
 
+// One component's term of Phi (kinds 1 Hernquist, 3 flattened log, 2 NFW,
+// 4 spherical harmonics); the sum is taken in component order from 0.
 template <class R>
+__device__ __forceinline__ R phi_term(int kind, R x, R y, R z, const PotDev &p, const R *sh) {
+    if (kind == 1) {
+        R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
+        R r2 = (x * x + y * y) + z * z;
+        return -(GM / (sqrt(r2) + aa));
+    } else if (kind == 3) {
+        R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), hv = KC(R, p.c[3], p.cf[3]);
+        R R2 = x * x + y * y;
+        R D = (Rc2 + R2) + (z * z) * iq2;
+        return hv * plog(D);
+    } else if (kind == 2) {
+        // Phi = -C ln(1+u)/r, C = 4 pi rho_s r_s^3, evaluated in double
+        // and rounded once; the r -> 0 limit is -C / r_s
+        double xd = x, yd = y, zd = z;
+        double r = sqrt(xd * xd + yd * yd + zd * zd);
+        double u = r * p.c[2];
+        double v = r > 0 ? -p.c[0] * log1p(u) / r : -p.c[0] * p.c[2];
+        return (R)v;
+    } else if (kind == 4) {
+        return sh_phi<R>(x, y, z, sh, p);
+    }
+    return R(0);
+}
+
+// Phi at (x, y, z): the compiled signatures take the same terms in the
+// same order as the run-time walk of the component list.
+template <class R, int PK = PK_ANY>
 __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R *sh = nullptr) {
     R phi = R(0);
-    for (int k = 0; k < a.npot; ++k) {
-        const PotDev &p = a.pot[k];
-        if (p.kind == 1) {
-            R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
-            R r2 = (x * x + y * y) + z * z;
-            phi = phi + (-(GM / (sqrt(r2) + aa)));
-        } else if (p.kind == 3) {
-            R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), hv = KC(R, p.c[3], p.cf[3]);
-            R R2 = x * x + y * y;
-            R D = (Rc2 + R2) + (z * z) * iq2;
-            phi = phi + hv * plog(D);
-        } else if (p.kind == 2) {
-            // Phi = -C ln(1+u)/r, C = 4 pi rho_s r_s^3, evaluated in double
-            // and rounded once; the r -> 0 limit is -C / r_s
-            double xd = x, yd = y, zd = z;
-            double r = sqrt(xd * xd + yd * yd + zd * zd);
-            double u = r * p.c[2];
-            double v = r > 0 ? -p.c[0] * log1p(u) / r : -p.c[0] * p.c[2];
-            phi = phi + (R)v;
-        } else if (p.kind == 4) {
-            phi = phi + sh_phi<R>(x, y, z, sh, p);
-        }
+    if constexpr (PK == PK_HERNQUIST) {
+        return phi + phi_term<R>(1, x, y, z, a.pot[0], sh);
+    } else if constexpr (PK == PK_LOG) {
+        return phi + phi_term<R>(3, x, y, z, a.pot[0], sh);
+    } else if constexpr (PK == PK_SH) {
+        return phi + phi_term<R>(4, x, y, z, a.pot[0], sh);
+    } else if constexpr (PK == PK_HERNQUIST_NFW) {
+        phi = phi + phi_term<R>(1, x, y, z, a.pot[0], sh);
+        return phi + phi_term<R>(2, x, y, z, a.pot[1], sh);
     }
+    for (int k = 0; k < a.npot; ++k) phi = phi + phi_term<R>(a.pot[k].kind, x, y, z, a.pot[k], sh);
     return phi;
 }
 

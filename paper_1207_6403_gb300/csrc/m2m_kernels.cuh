@@ -14,6 +14,7 @@
 //             cell means sum/count and w_hat_i = mean of i's cell.
 // k_cells     cell export for tests.
 #pragma once
+#include <limits.h>
 #include <math.h>
 #include <type_traits>
 #include "m2m_device.cuh"
@@ -99,19 +100,27 @@ __device__ void prior_setup(const PassArgs &a, R *pe, R *pl, float *gp) {
     __syncthreads();
 }
 
-template <class R>
+// Order-preserving integer key of a float that is not NaN (-0 below +0)
+// and its inverse.
+__device__ __forceinline__ int fkey(float v) {
+    const int b = __float_as_int(v);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+template <class R, int PK = PK_ANY>
 __device__ __forceinline__ void energy_lz(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a, const R *sh,
                                           R &E, R &Lz) {
     R v2 = (vx * vx + vy * vy) + vz * vz;
-    E = R(0.5) * v2 + potential<R>(x, y, z, a, sh);
+    E = R(0.5) * v2 + potential<R, PK>(x, y, z, a, sh);
     Lz = x * vy - y * vx;
 }
 
-template <class R>
+template <class R, int PK = PK_ANY>
 __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a,
                                           const R *pe, const R *pl, const float *gp, const R *sh) {
     R E, Lz;
-    energy_lz<R>(x, y, z, vx, vy, vz, a, sh, E, Lz);
+    energy_lz<R, PK>(x, y, z, vx, vy, vz, a, sh, E, Lz);
     if (a.prior_kind == M2M_PRIOR_E_LZ) {
         int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
         int iL = count_le<R>(Lz, pl, a.nL, gp[2], gp[3]);
@@ -229,6 +238,7 @@ struct PassSmem {
     const R *sh;             // spherical-harmonic node table
     unsigned *c_lo, *c_hi, *c_cnt;   // FP32C prior-cell sums / counts
     double *c_d;                     // FP64 prior-cell sums
+    int *mmk;                        // FP32C range keys: min E, max E, max |L_z|
 };
 
 // Observable layouts compiled as straight-line code (set order, geometry,
@@ -505,13 +515,31 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     }
     if (fl & F_MINMAX) {
         R E, Lz;
-        energy_lz<R>(x, y, z, vx, vy, vz, a, S.sh, E, Lz);
-        emin = fmin(emin, E);
-        emax = fmax(emax, E);
-        lzm = fmax(lzm, fabs(Lz));
+        energy_lz<R, PK>(x, y, z, vx, vy, vz, a, S.sh, E, Lz);
+        if constexpr (sizeof(R) == 4) {
+            // FP32C: the warp's min E, max E, max |L_z| as order-preserving
+            // integer keys (one warp reduction each), then the block's by
+            // shared-memory atomics: nothing carried across the particle loop
+            const bool ok = E == E;
+            const int kE = ok ? fkey((float)E) : 0;
+            const float al = fabsf((float)Lz);
+            const unsigned m = __activemask();
+            const int r0 = __reduce_min_sync(m, ok ? kE : INT_MAX);
+            const int r1 = __reduce_max_sync(m, ok ? kE : INT_MIN);
+            const int r2 = __reduce_max_sync(m, al == al ? __float_as_int(al) : 0);
+            if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
+                atomicMin(S.mmk, r0);
+                atomicMax(S.mmk + 1, r1);
+                atomicMax(S.mmk + 2, r2);
+            }
+        } else {
+            emin = fmin(emin, E);
+            emax = fmax(emax, E);
+            lzm = fmax(lzm, fabs(Lz));
+        }
     }
     if (fl & F_CELLS) {
-        int c = prior_cell<R>(x, y, z, vx, vy, vz, a, S.pe, S.pl, S.gp, S.sh);
+        int c = prior_cell<R, PK>(x, y, z, vx, vy, vz, a, S.pe, S.pl, S.gp, S.sh);
         a.cell_ids[i] = c;
         cell_add<R>(a, S, c, wn, t.ovf);
     }
@@ -633,6 +661,11 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 }
             }
         }
+    }
+    __shared__ int mmk[3];
+    S.mmk = mmk;
+    if ((fl & F_MINMAX) && threadIdx.x == 0) {
+        mmk[0] = fkey(INFINITY); mmk[1] = fkey(-INFINITY); mmk[2] = 0;
     }
     if (fl & F_CELLS) {
         if (FX) {
@@ -877,7 +910,13 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
             a.stat_slots[2 * bid + 1] = w_tot;
         }
     }
-    if (fl & F_MINMAX) {
+    if ((fl & F_MINMAX) && FX) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            R *o = (R *)a.mm_slots + 4 * bid;
+            o[0] = fkey_inv(S.mmk[0]); o[1] = fkey_inv(S.mmk[1]); o[2] = __int_as_float(S.mmk[2]); o[3] = R(0);
+        }
+    } else if (fl & F_MINMAX) {
         __shared__ R mm[3][32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
