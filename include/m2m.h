@@ -206,8 +206,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n,
 int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma);
 
 /* Replace the potential (fixed, known potential of Section 2; an SH
- * component is expanded at once from the current positions and weights).
- * M2M_ERR_STATE while an update is pending. */
+ * component is expanded at once from the current positions and weights,
+ * after a pending weight update is applied). */
 int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot);
 
 /* Copy the SH node table to host memory as doubles, K rows of M2M_SH_ROW:
@@ -236,8 +236,29 @@ int m2m_priors(m2m_ctx *ctx);
 int m2m_push(m2m_ctx *ctx, int64_t nsteps);
 
 /* nsteps full M2M steps (1-5 above).  On return the particle arrays, w and
- * w_hat hold the state after the last step. */
+ * w_hat hold the state after the last step (unless lazy weight updates are
+ * on: see m2m_set_lazy_update). */
 int m2m_step(m2m_ctx *ctx, int64_t nsteps);
+
+/* Lazy weight updates (on != 0; default off).  The weight update of a step
+ * (Eq. 2, at the positions the step's scatter used) is fused into the next
+ * step's particle pass; with lazy updates on, m2m_step leaves the update of
+ * its last step pending instead of applying it with an update-only pass
+ * before it returns, so that a caller stepping once per call (reading each
+ * step's record, say) pays one pass per step.  A pending update is applied
+ * by the next m2m_step, by m2m_finish_update, and first thing by every call
+ * that reads or changes the particle state (m2m_observe,
+ * m2m_update_weights, m2m_priors, m2m_push, m2m_potential, m2m_set_layout,
+ * m2m_autotune, m2m_free), and when lazy updates are turned off.  Until
+ * then the caller's w array holds the weights before that update: call
+ * m2m_finish_update before reading it directly.  Records, observables and
+ * chi^2 of every step are complete either way, and the state after
+ * m2m_finish_update is bit-identical to stepping without lazy updates. */
+int m2m_set_lazy_update(m2m_ctx *ctx, int32_t on);
+
+/* Apply a pending weight update now (nothing if none is pending).
+ * Asynchronous on the context's stream. */
+int m2m_finish_update(m2m_ctx *ctx);
 
 /* Host copies (synchronise the stream).  Any pointer may be NULL.
  * y, Delta, Dt: observable count doubles (last scatter).  Returns the
@@ -248,6 +269,16 @@ int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt);
  * (capacity M2M_HISTORY). */
 #define M2M_HISTORY 16384
 int m2m_get_record(m2m_ctx *ctx, m2m_record *out);
+
+/* The last record, copied on the context's stream without waiting for it:
+ * the copy is enqueued after the work of every call made so far, and *out
+ * holds the record once the stream has reached it (an event recorded after
+ * this call, or a synchronisation).  out should be page-locked host memory
+ * (from pageable memory the copy runs synchronously, by CUDA's rules).
+ * No error-word check: a sticky kernel error is returned by the next
+ * synchronising call (m2m_get_record, m2m_get_obs).  For loops that read
+ * each step's record while the next step runs. */
+int m2m_get_record_async(m2m_ctx *ctx, m2m_record *out);
 
 /* Records for steps [first, first+count) still in the ring, to host. */
 int m2m_get_history(m2m_ctx *ctx, int64_t first, int64_t count, m2m_record *out);

@@ -83,6 +83,7 @@ struct m2m_ctx {
     int cell_shift;      // FP32C prior-cell sums: weight * 2^cell_shift (2^-60 of the initial total)
     long long t;
     bool pending;
+    bool lazy_update = false;        // m2m_step leaves the last update pending
     int last_grid;       // grid of the last scatter pass (slots to reduce)
     int layout;          // compiled observable layout of the pass kernel
     int cache_bits;      // bits of the packed per-particle cell cache
@@ -392,6 +393,15 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
         k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->d_lnwhat, ctx->n);
         CU(cudaGetLastError());
     }
+    return M2M_OK;
+}
+
+// Applies a pending weight update with an update-only pass.
+int finish_update(m2m_ctx *ctx) {
+    if (!ctx->pending) return M2M_OK;
+    int rc = launch_pass(ctx, F_UPD);
+    if (rc) return rc;
+    ctx->pending = false;
     return M2M_OK;
 }
 
@@ -881,7 +891,8 @@ int m2m_set_targets(m2m_ctx *ctx, const double *Y, const double *sigma) {
 
 int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
     if (!ctx) return M2M_ERR_ARG;
-    if (ctx->pending) return set_err(ctx, M2M_ERR_STATE, "update pending");
+    int rc0 = finish_update(ctx);
+    if (rc0) return rc0;
     const int oldK = ctx->sh_on ? ctx->sh_K : 0;
     const double oldr0 = ctx->sh_rmin, oldr1 = ctx->sh_rmax;
     int rc = build_potential(ctx, pot, npot);
@@ -911,25 +922,32 @@ int m2m_get_sh_table(m2m_ctx *ctx, double *out) {
 
 int m2m_observe(m2m_ctx *ctx, int32_t mode) {
     if (!ctx || mode < 0 || mode > 2) return set_err(ctx, M2M_ERR_ARG, "bad context or mode");
-    if (ctx->pending) return set_err(ctx, M2M_ERR_STATE, "update pending");
+    int rc = finish_update(ctx);
+    if (rc) return rc;
     return observe_now(ctx, 0, mode, ctx->t, 0);
 }
 
 int m2m_update_weights(m2m_ctx *ctx) {
     if (!ctx) return M2M_ERR_ARG;
+    int rc = finish_update(ctx);
+    if (rc) return rc;
     return launch_pass(ctx, F_UPD);
 }
 
 int m2m_priors(m2m_ctx *ctx) {
     if (!ctx) return M2M_ERR_ARG;
     if (ctx->prior.kind == M2M_PRIOR_FLAT) return set_err(ctx, M2M_ERR_STATE, "priors are flat");
-    int rc = launch_pass(ctx, F_MINMAX);
+    int rc = finish_update(ctx);
+    if (rc) return rc;
+    rc = launch_pass(ctx, F_MINMAX);
     if (rc) return rc;
     return prior_recompute(ctx, 0);
 }
 
 int m2m_push(m2m_ctx *ctx, int64_t nsteps) {
     if (!ctx || nsteps < 0) return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    int rc0 = finish_update(ctx);
+    if (rc0) return rc0;
     for (int64_t k = 0; k < nsteps; ++k) {
         int rc = launch_pass(ctx, F_PUSH);
         if (rc) return rc;
@@ -971,12 +989,19 @@ int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
             if (rc) return rc;
         }
     }
-    if (ctx->pending) {
-        int rc = launch_pass(ctx, F_UPD);
-        if (rc) return rc;
-        ctx->pending = false;
-    }
+    if (!ctx->lazy_update) return finish_update(ctx);
     return M2M_OK;
+}
+
+int m2m_set_lazy_update(m2m_ctx *ctx, int32_t on) {
+    if (!ctx) return M2M_ERR_ARG;
+    ctx->lazy_update = on != 0;
+    return on ? M2M_OK : finish_update(ctx);
+}
+
+int m2m_finish_update(m2m_ctx *ctx) {
+    if (!ctx) return M2M_ERR_ARG;
+    return finish_update(ctx);
 }
 
 int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt) {
@@ -994,6 +1019,14 @@ int m2m_get_record(m2m_ctx *ctx, m2m_record *out) {
     if (rc) return rc;
     CU(cudaMemcpyAsync(out, ctx->d_last, sizeof *out, cudaMemcpyDeviceToHost, ctx->st));
     return check_err_word(ctx);
+}
+
+int m2m_get_record_async(m2m_ctx *ctx, m2m_record *out) {
+    if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
+    int rc = finish_record(ctx);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(out, ctx->d_last, sizeof *out, cudaMemcpyDeviceToHost, ctx->st));
+    return M2M_OK;
 }
 
 int m2m_get_history(m2m_ctx *ctx, int64_t first, int64_t count, m2m_record *out) {
@@ -1096,6 +1129,7 @@ int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, 
             if (out->from_cache) return M2M_OK;
         }
     }
+    if (int rc0 = finish_update(ctx)) return rc0;
     const int shapes[] = {1024, 512, 256};
     const int flushes[] = {4, 2, 4 | 1, 2 | 1};
     const bool was_timing = ctx->timing;
@@ -1152,6 +1186,8 @@ int m2m_set_layout(m2m_ctx *ctx, int32_t layout) {
     if (layout < 0) layout = detect_layout(ctx);
     if (layout != 0 && layout != detect_layout(ctx))
         return set_err(ctx, M2M_ERR_ARG, "layout %d does not match the observable sets", layout);
+    int rc = finish_update(ctx);
+    if (rc) return rc;
     if (layout != ctx->layout) ctx->cache_valid = false;
     ctx->layout = layout;
     return M2M_OK;
@@ -1193,6 +1229,7 @@ const char *m2m_last_error(const m2m_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 int m2m_free(m2m_ctx *ctx) {
     if (!ctx) return M2M_OK;
+    finish_update(ctx);             // the caller's weights: best effort
     cudaStreamSynchronize(ctx->st);
     free_all(ctx);
     delete ctx;

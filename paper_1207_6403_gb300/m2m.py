@@ -111,6 +111,9 @@ def library():
         "m2m_set_launch": (c_int32, [P, c_int32, c_int32]),
         "m2m_set_layout": (c_int32, [P, c_int32]),
         "m2m_set_pipeline": (c_int32, [P, c_int32]),
+        "m2m_set_lazy_update": (c_int32, [P, c_int32]),
+        "m2m_finish_update": (c_int32, [P]),
+        "m2m_get_record_async": (c_int32, [P, P]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
@@ -200,6 +203,12 @@ class Context:
         _check(library().m2m_get_record(self.ptr, byref(r)), self.ptr)
         return r.as_dict()
 
+    def m2m_get_record_async(self, host_ptr):
+        """Enqueue a copy of the last record to host_ptr (page-locked host
+        memory of ctypes.sizeof(m2m_record) bytes); read it with
+        m2m_record.from_address(host_ptr) once the stream has got there."""
+        _check(library().m2m_get_record_async(self.ptr, c_void_p(host_ptr)), self.ptr)
+
     def m2m_get_history(self, first, count):
         out = (m2m_record * count)()
         _check(library().m2m_get_history(self.ptr, first, count, out), self.ptr)
@@ -230,6 +239,12 @@ class Context:
 
     def m2m_set_pipeline(self, enable=True):
         _check(library().m2m_set_pipeline(self.ptr, int(enable)), self.ptr)
+
+    def m2m_set_lazy_update(self, on=True):
+        _check(library().m2m_set_lazy_update(self.ptr, 1 if on else 0), self.ptr)
+
+    def m2m_finish_update(self):
+        _check(library().m2m_finish_update(self.ptr), self.ptr)
 
     def m2m_set_timing(self, enable):
         _check(library().m2m_set_timing(self.ptr, 1 if enable else 0), self.ptr)
@@ -270,8 +285,11 @@ class Context:
 
     # -- conveniences --
     def state(self):
-        """Host copies of the particle state (synchronises)."""
+        """Host copies of the particle state, a pending weight update applied
+        (synchronises)."""
         import torch
+        if self.ptr:
+            self.m2m_finish_update()
         torch.cuda.current_stream().synchronize()
         return {k: v.cpu().numpy() for k, v in self.t.items()}
 

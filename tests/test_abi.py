@@ -79,3 +79,12 @@ def test_init_rejects_bad_arguments_without_touching_memory(kw, needle):
     rc, ctx, msg = _init(**kw)
     assert rc == -1 and not ctx.value
     assert needle in msg
+
+
+def test_null_context_is_an_argument_error():
+    L = B.library()
+    assert L.m2m_set_lazy_update(None, 1) == -1
+    assert L.m2m_finish_update(None) == -1
+    assert L.m2m_get_record_async(None, None) == -1
+    assert L.m2m_step(None, 1) == -1
+    assert L.m2m_free(None) == 0
