@@ -1,7 +1,7 @@
 """GPU parity: every stage of the CUDA path against the CPU oracle on the
 same seeded inputs, called through the C-ABI (thin binding).
 
-Tolerances (written here, derived in the design doc):
+Tolerances (each follows from the arithmetic of the path it checks):
 * bin and prior-cell indices: bit-exact (float and double), except prior
   cells built on the logarithmic potential (its E contains ln), where a
   mismatch is allowed only for particles whose E sits within a few ulp of a
