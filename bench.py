@@ -9,7 +9,7 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|sh]
+                  [--workload flat-log|batched|sh|ifu-lut]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
@@ -17,6 +17,8 @@ Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
 --workload sh times the self-consistent disc + bulge (N = 8,000,000) in the
 spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
 recomputed every 50 steps).
+--workload ifu-lut times the flat-log galaxy observed through 300 Voronoi
+bins and a long slit (apertures given by sky-pixel lookup tables).
 
 Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
 FP64 GPU path is measured on the same box and reported under "fp64_gpu".
@@ -480,15 +482,39 @@ def run_batched(args, D):
     bt.m2m_batch_free()
 
 
-def run_sh(args, D):
+# workloads timed by run_single: the problem, its default size, the label of
+# its bench line and the particle stride of the oracle sample
+SINGLE = {
+    "sh": dict(
+        problem="sh-selfcons", n=8_000_000, seeds=(9, 10), stride=64,
+        metric="M2M particle-steps/s, self-consistent SH potential (N=8M)",
+        dtype="f32 (FP32-compensated; f64 weights, exact fixed-point SH sums)",
+        kernel="k_pass (step pass: update + push in the expansion + scatter)",
+        describe="sh-selfcons: N={n:,} Miyamoto-Nagai disc (a=1, b=0.2) + Hernquist bulge (a=0.3), 1:3, in "
+                 "the even-l <= 8 multipole expansion of its own weighted particles on 256 log nodes in "
+                 "[1e-3, 100], recomputed every 50 steps; 100 shells + 60 annuli x h0..h4, flat priors, dt=0.01"),
+    "ifu-lut": dict(
+        problem="ifu-lut", n=4_000_000, seeds=(5, 6), stride=8,
+        metric="M2M particle-steps/s, IFU Voronoi bins + long slit by aperture lookup tables (N=4M)",
+        dtype="f32 (FP32-compensated; f64 weights)",
+        kernel="k_pass (step pass, run-time set walk: update + push + scatter through the lookup tables)",
+        describe="ifu-lut: N={n:,} particles, flattened logarithmic potential (v0=1, Rc=0.1, q=0.8) at 60 deg; "
+                 "64x64 pixels (mass) + 300 Voronoi bins on a 160x160 pixel table over [-2, 2]^2 x h0..h4 + "
+                 "a long slit (pa 30 deg, width 0.2, 40 segments) on a 256x256 pixel table x h0..h4 "
+                 "(5796 observables), (E, L_z) 128x64 moving priors every 25 steps, dt=0.01"),
+}
+
+
+def run_single(args, D):
     import torch
     from paper_1207_6403_gb300 import inputs as I
     from paper_1207_6403_gb300 import m2m as B
+    W = SINGLE[args.workload]
     dev = f"cuda:{D.local}"
     torch.cuda.set_device(dev)
-    n = args.n if args.n != N_DEFAULT else 8_000_000
-    P = I.make_problem("sh-selfcons", n=n, precision="fp32c", seed_model=9 + 1000 * D.rank,
-                       seed_target=10 + 1000 * D.rank)
+    n = args.n if args.n != N_DEFAULT else W["n"]
+    P = I.make_problem(W["problem"], n=n, precision="fp32c", seed_model=W["seeds"][0] + 1000 * D.rank,
+                       seed_target=W["seeds"][1] + 1000 * D.rank)
     P = P.with_targets(B.observe_targets(P, "fp32c", dev))
     steps = args.steps if args.steps_given else 1000
     stream = torch.cuda.current_stream()
@@ -521,35 +547,33 @@ def run_sh(args, D):
     tot_ms = sum(tm["ms"].values())
     shares = {k: round(v / tot_ms, 4) for k, v in tm["ms"].items() if v > 0}
     pass_ms = tm["ms"]["step_upd"] / max(1, tm["launches"]["step_upd"])
-    sh_ms = tm["ms"]["sh"] / max(1, tm["launches"]["sh"] // 2)
     peak, peak_kind = peaks()
     achieved = BYTES_PER_PARTICLE_FP32C * n / (pass_ms * 1e-3) / 1e9
     rec = ctx.m2m_get_record()
     ctx.m2m_free()
     cpu = None
     if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
-        rate, ns, secs = time_oracle(P, 3, 64)
+        rate, ns, secs = time_oracle(P, 3, W["stride"])
         cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"every 64th particle ({ns:,} of {n:,}) of the workload, 3 oracle steps "
+               "sample": f"every {W['stride']}th particle ({ns:,} of {n:,}) of the workload, 3 oracle steps "
                          f"({secs:.1f} s, numpy, one thread)"}
     if D.rank == 0:
-        line = {"metric": "M2M particle-steps/s, self-consistent SH potential (N=8M)", "value": value,
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": W["kernel"],
+                "bytes_per_particle": BYTES_PER_PARTICLE_FP32C, "launch_ms": pass_ms,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel_time_shares": shares}
+        if tm["launches"]["sh"]:
+            roof["sh_recompute_ms"] = tm["ms"]["sh"] / max(1, tm["launches"]["sh"] // 2)
+        line = {"metric": W["metric"], "value": value,
                 "unit": "particle-steps/s", "n_gpus": D.world, "steps": steps, "warmup": args.warmup,
                 "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 (FP32-compensated; f64 weights, exact fixed-point SH sums)", "data": "synthetic",
-                "config": {"workload": f"sh-selfcons: N={n:,} Miyamoto-Nagai disc (a=1, b=0.2) + Hernquist "
-                                       "bulge (a=0.3), 1:3, in the even-l <= 8 multipole expansion of its own "
-                                       "weighted particles on 256 log nodes in [1e-3, 100], recomputed every "
-                                       "50 steps; 100 shells + 60 annuli x h0..h4, flat priors, dt=0.01",
-                           "n_particles": n, "global_particles": n * D.world,
-                           "l2": "particle arrays (576 MB/step) exceed the 129 MB L2; no flush needed"},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None,
-                             "kernel": "k_pass (step pass: update + push in the expansion + scatter)",
-                             "bytes_per_particle": BYTES_PER_PARTICLE_FP32C, "launch_ms": pass_ms,
-                             "sh_recompute_ms": sh_ms,
-                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                             "kernel_time_shares": shares},
+                "dtype": W["dtype"], "data": "synthetic",
+                "config": {"workload": W["describe"].format(n=n),
+                           "n_particles": n, "global_particles": n * D.world, "observables": P.nobs,
+                           "l2": f"particle arrays ({72 * n // 10**6} MB/step) exceed the 129 MB L2; "
+                                 "no flush needed"},
+                "roofline": roof,
                 "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks.summary(w0, w1),
                 "tuning": tuning, "last_record": {k: rec[k] for k in ("step", "chi2", "S", "sum_w", "F")}}
         print(json.dumps(line), flush=True)
@@ -563,7 +587,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh"])
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh", "ifu-lut"])
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()
@@ -576,8 +600,8 @@ def main():
             run_reference(args, D)
         elif args.workload == "batched":
             run_batched(args, D)
-        elif args.workload == "sh":
-            run_sh(args, D)
+        elif args.workload in SINGLE:
+            run_single(args, D)
         else:
             run_ours(args, D)
     finally:

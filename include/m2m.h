@@ -116,6 +116,10 @@ typedef struct {
  *      ANNULUS: projected annuli, edges of R^2 = X*X + Y*Y
  *      GRID:    sky rectangles (pixels, IFU apertures), edges of X and of Y,
  *               cell = iy*nx + ix
+ *      LUT:     sky apertures of any shape (Voronoi-binned IFU spaxels,
+ *               long-slit segments): the sky pixel (ix, iy) by the edges of
+ *               X and of Y as for GRID, then cell = lut[iy*nx + ix] (-1: no
+ *               cell); the apertures are cells 0..ncell-1
  * Sky coordinates for the line of sight s = (0, sin i, cos i):
  *   X = x, Y = z*sin_i - y*cos_i, v_los = vy*sin_i + vz*cos_i.
  * quant MASS:  K = 1;  VLOS2: K = v_los^2;
@@ -129,17 +133,21 @@ typedef struct {
 #define M2M_GEOM_SHELL   1
 #define M2M_GEOM_ANNULUS 2
 #define M2M_GEOM_GRID    3
+#define M2M_GEOM_LUT     4
+#define M2M_MAX_LUT_PIXELS (1 << 22)   /* lookup-table pixels of all LUT sets */
 #define M2M_Q_MASS  1
 #define M2M_Q_VLOS2 2
 #define M2M_Q_GH    3
 typedef struct {
     int32_t geom, quant;
-    int32_t nx, ny;             /* ny = 1 unless GRID */
+    int32_t nx, ny;             /* ny = 1 unless GRID or LUT */
     const double *edges_x;      /* host, nx+1 strictly increasing */
-    const double *edges_y;      /* host, ny+1 (GRID) or NULL */
-    const double *gh_V;         /* host, nx*ny (GH) or NULL */
-    const double *gh_S;         /* host, nx*ny (GH), > 0, or NULL */
+    const double *edges_y;      /* host, ny+1 (GRID, LUT) or NULL */
+    const double *gh_V;         /* host, one per cell (GH) or NULL */
+    const double *gh_S;         /* host, one per cell (GH), > 0, or NULL */
     double sigma_kernel;        /* GH velocity kernel width (>= 0) */
+    const int32_t *lut;         /* LUT: host, nx*ny cell ids in [-1, ncell); else NULL */
+    int32_t ncell;              /* LUT: number of cells (apertures); else ignored */
 } m2m_obs_desc;
 
 /* ---- priors (Section 2.1) ----
@@ -440,7 +448,8 @@ int m2m_batch_free(m2m_batch *batch);
  *   n            particle count, 1 <= n < 2^31
  *   x..vz        device float arrays (the FP32C state), w device double
  *                array; all caller-owned, 16-byte aligned, only read
- *   obs, nsets   observable sets as for m2m_init (host, copied); at most
+ *   obs, nsets   observable sets as for m2m_init (host, copied; no LUT
+ *                sets); at most
  *                M2M_STATIC_MAX_OBS observables, M2M_STATIC_MAX_EDGES edges
  *                in total and M2M_STATIC_MAX_GH_CELLS Gauss-Hermite cells,
  *                else M2M_ERR_ARG with the reason in m2m_last_error(NULL)

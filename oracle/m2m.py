@@ -145,6 +145,13 @@ def cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i):
             ix = bin_index(X, s.edges_x)
             iy = bin_index(Ys, s.edges_y)
             cell = np.where((ix >= 0) & (iy >= 0), iy * s.nx + ix, -1)
+        elif s.geom == "lut":
+            # the sky pixel as for a grid, then the aperture that owns it
+            ix = bin_index(X, s.edges_x)
+            iy = bin_index(Ys, s.edges_y)
+            inside = (ix >= 0) & (iy >= 0)
+            lut = np.asarray(s.lut, np.int64).reshape(s.ny, s.nx)
+            cell = np.where(inside, lut[np.where(inside, iy, 0), np.where(inside, ix, 0)], -1)
         else:
             raise ValueError(s.geom)
         if s.quant == "mass":

@@ -55,6 +55,7 @@ struct m2m_ctx {
     int ncells;
     int edge_len, gh_len;
     void *d_edges, *d_gh;
+    int *d_lut = nullptr;            // aperture lookup tables of the LUT sets
     double *d_Y, *d_sigma, *d_isig, *d_Dt, *d_y, *d_Delta, *d_coef_d;
     void *d_coef_r;
     void *d_slots;
@@ -203,11 +204,13 @@ size_t pass_smem(const m2m_ctx *c, int flags) {
 // Compile-time observable layout matching the context's sets (see
 // for_each_set); 0 = generic.  Layouts need index guesses good to one cell.
 int detect_layout(const m2m_ctx *c) {
-    // radial sets need log-uniform edges, grids value-uniform edges
+    // radial sets need log-uniform edges, grids and lookup tables
+    // value-uniform edges
     for (int k = 0; k < c->nsets; ++k) {
         const SetDev &s = c->sets[k];
-        if (s.geom == M2M_GEOM_GRID && (s.gx_mode != G_LIN || s.gy_mode != G_LIN)) return 0;
-        if (s.geom != M2M_GEOM_GRID && s.gx_mode != G_LOG) return 0;
+        const bool two_d = s.geom == M2M_GEOM_GRID || s.geom == M2M_GEOM_LUT;
+        if (two_d && (s.gx_mode != G_LIN || s.gy_mode != G_LIN)) return 0;
+        if (!two_d && s.gx_mode != G_LOG) return 0;
     }
     if (c->cache_bits > 32) return 0;
     auto is = [&](int k, int g, int q) { return c->sets[k].geom == g && c->sets[k].quant == q; };
@@ -216,6 +219,10 @@ int detect_layout(const m2m_ctx *c) {
     if (c->nsets == 3 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_MASS) &&
         is(2, M2M_GEOM_ANNULUS, M2M_Q_VLOS2))
         return 3;
+    // lookup-table apertures: compiled for FP32C only (FP64 walks the sets)
+    if (c->prec == M2M_FP32C && c->nsets == 3 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) &&
+        is(1, M2M_GEOM_LUT, M2M_Q_GH) && is(2, M2M_GEOM_LUT, M2M_Q_GH))
+        return 4;
     return 0;
 }
 
@@ -300,10 +307,10 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
         // block-level bulk-copy pipeline when its stage buffers fit beside the tables
         void *fp = flags == F_STEADY ? pass_kernel_f32_pipe_steady(ctx->layout) : pass_kernel_f32_pipe(ctx->layout);
         size_t smp = sm + (size_t)PIPE_STAGES * Chunk<float, 1024>::BYTES;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
+        if (fp) CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fp, 1024, smp));
         if (occ >= 1) { ks = {fp, 1024}; sm = smp; }
     }
-    if (occ < 1 && ctx->prec == M2M_FP32C && ctx->threads == 1024 && ctx->layout != 0) {
+    if (occ < 1 && ctx->prec == M2M_FP32C && ctx->threads == 1024) {
         void *f = pass_kernel_f32_compiled(flags, ctx->layout, potential_signature(ctx));
         if (f) ks = {f, 1024};
     }
@@ -441,7 +448,7 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat};
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -624,28 +631,49 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     const bool f32 = precision == M2M_FP32C;
     std::vector<double> edges_d;
     std::vector<double> gh_d;
+    std::vector<int> lut_h;                  // the LUT sets' tables, concatenated
+    int lut_off[MAXSETS] = {0};
     int nobs = 0;
     for (int s = 0; s < nsets; ++s) {
         const m2m_obs_desc &o = obs[s];
         SetDev &d = ctx->sets[s];
         memset(&d, 0, sizeof d);
-        d.geom = o.geom; d.quant = o.quant; d.nx = o.nx; d.ny = o.geom == M2M_GEOM_GRID ? o.ny : 1;
-        if (o.geom < 1 || o.geom > 3 || o.quant < 1 || o.quant > 3 || o.nx < 1 || d.ny < 1 || !o.edges_x ||
-            (o.geom == M2M_GEOM_GRID && !o.edges_y)) {
+        const bool two_d = o.geom == M2M_GEOM_GRID || o.geom == M2M_GEOM_LUT;
+        d.geom = o.geom; d.quant = o.quant; d.nx = o.nx; d.ny = two_d ? o.ny : 1;
+        if (o.geom < 1 || o.geom > 4 || o.quant < 1 || o.quant > 3 || o.nx < 1 || d.ny < 1 || !o.edges_x ||
+            (two_d && !o.edges_y) || (o.geom == M2M_GEOM_LUT && (!o.lut || o.ncell < 1)) ||
+            (long long)d.nx * d.ny > M2M_MAX_LUT_PIXELS) {
             set_err(nullptr, M2M_ERR_ARG, "observable set %d: bad geometry/quantity/sizes/edges", s);
             delete ctx; return M2M_ERR_ARG;
         }
         d.nmom = o.quant == M2M_Q_GH ? 5 : 1;
         d.gx_top = (float)(d.nx - 1);
         d.gy_top = (float)(d.ny - 1);
-        long long cells = (long long)d.nx * d.ny;
+        long long cells = o.geom == M2M_GEOM_LUT ? o.ncell : (long long)d.nx * d.ny;
+        d.ncell = (int)cells;
+        if (o.geom == M2M_GEOM_LUT) {
+            const long long npx = (long long)d.nx * d.ny;
+            if ((long long)lut_h.size() + npx > M2M_MAX_LUT_PIXELS) {
+                set_err(nullptr, M2M_ERR_ARG, "more than %d lookup-table pixels in total", M2M_MAX_LUT_PIXELS);
+                delete ctx; return M2M_ERR_ARG;
+            }
+            for (long long k = 0; k < npx; ++k) {
+                if (o.lut[k] < -1 || o.lut[k] >= o.ncell) {
+                    set_err(nullptr, M2M_ERR_ARG, "observable set %d: lookup-table entry %lld = %d not in [-1, %d)",
+                            s, k, o.lut[k], o.ncell);
+                    delete ctx; return M2M_ERR_ARG;
+                }
+            }
+            lut_off[s] = (int)lut_h.size();
+            lut_h.insert(lut_h.end(), o.lut, o.lut + npx);
+        }
         d.obs_off = nobs;
         if (nobs + cells * d.nmom > MAXOBS) {
             set_err(nullptr, M2M_ERR_ARG, "more than %d observables", MAXOBS);
             delete ctx; return M2M_ERR_ARG;
         }
         nobs += (int)(cells * d.nmom);
-        for (int ax = 0; ax < (o.geom == M2M_GEOM_GRID ? 2 : 1); ++ax) {
+        for (int ax = 0; ax < (two_d ? 2 : 1); ++ax) {
             const double *e = ax == 0 ? o.edges_x : o.edges_y;
             int nb = ax == 0 ? d.nx : d.ny;
             for (int k = 0; k <= nb; ++k) {
@@ -687,7 +715,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     {
         int bits = 0;
         for (int k = 0; k < nsets; ++k) {
-            int cells = ctx->sets[k].nx * ctx->sets[k].ny, b = 1;
+            int cells = obs[k].geom == M2M_GEOM_LUT ? obs[k].ncell : ctx->sets[k].nx * ctx->sets[k].ny, b = 1;
             while ((1 << b) < cells + 1) ++b;
             ctx->sets[k].cshift = bits < 32 ? bits : 0;
             ctx->sets[k].cmask = (1 << b) - 1;
@@ -752,6 +780,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_err, 4);
     ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
     ALLOC(ctx->d_cell_cache, 4 * (size_t)n);
+    if (!lut_h.empty()) ALLOC(ctx->d_lut, 4 * lut_h.size());
     if (f32) ALLOC(ctx->d_lnwhat, 4 * (size_t)n);
     if (ctx->ncells) {
         ALLOC(ctx->d_cell_ids, 4 * (size_t)n);
@@ -790,7 +819,11 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         cudaError_t e8 = cudaMemset(ctx->d_coef_r, 0, rs * nobs);
         cudaError_t e9 = cudaMemset(ctx->d_ring, 0, sizeof(m2m_record) * M2M_HISTORY);
         cudaError_t e10 = cudaMemset(ctx->d_y_acc, 0, 8 * (size_t)nobs);
-        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9, e10};
+        cudaError_t e11 = lut_h.empty() ? cudaSuccess
+                                        : cudaMemcpy(ctx->d_lut, lut_h.data(), 4 * lut_h.size(), cudaMemcpyHostToDevice);
+        for (int k = 0; k < nsets; ++k)
+            if (ctx->sets[k].geom == M2M_GEOM_LUT) ctx->sets[k].lut = ctx->d_lut + lut_off[k];
+        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9, e10, e11};
         for (cudaError_t e : es)
             if (e != cudaSuccess) {
                 set_err(nullptr, M2M_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
@@ -802,12 +835,11 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64(), (void *)k_sh_coef<float>,
                                 (void *)k_sh_coef<double>, (void *)k_sh_tables<float>, (void *)k_sh_tables<double>};
-    for (int lay = 0; lay < 4; ++lay) {
+    for (int lay = 0; lay < 5; ++lay) {
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
-        if (lay)
-            for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW})
+        for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW})
                 for (int fl : {F_STEADY, F_STEADY | F_MINMAX, F_PUSH | F_SCAT | F_STATS,
                                F_PUSH | F_SCAT | F_STATS | F_MINMAX, F_CELLS | F_UPD})
                     if (void *f = pass_kernel_f32_compiled(fl, lay, pk)) kfns.push_back(f);
@@ -817,6 +849,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         if (lay == 2) kfns.push_back(pass_kernel_f32_batch(lay, true, PK_HERNQUIST_NFW));
     }
     for (void *f : kfns) {
+        if (!f) continue;                    // no such variant compiled
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, f);
         if (e == cudaSuccess)
@@ -1104,7 +1137,7 @@ int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, 
         if (ch == '"' || ch == '\\' || ch == '\n') ch = ' ';
     auto valid = [&](int nt, int pl) {
         if (ctx->prec != M2M_FP32C && (nt == 1024 || (pl & 1) || (pl & 2))) return false;
-        if ((pl & 1) && !(nt == 1024 && ctx->layout != 0)) return false;
+        if ((pl & 1) && !(nt == 1024 && pass_kernel_f32_pipe(ctx->layout))) return false;
         return true;
     };
     if (cache_path) {

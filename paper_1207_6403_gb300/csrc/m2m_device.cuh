@@ -24,6 +24,7 @@ enum { ERR_NONFINITE = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
 
 struct SetDev {
     int geom, quant, nx, ny, nmom;
+    int ncell;            // cells of the set (nx*ny pixels of a grid, nx shells or annuli, the LUT's apertures)
     int obs_off;          // first observable of this set
     int ex_off, ey_off;   // offsets into the edge table
     int gh_off;           // offset into the GH table (5 values per cell)
@@ -32,6 +33,7 @@ struct SetDev {
     float gx_a, gx_b, gy_a, gy_b;
     float gx_top, gy_top; // nx - 1, ny - 1 as floats (clamp of the guess)
     int cshift, cmask;    // packed cell cache: ((cell + 1) & cmask) << cshift
+    const int *lut;       // geometry 4: device table of nx*ny cell ids (-1: none)
 };
 
 struct PotDev {
@@ -611,7 +613,8 @@ __device__ __forceinline__ int set_cell(const SetDev &s, const R *edges, R x, R 
         if (ix < 0) return -1;
         int iy = find_bin<R>(Ys, edges + s.ey_off, s.ny, s.gy_mode, s.gy_a, s.gy_b);
         if (iy < 0) return -1;
-        return iy * s.nx + ix;
+        // grid: the pixel is the cell; lookup table: the pixel's aperture
+        return s.geom == 4 ? __ldg(s.lut + iy * s.nx + ix) : iy * s.nx + ix;
     }
 }
 
@@ -641,7 +644,8 @@ __device__ __forceinline__ int find_fast(R v, const Pair<R> *e, int nb, float ga
 }
 
 // Cell of a particle in a set of compile-time geometry G whose edge tables
-// are uniform in value (G_LIN: grids) or in log (G_LOG: shells, annuli).
+// are uniform in value (G_LIN: grids, lookup tables) or in log (G_LOG:
+// shells, annuli).
 template <class R, int G>
 __device__ __forceinline__ int cell_t(const SetDev &s, const Pair<R> *edges, R x, R y, R z, R X, R Ys) {
     if constexpr (G == 1) {
@@ -653,6 +657,8 @@ __device__ __forceinline__ int cell_t(const SetDev &s, const Pair<R> *edges, R x
     } else {
         int ix = find_fast<R, G_LIN>(X, edges + s.ex_off, s.nx, s.gx_a, s.gx_b, s.gx_top);
         int iy = find_fast<R, G_LIN>(Ys, edges + s.ey_off, s.ny, s.gy_a, s.gy_b, s.gy_top);
+        if constexpr (G == 4)          // lookup table: the aperture that owns the pixel
+            return (ix < 0 || iy < 0) ? -1 : __ldg(s.lut + iy * s.nx + ix);
         return (ix < 0 || iy < 0) ? -1 : iy * s.nx + ix;
     }
 }

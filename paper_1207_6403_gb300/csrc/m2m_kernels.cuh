@@ -246,6 +246,8 @@ struct PassSmem {
 //   1: grid/mass + grid/GH            (pixels + IFU apertures)
 //   2: shell/mass + annulus/GH        (shells + kinematic annuli)
 //   3: shell/mass + annulus/mass + annulus/v_los^2
+//   4: grid/mass + lookup-table/GH + lookup-table/GH (pixels + Voronoi-binned
+//      IFU + long slit)
 template <int V> using IC = std::integral_constant<int, V>;
 template <int L, class F>
 __device__ __forceinline__ void for_each_set(F &&f) {
@@ -259,6 +261,10 @@ __device__ __forceinline__ void for_each_set(F &&f) {
         f(IC<0>{}, IC<M2M_GEOM_SHELL>{}, IC<M2M_Q_MASS>{});
         f(IC<1>{}, IC<M2M_GEOM_ANNULUS>{}, IC<M2M_Q_MASS>{});
         f(IC<2>{}, IC<M2M_GEOM_ANNULUS>{}, IC<M2M_Q_VLOS2>{});
+    } else if constexpr (L == 4) {
+        f(IC<0>{}, IC<M2M_GEOM_GRID>{}, IC<M2M_Q_MASS>{});
+        f(IC<1>{}, IC<M2M_GEOM_LUT>{}, IC<M2M_Q_GH>{});
+        f(IC<2>{}, IC<M2M_GEOM_LUT>{}, IC<M2M_Q_GH>{});
     }
 }
 
@@ -635,8 +641,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         for (int k = 0; k < a.nsets; ++k) {
             const SetDev &st = a.sets[k];
             if (st.quant != M2M_Q_GH) continue;
-            const int ncell = st.nx * st.ny;
-            for (int c = threadIdx.x; c < ncell; c += NT) {
+            for (int c = threadIdx.x; c < st.ncell; c += NT) {
                 const R *g = (const R *)a.gh_tab + st.gh_off + 5 * c;
                 const R t2 = g[3], nrm = g[4];
                 R P[5] = {R(0), R(0), R(0), R(0), R(0)};

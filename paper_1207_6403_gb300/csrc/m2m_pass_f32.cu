@@ -11,6 +11,7 @@ static void *pick_layout_f32(int layout) {
         case 1: return (void *)k_pass<float, NT, MINB, 1, 0>;
         case 2: return (void *)k_pass<float, NT, MINB, 2, 0>;
         case 3: return (void *)k_pass<float, NT, MINB, 3, 0>;
+        case 4: return (void *)k_pass<float, NT, MINB, 4, 0>;
         default: return (void *)k_pass<float, NT, MINB, 0, 0>;
     }
 }
@@ -24,8 +25,9 @@ void *pass_kernel_f32(int threads, int layout) {
 }
 
 // The steady-state step (pending update + push + scatter + stats) with its
-// flags compiled in (1024 threads, plain loads), for every compiled layout
-// and potential signature (PK_ANY: the run-time component walk).
+// flags compiled in (1024 threads, plain loads), for every layout (0: the
+// run-time set walk) and potential signature (PK_ANY: the run-time
+// component walk).
 template <int L>
 static void *steady_pk(int pk) {
     switch (pk) {
@@ -39,9 +41,13 @@ static void *steady_pk(int pk) {
 
 void *pass_kernel_f32_steady(int layout, int pk) {
     switch (layout) {
+        case 0: return steady_pk<0>(pk);
         case 1: return steady_pk<1>(pk);
         case 2: return steady_pk<2>(pk);
         case 3: return steady_pk<3>(pk);
+        case 4:     // lookup-table apertures: the logarithmic potential of their workload
+            return pk == PK_LOG ? (void *)k_pass<float, 1024, 1, 4, 0, F_STEADY, PK_LOG>
+                                : (void *)k_pass<float, 1024, 1, 4, 0, F_STEADY>;
         default: return nullptr;
     }
 }

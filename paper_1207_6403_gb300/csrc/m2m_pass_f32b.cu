@@ -33,6 +33,7 @@ void *pass_kernel_f32_batch(int layout, bool steady, int pk) {
             case 1: return (void *)k_pass_batch<float, 1024, 1, 1, F_STEADY>;
             case 2: return (void *)k_pass_batch<float, 1024, 1, 2, F_STEADY>;
             case 3: return (void *)k_pass_batch<float, 1024, 1, 3, F_STEADY>;
+            case 4: return (void *)k_pass_batch<float, 1024, 1, 4, F_STEADY>;
             default: break;
         }
     }
@@ -40,6 +41,7 @@ void *pass_kernel_f32_batch(int layout, bool steady, int pk) {
         case 1: return (void *)k_pass_batch<float, 1024, 1, 1>;
         case 2: return (void *)k_pass_batch<float, 1024, 1, 2>;
         case 3: return (void *)k_pass_batch<float, 1024, 1, 3>;
+        case 4: return (void *)k_pass_batch<float, 1024, 1, 4>;
         default: return (void *)k_pass_batch<float, 1024, 1, 0>;
     }
 }

@@ -175,6 +175,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
         d.gx_top = (float)(d.nx - 1);
         d.gy_top = (float)(d.ny - 1);
         const long long cells = (long long)d.nx * d.ny;
+        d.ncell = (int)cells;
         d.obs_off = nobs;
         if (nobs + cells * d.nmom > M2M_STATIC_MAX_OBS)
             return fail(M2M_ERR_ARG, "more than %d observables (the static scratch capacity)", M2M_STATIC_MAX_OBS);

@@ -75,6 +75,10 @@ class ObservableSet:
           'annulus' : cells are projected annuli, edges_x are edges of R^2
           'grid'    : cells are rectangles of the sky plane (pixels or IFU
                       apertures), edges_x / edges_y are edges of X / Y
+          'lut'     : cells are sky apertures of any shape (Voronoi bins,
+                      long-slit segments): the sky pixel (ix, iy) by edges_x /
+                      edges_y as for 'grid', then cell = lut[iy, ix] (-1: no
+                      cell); n_apertures cells
     quant 'mass'    : K = 1 in the cell
           'vlos2'   : K = v_los^2 in the cell (luminosity-weighted 2nd moment)
           'gh'      : K_n = Gauss-Hermite kernel u_n, n = 0..4, in the cell,
@@ -91,6 +95,8 @@ class ObservableSet:
     gh_V: Optional[np.ndarray] = None
     gh_S: Optional[np.ndarray] = None
     sigma_kernel: float = 0.0
+    lut: Optional[np.ndarray] = None       # 'lut': (ny, nx) int32 cell ids
+    n_apertures: int = 0                   # 'lut': number of cells
 
     @property
     def nx(self) -> int:
@@ -102,7 +108,7 @@ class ObservableSet:
 
     @property
     def ncells(self) -> int:
-        return self.nx * self.ny
+        return self.n_apertures if self.geom == "lut" else self.nx * self.ny
 
     @property
     def nmom(self) -> int:
@@ -463,10 +469,57 @@ def error_model(Y, obs_sets, frac=0.02):
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
-WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons")
+WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons", "ifu-lut")
 
 _DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000, "sh-selfcons": 8_000_000,
-              "flat-log": 4_000_000}
+              "flat-log": 4_000_000, "ifu-lut": 4_000_000}
+
+
+# --------------------------------------------------------------------------
+# Aperture lookup tables (sky pixel -> aperture) for the 'lut' geometry
+# --------------------------------------------------------------------------
+def _pixel_centres(edges_x, edges_y):
+    cx = 0.5 * (edges_x[:-1] + edges_x[1:])
+    cy = 0.5 * (edges_y[:-1] + edges_y[1:])
+    return np.meshgrid(cx, cy)          # (ny, nx) each
+
+
+def voronoi_lut(edges_x, edges_y, generators, rmax=None):
+    """Voronoi binning: each pixel belongs to the generator nearest to its
+    centre (the lowest index on a tie); pixels whose centre lies beyond rmax
+    from the origin (the instrument's footprint) belong to none (-1)."""
+    X, Y = _pixel_centres(edges_x, edges_y)
+    g = np.asarray(generators, np.float64)
+    d2 = (X[..., None] - g[:, 0]) ** 2 + (Y[..., None] - g[:, 1]) ** 2
+    lut = np.argmin(d2, axis=-1).astype(np.int32)
+    if rmax is not None:
+        lut[X * X + Y * Y >= rmax * rmax] = -1
+    return lut
+
+
+def slit_lut(edges_x, edges_y, pa_deg, width, u_edges, centre=(0.0, 0.0)):
+    """A long slit at position angle pa_deg (from the X axis) through
+    `centre`, `width` wide, cut into segments by u_edges along it: a pixel
+    belongs to segment k if its centre, at (u, v) along / across the slit,
+    has |v| < width/2 and u_edges[k] <= u < u_edges[k+1]; else to none."""
+    X, Y = _pixel_centres(edges_x, edges_y)
+    c, s = math.cos(math.radians(pa_deg)), math.sin(math.radians(pa_deg))
+    dx, dy = X - centre[0], Y - centre[1]
+    u = c * dx + s * dy
+    v = -s * dx + c * dy
+    k = np.searchsorted(u_edges, u, side="right") - 1
+    ok = (np.abs(v) < 0.5 * width) & (k >= 0) & (k < len(u_edges) - 1)
+    return np.where(ok, k, -1).astype(np.int32)
+
+
+def ifu_generators(n, seed, rmax):
+    """n Voronoi generators in the disc r < rmax, denser towards the centre
+    (r = rmax u^0.7), as adaptive binning to a fixed signal-to-noise makes
+    them."""
+    g = rng(seed)
+    r = rmax * g.random(n) ** 0.7
+    phi = 2 * math.pi * g.random(n)
+    return np.stack([r * np.cos(phi), r * np.sin(phi)], axis=1)
 
 
 def _gh_set_annuli(nb, rmin, rmax, sigma_kernel, GM=1.0, a=1.0):
@@ -528,6 +581,32 @@ def make_problem(name, n=None, precision=None, seed_model=None,
                ObservableSet("grid", "gh", ap, ap.copy(),
                              gh_V=np.zeros(400), gh_S=np.full(400, v0 / math.sqrt(2.0)),
                              sigma_kernel=0.1)]
+        pot = [PotentialComponent("log", (v0, Rc, q))]
+        prior = PriorSpec("e_lz", nE=128, nL=64, period=25)
+        inc = math.radians(60.0)
+        sin_i, cos_i = math.sin(inc), math.cos(inc)
+        prec = precision or "fp32c"
+        steps = nsteps or 5000
+    elif name == "ifu-lut":
+        # the flat-log galaxy observed through a Voronoi-binned IFU and a
+        # long slit (apertures of any shape by sky-pixel lookup tables)
+        sm, st = seed_model or 5, seed_target or 6
+        v0, Rc, q = 1.0, 0.1, 0.8
+        pos, vel = log_flattened_realisation(n, sm, v0, Rc, q)
+        tp = tv = None
+        if with_target:
+            tp, tv = log_flattened_realisation(n, st, v0, Rc, q, stream_frac=0.5)
+        px = uniform_edges(160, -2.0, 2.0)
+        vor = voronoi_lut(px, px, ifu_generators(300, 11, 2.0), rmax=2.0)
+        sx = uniform_edges(256, -3.2, 3.2)
+        slit = slit_lut(sx, sx, 30.0, 0.2, uniform_edges(40, -3.0, 3.0))
+        S0 = v0 / math.sqrt(2.0)
+        obs = [ObservableSet("grid", "mass", uniform_edges(64, -3.2, 3.2),
+                             uniform_edges(64, -3.2, 3.2)),
+               ObservableSet("lut", "gh", px, px.copy(), gh_V=np.zeros(300), gh_S=np.full(300, S0),
+                             sigma_kernel=0.1, lut=vor, n_apertures=300),
+               ObservableSet("lut", "gh", sx, sx.copy(), gh_V=np.zeros(40), gh_S=np.full(40, S0),
+                             sigma_kernel=0.1, lut=slit, n_apertures=40)]
         pot = [PotentialComponent("log", (v0, Rc, q))]
         prior = PriorSpec("e_lz", nE=128, nL=64, period=25)
         inc = math.radians(60.0)

@@ -20,7 +20,7 @@ ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE", -4: "M
 FP64, FP32C = 0, 1
 POT = {"hernquist": 1, "nfw": 2, "log": 3, "sh": 4}
 SH_ROW = 21
-GEOM = {"shell": 1, "annulus": 2, "grid": 3}
+GEOM = {"shell": 1, "annulus": 2, "grid": 3, "lut": 4}
 QUANT = {"mass": 1, "vlos2": 2, "gh": 3}
 PRIOR = {"flat": 0, "e_lc": 1, "e_lz": 2}
 HISTORY = 16384
@@ -34,7 +34,7 @@ class m2m_obs_desc(ctypes.Structure):
     _fields_ = [("geom", c_int32), ("quant", c_int32), ("nx", c_int32), ("ny", c_int32),
                 ("edges_x", POINTER(c_double)), ("edges_y", POINTER(c_double)),
                 ("gh_V", POINTER(c_double)), ("gh_S", POINTER(c_double)),
-                ("sigma_kernel", c_double)]
+                ("sigma_kernel", c_double), ("lut", POINTER(c_int32)), ("ncell", c_int32)]
 
 
 class m2m_prior_desc(ctypes.Structure):
@@ -332,23 +332,7 @@ def m2m_init(precision, pos, vel, w, what, potential, obs, params, prior=None, Y
     keep = {}
     pot_arr, npot = _pot_array(potential)
     keep["pot"] = pot_arr
-    od = (m2m_obs_desc * len(obs))()
-    for k, s in enumerate(obs):
-        ex = np.ascontiguousarray(s.edges_x, dtype=np.float64)
-        keep[f"ex{k}"] = ex
-        od[k].geom, od[k].quant = GEOM[s.geom], QUANT[s.quant]
-        od[k].nx, od[k].ny = len(ex) - 1, (1 if s.edges_y is None else len(s.edges_y) - 1)
-        od[k].edges_x = _dptr(ex)
-        if s.edges_y is not None:
-            ey = np.ascontiguousarray(s.edges_y, dtype=np.float64)
-            keep[f"ey{k}"] = ey
-            od[k].edges_y = _dptr(ey)
-        if s.quant == "gh":
-            V = np.ascontiguousarray(s.gh_V, dtype=np.float64)
-            S = np.ascontiguousarray(s.gh_S, dtype=np.float64)
-            keep[f"V{k}"], keep[f"S{k}"] = V, S
-            od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
-        od[k].sigma_kernel = float(s.sigma_kernel)
+    od = _obs_array(obs, keep.setdefault("obs_arrays", []))
     keep["obs"] = od
     keep["nsets"] = len(obs)
     nobs = sum(s.nobs for s in obs)
@@ -411,23 +395,7 @@ def m2m_observe_static(pos, vel, w, obs, incl_sin, incl_cos, weight_scale, y_out
     import torch
     lib = library()
     keep = []
-    od = (m2m_obs_desc * len(obs))()
-    for k, s in enumerate(obs):
-        ex = np.ascontiguousarray(s.edges_x, dtype=np.float64)
-        keep.append(ex)
-        od[k].geom, od[k].quant = GEOM[s.geom], QUANT[s.quant]
-        od[k].nx, od[k].ny = len(ex) - 1, (1 if s.edges_y is None else len(s.edges_y) - 1)
-        od[k].edges_x = _dptr(ex)
-        if s.edges_y is not None:
-            ey = np.ascontiguousarray(s.edges_y, dtype=np.float64)
-            keep.append(ey)
-            od[k].edges_y = _dptr(ey)
-        if s.quant == "gh":
-            V = np.ascontiguousarray(s.gh_V, dtype=np.float64)
-            S = np.ascontiguousarray(s.gh_S, dtype=np.float64)
-            keep += [V, S]
-            od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
-        od[k].sigma_kernel = float(s.sigma_kernel)
+    od = _obs_array(obs, keep)
     st = (stream or torch.cuda.current_stream()).cuda_stream
     ptrs = [c_void_p(t.data_ptr()) for t in (*pos, *vel, w)]
     rc = lib.m2m_observe_static(int(w.shape[0]), *ptrs, od, len(obs), float(incl_sin), float(incl_cos),
@@ -453,6 +421,11 @@ def _obs_array(obs, keep):
             keep += [V, S]
             od[k].gh_V, od[k].gh_S = _dptr(V), _dptr(S)
         od[k].sigma_kernel = float(s.sigma_kernel)
+        if s.geom == "lut":
+            lut = np.ascontiguousarray(s.lut, dtype=np.int32).reshape(-1)
+            keep.append(lut)
+            od[k].lut = lut.ctypes.data_as(POINTER(c_int32))
+            od[k].ncell = int(s.ncells)
     keep.append(od)
     return od
 

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(B.m2m_potential_desc) == 40
-    assert ctypes.sizeof(B.m2m_obs_desc) == 56
+    assert ctypes.sizeof(B.m2m_obs_desc) == 72
     assert ctypes.sizeof(B.m2m_prior_desc) == 32
     assert ctypes.sizeof(B.m2m_params) == 56
     assert ctypes.sizeof(B.m2m_record) == 56
@@ -88,3 +88,31 @@ def test_null_context_is_an_argument_error():
     assert L.m2m_get_record_async(None, None) == -1
     assert L.m2m_step(None, 1) == -1
     assert L.m2m_free(None) == 0
+
+
+@pytest.mark.parametrize("entries,ncell,needle", [
+    ([0, 1, 2, 5], 3, "lookup-table entry 3 = 5"),
+    ([0, -2, 1, 1], 3, "lookup-table entry 1 = -2"),
+    ([0, 1, 1, 0], 0, "bad geometry"),
+    (None, 3, "bad geometry"),
+])
+def test_lut_sets_are_checked_before_any_device_work(entries, ncell, needle):
+    """A 2 x 2 pixel lookup-table set: every entry must name an aperture of
+    the set or -1; the table and a positive aperture count are required."""
+    L = B.library()
+    P = ctypes.c_void_p
+    e = (ctypes.c_double * 3)(0.0, 1.0, 2.0)
+    od = (B.m2m_obs_desc * 1)()
+    od[0].geom, od[0].quant, od[0].nx, od[0].ny = 4, 1, 2, 2
+    od[0].edges_x = ctypes.cast(e, ctypes.POINTER(ctypes.c_double))
+    od[0].edges_y = ctypes.cast(e, ctypes.POINTER(ctypes.c_double))
+    if entries is not None:
+        lut = (ctypes.c_int32 * 4)(*entries)
+        od[0].lut = ctypes.cast(lut, ctypes.POINTER(ctypes.c_int32))
+    od[0].ncell = ncell
+    ctx = P()
+    par = B.m2m_params(0, 0, 0.01, 0.5, 1, 0, 1)
+    rc = L.m2m_init(ctypes.byref(ctx), B.FP32C, 100, *([P(1 << 20)] * 8), None, 0, od, 1, None, None,
+                    ctypes.byref(par), None, None)
+    assert rc == -1 and not ctx.value
+    assert needle in L.m2m_last_error(None).decode()

@@ -86,7 +86,7 @@ def test_push_nfw_plus_hernquist_close(prec, rtol):
 
 # ------------------------------------------------------------------ cells
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log"])
+@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log", "ifu-lut"])
 def test_observable_cells_are_bit_exact(prec, name):
     P = problem(name, 20011, prec)
     ctx = B.from_problem(P, prec)
@@ -107,8 +107,10 @@ def test_cells_on_edges_nan_and_out_of_range(prec):
     T = np.float64 if prec == "fp64" else np.float32
     ex = I.uniform_edges(8, -2.0, 2.0)
     ey = I.uniform_edges(4, -1.0, 1.0)
+    lut = np.array([[0, 1, 1, -1, 2, 2, 3, 0]] * 2 + [[-1, 4, 4, 4, 4, 5, 5, -1]] * 2, np.int32)
     obs = [I.ObservableSet("grid", "mass", ex, ey),
-           I.ObservableSet("shell", "mass", I.log_shell_edges(5, 0.1, 3.0))]
+           I.ObservableSet("shell", "mass", I.log_shell_edges(5, 0.1, 3.0)),
+           I.ObservableSet("lut", "mass", ex, ey, lut=lut, n_apertures=6)]
     xs = np.concatenate([ex.astype(T), ex.astype(T) - np.abs(ex.astype(T)) * 1e-7,
                          np.array([np.nan, np.inf, -np.inf, 2.0, -2.0, 0.0], T)])
     n = xs.size
@@ -235,7 +237,7 @@ def test_prior_cells_log_potential_match_except_at_edges(prec):
 # --------------------------------------------------------- observe, update
 @pytest.mark.parametrize("layout", [-1, 0])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32c", 1e-5)])
-@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log"])
+@pytest.mark.parametrize("name", ["plain-fp64", "moving-priors", "flat-log", "ifu-lut"])
 def test_observe_residual_and_update_match(prec, tol, name, layout):
     """layout -1: the kernels compiled for the workload's observable sets;
     0: the run-time walk over the set descriptors."""
@@ -327,6 +329,29 @@ def test_flat_log_fp32c_200_steps():
     assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
 
 
+def test_ifu_lut_fp32c_200_steps():
+    """The flat-log galaxy seen through Voronoi-binned IFU apertures and a
+    long slit (lookup-table apertures, run-time set walk)."""
+    P = problem("ifu-lut", 40000, "fp32c")
+    g, (y, D, Dt), hist, st = _run_both(P, "fp32c", 200)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    # prior cells of the log potential may differ for particles at an edge
+    rel = np.abs(g["w"] / st.w - 1)
+    assert np.quantile(rel, 0.999) < 1e-4
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
+
+
+def test_ifu_lut_fp64_100_steps():
+    P = problem("ifu-lut", 20011, "fp64")
+    g, (y, D, Dt), hist, st = _run_both(P, "fp64", 100)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    rel = np.abs(g["w"] / st.w - 1)
+    assert np.quantile(rel, 0.999) < 1e-10
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-10)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 @pytest.mark.parametrize("n", [1, 3, 31, 33, 4097])
 def test_small_and_ragged_sizes(prec, n):
@@ -375,11 +400,12 @@ def test_full_size_flat_log_one_step_sampled():
     assert r["sum_w"] == pytest.approx(st.history[-1]["sum_w"], rel=1e-6)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-def test_compiled_and_generic_layouts_agree_over_a_run(prec):
+@pytest.mark.parametrize("prec,name", [("fp64", "moving-priors"), ("fp32c", "moving-priors"),
+                                       ("fp32c", "ifu-lut")])
+def test_compiled_and_generic_layouts_agree_over_a_run(prec, name):
     """Both code paths for the same sets give the same trajectory, weights
     and observables (the fixed-point histogram makes FP32C sums exact)."""
-    P = problem("moving-priors", 20000, prec)
+    P = problem(name, 20000, prec)
     out = []
     for layout in (-1, 0):
         ctx = B.from_problem(P, prec)
@@ -436,3 +462,8 @@ def test_layout_override_is_checked():
     ctx.m2m_set_layout(3)
     ctx.m2m_set_layout(0)
     ctx.m2m_set_layout(-1)
+    # lookup-table apertures: compiled for FP32C, walked at run time in FP64
+    P = problem("ifu-lut", 2000, "fp32c")
+    B.from_problem(P, "fp32c").m2m_set_layout(4)
+    with pytest.raises(B.M2MError):
+        B.from_problem(P, "fp64").m2m_set_layout(4)

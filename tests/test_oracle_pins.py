@@ -267,6 +267,70 @@ def test_complete_grid_sums_to_total_weight_exactly():
     assert yv.sum() == w.sum()
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_lut_apertures_match_a_per_particle_loop(dtype):
+    """Aperture lookup tables: each particle's sky pixel found by scanning
+    the edges, its aperture read from the table, weights summed one by one;
+    holes (-1) and pixels outside the table collect nothing."""
+    g = np.random.default_rng(13)
+    n = 3000
+    x, y, z = (g.normal(size=(3, n)) * 1.2).astype(dtype)
+    w = g.uniform(0.5, 1.5, n) / n
+    si, ci = math.sin(math.radians(40)), math.cos(math.radians(40))
+    ex, ey = I.uniform_edges(7, -2.1, 2.1), I.uniform_edges(5, -1.5, 1.5)
+    lut = g.integers(-1, 6, size=(5, 7)).astype(np.int32)
+    s = I.ObservableSet("lut", "mass", ex, ey, lut=lut, n_apertures=6)
+    yv = O.observe(x, y, z, x * 0, y * 0, z * 0, w, [s], si, ci)
+    T = np.dtype(dtype).type
+    ref = np.zeros(6)
+    for i in range(n):
+        Ys = T(z[i] * T(si)) - T(y[i] * T(ci))
+        cx = _brute_cells([x[i]], ex)[0]
+        cy = _brute_cells([Ys], ey)[0]
+        if cx < 0 or cy < 0 or lut[cy, cx] < 0:
+            continue
+        ref[lut[cy, cx]] += w[i]
+    np.testing.assert_allclose(yv, ref, rtol=1e-13, atol=1e-16)
+
+
+def test_identity_lut_is_the_grid():
+    """A table that gives every pixel its own aperture (cell = iy*nx + ix)
+    reproduces the grid geometry exactly, kernels included."""
+    g = np.random.default_rng(17)
+    n = 4000
+    x, y, z = g.normal(size=(3, n))
+    vx, vy, vz = g.normal(size=(3, n)) * 0.5
+    w = g.uniform(0.5, 1.5, n) / n
+    ex, ey = I.uniform_edges(6, -2.0, 2.0), I.uniform_edges(4, -1.0, 1.0)
+    V, S = g.normal(size=24) * 0.1, g.uniform(0.4, 0.8, 24)
+    grid = I.ObservableSet("grid", "gh", ex, ey, gh_V=V, gh_S=S, sigma_kernel=0.1)
+    lut = I.ObservableSet("lut", "gh", ex, ey, gh_V=V, gh_S=S, sigma_kernel=0.1,
+                          lut=np.arange(24, dtype=np.int32).reshape(4, 6), n_apertures=24)
+    si, ci = 0.6, 0.8
+    a = O.cells_and_kernels(x, y, z, vx, vy, vz, [grid], si, ci)[0]
+    b = O.cells_and_kernels(x, y, z, vx, vy, vz, [lut], si, ci)[0]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(O.observe(x, y, z, vx, vy, vz, w, [grid], si, ci),
+                          O.observe(x, y, z, vx, vy, vz, w, [lut], si, ci))
+
+
+def test_voronoi_and_slit_tables_by_hand():
+    """Two generators at (-1, 0) and (1, 0) split a 4 x 2 pixel grid over
+    [-2, 2] x [-1, 1] down the middle; a slit along X (pa 0) of width 1
+    through the origin, cut at X = -2, 0, 2, keeps the pixels whose centre
+    has |Y| < 0.5 -- none here, as every centre sits at |Y| = 0.5 -- and a
+    slit at pa 90 cut along Y keeps the centre columns' pixels only."""
+    ex, ey = I.uniform_edges(4, -2.0, 2.0), I.uniform_edges(2, -1.0, 1.0)
+    vor = I.voronoi_lut(ex, ey, [(-1.0, 0.0), (1.0, 0.0)])
+    assert vor.tolist() == [[0, 0, 1, 1], [0, 0, 1, 1]]
+    assert I.voronoi_lut(ex, ey, [(-1.0, 0.0), (1.0, 0.0)], rmax=1.2).tolist() == \
+        [[-1, 0, 1, -1], [-1, 0, 1, -1]]
+    assert (I.slit_lut(ex, ey, 0.0, 1.0, [-2.0, 0.0, 2.0]) == -1).all()
+    assert I.slit_lut(ex, ey, 0.0, 1.01, [-2.0, 0.0, 2.0]).tolist() == [[0, 0, 1, 1], [0, 0, 1, 1]]
+    # pa 90: u runs along +Y, v = -X; width 1.2 keeps the columns at X = +-0.5
+    assert I.slit_lut(ex, ey, 90.0, 1.2, [-1.0, 0.0, 1.0]).tolist() == [[-1, 0, 0, -1], [-1, 1, 1, -1]]
+
+
 def test_gh_orthonormality_by_gauss_hermite_quadrature():
     xk, wk = np.polynomial.hermite.hermgauss(64)
     H = G.hermite(xk)
