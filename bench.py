@@ -9,7 +9,7 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|sh|ifu-lut]
+                  [--workload flat-log|batched|sh|ifu-lut|ifu-lut-seeing]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
@@ -18,7 +18,8 @@ Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
 spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
 recomputed every 50 steps).
 --workload ifu-lut times the flat-log galaxy observed through 300 Voronoi
-bins and a long slit (apertures given by sky-pixel lookup tables).
+bins and a long slit (apertures given by sky-pixel lookup tables);
+--workload ifu-lut-seeing the same through a Gaussian PSF.
 
 Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
 FP64 GPU path is measured on the same box and reported under "fp64_gpu".
@@ -502,6 +503,14 @@ SINGLE = {
                  "64x64 pixels (mass) + 300 Voronoi bins on a 160x160 pixel table over [-2, 2]^2 x h0..h4 + "
                  "a long slit (pa 30 deg, width 0.2, 40 segments) on a 256x256 pixel table x h0..h4 "
                  "(5796 observables), (E, L_z) 128x64 moving priors every 25 steps, dt=0.01"),
+    "ifu-lut-seeing": dict(
+        problem="ifu-lut", kwargs=dict(seeing=0.1), n=4_000_000, seeds=(5, 6), stride=8,
+        metric="M2M particle-steps/s, IFU Voronoi bins + long slit seen through a Gaussian PSF (N=4M)",
+        dtype="f32 (FP32-compensated; f64 weights)",
+        kernel="k_pass (step pass, run-time set walk: update + push + scatter, PSF draws per set)",
+        describe="ifu-lut-seeing: the ifu-lut workload (N={n:,}) with its Voronoi and slit sets seen through a "
+                 "Gaussian PSF of dispersion 0.1 per axis (4096-entry quantile table, one Philox4x32-10 draw "
+                 "per particle, set and push)"),
 }
 
 
@@ -514,7 +523,7 @@ def run_single(args, D):
     torch.cuda.set_device(dev)
     n = args.n if args.n != N_DEFAULT else W["n"]
     P = I.make_problem(W["problem"], n=n, precision="fp32c", seed_model=W["seeds"][0] + 1000 * D.rank,
-                       seed_target=W["seeds"][1] + 1000 * D.rank)
+                       seed_target=W["seeds"][1] + 1000 * D.rank, **W.get("kwargs", {}))
     P = P.with_targets(B.observe_targets(P, "fp32c", dev))
     steps = args.steps if args.steps_given else 1000
     stream = torch.cuda.current_stream()
@@ -587,7 +596,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh", "ifu-lut"])
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh", "ifu-lut",
+                                                               "ifu-lut-seeing"])
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()

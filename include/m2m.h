@@ -148,6 +148,21 @@ typedef struct {
     double sigma_kernel;        /* GH velocity kernel width (>= 0) */
     const int32_t *lut;         /* LUT: host, nx*ny cell ids in [-1, ncell); else NULL */
     int32_t ncell;              /* LUT: number of cells (apertures); else ignored */
+    /* Seeing (ANNULUS, GRID, LUT only; NULL = none): a host table of
+     * 2^psf_bits displacement quantiles of the PSF along one sky axis
+     * (finite, non-decreasing; rounded once to the state precision).  Each
+     * time the cells of particle i (its index in the arrays) are evaluated
+     * at positions that have had e pushes (e counts every push since
+     * m2m_init), its sky position becomes (X + q[u0 >> (32 - psf_bits)],
+     * Y + q[u1 >> (32 - psf_bits)]), the sums in the state precision, where
+     * (u0, u1, -, -) = Philox4x32-10 (Salmon et al. 2011, 10 rounds) of the
+     * counter (i, e mod 2^32, set index, e >> 32) under the key
+     * (psf_seed, 0): the same draw for the scatter and for the weight
+     * update at those positions.  Sets with a PSF take the run-time set
+     * walk. */
+    const double *psf_q;
+    int32_t psf_bits;           /* 1..16 */
+    uint32_t psf_seed;
 } m2m_obs_desc;
 
 /* ---- priors (Section 2.1) ----
@@ -449,7 +464,7 @@ int m2m_batch_free(m2m_batch *batch);
  *   x..vz        device float arrays (the FP32C state), w device double
  *                array; all caller-owned, 16-byte aligned, only read
  *   obs, nsets   observable sets as for m2m_init (host, copied; no LUT
- *                sets); at most
+ *                sets, no seeing); at most
  *                M2M_STATIC_MAX_OBS observables, M2M_STATIC_MAX_EDGES edges
  *                in total and M2M_STATIC_MAX_GH_CELLS Gauss-Hermite cells,
  *                else M2M_ERR_ARG with the reason in m2m_last_error(NULL)

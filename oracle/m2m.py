@@ -37,6 +37,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import gh as _gh
+from . import philox as _philox
 from . import sh as _sh
 from .potentials import acceleration as _analytic_acceleration
 from .potentials import potential as _analytic_potential
@@ -129,14 +130,35 @@ def sky(x, y, z, vx, vy, vz, sin_i, cos_i):
     return x, z * s - y * c, vy * s + vz * c
 
 
-def cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i):
-    """Per observable set: (cell index per particle, K per particle (n, nmom))."""
-    X, Ys, _ = sky(x, y, z, vx, vy, vz, sin_i, cos_i)
+def seeing(X, Ys, s, k, epoch):
+    """The sky position of each particle as seen through the set's PSF
+    (seeing): displaced by (q[u0 >> (32 - b)], q[u1 >> (32 - b)]), q the
+    set's table of 2^b displacement quantiles along one axis (rounded to the
+    state precision), (u0, u1) the first two words of Philox4x32-10 at
+    counter (i, epoch mod 2^32, k, epoch >> 32) and key (psf_seed, 0), i the
+    particle index, k the set's index and epoch the number of pushes the
+    positions have had; the sum is taken in the state precision."""
+    T = X.dtype.type
+    q = np.asarray(s.psf_q, dtype=np.float64).astype(T)
+    b = int(round(np.log2(q.size)))
+    i = np.arange(X.shape[0], dtype=np.uint64)
+    e = int(epoch)
+    u = _philox.philox4x32_10(i, e & 0xFFFFFFFF, k, e >> 32, s.psf_seed, 0)
+    sh = np.uint32(32 - b)
+    return X + q[u[0] >> sh], Ys + q[u[1] >> sh]
+
+
+def cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i, epoch=0):
+    """Per observable set: (cell index per particle, K per particle (n, nmom)).
+    epoch: the number of pushes the positions have had (draws of the sets
+    with a PSF)."""
+    X0, Ys0, _ = sky(x, y, z, vx, vy, vz, sin_i, cos_i)
     # the kernel values are float64 functions of the stored state
     vd = (np.asarray(vy, np.float64) * np.float64(sin_i)
           + np.asarray(vz, np.float64) * np.float64(cos_i))
     out = []
-    for s in obs_sets:
+    for k, s in enumerate(obs_sets):
+        X, Ys = (X0, Ys0) if getattr(s, "psf_q", None) is None else seeing(X0, Ys0, s, k, epoch)
         if s.geom == "shell":
             cell = bin_index((x * x + y * y) + z * z, s.edges_x)
         elif s.geom == "annulus":
@@ -183,8 +205,8 @@ def observe_from(kern, w, obs_sets):
     return np.concatenate(ys)
 
 
-def observe(x, y, z, vx, vy, vz, w, obs_sets, sin_i, cos_i):
-    kern = cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i)
+def observe(x, y, z, vx, vy, vz, w, obs_sets, sin_i, cos_i, epoch=0):
+    kern = cells_and_kernels(x, y, z, vx, vy, vz, obs_sets, sin_i, cos_i, epoch)
     return observe_from(kern, np.asarray(w, np.float64), obs_sets)
 
 
@@ -328,6 +350,7 @@ class State:
     Delta: np.ndarray = None
     history: list = field(default_factory=list)
     sh: tuple = None
+    epoch: int = 0               # pushes the positions have had
 
     @property
     def pos(self):
@@ -366,8 +389,9 @@ def step(st, problem, push=True):
     if push:
         st.x, st.y, st.z, st.vx, st.vy, st.vz = kdk(
             st.x, st.y, st.z, st.vx, st.vy, st.vz, P.potential, P.dt, st.sh)
+        st.epoch += 1
     kern = cells_and_kernels(st.x, st.y, st.z, st.vx, st.vy, st.vz, P.obs,
-                             P.incl_sin, P.incl_cos)
+                             P.incl_sin, P.incl_cos, st.epoch)
     yv = observe_from(kern, w_used, P.obs)
     Delta, Dt, coef, chi2, chi2_raw = residual(yv, P.Y, P.sigma, st.Dt,
                                                P.alpha, False)

@@ -56,6 +56,8 @@ struct m2m_ctx {
     int edge_len, gh_len;
     void *d_edges, *d_gh;
     int *d_lut = nullptr;            // aperture lookup tables of the LUT sets
+    void *d_psf = nullptr;           // seeing quantile tables (state precision)
+    long long epoch = 0;             // pushes the positions have had since m2m_init
     double *d_Y, *d_sigma, *d_isig, *d_Dt, *d_y, *d_Delta, *d_coef_d;
     void *d_coef_r;
     void *d_slots;
@@ -209,6 +211,7 @@ int detect_layout(const m2m_ctx *c) {
     for (int k = 0; k < c->nsets; ++k) {
         const SetDev &s = c->sets[k];
         const bool two_d = s.geom == M2M_GEOM_GRID || s.geom == M2M_GEOM_LUT;
+        if (s.psf_shift) return 0;                 // seeing: the run-time set walk
         if (two_d && (s.gx_mode != G_LIN || s.gy_mode != G_LIN)) return 0;
         if (!two_d && s.gx_mode != G_LOG) return 0;
     }
@@ -236,6 +239,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     memset(&a, 0, sizeof a);
     a.x = c->x; a.y = c->y; a.z = c->z; a.vx = c->vx; a.vy = c->vy; a.vz = c->vz;
     a.w = c->w; a.what = c->what; a.lnwhat = c->d_lnwhat; a.n = c->n; a.flags = flags;
+    a.epoch = c->epoch;
     a.nsets = c->nsets; a.nobs = c->nobs; a.npot = c->npot;
     memcpy(a.sets, c->sets, sizeof a.sets);
     memcpy(a.pot, c->pot, sizeof a.pot);
@@ -335,6 +339,7 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
     if (flags & F_SCAT) ctx->cache_valid = ctx->layout != 0;
     else if (flags & F_PUSH) ctx->cache_valid = false;
+    if (flags & F_PUSH) ++ctx->epoch;
     if (grid_out) *grid_out = (int)grid;
     return M2M_OK;
 }
@@ -448,7 +453,7 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut};
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_psf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -633,6 +638,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     std::vector<double> gh_d;
     std::vector<int> lut_h;                  // the LUT sets' tables, concatenated
     int lut_off[MAXSETS] = {0};
+    std::vector<double> psf_h;               // the seeing tables, concatenated
+    int psf_off[MAXSETS] = {0};
     int nobs = 0;
     for (int s = 0; s < nsets; ++s) {
         const m2m_obs_desc &o = obs[s];
@@ -666,6 +673,21 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
             }
             lut_off[s] = (int)lut_h.size();
             lut_h.insert(lut_h.end(), o.lut, o.lut + npx);
+        }
+        if (o.psf_q) {
+            bool ok = o.geom != M2M_GEOM_SHELL && o.psf_bits >= 1 && o.psf_bits <= 16;
+            const int len = ok ? 1 << o.psf_bits : 0;
+            for (int k = 0; ok && k < len; ++k)
+                ok = isfinite(o.psf_q[k]) && (k == 0 || o.psf_q[k] >= o.psf_q[k - 1]);
+            if (!ok) {
+                set_err(nullptr, M2M_ERR_ARG, "observable set %d: seeing needs a projected set and "
+                                              "2^psf_bits (1..16) finite, non-decreasing quantiles", s);
+                delete ctx; return M2M_ERR_ARG;
+            }
+            psf_off[s] = (int)psf_h.size();
+            psf_h.insert(psf_h.end(), o.psf_q, o.psf_q + len);
+            d.psf_shift = 32 - o.psf_bits;
+            d.psf_seed = o.psf_seed;
         }
         d.obs_off = nobs;
         if (nobs + cells * d.nmom > MAXOBS) {
@@ -781,6 +803,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
     ALLOC(ctx->d_cell_cache, 4 * (size_t)n);
     if (!lut_h.empty()) ALLOC(ctx->d_lut, 4 * lut_h.size());
+    if (!psf_h.empty()) ALLOC(ctx->d_psf, rs * psf_h.size());
     if (f32) ALLOC(ctx->d_lnwhat, 4 * (size_t)n);
     if (ctx->ncells) {
         ALLOC(ctx->d_cell_ids, 4 * (size_t)n);
@@ -823,7 +846,17 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
                                         : cudaMemcpy(ctx->d_lut, lut_h.data(), 4 * lut_h.size(), cudaMemcpyHostToDevice);
         for (int k = 0; k < nsets; ++k)
             if (ctx->sets[k].geom == M2M_GEOM_LUT) ctx->sets[k].lut = ctx->d_lut + lut_off[k];
-        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9, e10, e11};
+        // seeing tables in the state precision (FP32C: rounded once to float)
+        std::vector<unsigned char> pb(rs * psf_h.size());
+        for (size_t k = 0; k < psf_h.size(); ++k) {
+            if (f32) ((float *)pb.data())[k] = (float)psf_h[k];
+            else ((double *)pb.data())[k] = psf_h[k];
+        }
+        cudaError_t e12 = psf_h.empty() ? cudaSuccess
+                                        : cudaMemcpy(ctx->d_psf, pb.data(), pb.size(), cudaMemcpyHostToDevice);
+        for (int k = 0; k < nsets; ++k)
+            if (obs[k].psf_q) ctx->sets[k].psf = (const unsigned char *)ctx->d_psf + rs * psf_off[k];
+        cudaError_t es[] = {e1, e2, e3, e4, e5, e6, e7, e8, e9, e10, e11, e12};
         for (cudaError_t e : es)
             if (e != cudaSuccess) {
                 set_err(nullptr, M2M_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
@@ -1624,6 +1657,7 @@ int m2m_batch_step(m2m_batch *b, int64_t nsteps) {
     for (int m = 0; m < b->nmodels; ++m) {
         m2m_ctx *c = b->ctx[m];
         c->t = t0 + nsteps;
+        c->epoch += nsteps;                  // one push per step
         c->pending = false;
         c->cache_valid = true;
         c->last_grid = b->pcount[m];

@@ -34,6 +34,9 @@ struct SetDev {
     float gx_top, gy_top; // nx - 1, ny - 1 as floats (clamp of the guess)
     int cshift, cmask;    // packed cell cache: ((cell + 1) & cmask) << cshift
     const int *lut;       // geometry 4: device table of nx*ny cell ids (-1: none)
+    const void *psf;      // seeing: 2^bits displacement quantiles (state precision), or null
+    int psf_shift;        // 32 - bits
+    unsigned psf_seed;    // key word 0 of the draws
 };
 
 struct PotDev {
@@ -60,6 +63,7 @@ struct PassArgs {
     double *w, *what;
     const float *lnwhat;                    // FP32C: ln w_hat per particle (library-owned)
     long long n;
+    long long epoch;                        // pushes the positions have had at the pass's start
     int flags;
     int nsets, nobs, npot;
     SetDev sets[MAXSETS];
@@ -598,6 +602,33 @@ __device__ __forceinline__ void gh_eval_rec(float vlos, const float4 *r, float u
 
 __device__ __forceinline__ float gh_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double gh_exp(double x) { return exp(x); }
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC'11): the
+// round multipliers and Weyl key increments of that publication.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The sky position of particle i seen through set k's PSF at positions that
+// have had `epoch` pushes: one draw, two table entries, added in the state
+// precision.
+template <class R>
+__device__ __forceinline__ void seeing(const SetDev &s, int k, long long i, long long epoch, R &X, R &Ys) {
+    const uint4 u = philox4x32_10(make_uint4((unsigned)i, (unsigned)epoch, (unsigned)k,
+                                             (unsigned)((unsigned long long)epoch >> 32)),
+                                  make_uint2(s.psf_seed, 0u));
+    const R *q = (const R *)s.psf;
+    X = X + __ldg(q + (u.x >> s.psf_shift));
+    Ys = Ys + __ldg(q + (u.y >> s.psf_shift));
+}
 
 // Cell of particle in set s (-1 = none).  X = x, Ys = z*sin - y*cos.
 template <class R>

@@ -271,12 +271,15 @@ __device__ __forceinline__ void for_each_set(F &&f) {
 // dot = sum_j K_j coef_j over the particle's cells, in set and moment order
 template <class R, int L>
 __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                     R X, R Ys, R vlos, bool cached, unsigned cc) {
+                                     R X, R Ys, R vlos, bool cached, unsigned cc,
+                                     long long i, long long epoch) {
     R dot = R(0);
     if constexpr (L == 0) {
         for (int k = 0; k < a.nsets; ++k) {
             const SetDev &s = a.sets[k];
-            int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+            R Xk = X, Yk = Ys;
+            if (s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);
+            int c = set_cell<R>(s, S.edges, x, y, z, Xk, Yk);
             if (c < 0) continue;
             int b = s.obs_off + c * s.nmom;
             if (s.quant == M2M_Q_MASS) {
@@ -349,13 +352,16 @@ __device__ __forceinline__ void hist_add(const PassSmem<double> &S, int b, doubl
 
 template <class R, int L>
 __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R> &S, R x, R y, R z,
-                                            R X, R Ys, R vlos, R wv, float fs, ThreadAcc &ovf) {
+                                            R X, R Ys, R vlos, R wv, float fs, ThreadAcc &ovf,
+                                            long long i, long long epoch) {
     const int sh = a.fx_shift;
     unsigned packed = 0u;
     if constexpr (L == 0) {
         for (int k = 0; k < a.nsets; ++k) {
             const SetDev &s = a.sets[k];
-            int c = set_cell<R>(s, S.edges, x, y, z, X, Ys);
+            R Xk = X, Yk = Ys;
+            if (s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);
+            int c = set_cell<R>(s, S.edges, x, y, z, Xk, Yk);
             if (c < 0) continue;
             int b = s.obs_off + c * s.nmom;
             if (s.quant == M2M_Q_MASS) {
@@ -498,7 +504,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             if (fl & F_UPD) {
                 R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
                 const bool cached = L != 0 && a.cache_read;
-                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc);
+                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc, i, a.epoch);
                 wn = upd_weight(w, what, dot, a, wr, L1);
                 if (d_bad(wn)) t.bad = true;
             } else {
@@ -516,7 +522,9 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
         // the scattered weight is a function of the stored (double) weight
         // alone, whichever pass applied the update
         const R wv = to_r(wn, (R *)nullptr);
-        const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t);
+        // the scatter sees the positions after this pass's push, if any
+        const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t, i,
+                                              a.epoch + ((fl & F_PUSH) ? 1 : 0));
         if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
     }
     if (fl & F_MINMAX) {
@@ -1393,7 +1401,11 @@ __global__ void k_cells(const __grid_constant__ PassArgs a, int *obs_cells, int 
         R x = ((const R *)a.x)[i], y = ((const R *)a.y)[i], z = ((const R *)a.z)[i];
         R vx = ((const R *)a.vx)[i], vy = ((const R *)a.vy)[i], vz = ((const R *)a.vz)[i];
         R X = x, Ys = z * s - y * c;
-        for (int k = 0; k < a.nsets; ++k) obs_cells[(long long)k * a.n + i] = set_cell<R>(a.sets[k], edges, x, y, z, X, Ys);
+        for (int k = 0; k < a.nsets; ++k) {
+            R Xk = X, Yk = Ys;
+            if (a.sets[k].psf) seeing<R>(a.sets[k], k, i, a.epoch, Xk, Yk);
+            obs_cells[(long long)k * a.n + i] = set_cell<R>(a.sets[k], edges, x, y, z, Xk, Yk);
+        }
         if (prior_cells) prior_cells[i] = prior_cell<R>(x, y, z, vx, vy, vz, a, pe, pl, gp, (const R *)a.sh_tab);
     }
 }

@@ -169,7 +169,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
         SetDev &d = a.sets[s];
         d.geom = o.geom; d.quant = o.quant; d.nx = o.nx; d.ny = o.geom == M2M_GEOM_GRID ? o.ny : 1;
         if (o.geom < 1 || o.geom > 3 || o.quant < 1 || o.quant > 3 || o.nx < 1 || d.ny < 1 || !o.edges_x ||
-            (o.geom == M2M_GEOM_GRID && !o.edges_y))
+            (o.geom == M2M_GEOM_GRID && !o.edges_y) || o.psf_q)
             return fail(M2M_ERR_ARG, "observable set %d: bad geometry/quantity/sizes/edges", s);
         d.nmom = o.quant == M2M_Q_GH ? 5 : 1;
         d.gx_top = (float)(d.nx - 1);

@@ -97,6 +97,10 @@ class ObservableSet:
     sigma_kernel: float = 0.0
     lut: Optional[np.ndarray] = None       # 'lut': (ny, nx) int32 cell ids
     n_apertures: int = 0                   # 'lut': number of cells
+    # seeing (projected sets): 2^b displacement quantiles of the PSF along
+    # one sky axis, and the key of the counter-based draws
+    psf_q: Optional[np.ndarray] = None
+    psf_seed: int = 0
 
     @property
     def nx(self) -> int:
@@ -512,6 +516,16 @@ def slit_lut(edges_x, edges_y, pa_deg, width, u_edges, centre=(0.0, 0.0)):
     return np.where(ok, k, -1).astype(np.int32)
 
 
+def gaussian_psf_table(sigma, bits=12):
+    """A Gaussian PSF of dispersion sigma per sky axis as 2^bits quantiles,
+    sigma * Phi^-1((k + 1/2) / 2^bits): a uniform 32-bit draw u picks entry
+    u >> (32 - bits)."""
+    from statistics import NormalDist
+    nd = NormalDist()
+    m = 1 << bits
+    return sigma * np.array([nd.inv_cdf((k + 0.5) / m) for k in range(m)])
+
+
 def ifu_generators(n, seed, rmax):
     """n Voronoi generators in the disc r < rmax, denser towards the centre
     (r = rmax u^0.7), as adaptive binning to a fixed signal-to-noise makes
@@ -531,7 +545,7 @@ def _gh_set_annuli(nb, rmin, rmax, sigma_kernel, GM=1.0, a=1.0):
 
 
 def make_problem(name, n=None, precision=None, seed_model=None,
-                 seed_target=None, with_target=True, nsteps=None):
+                 seed_target=None, with_target=True, nsteps=None, seeing=None):
     """Build the workload `name` (see module docstring), optionally at another
     particle count `n` with the same structure.  Weights and priors start at
     1/n.  eps is the workload's epsilon divided by the workload's nominal N
@@ -607,6 +621,11 @@ def make_problem(name, n=None, precision=None, seed_model=None,
                              sigma_kernel=0.1, lut=vor, n_apertures=300),
                ObservableSet("lut", "gh", sx, sx.copy(), gh_V=np.zeros(40), gh_S=np.full(40, S0),
                              sigma_kernel=0.1, lut=slit, n_apertures=40)]
+        if seeing:
+            # the spectroscopic sets seen through a Gaussian PSF of
+            # dispersion `seeing` per axis (one stream of draws per set)
+            for k in (1, 2):
+                obs[k] = replace(obs[k], psf_q=gaussian_psf_table(seeing), psf_seed=12345 + k)
         pot = [PotentialComponent("log", (v0, Rc, q))]
         prior = PriorSpec("e_lz", nE=128, nL=64, period=25)
         inc = math.radians(60.0)

@@ -34,7 +34,8 @@ class m2m_obs_desc(ctypes.Structure):
     _fields_ = [("geom", c_int32), ("quant", c_int32), ("nx", c_int32), ("ny", c_int32),
                 ("edges_x", POINTER(c_double)), ("edges_y", POINTER(c_double)),
                 ("gh_V", POINTER(c_double)), ("gh_S", POINTER(c_double)),
-                ("sigma_kernel", c_double), ("lut", POINTER(c_int32)), ("ncell", c_int32)]
+                ("sigma_kernel", c_double), ("lut", POINTER(c_int32)), ("ncell", c_int32),
+                ("psf_q", POINTER(c_double)), ("psf_bits", c_int32), ("psf_seed", ctypes.c_uint32)]
 
 
 class m2m_prior_desc(ctypes.Structure):
@@ -426,6 +427,13 @@ def _obs_array(obs, keep):
             keep.append(lut)
             od[k].lut = lut.ctypes.data_as(POINTER(c_int32))
             od[k].ncell = int(s.ncells)
+        if getattr(s, "psf_q", None) is not None:
+            q = np.ascontiguousarray(s.psf_q, dtype=np.float64)
+            bits = int(q.size).bit_length() - 1
+            if q.size != 1 << bits:
+                raise ValueError("the seeing table needs a power-of-two length")
+            keep.append(q)
+            od[k].psf_q, od[k].psf_bits, od[k].psf_seed = _dptr(q), bits, int(s.psf_seed) & 0xFFFFFFFF
     keep.append(od)
     return od
 

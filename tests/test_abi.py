@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(B.m2m_potential_desc) == 40
-    assert ctypes.sizeof(B.m2m_obs_desc) == 72
+    assert ctypes.sizeof(B.m2m_obs_desc) == 88
     assert ctypes.sizeof(B.m2m_prior_desc) == 32
     assert ctypes.sizeof(B.m2m_params) == 56
     assert ctypes.sizeof(B.m2m_record) == 56

@@ -342,6 +342,44 @@ def test_ifu_lut_fp32c_200_steps():
     assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_seeing_cells_are_bit_exact(prec):
+    """Sets seen through a PSF: the GPU's counter-based draws and displaced
+    cells equal the oracle's after any number of pushes."""
+    P = problem("ifu-lut", 20011, prec, seeing=0.1)
+    ctx = B.from_problem(P, prec)
+    st = O.init(P, prec)
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    for e in range(3):
+        oc, _ = ctx.m2m_get_cells()
+        oc = oc.cpu().numpy()
+        kern = O.cells_and_kernels(*s, P.obs, P.incl_sin, P.incl_cos, epoch=e)
+        for k, (cell, _) in enumerate(kern):
+            assert np.array_equal(oc[k], cell), f"epoch {e} set {k}: {np.sum(oc[k] != cell)} mismatches"
+        ctx.m2m_push(1)
+        s = O.kdk(*s, P.potential, P.dt)
+
+
+def test_ifu_lut_seeing_fp32c_200_steps():
+    P = problem("ifu-lut", 40000, "fp32c", seeing=0.1)
+    g, (y, D, Dt), hist, st = _run_both(P, "fp32c", 200)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    rel = np.abs(g["w"] / st.w - 1)
+    assert np.quantile(rel, 0.999) < 1e-4
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-5)
+
+
+def test_ifu_lut_seeing_fp64_100_steps():
+    P = problem("ifu-lut", 20011, "fp64", seeing=0.1)
+    g, (y, D, Dt), hist, st = _run_both(P, "fp64", 100)
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    rel = np.abs(g["w"] / st.w - 1)
+    assert np.quantile(rel, 0.999) < 1e-10
+    assert_obs_close(y, st.y_obs, P.sigma, 1e-10)
+
+
 def test_ifu_lut_fp64_100_steps():
     P = problem("ifu-lut", 20011, "fp64")
     g, (y, D, Dt), hist, st = _run_both(P, "fp64", 100)

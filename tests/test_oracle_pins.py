@@ -331,6 +331,72 @@ def test_voronoi_and_slit_tables_by_hand():
     assert I.slit_lut(ex, ey, 90.0, 1.2, [-1.0, 0.0, 1.0]).tolist() == [[-1, 0, 0, -1], [-1, 1, 1, -1]]
 
 
+def test_philox_is_a_bijection_of_the_counter_with_uniform_words():
+    """For a fixed key the 10-round network permutes the counters (2^16
+    distinct counters give 2^16 distinct outputs), every output word is
+    uniform (chi^2 over 64 bins of the top bits) and another key gives
+    another stream."""
+    from oracle import philox as PH
+    i = np.arange(1 << 16, dtype=np.uint64)
+    u = PH.philox4x32_10(i, 7, 1, 0, 12345, 0)
+    full = np.stack(u, axis=1).view(np.dtype((np.void, 16)))
+    assert np.unique(full).size == i.size
+    for w in u:
+        cnt = np.bincount((w >> np.uint32(26)).astype(np.int64), minlength=64)
+        chi2 = ((cnt - i.size / 64) ** 2 / (i.size / 64)).sum()
+        assert chi2 < 120            # 63 degrees of freedom: p < 1e-5 above 120
+    v = PH.philox4x32_10(i, 7, 1, 0, 12346, 0)
+    assert np.mean(v[0] == u[0]) < 1e-3
+    # counter words all matter
+    for shift in ((8, 1, 0), (7, 2, 0), (7, 1, 1)):
+        w = PH.philox4x32_10(i, shift[0], shift[1], shift[2], 12345, 0)
+        assert np.mean(w[0] == u[0]) < 1e-3
+
+
+def test_seeing_spreads_a_point_source_by_the_table():
+    """200,000 particles at one sky point, one draw each: the weight in each
+    pixel is the exact probability that the table's displacement moves the
+    point into it (a product of per-axis counts over the 4096 equiprobable
+    entries), within 5 binomial standard deviations; a zero table gives the
+    undisplaced cells and the draws repeat for the same particle and epoch."""
+    n = 200_000
+    T = np.float32
+    x = np.full(n, 0.3, T); y = np.zeros(n, T); z = np.full(n, -0.2, T)
+    w = np.full(n, 1.0 / n)
+    q = I.gaussian_psf_table(0.4)
+    ex = I.uniform_edges(10, -2.0, 2.0)
+    s = I.ObservableSet("grid", "mass", ex, ex.copy(), psf_q=q, psf_seed=99)
+    # line of sight along y (sin i = 1): the sky point is (X, Y) = (x, z) = (0.3, -0.2)
+    yv = O.observe(x, y, z, x * 0, y * 0, z * 0, w, [s], 1.0, 0.0, epoch=5).reshape(10, 10)
+    qf = q.astype(T)
+    px = np.bincount(O.bin_index(T(0.3) + qf, ex) + 1, minlength=12)[1:11] / q.size
+    py = np.bincount(O.bin_index(T(-0.2) + qf, ex) + 1, minlength=12)[1:11] / q.size
+    p = np.outer(py, px)
+    assert np.all(np.abs(yv - p) <= 5 * np.sqrt(p * (1 - p) / n) + 1e-12)
+    k0 = O.cells_and_kernels(x, y, z, x, y, z, [s], 0.0, 1.0, epoch=5)[0][0]
+    k1 = O.cells_and_kernels(x, y, z, x, y, z, [s], 0.0, 1.0, epoch=5)[0][0]
+    k2 = O.cells_and_kernels(x, y, z, x, y, z, [s], 0.0, 1.0, epoch=6)[0][0]
+    assert np.array_equal(k0, k1) and np.mean(k0 == k2) < 0.5
+    s0 = I.ObservableSet("grid", "mass", ex, ex.copy(), psf_q=np.zeros(16), psf_seed=99)
+    plain = I.ObservableSet("grid", "mass", ex, ex.copy())
+    assert np.array_equal(O.cells_and_kernels(x, y, z, x, y, z, [s0], 0.0, 1.0, epoch=3)[0][0],
+                          O.cells_and_kernels(x, y, z, x, y, z, [plain], 0.0, 1.0)[0][0])
+
+
+def test_init_state_holds_the_initial_observe():
+    """At t = 0 the state carries y of an observe at (x_0, w_0), Delta of it
+    against the targets, Delta~ = Delta, no pushes and no steps."""
+    P = I.make_problem("plain-fp64", n=3000)
+    P = P.with_targets(O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs,
+                                 P.incl_sin, P.incl_cos))
+    st = O.init(P, "fp64")
+    y = O.observe(st.x, st.y, st.z, st.vx, st.vy, st.vz, st.w, P.obs, P.incl_sin, P.incl_cos)
+    assert np.array_equal(st.y_obs, y)
+    m = P.sigma > 0
+    np.testing.assert_allclose(st.Delta[m], (y[m] - P.Y[m]) / P.sigma[m], rtol=1e-14, atol=0)
+    assert np.array_equal(st.Dt, st.Delta) and st.t == 0 and st.epoch == 0
+
+
 def test_gh_orthonormality_by_gauss_hermite_quadrature():
     xk, wk = np.polynomial.hermite.hermgauss(64)
     H = G.hermite(xk)
