@@ -211,18 +211,23 @@ int detect_layout(const m2m_ctx *c) {
     for (int k = 0; k < c->nsets; ++k) {
         const SetDev &s = c->sets[k];
         const bool two_d = s.geom == M2M_GEOM_GRID || s.geom == M2M_GEOM_LUT;
-        if (s.psf_shift) return 0;                 // seeing: the run-time set walk
         if (two_d && (s.gx_mode != G_LIN || s.gy_mode != G_LIN)) return 0;
         if (!two_d && s.gx_mode != G_LOG) return 0;
     }
     if (c->cache_bits > 32) return 0;
     auto is = [&](int k, int g, int q) { return c->sets[k].geom == g && c->sets[k].quant == q; };
+    bool seeing = false;
+    for (int k = 0; k < c->nsets; ++k) seeing |= c->sets[k].psf_shift != 0;
+    if (seeing && !(c->prec == M2M_FP32C && c->nsets == 3 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) &&
+                    is(1, M2M_GEOM_LUT, M2M_Q_GH) && is(2, M2M_GEOM_LUT, M2M_Q_GH)))
+        return 0;
     if (c->nsets == 2 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) && is(1, M2M_GEOM_GRID, M2M_Q_GH)) return 1;
     if (c->nsets == 2 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_GH)) return 2;
     if (c->nsets == 3 && is(0, M2M_GEOM_SHELL, M2M_Q_MASS) && is(1, M2M_GEOM_ANNULUS, M2M_Q_MASS) &&
         is(2, M2M_GEOM_ANNULUS, M2M_Q_VLOS2))
         return 3;
-    // lookup-table apertures: compiled for FP32C only (FP64 walks the sets)
+    // lookup-table apertures: compiled for FP32C only (FP64 walks the sets);
+    // the one compiled layout that takes seeing
     if (c->prec == M2M_FP32C && c->nsets == 3 && is(0, M2M_GEOM_GRID, M2M_Q_MASS) &&
         is(1, M2M_GEOM_LUT, M2M_Q_GH) && is(2, M2M_GEOM_LUT, M2M_Q_GH))
         return 4;
@@ -1571,6 +1576,8 @@ int m2m_batch_init(m2m_batch **out, int32_t precision, int32_t nmodels, const m2
     for (m2m_ctx *c : b->ctx) {
         const int per = c->prior.kind == M2M_PRIOR_FLAT ? 0 : c->prior.period;
         if (c->layout != b->layout || per != b->period || c->sh_on) b->fusable = false;
+        for (int k = 0; k < c->nsets; ++k)
+            if (c->sets[k].psf_shift) b->fusable = false;   // seeing draws need each model's push count
     }
     if (b->fusable) {
         int rc = batch_plan(b, 1);

@@ -297,8 +297,14 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
-            const int c = cached ? (int)((cc >> s.cshift) & (unsigned)s.cmask) - 1
-                                 : cell_t<R, g>(s, S.epair, x, y, z, X, Ys);
+            int c;
+            if (cached) {
+                c = (int)((cc >> s.cshift) & (unsigned)s.cmask) - 1;
+            } else {
+                R Xk = X, Yk = Ys;
+                if (L == 4 && s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);   // seeing: lookup-table layout
+                c = cell_t<R, g>(s, S.epair, x, y, z, Xk, Yk);
+            }
             if (c >= 0) {
                 if constexpr (q == M2M_Q_MASS) {
                     dot = dot + S.coef[s.obs_off + c];
@@ -379,7 +385,9 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
-            const int c = cell_t<R, g>(s, S.epair, x, y, z, X, Ys);
+            R Xk = X, Yk = Ys;
+            if (L == 4 && s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);       // seeing: lookup-table layout
+            const int c = cell_t<R, g>(s, S.epair, x, y, z, Xk, Yk);
             packed |= (unsigned)(c + 1) << s.cshift;
             if (c >= 0 && wv != R(0)) {
                 if constexpr (q == M2M_Q_MASS || q == M2M_Q_VLOS2) {
