@@ -9,11 +9,13 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|sh|ifu-lut|ifu-lut-seeing]
+                  [--workload flat-log|batched|scan|sh|ifu-lut|ifu-lut-seeing]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
 3e7 particles in all) advanced together by m2m_batch_step.
+--workload scan fits one data set in the same 48 trial halos (400,000
+particles each) and gathers every model's record (the potential scan).
 --workload sh times the self-consistent disc + bulge (N = 8,000,000) in the
 spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
 recomputed every 50 steps).
@@ -428,10 +430,20 @@ def run_batched(args, D):
     from paper_1207_6403_gb300 import m2m as B
     dev = f"cuda:{D.local}"
     torch.cuda.set_device(dev)
-    problems = I.make_batch(nmodels=48, seed=7 + 1000 * D.rank)
-    for k, P in enumerate(problems):
-        Y = B.observe_targets(P, "fp32c", dev)
-        problems[k] = P.with_targets(Y)
+    scan = args.workload == "scan"
+    if scan:
+        # one data set (isotropic Hernquist stars in halo (2, 5)) fitted in
+        # the 6 x 8 grid of trial halos, 400,000 particles per model
+        halos = [(r, s) for r in I.HALO_MASS_RATIOS for s in I.HALO_RS]
+        problems = I.make_scan(halos, (2.0, 5.0), n=400_000, n_target=2_000_000, seed=21 + 1000 * D.rank,
+                               target_ra=None)
+        Y = B.observe_targets(problems[0], "fp32c", dev)
+        problems = [P.with_targets(Y) for P in problems]
+    else:
+        problems = I.make_batch(nmodels=48, seed=7 + 1000 * D.rank)
+        for k, P in enumerate(problems):
+            Y = B.observe_targets(P, "fp32c", dev)
+            problems[k] = P.with_targets(Y)
     ntot = sum(P.n for P in problems)
     bt = B.m2m_batch_init("fp32c", problems, device=dev)
     st = bt.stream
@@ -453,6 +465,17 @@ def run_batched(args, D):
         clocks.stop()
     fused = bt.m2m_batch_fused()
     ms = D.max(e0.elapsed_time(e1))
+    scan_out = None
+    if scan:
+        t0 = time.perf_counter()
+        recs = bt.m2m_batch_get_records()
+        gather_ms = 1e3 * (time.perf_counter() - t0)
+        chi = [r["chi2"] for r in recs]
+        best = min(range(len(chi)), key=chi.__getitem__)
+        scan_out = {"best": {"mass_ratio": problems[best].meta["mass_ratio"], "r_s": problems[best].meta["r_s"]},
+                    "true": {"mass_ratio": 2.0, "r_s": 5.0}, "chi2_min": min(chi), "chi2_max": max(chi),
+                    "steps_fitted": args.warmup + steps + 2 * max(2, args.warmup // 6) * tuning["candidates"],
+                    "record_gather_ms": gather_ms}
     value = D.world * ntot * steps / (ms * 1e-3)
     peak, peak_kind = peaks()
     # the step's algorithmic traffic: 72 B per particle-step over all models
@@ -464,13 +487,18 @@ def run_batched(args, D):
                "sample": f"every 4th particle of model 0 ({ns:,} of {problems[0].n:,}), 3 oracle steps "
                          f"({secs:.1f} s)"}
     if D.rank == 0:
-        line = {"metric": "M2M particle-steps/s, 48 batched trial-potential models", "value": value,
+        what = ("scan: one data set (2,000,000 isotropic Hernquist stars in halo M_h/M_* = 2, r_s/a = 5) "
+                "fitted in 48 trial Hernquist + NFW potentials (6 x 8 grid), 400,000 particles each, "
+                "100 shells + 60 annuli x h0..h4, flat priors" if scan else
+                "batched: 48 models, Hernquist stars in Hernquist + NFW halos "
+                "(M_h/M_* x r_s/a = 6 x 8 grid), N log-uniform in [1e5, 2e6], "
+                "100 shells + 60 annuli x h0..h4 each, flat priors")
+        line = {"metric": ("M2M particle-steps/s, potential scan over 48 trial halos (one data set)" if scan else
+                           "M2M particle-steps/s, 48 batched trial-potential models"), "value": value,
                 "unit": "particle-steps/s", "n_gpus": D.world, "steps": steps, "warmup": args.warmup,
                 "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 (FP32-compensated; f64 weights)", "data": "synthetic",
-                "config": {"workload": "batched: 48 models, Hernquist stars in Hernquist + NFW halos "
-                                       "(M_h/M_* x r_s/a = 6 x 8 grid), N log-uniform in [1e5, 2e6], "
-                                       "100 shells + 60 annuli x h0..h4 each, flat priors",
+                "config": {"workload": what,
                            "models": len(problems), "global_particles": ntot * D.world,
                            "launch": {2: "one launch per stage, CUDA graph", 1: "one launch per stage",
                                       0: "model by model"}[fused]},
@@ -479,6 +507,8 @@ def run_batched(args, D):
                              "kernel": "whole step (batched k_pass + batched residual), 72 B/particle",
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
                 "cpu_baseline": cpu, "clocks": clocks.summary(w0, w1), "tuning": tuning}
+        if scan_out:
+            line["scan"] = scan_out
         print(json.dumps(line), flush=True)
     bt.m2m_batch_free()
 
@@ -596,7 +626,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "sh", "ifu-lut",
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "ifu-lut",
                                                                "ifu-lut-seeing"])
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
@@ -608,7 +638,7 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, D)
-        elif args.workload == "batched":
+        elif args.workload in ("batched", "scan"):
             run_batched(args, D)
         elif args.workload in SINGLE:
             run_single(args, D)

@@ -438,6 +438,13 @@ int m2m_batch_autotune(m2m_batch *b, int32_t steps_per_trial, m2m_tuning *out);
 
 int m2m_batch_context(m2m_batch *batch, int32_t model, m2m_ctx **ctx_out);
 
+/* The last record of every model (out: host array of nmodels records, in
+ * model order), gathered on the device and copied in one transfer: the
+ * comparison of chi^2 and F across a sequence of trial potentials fitted to
+ * the same data (Section 4).  Synchronises; returns the first model's
+ * sticky kernel error, if any. */
+int m2m_batch_get_records(m2m_batch *batch, m2m_record *out);
+
 /* 1 if the last m2m_batch_step used one launch per stage for all models
  * (2 if also through a CUDA graph), 0 if it stepped them one by one. */
 int m2m_batch_fused(const m2m_batch *batch);

@@ -1327,6 +1327,7 @@ struct m2m_batch {
     int mult = 1;                // pass blocks = mult * SMs * resident blocks (autotuned)
     std::vector<int> pcount, rcount;
     long long *d_step = nullptr; // step counter read by the batched residual
+    void *d_gather = nullptr;    // record gather: source pointers, records, error words
     long long t = 0;
     int last_mode = 0;
     std::map<std::tuple<long long, long long, int>, cudaGraphExec_t> graphs;
@@ -1353,7 +1354,7 @@ void batch_free_all(m2m_batch *b) {
     b->graphs.clear();
     for (m2m_ctx *c : b->ctx) m2m_free(c);
     b->ctx.clear();
-    void *ptrs[] = {b->d_pass, b->d_res, b->d_tab, b->d_step};
+    void *ptrs[] = {b->d_pass, b->d_res, b->d_tab, b->d_step, b->d_gather};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1719,6 +1720,38 @@ int m2m_batch_context(m2m_batch *b, int32_t model, m2m_ctx **ctx_out) {
 }
 
 int m2m_batch_fused(const m2m_batch *b) { return b ? b->last_mode : -1; }
+
+int m2m_batch_get_records(m2m_batch *b, m2m_record *out) {
+    if (!b || !out) return berr(b, M2M_ERR_ARG, "NULL argument");
+    const int n = b->nmodels;
+    // device scratch: record pointers, error-word pointers, records, error words
+    const size_t o_err = 8 * (size_t)n, o_rec = 16 * (size_t)n, o_w = o_rec + sizeof(m2m_record) * n;
+    const size_t bytes = o_w + 4 * (size_t)n;
+    if (!b->d_gather) {
+        if (cudaMalloc(&b->d_gather, bytes) != cudaSuccess) return berr(b, M2M_ERR_NOMEM, "cudaMalloc(%zu)", bytes);
+        std::vector<const void *> ptr(2 * (size_t)n);
+        for (int m = 0; m < n; ++m) { ptr[m] = b->ctx[m]->d_last; ptr[n + m] = b->ctx[m]->d_err; }
+        if (cudaMemcpy(b->d_gather, ptr.data(), 16 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+            return berr(b, M2M_ERR_CUDA, "record gather table");
+    }
+    for (int m = 0; m < n; ++m) {
+        // records a model's next pass would write (models stepped one by one)
+        int rc = finish_record(b->ctx[m]);
+        if (rc) return berr(b, rc, "model %d record: %s", m, b->ctx[m]->err.c_str());
+    }
+    unsigned char *g = (unsigned char *)b->d_gather;
+    k_gather_records<<<(n + 127) / 128, 128, 0, b->st>>>((const m2m_record *const *)g, (const int *const *)(g + o_err),
+                                                         n, (m2m_record *)(g + o_rec), (int *)(g + o_w));
+    std::vector<int> errw(n);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, g + o_rec, sizeof(m2m_record) * n, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(errw.data(), g + o_w, 4 * (size_t)n, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return berr(b, M2M_ERR_CUDA, "record gather: %s", cudaGetErrorString(e));
+    for (int m = 0; m < n; ++m)
+        if (errw[m]) return berr(b, check_err_word(b->ctx[m]), "model %d: %s", m, b->ctx[m]->err.c_str());
+    return M2M_OK;
+}
 
 int m2m_batch_free(m2m_batch *b) {
     if (!b) return M2M_OK;

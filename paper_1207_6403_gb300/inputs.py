@@ -43,7 +43,7 @@ __all__ = [
     "PotentialComponent", "ObservableSet", "PriorSpec", "Problem",
     "rng", "hernquist_positions", "hernquist_isotropic", "hernquist_om_target",
     "log_flattened_realisation", "log_shell_edges", "uniform_edges",
-    "error_model", "make_problem", "make_batch", "WORKLOADS", "disc_bulge_realisation",
+    "error_model", "make_problem", "make_batch", "make_scan", "WORKLOADS", "disc_bulge_realisation",
 ]
 
 
@@ -692,6 +692,42 @@ def hernquist_in_halo(n, seed, rho_s, r_s, ra=None, GM=1.0, a=1.0, rmax=100.0):
 
 HALO_MASS_RATIOS = (0.5, 1.0, 2.0, 4.0, 8.0, 16.0)
 HALO_RS = tuple(float(v) for v in np.geomspace(1.0, 20.0, 8))
+
+
+def make_scan(halos, true_halo, n=100_000, n_target=None, seed=21, precision="fp32c", target_ra=1.0):
+    """One data set fitted in a sequence of trial potentials (Section 4):
+    Hernquist stars (GM = a = 1) in Hernquist + NFW halos.  halos: list of
+    (M_h/M_*, r_s/a) trial halos; true_halo: the halo of the target galaxy
+    (Osipkov-Merritt-like anisotropy radius target_ra, None for isotropic;
+    seed `seed`, n_target particles) whose observables every model fits.  Model m starts isotropic in its own trial
+    potential (seed 1000 + m); all share the observables (100 shells + 60
+    annuli x h0..h4 about the target's Jeans dispersion), flat priors and
+    eps = 0.05 / n.  The targets are left to the caller to observe
+    (Problem.target_* of every model hold the same galaxy)."""
+    n_target = n_target or n
+    rt, st = true_halo
+    rho_t = nfw_rho_s(rt, st)
+    tp, tv = hernquist_in_halo(n_target, seed, rho_t, st, ra=target_ra)
+    tw = np.full(n_target, 1.0 / n_target)
+    e = log_shell_edges(60, 0.05, 20.0)
+    rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+    rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x),
+                                   lambda x: _hernquist_mass(x) + _nfw_mass(x, rho_t, st))
+    S = np.sqrt(_Interp(rr, s2)(rmid))
+    obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+           ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
+    out = []
+    for m, (ratio, r_s) in enumerate(halos):
+        rho_s = nfw_rho_s(ratio, r_s)
+        pos, vel = hernquist_in_halo(n, 1000 + m, rho_s, r_s)
+        w0 = np.full(n, 1.0 / n)
+        pot = [PotentialComponent("hernquist", (1.0, 1.0)), PotentialComponent("nfw", (rho_s, r_s))]
+        out.append(Problem(name=f"scan-{m}", n=n, pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel),
+                           w0=w0, what0=w0.copy(), potential=pot, obs=obs, incl_sin=0.0, incl_cos=1.0,
+                           eps=0.05 / n, mu=1e-3, dt=0.01, alpha=0.02, prior=PriorSpec("flat"),
+                           nsteps=1000, precision=precision, target_pos=tp, target_vel=tv, target_w=tw,
+                           meta={"mass_ratio": ratio, "r_s": r_s, "rho_s": rho_s}))
+    return out
 
 
 def make_batch(nmodels=48, n_lo=100_000, n_hi=2_000_000, seed=7, n_scale=1.0, precision="fp32c",

@@ -126,6 +126,7 @@ def library():
         "m2m_batch_step": (c_int32, [P, c_int64]),
         "m2m_batch_autotune": (c_int32, [P, c_int32, POINTER(m2m_tuning)]),
         "m2m_batch_context": (c_int32, [P, c_int32, POINTER(P)]),
+        "m2m_batch_get_records": (c_int32, [P, POINTER(m2m_record)]),
         "m2m_batch_fused": (c_int32, [P]),
         "m2m_batch_free": (c_int32, [P]),
         "m2m_last_error": (ctypes.c_char_p, [P]),
@@ -460,6 +461,11 @@ class Batch:
 
     def m2m_batch_fused(self):
         return library().m2m_batch_fused(self.ptr)
+
+    def m2m_batch_get_records(self):
+        out = (m2m_record * len(self.problems))()
+        _check(library().m2m_batch_get_records(self.ptr, out), None)
+        return [r.as_dict() for r in out]
 
     def m2m_batch_context(self, m):
         cp = c_void_p()

@@ -116,3 +116,8 @@ def test_lut_sets_are_checked_before_any_device_work(entries, ncell, needle):
                     ctypes.byref(par), None, None)
     assert rc == -1 and not ctx.value
     assert needle in L.m2m_last_error(None).decode()
+
+
+def test_batch_record_gather_rejects_null():
+    L = B.library()
+    assert L.m2m_batch_get_records(None, None) == -1

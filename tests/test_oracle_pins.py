@@ -706,3 +706,13 @@ def test_plain_run_chi2_falls_and_mass_is_kept():
     h = st.history
     assert h[-1]["chi2_raw"] < 0.75 * h[0]["chi2_raw"]
     assert abs(h[-1]["sum_w"] - 1.0) < 0.02
+
+
+def test_scan_models_share_data_and_differ_in_halo():
+    halos = [(0.5, 2.0), (2.0, 2.0)]
+    probs = I.make_scan(halos, halos[1], n=500, n_target=800)
+    a, b = probs
+    assert a.obs is b.obs and a.target_pos is b.target_pos and a.target_pos.shape == (3, 800)
+    assert [p.meta["mass_ratio"] for p in probs] == [0.5, 2.0]
+    assert a.potential[1].params != b.potential[1].params
+    assert a.potential[1].params[1] == b.potential[1].params[1] == 2.0
