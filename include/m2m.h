@@ -323,11 +323,13 @@ int64_t m2m_steps_taken(const m2m_ctx *ctx);
 int m2m_set_launch(m2m_ctx *ctx, int32_t threads, int32_t blocks_per_sm);
 
 /* Observable layout of the particle kernels: the common set combinations
- * (pixels + IFU GH apertures; shells + GH annuli; shells + mass and v_los^2
- * annuli) run as code compiled for them when every edge table is uniform in
- * value or in log; anything else walks the sets at run time.  layout -1:
- * automatic (the default); 0: force the run-time walk; 1-3: the compiled
- * layout, only if it matches (else M2M_ERR_ARG).  Results are identical. */
+ * (1: pixels + IFU GH apertures; 2: shells + GH annuli; 3: shells + mass
+ * and v_los^2 annuli; 4, FP32C only: pixels + two lookup-table GH sets, with
+ * or without seeing) run as code compiled for them when every edge table is
+ * uniform in value or in log; anything else, and seeing outside layout 4,
+ * walks the sets at run time.  layout -1: automatic (the default); 0:
+ * force the run-time walk; 1-4: the compiled layout, only if it matches
+ * (else M2M_ERR_ARG).  FP32C results are identical either way. */
 int m2m_set_layout(m2m_ctx *ctx, int32_t layout);
 
 /* Streaming and reduction options of the FP32C passes (bit flags):
