@@ -9,7 +9,7 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|scan|sh|ifu-lut|ifu-lut-seeing]
+                  [--workload flat-log|batched|scan|sh|ifu-lut|ifu-lut-seeing|recovery]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
@@ -22,6 +22,8 @@ recomputed every 50 steps).
 --workload ifu-lut times the flat-log galaxy observed through 300 Voronoi
 bins and a long slit (apertures given by sky-pixel lookup tables);
 --workload ifu-lut-seeing the same through a Gaussian PSF.
+--workload recovery runs the anisotropy-recovery experiment (three initial
+models of the moving-prior workload) and reports beta(r).
 
 Prints one JSON line (rank 0).  `value` is the FP32-compensated path; the
 FP64 GPU path is measured on the same box and reported under "fp64_gpu".
@@ -618,6 +620,42 @@ def run_single(args, D):
         print(json.dumps(line), flush=True)
 
 
+def run_recovery(args, D):
+    """Anisotropy recovery from three initial models (Section 3, Fig. 1):
+    the moving-prior workload at N = 1,000,000 from isotropic, radial and
+    tangential initial models; particle-steps/s over the three runs and
+    beta(r) before and after."""
+    import numpy as np
+    import torch
+    from paper_1207_6403_gb300 import recovery as RC
+    dev = f"cuda:{D.local}"
+    torch.cuda.set_device(dev)
+    n = args.n if args.n != N_DEFAULT else 1_000_000
+    steps = args.steps if args.steps_given else 20000
+    r_edges = np.geomspace(0.2, 5.0, 9)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, target = RC.recovery(n, steps, r_edges, device=dev)
+    secs = D.max(time.perf_counter() - t0)
+    if D.rank == 0:
+        rm = np.sqrt(r_edges[:-1] * r_edges[1:])
+        prof = {k: {"initial": [round(float(v), 3) for v in b0], "final": [round(float(v), 3) for v in b1],
+                    "chi2": rec["chi2"]} for k, (b0, b1, rec) in out.items()}
+        spread0 = float(np.max(np.ptp(np.array([b0 for b0, _, _ in out.values()]), axis=0)))
+        spread1 = float(np.max(np.ptp(np.array([b1 for _, b1, _ in out.values()]), axis=0)))
+        line = {"metric": "M2M anisotropy recovery from three initial models (Section 3, Fig. 1)",
+                "value": D.world * 3 * n * steps / secs, "unit": "particle-steps/s (wall clock, setup included)",
+                "n_gpus": D.world, "steps": steps, "higher_is_better": True, "data": "synthetic",
+                "config": {"workload": f"moving-priors: N={n:,} Hernquist stars, Osipkov-Merritt-like target "
+                                       "r_a = 1; initial models isotropic, radial (r_a = 0.3), tangential "
+                                       "(beta = -0.5); (E, L^2/L_c^2) 64x32 priors every 25 steps",
+                           "shell_radii": [round(float(v), 3) for v in rm]},
+                "beta_target": [round(float(v), 3) for v in target],
+                "beta_target_formula": [round(float(v * v / (v * v + 1.0)), 3) for v in rm],
+                "models": prof, "max_spread_initial": spread0, "max_spread_final": spread1}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -627,7 +665,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "ifu-lut",
-                                                               "ifu-lut-seeing"])
+                                                               "ifu-lut-seeing", "recovery"])
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()
@@ -640,6 +678,8 @@ def main():
             run_reference(args, D)
         elif args.workload in ("batched", "scan"):
             run_batched(args, D)
+        elif args.workload == "recovery":
+            run_recovery(args, D)
         elif args.workload in SINGLE:
             run_single(args, D)
         else:

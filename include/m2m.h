@@ -283,6 +283,18 @@ int m2m_set_lazy_update(m2m_ctx *ctx, int32_t on);
  * Asynchronous on the context's stream. */
 int m2m_finish_update(m2m_ctx *ctx);
 
+/* Velocity-ellipsoid moments of the weighted particles in spherical shells
+ * (an analysis of the model, not a step: the anisotropy beta(r) of the
+ * recovery experiment of Section 3).  r2_edges: host, nshell+1 strictly
+ * increasing edges of r^2 (1 <= nshell <= 1024; membership as for SHELL
+ * sets, r^2 = (x*x + y*y) + z*z in the state precision).  out: host,
+ * 4*nshell doubles, per shell sum w, sum w v_r^2, sum w v_theta^2,
+ * sum w v_phi^2 with v_r = x.v/r, v_phi = (x vy - y vx)/R, v_theta^2 =
+ * v^2 - v_r^2 - v_phi^2 in double from the stored state (v_r = 0 at r = 0,
+ * v_phi = 0 at R = 0); the sums are double atomics (order-dependent at
+ * rounding level).  Applies a pending weight update first.  Synchronises. */
+int m2m_velocity_moments(m2m_ctx *ctx, const double *r2_edges, int32_t nshell, double *out);
+
 /* Host copies (synchronise the stream).  Any pointer may be NULL.
  * y, Delta, Dt: observable count doubles (last scatter).  Returns the
  * sticky kernel error if one was raised. */

@@ -210,6 +210,36 @@ def observe(x, y, z, vx, vy, vz, w, obs_sets, sin_i, cos_i, epoch=0):
     return observe_from(kern, np.asarray(w, np.float64), obs_sets)
 
 
+def velocity_moments(x, y, z, vx, vy, vz, w, r2_edges):
+    """Velocity-ellipsoid moments per spherical shell (edges of r^2,
+    membership as for shell sets): columns sum w, sum w v_r^2,
+    sum w v_theta^2, sum w v_phi^2, the velocities float64 functions of the
+    stored state: v_r = x.v / r, v_phi = (x vy - y vx) / R, v_theta^2 =
+    v^2 - v_r^2 - v_phi^2 (v_r = 0 at r = 0, v_phi = 0 at R = 0)."""
+    cell = bin_index((x * x + y * y) + z * z, r2_edges)
+    X, Y, Z, U, V, W = (np.asarray(a, np.float64) for a in (x, y, z, vx, vy, vz))
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    R = np.sqrt(X * X + Y * Y)
+    vr = np.where(r > 0, (X * U + Y * V + Z * W) / np.where(r > 0, r, 1.0), 0.0)
+    vp = np.where(R > 0, (X * V - Y * U) / np.where(R > 0, R, 1.0), 0.0)
+    v2 = U * U + V * V + W * W
+    vt2 = v2 - vr * vr - vp * vp
+    m = cell >= 0
+    nsh = len(r2_edges) - 1
+    out = np.zeros((nsh, 4))
+    for k, q in enumerate((np.ones_like(r), vr * vr, vt2, vp * vp)):
+        out[:, k] = np.bincount(cell[m], weights=np.asarray(w, np.float64)[m] * q[m], minlength=nsh)
+    return out
+
+
+def anisotropy(moments):
+    """beta = 1 - (sigma_theta^2 + sigma_phi^2) / (2 sigma_r^2) per shell
+    (no mean streaming assumed), NaN where a shell is empty."""
+    m = np.asarray(moments, np.float64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return 1.0 - (m[:, 2] + m[:, 3]) / (2.0 * m[:, 1])
+
+
 # --------------------------------------------------------------------------
 # 3. residuals
 # --------------------------------------------------------------------------

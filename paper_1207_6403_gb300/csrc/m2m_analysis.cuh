@@ -1,0 +1,58 @@
+// Analysis kernels outside the step: the velocity-ellipsoid moments of the
+// anisotropy analysis and the gather of a batch's records.
+#pragma once
+#include "m2m_kernels.cuh"
+
+namespace m2m {
+
+// Velocity-ellipsoid moments per spherical shell: block-private double sums
+// in shared memory (4 per shell), then one global atomic per sum.  The
+// shell is the last edge <= r^2 (r^2 in the state precision, compared in
+// double), by bisection over the edges in shared memory.
+template <class R>
+__global__ void __launch_bounds__(256) k_vmoments(const R *x, const R *y, const R *z, const R *vx, const R *vy,
+                                                  const R *vz, const double *w, long long n, const double *e2,
+                                                  int nsh, double *out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *acc = (double *)smem;
+    double *ed = acc + 4 * nsh;
+    for (int k = threadIdx.x; k < 4 * nsh; k += blockDim.x) acc[k] = 0.0;
+    for (int k = threadIdx.x; k <= nsh; k += blockDim.x) ed[k] = e2[k];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const R xs = x[i], ys = y[i], zs = z[i];
+        const double r2 = (double)((xs * xs + ys * ys) + zs * zs);
+        if (!(r2 >= ed[0] && r2 < ed[nsh])) continue;      // outside (or NaN)
+        int lo = 0, hi = nsh;                               // ed[lo] <= r2 < ed[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (ed[mid] <= r2) lo = mid; else hi = mid;
+        }
+        const double X = xs, Y = ys, Z = zs, U = vx[i], V = vy[i], W = vz[i];
+        const double r = sqrt(X * X + Y * Y + Z * Z), Rc = sqrt(X * X + Y * Y);
+        const double vr = r > 0 ? (X * U + Y * V + Z * W) / r : 0.0;
+        const double vp = Rc > 0 ? (X * V - Y * U) / Rc : 0.0;
+        const double v2 = U * U + V * V + W * W;
+        const double wi = w[i];
+        atomicAdd(acc + 4 * lo, wi);
+        atomicAdd(acc + 4 * lo + 1, wi * (vr * vr));
+        atomicAdd(acc + 4 * lo + 2, wi * ((v2 - vr * vr) - vp * vp));
+        atomicAdd(acc + 4 * lo + 3, wi * (vp * vp));
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * nsh; k += blockDim.x)
+        if (acc[k] != 0.0) atomicAdd(out + k, acc[k]);
+}
+
+// The last record and the error word of every model of a batch into one
+// array each (one thread per model).
+__global__ void k_gather_records(const m2m_record *const *src, const int *const *err, int n, m2m_record *dst,
+                                 int *err_out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) {
+        dst[m] = *src[m];
+        err_out[m] = *err[m];
+    }
+}
+
+}  // namespace m2m

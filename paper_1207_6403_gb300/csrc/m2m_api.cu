@@ -24,6 +24,7 @@
 #include "m2m.h"
 #define M2M_COMMON_KERNELS
 #include "m2m_kernels.cuh"
+#include "m2m_analysis.cuh"
 
 using namespace m2m;
 static_assert(SH_ROW == M2M_SH_ROW, "node table row");
@@ -1073,6 +1074,43 @@ int m2m_set_lazy_update(m2m_ctx *ctx, int32_t on) {
 int m2m_finish_update(m2m_ctx *ctx) {
     if (!ctx) return M2M_ERR_ARG;
     return finish_update(ctx);
+}
+
+int m2m_velocity_moments(m2m_ctx *ctx, const double *r2_edges, int32_t nshell, double *out) {
+    if (!ctx || !r2_edges || !out || nshell < 1 || nshell > 1024)
+        return set_err(ctx, M2M_ERR_ARG, "bad argument (1 <= nshell <= 1024, non-NULL arrays)");
+    for (int k = 0; k <= nshell; ++k)
+        if (!(r2_edges[k] == r2_edges[k]) || (k > 0 && !(r2_edges[k] > r2_edges[k - 1])))
+            return set_err(ctx, M2M_ERR_ARG, "edges must be strictly increasing");
+    int rc = finish_update(ctx);
+    if (rc) return rc;
+    const size_t eb = 8 * (size_t)(nshell + 1), ob = 32 * (size_t)nshell;
+    void *d = nullptr;
+    CU(cudaMallocAsync(&d, eb + ob, ctx->st));
+    double *de = (double *)d, *dout = de + (nshell + 1);
+    cudaError_t e = cudaMemcpyAsync(de, r2_edges, eb, cudaMemcpyHostToDevice, ctx->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, ob, ctx->st);
+    if (e == cudaSuccess) {
+        const size_t sm = ob + eb;
+        int g = ctx->nsm * 4;
+        long long need = (ctx->n + 255) / 256;
+        if (g > need) g = (int)need;
+        if (ctx->prec == M2M_FP32C)
+            k_vmoments<float><<<g, 256, sm, ctx->st>>>((const float *)ctx->x, (const float *)ctx->y, (const float *)ctx->z,
+                                                        (const float *)ctx->vx, (const float *)ctx->vy,
+                                                        (const float *)ctx->vz, ctx->w, ctx->n, de, nshell, dout);
+        else
+            k_vmoments<double><<<g, 256, sm, ctx->st>>>((const double *)ctx->x, (const double *)ctx->y,
+                                                         (const double *)ctx->z, (const double *)ctx->vx,
+                                                         (const double *)ctx->vy, (const double *)ctx->vz, ctx->w,
+                                                         ctx->n, de, nshell, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ob, cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    cudaFreeAsync(d, ctx->st);
+    if (e != cudaSuccess) return set_err(ctx, M2M_ERR_CUDA, "velocity moments: %s", cudaGetErrorString(e));
+    return check_err_word(ctx);
 }
 
 int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt) {

@@ -1164,17 +1164,6 @@ __global__ void __launch_bounds__(RES_NT_FX) k_residual_batch(const __grid_const
     residual_body(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
-// The last record and the error word of every model of a batch into one
-// array each (one thread per model).
-__global__ void k_gather_records(const m2m_record *const *src, const int *const *err, int n, m2m_record *dst,
-                                 int *err_out) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m < n) {
-        dst[m] = *src[m];
-        err_out[m] = *err[m];
-    }
-}
-
 // 1/sigma_j (0 where sigma_j <= 0: masked observable)
 __global__ void k_inv_sigma(const double *sigma, double *isig, int nobs) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;

@@ -212,18 +212,22 @@ def _hernquist_mass(r, M=1.0, a=1.0):
     return M * r * r / ((r + a) ** 2)
 
 
-def _jeans_sigma_r2_table(rho, mass, ra=None, rmin=1e-5, rmax=1e4, npts=480):
+def _jeans_sigma_r2_table(rho, mass, ra=None, rmin=1e-5, rmax=1e4, npts=480, beta=None):
     """sigma_r^2(r) on a log grid from the spherical Jeans equation.
 
     Isotropic (ra None):  rho sigma^2 = int_r^inf rho M / r'^2 dr'.
     Osipkov-Merritt-like beta = r^2/(r^2+ra^2):
         rho (r^2+ra^2) sigma_r^2 = int_r^inf (r'^2+ra^2) rho M / r'^2 dr'.
+    Constant beta:  rho r^(2 beta) sigma_r^2 = int_r^inf r'^(2 beta) rho M / r'^2 dr'.
     Integrated in ln r' with composite Simpson on a fine grid plus an
     analytic r'^-4 tail beyond rmax.
     """
     lr = np.linspace(math.log(rmin), math.log(rmax), 8 * npts + 1)
     r = np.exp(lr)
-    g = np.ones_like(r) if ra is None else r * r + ra * ra
+    if beta is not None:
+        g = r ** (2.0 * beta)
+    else:
+        g = np.ones_like(r) if ra is None else r * r + ra * ra
     f = g * rho(r) * mass(r) / (r * r) * r          # integrand in d ln r
     # cumulative integral from each grid point to rmax (trapezoid on a fine grid
     # is refined by Richardson with the half grid: error ~ h^4)
@@ -316,6 +320,18 @@ def hernquist_om_target(n, seed, ra=1.0, GM=1.0, a=1.0, rmax=100.0):
     beta = r * r / (r * r + ra * ra)
     st = np.sqrt(1.0 - beta) * sr
     vel = _spherical_gaussian_velocities(g, pos, r, sr, st)
+    return pos, vel
+
+
+def hernquist_const_beta(n, seed, beta, GM=1.0, a=1.0, rmax=100.0):
+    """Hernquist realisation with a constant anisotropy beta (< 0:
+    tangential), sigma_t = sqrt(1-beta) sigma_r from the Jeans equation,
+    Gaussian velocities."""
+    pos, r, g = hernquist_positions(n, seed, GM, a, rmax)
+    rr, s2 = _jeans_sigma_r2_table(lambda x: _hernquist_rho(x, GM, a),
+                                   lambda x: _hernquist_mass(x, GM, a), beta=beta)
+    sr = np.sqrt(_Interp(rr, s2)(r))
+    vel = _spherical_gaussian_velocities(g, pos, r, sr, math.sqrt(1.0 - beta) * sr)
     return pos, vel
 
 

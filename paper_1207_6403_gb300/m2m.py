@@ -115,6 +115,7 @@ def library():
         "m2m_set_lazy_update": (c_int32, [P, c_int32]),
         "m2m_finish_update": (c_int32, [P]),
         "m2m_get_record_async": (c_int32, [P, P]),
+        "m2m_velocity_moments": (c_int32, [P, POINTER(c_double), c_int32, POINTER(c_double)]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
@@ -210,6 +211,14 @@ class Context:
         memory of ctypes.sizeof(m2m_record) bytes); read it with
         m2m_record.from_address(host_ptr) once the stream has got there."""
         _check(library().m2m_get_record_async(self.ptr, c_void_p(host_ptr)), self.ptr)
+
+    def m2m_velocity_moments(self, r2_edges):
+        """(nshell, 4): sum w, sum w v_r^2, sum w v_theta^2, sum w v_phi^2 per
+        shell of the r^2 edges."""
+        e = np.ascontiguousarray(r2_edges, dtype=np.float64)
+        out = np.zeros((len(e) - 1, 4))
+        _check(library().m2m_velocity_moments(self.ptr, _dptr(e), len(e) - 1, _dptr(out)), self.ptr)
+        return out
 
     def m2m_get_history(self, first, count):
         out = (m2m_record * count)()

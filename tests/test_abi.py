@@ -121,3 +121,8 @@ def test_lut_sets_are_checked_before_any_device_work(entries, ncell, needle):
 def test_batch_record_gather_rejects_null():
     L = B.library()
     assert L.m2m_batch_get_records(None, None) == -1
+
+
+def test_velocity_moments_rejects_null():
+    L = B.library()
+    assert L.m2m_velocity_moments(None, None, 1, None) == -1

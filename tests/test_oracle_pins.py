@@ -716,3 +716,44 @@ def test_scan_models_share_data_and_differ_in_halo():
     assert [p.meta["mass_ratio"] for p in probs] == [0.5, 2.0]
     assert a.potential[1].params != b.potential[1].params
     assert a.potential[1].params[1] == b.potential[1].params[1] == 2.0
+
+
+def test_velocity_moments_of_radial_and_circular_orbits():
+    """Purely radial velocities put all of v^2 into v_r^2 (beta = 1);
+    circular motion about z puts it into v_phi^2; a rotation about z leaves
+    every moment unchanged; shells follow the shell-set membership."""
+    g = np.random.default_rng(31)
+    n = 5000
+    pos = g.normal(size=(3, n))
+    r = np.sqrt((pos ** 2).sum(0))
+    e2 = I.log_shell_edges(6, 0.1, 4.0)
+    w = g.uniform(0.5, 1.5, n) / n
+    s = g.normal(size=n)
+    m = O.velocity_moments(*pos, *(pos / r * s), w, e2)
+    v2 = s * s
+    cell = O.bin_index((pos[0] * pos[0] + pos[1] * pos[1]) + pos[2] * pos[2], e2)
+    ok = cell >= 0
+    np.testing.assert_allclose(m[:, 0], np.bincount(cell[ok], weights=w[ok], minlength=6), rtol=1e-14)
+    np.testing.assert_allclose(m[:, 1], np.bincount(cell[ok], weights=(w * v2)[ok], minlength=6), rtol=1e-12)
+    assert np.all(np.abs(m[:, 2:]) <= 1e-12 * m[:, 1:2])
+    np.testing.assert_allclose(O.anisotropy(m), 1.0, atol=1e-12)
+    R = np.sqrt(pos[0] ** 2 + pos[1] ** 2)
+    vc = np.stack([-pos[1] / R, pos[0] / R, 0 * R]) * s
+    mc = O.velocity_moments(*pos, *vc, w, e2)
+    np.testing.assert_allclose(mc[:, 3], m[:, 1], rtol=1e-12)
+    assert np.all(np.abs(mc[:, 1:3]) <= 1e-12 * mc[:, 3:4])
+    c, sn = math.cos(0.7), math.sin(0.7)
+    rot = lambda a: np.stack([c * a[0] - sn * a[1], sn * a[0] + c * a[1], a[2]])  # noqa: E731
+    v = g.normal(size=(3, n))
+    np.testing.assert_allclose(O.velocity_moments(*rot(pos), *rot(v), w, e2),
+                               O.velocity_moments(*pos, *v, w, e2), rtol=1e-9, atol=1e-15)
+
+
+def test_constant_beta_realisation_has_its_anisotropy():
+    """The tangential initial model (beta = -0.5) and the isotropic one
+    measure their beta within sampling noise in every shell."""
+    n = 200_000
+    e2 = I.log_shell_edges(5, 0.3, 3.0)
+    for beta, (pos, vel) in ((-0.5, I.hernquist_const_beta(n, 4, -0.5)), (0.0, I.hernquist_isotropic(n, 4))):
+        b = O.anisotropy(O.velocity_moments(*pos, *vel, np.full(n, 1.0 / n), e2))
+        np.testing.assert_allclose(b, beta, atol=0.05)
