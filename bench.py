@@ -662,7 +662,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--n", "--particles", dest="n", type=int, default=N_DEFAULT,
+                    help="particles per GPU (--particles also passes through torchrun)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "ifu-lut",
                                                                "ifu-lut-seeing", "recovery"])
