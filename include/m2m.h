@@ -516,7 +516,9 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
  * or m2m_observe_static when ctx is NULL). */
 const char *m2m_last_error(const m2m_ctx *ctx);
 
-/* Release library-owned memory; particle arrays are not touched. */
+/* Release library-owned memory.  The particle arrays are left as they are,
+ * except that a pending weight update (lazy updates) is applied to w first
+ * (best effort: an error there is not reported).  Synchronises. */
 int m2m_free(m2m_ctx *ctx);
 
 #ifdef __cplusplus
