@@ -1,0 +1,90 @@
+"""The general multipole expansion (every l <= lmax, every m) of the
+weighted particles (oracle; test infrastructure only).  The self-consistent
+potential of the step (:mod:`oracle.sh`) keeps the axisymmetric, even-l
+part; this module is its non-axisymmetric generalisation, for triaxial
+models, written as direct sums with no radial nodes.
+
+Real spherical harmonics, orthonormal on the unit sphere:
+  Y_l0  = N_l0 P_l^0(mu),
+  Y_lm  = sqrt(2) N_lm P_l^m(mu) cos(m phi),    m > 0,
+  Y_l-m = sqrt(2) N_lm P_l^m(mu) sin(m phi),    m > 0,
+  N_lm  = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),  mu = cos theta,
+with P_l^m the associated Legendre functions without the Condon-Shortley
+phase (its sign cancels in every product Y_lm Y_lm).  The potential of
+particles of weight w_i (G = 1) truncated at lmax:
+  Phi(x) = - sum_i w_i sum_(l <= lmax) sum_m 4 pi/(2l+1) Y_lm(x^) Y_lm(x_i^)
+                    r_<^l / r_>^(l+1),
+r_< and r_> the smaller and larger of |x| and |x_i|; by the addition
+theorem the inner sum over m is P_l(x^ . x_i^) and the full series is
+-sum_i w_i / |x - x_i|.
+"""
+import math
+
+import numpy as np
+
+
+def assoc_legendre(lmax, mu):
+    """P_l^m(mu) for 0 <= m <= l <= lmax (no Condon-Shortley phase), as a
+    dict {(l, m): array}, by the standard recurrences in l at fixed m."""
+    mu = np.asarray(mu, dtype=np.float64)
+    s = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    P = {}
+    pmm = np.ones_like(mu)
+    for m in range(lmax + 1):
+        if m > 0:
+            pmm = pmm * (2 * m - 1) * s               # P_m^m = (2m-1)!! s^m
+        P[(m, m)] = pmm
+        if m + 1 <= lmax:
+            P[(m + 1, m)] = (2 * m + 1) * mu * pmm
+        for l in range(m + 2, lmax + 1):
+            P[(l, m)] = ((2 * l - 1) * mu * P[(l - 1, m)] - (l + m - 1) * P[(l - 2, m)]) / (l - m)
+    return P
+
+
+def index(lmax):
+    """(l, m) of every real harmonic up to lmax, m = -l..l in order."""
+    return [(l, m) for l in range(lmax + 1) for m in range(-l, l + 1)]
+
+
+def real_harmonics(lmax, x, y, z):
+    """Y_lm at the directions of (x, y, z), shape ((lmax+1)^2, n) in the
+    order of :func:`index`; the direction of the origin is taken as +z."""
+    x, y, z = (np.asarray(a, dtype=np.float64) for a in (x, y, z))
+    r = np.sqrt(x * x + y * y + z * z)
+    rs = np.where(r > 0, r, 1.0)
+    mu = np.where(r > 0, z / rs, 1.0)
+    phi = np.arctan2(y, x)
+    P = assoc_legendre(lmax, mu)
+    out = []
+    for l, m in index(lmax):
+        am = abs(m)
+        N = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+        if m == 0:
+            out.append(N * P[(l, 0)])
+        elif m > 0:
+            out.append(math.sqrt(2.0) * N * P[(l, am)] * np.cos(am * phi))
+        else:
+            out.append(math.sqrt(2.0) * N * P[(l, am)] * np.sin(am * phi))
+    return np.stack(out)
+
+
+def potential(px, py, pz, x, y, z, w, lmax):
+    """Phi at the points (px, py, pz) of the particles (x, y, z, w),
+    truncated at lmax: the double sum written out over particles, l and m
+    (a point at a particle's radius counts that particle as inside)."""
+    px, py, pz = (np.atleast_1d(np.asarray(a, dtype=np.float64)) for a in (px, py, pz))
+    x, y, z, w = (np.asarray(a, dtype=np.float64) for a in (x, y, z, w))
+    Yp = real_harmonics(lmax, px, py, pz)
+    Yi = real_harmonics(lmax, x, y, z)
+    rp = np.sqrt(px * px + py * py + pz * pz)
+    ri = np.sqrt(x * x + y * y + z * z)
+    out = np.zeros(px.shape[0])
+    for j in range(px.shape[0]):
+        rl = np.minimum(rp[j], ri)
+        rg = np.maximum(rp[j], ri)
+        rg = np.where(rg > 0, rg, 1.0)
+        acc = np.zeros_like(ri)
+        for k, (l, m) in enumerate(index(lmax)):
+            acc += 4 * math.pi / (2 * l + 1) * Yp[k, j] * Yi[k] * rl ** l / rg ** (l + 1)
+        out[j] = -np.sum(w * acc)
+    return out

@@ -1,0 +1,107 @@
+"""Pins of the general (all l, m) multipole expansion of the oracle."""
+import math
+
+import numpy as np
+
+from oracle import sh as SH
+from oracle import sh_full as F
+
+
+def test_real_harmonics_are_orthonormal_by_quadrature():
+    """Gauss-Legendre in mu (9 points) times 17 equally spaced phi integrate
+    every product of two harmonics with l <= 8 exactly."""
+    L = 8
+    mu, wm = np.polynomial.legendre.leggauss(L + 1)
+    nphi = 2 * L + 1
+    phi = 2 * math.pi * np.arange(nphi) / nphi
+    M, PH = np.meshgrid(mu, phi, indexing="ij")
+    s = np.sqrt(1 - M * M)
+    Y = F.real_harmonics(L, (s * np.cos(PH)).ravel(), (s * np.sin(PH)).ravel(), M.ravel())
+    wq = (np.outer(wm, np.full(nphi, 2 * math.pi / nphi))).ravel()
+    G = (Y * wq) @ Y.T
+    np.testing.assert_allclose(G, np.eye(Y.shape[0]), atol=1e-12)
+
+
+def test_addition_theorem():
+    """sum_m Y_lm(a) Y_lm(b) = (2l+1)/(4 pi) P_l(a.b) with P_l by Bonnet's
+    recurrence."""
+    g = np.random.default_rng(3)
+    a, b = g.normal(size=(2, 3, 50))
+    Ya = F.real_harmonics(8, *a)
+    Yb = F.real_harmonics(8, *b)
+    cosg = (a * b).sum(0) / np.sqrt((a * a).sum(0) * (b * b).sum(0))
+    P = SH.legendre(cosg, 8)
+    idx = F.index(8)
+    for l in range(9):
+        rows = [k for k, (ll, _) in enumerate(idx) if ll == l]
+        np.testing.assert_allclose((Ya[rows] * Yb[rows]).sum(0), (2 * l + 1) / (4 * math.pi) * P[l],
+                                   rtol=1e-11, atol=1e-13)
+
+
+def test_truncated_series_converges_to_the_newtonian_potential():
+    """|Phi_lmax - Phi| <= sum_i w_i q_i^(lmax+1) / (r_> (1 - q_i)), q = r_</r_>."""
+    g = np.random.default_rng(5)
+    x, y, z = g.normal(size=(3, 40)) * 0.4
+    w = g.uniform(0.5, 1.5, 40)
+    p = np.array([[1.7, -0.9, 1.2], [0.05, 0.1, -0.08]]).T
+    for j in range(p.shape[1]):
+        d = np.sqrt((p[0, j] - x) ** 2 + (p[1, j] - y) ** 2 + (p[2, j] - z) ** 2)
+        exact = -np.sum(w / d)
+        rp, ri = np.linalg.norm(p[:, j]), np.sqrt(x * x + y * y + z * z)
+        q = np.minimum(rp, ri) / np.maximum(rp, ri)
+        prev = None
+        for L in (4, 8, 12):
+            err = abs(F.potential(*p[:, j:j + 1], x, y, z, w, L)[0] - exact)
+            bound = np.sum(w * q ** (L + 1) / (np.maximum(rp, ri) * (1 - q)))
+            assert err <= bound + 1e-12
+            if prev is not None and bound < 1e-3:
+                assert err < prev
+            prev = err
+
+
+def test_axisymmetric_even_part_is_the_step_expansion_at_a_node():
+    """Restricted to m = 0 and even l <= 8, the general expansion at a node
+    radius equals -sum_l P_l(mu) F_l(k) of the step's expansion tables."""
+    g = np.random.default_rng(7)
+    n = 300
+    x, y, z = g.normal(size=(3, n))
+    w = g.uniform(0.5, 1.5, n) / n
+    rn = SH.nodes(0.05, 20.0, 16)
+    A, B = SH.coefficients(x, y, z, w, rn)
+    Ft, Dt = SH.tables(A, B, rn)
+    k = 9
+    mu = np.array([-0.8, 0.1, 0.6])
+    ph = np.array([0.3, 2.0, -1.1])
+    s = np.sqrt(1 - mu * mu)
+    px, py, pz = rn[k] * s * np.cos(ph), rn[k] * s * np.sin(ph), rn[k] * mu
+    Yp = F.real_harmonics(8, px, py, pz)
+    Yi = F.real_harmonics(8, x, y, z)
+    ri = np.sqrt(x * x + y * y + z * z)
+    ref = -(SH.legendre(mu, 8)[list(SH.LS)] * Ft[:, k:k + 1]).sum(0)
+    out = np.zeros(3)
+    for j in range(3):
+        inside = ri * ri < rn[k] ** 2
+        rl = np.where(inside, ri, rn[k])
+        rg = np.where(inside, rn[k], ri)
+        for kk, (l, m) in enumerate(F.index(8)):
+            if m == 0 and l % 2 == 0:
+                out[j] -= np.sum(w * 4 * math.pi / (2 * l + 1) * Yp[kk, j] * Yi[kk] * rl ** l / rg ** (l + 1))
+    np.testing.assert_allclose(out, ref, rtol=1e-10)
+
+
+def test_mirror_symmetric_sets_keep_even_l_and_even_nonnegative_m():
+    """Particles mirrored in the three coordinate planes (a triaxial,
+    reflection-symmetric model): sum w r^l Y_lm vanishes unless l and m are
+    even and m >= 0."""
+    g = np.random.default_rng(9)
+    x, y, z = np.abs(g.normal(size=(3, 100)))
+    sx, sy, sz = np.meshgrid([1, -1], [1, -1], [1, -1], indexing="ij")
+    X = np.concatenate([a * x for a in sx.ravel()])
+    Y = np.concatenate([a * y for a in sy.ravel()])
+    Z = np.concatenate([a * z for a in sz.ravel()])
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    H = F.real_harmonics(8, X, Y, Z)
+    for k, (l, m) in enumerate(F.index(8)):
+        c = np.sum(r ** l * H[k])
+        if l % 2 or m % 2 or m < 0:
+            assert abs(c) < 1e-9 * np.sum(r ** l), (l, m, c)
