@@ -88,3 +88,80 @@ def potential(px, py, pz, x, y, z, w, lmax):
             acc += 4 * math.pi / (2 * l + 1) * Yp[k, j] * Yi[k] * rl ** l / rg ** (l + 1)
         out[j] = -np.sum(w * acc)
     return out
+
+
+# --------------------------------------------------------------------------
+# The same expansion tabulated on radial nodes, as the step's axisymmetric
+# expansion (:mod:`oracle.sh`) does for m = 0 and even l: the blueprint of a
+# non-axisymmetric kernel.
+#   A_lm(k) = sum_(r_i < r_k)          w_i r_i^l     Y_lm(x_i^),
+#   B_lm(k) = sum_(r_k <= r_i < rmax)  w_i r_i^-(l+1) Y_lm(x_i^),
+#   F_lm(k) = 4 pi/(2l+1) [A_lm(k) / r_k^(l+1) + B_lm(k) r_k^l],
+#   D_lm(k) = 4 pi/(2l+1) [-(l+1) A_lm(k) / r_k^(l+2) + l B_lm(k) r_k^(l-1)],
+#   Phi(x) = - sum_lm Y_lm(x^) F_lm(r),
+# sides by r^2 in the state precision against float64 r_k^2, F and D linear
+# in r between nodes, the exterior and interior laws outside them.
+# --------------------------------------------------------------------------
+def coefficients_nodes(x, y, z, w, rn, lmax):
+    """A_lm(r_k), B_lm(r_k), shape ((lmax+1)^2, K)."""
+    from . import sh as _sh
+    K = len(rn)
+    j = _sh.node_side(x, y, z, rn)
+    keep = j < K
+    xd, yd, zd = (np.asarray(v, dtype=np.float64)[keep] for v in (x, y, z))
+    w = np.asarray(w, dtype=np.float64)[keep]
+    j = j[keep]
+    r = np.sqrt(xd * xd + yd * yd + zd * zd)
+    rs = np.where(r > 0, r, 1.0)
+    Y = real_harmonics(lmax, xd, yd, zd)
+    A = np.zeros((Y.shape[0], K))
+    B = np.zeros((Y.shape[0], K))
+    for n, (l, m) in enumerate(index(lmax)):
+        ta = np.bincount(j, weights=w * Y[n] * r ** l, minlength=K)
+        tb = np.bincount(j, weights=np.where(j > 0, w * Y[n] * rs ** (-(l + 1)), 0.0), minlength=K)
+        A[n] = np.cumsum(ta)
+        B[n, :-1] = np.cumsum(tb[:0:-1])[::-1]
+    return A, B
+
+
+def tables_nodes(A, B, rn, lmax):
+    """F_lm(k), D_lm(k) with the 4 pi/(2l+1) of the addition theorem."""
+    F = np.zeros_like(A)
+    D = np.zeros_like(A)
+    for n, (l, m) in enumerate(index(lmax)):
+        c = 4 * math.pi / (2 * l + 1)
+        F[n] = c * (A[n] / rn ** (l + 1) + B[n] * rn ** l)
+        D[n] = c * (-(l + 1) * A[n] / rn ** (l + 2) + (l * B[n] * rn ** (l - 1) if l > 0 else 0.0))
+    return F, D
+
+
+def radial_nodes(F, D, rn, r, lmax):
+    """F_lm(r), D_lm(r): linear between nodes; beyond r_(K-1)
+    F(K-1) (r_(K-1)/r)^(l+1); inside r_0 F(0) (r/r_0)^l and
+    D(0) (r/r_0)^max(l-1, 1)."""
+    r = np.asarray(r, np.float64)
+    K = len(rn)
+    rc = np.clip(r, rn[0], rn[-1])
+    k = np.clip(np.searchsorted(rn, rc, side="right") - 1, 0, K - 2)
+    t = (rc - rn[k]) / (rn[k + 1] - rn[k])
+    Fr = F[:, k] * (1 - t) + F[:, k + 1] * t
+    Dr = D[:, k] * (1 - t) + D[:, k + 1] * t
+    ls = np.array([l for l, _ in index(lmax)], np.float64)[:, None]
+    out = r >= rn[-1]
+    ro = np.where(out, r, rn[-1])
+    Fo = F[:, -1:] * (rn[-1] / ro) ** (ls + 1)
+    Fr = np.where(out, Fo, Fr)
+    Dr = np.where(out, -(ls + 1) * Fo / ro, Dr)
+    inn = r < rn[0]
+    q = np.where(inn, r, rn[0]) / rn[0]
+    Fr = np.where(inn, F[:, :1] * q ** ls, Fr)
+    Dr = np.where(inn, D[:, :1] * q ** np.maximum(ls - 1, 1), Dr)
+    return Fr, Dr
+
+
+def potential_nodes(px, py, pz, F, D, rn, lmax):
+    """Phi of the tabulated expansion at the points (px, py, pz)."""
+    px, py, pz = (np.atleast_1d(np.asarray(a, dtype=np.float64)) for a in (px, py, pz))
+    r = np.sqrt(px * px + py * py + pz * pz)
+    Y = real_harmonics(lmax, px, py, pz)
+    return -np.sum(Y * radial_nodes(F, D, rn, r, lmax)[0], axis=0)

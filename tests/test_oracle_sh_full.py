@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle import sh as SH
 from oracle import sh_full as F
@@ -105,3 +106,52 @@ def test_mirror_symmetric_sets_keep_even_l_and_even_nonnegative_m():
         c = np.sum(r ** l * H[k])
         if l % 2 or m % 2 or m < 0:
             assert abs(c) < 1e-9 * np.sum(r ** l), (l, m, c)
+
+
+def _cloud(n=400, seed=11):
+    g = np.random.default_rng(seed)
+    x, y, z = g.normal(size=(3, n)) * np.array([[1.0], [0.7], [0.4]])     # triaxial
+    return x, y, z, g.uniform(0.5, 1.5, n) / n
+
+
+def test_tabulated_expansion_is_exact_at_the_nodes():
+    """At a node radius the tabulated potential is the direct double sum of
+    the same truncation (no interpolation there)."""
+    x, y, z, w = _cloud()
+    rn = SH.nodes(0.02, 30.0, 24)
+    A, B = F.coefficients_nodes(x, y, z, w, rn, 6)
+    Ft, Dt = F.tables_nodes(A, B, rn, 6)
+    g = np.random.default_rng(2)
+    for k in (3, 11, 17):
+        d = g.normal(size=(3, 4))
+        d = d / np.linalg.norm(d, axis=0) * rn[k]
+        np.testing.assert_allclose(F.potential_nodes(*d, Ft, Dt, rn, 6),
+                                   F.potential(*d, x, y, z, w, 6), rtol=1e-11)
+
+
+def test_tabulated_axisymmetric_part_is_the_step_expansion_everywhere():
+    """Keeping only m = 0 and even l, the tabulated general expansion equals
+    the step's axisymmetric expansion at any point (interpolated between
+    nodes and by the laws outside them alike)."""
+    x, y, z, w = _cloud()
+    rn = SH.nodes(0.05, 20.0, 16)
+    A, B = F.coefficients_nodes(x, y, z, w, rn, 8)
+    Ft, Dt = F.tables_nodes(A, B, rn, 8)
+    keep = np.array([m == 0 and l % 2 == 0 for l, m in F.index(8)])
+    Ft[~keep] = 0.0
+    Dt[~keep] = 0.0
+    Fa, Da = SH.tables(*SH.coefficients(x, y, z, w, rn), rn)
+    g = np.random.default_rng(4)
+    p = g.normal(size=(3, 30)) * np.geomspace(0.01, 40.0, 30)
+    np.testing.assert_allclose(F.potential_nodes(*p, Ft, Dt, rn, 8), SH.potential(*p, Fa, Da, rn),
+                               rtol=1e-11, atol=1e-13)
+
+
+def test_tabulated_monopole_obeys_gauss_at_the_last_node():
+    x, y, z, w = _cloud()
+    rn = SH.nodes(0.05, 20.0, 16)
+    A, B = F.coefficients_nodes(x, y, z, w, rn, 2)
+    Ft, _ = F.tables_nodes(A, B, rn, 2)
+    inside = (x * x + y * y) + z * z < rn[-1] ** 2
+    Y00 = 1.0 / math.sqrt(4 * math.pi)
+    assert Ft[0, -1] * Y00 == pytest.approx(np.sum(w[inside]) / rn[-1], rel=1e-13)
