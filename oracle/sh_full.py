@@ -165,3 +165,62 @@ def potential_nodes(px, py, pz, F, D, rn, lmax):
     r = np.sqrt(px * px + py * py + pz * pz)
     Y = real_harmonics(lmax, px, py, pz)
     return -np.sum(Y * radial_nodes(F, D, rn, r, lmax)[0], axis=0)
+
+
+def _q_table(lmax, mu):
+    """Q_l^m(mu) = d^m P_l / dmu^m for 0 <= m <= l + 1 <= lmax + 1 (zero
+    when m > l): P_l^m = (1 - mu^2)^(m/2) Q_l^m, the same recurrences as
+    :func:`assoc_legendre` started from Q_m^m = (2m-1)!!."""
+    mu = np.asarray(mu, dtype=np.float64)
+    Q = {}
+    qmm = np.ones_like(mu)
+    for m in range(lmax + 1):
+        if m > 0:
+            qmm = qmm * (2 * m - 1)
+        Q[(m, m)] = qmm
+        if m + 1 <= lmax:
+            Q[(m + 1, m)] = (2 * m + 1) * mu * qmm
+        for l in range(m + 2, lmax + 1):
+            Q[(l, m)] = ((2 * l - 1) * mu * Q[(l - 1, m)] - (l + m - 1) * Q[(l - 2, m)]) / (l - m)
+    zero = np.zeros_like(mu)
+    return lambda l, m: Q[(l, m)] if m <= l else zero
+
+
+def acceleration_nodes(px, py, pz, F, D, rn, lmax):
+    """-grad Phi of the tabulated expansion at (px, py, pz), shape (3, n).
+
+    Written with terms that stay regular on the z axis:
+      Y_lm(x) = c_lm Q_l^|m|(z/r) C_m(x, y) / r^|m|,
+    C_m = Re (x + i y)^m (m >= 0) or Im (x + i y)^|m| (m < 0), c_lm = N_l0
+    or sqrt(2) N_l|m|; then with n = x/r and mu = z/r
+      grad Y_lm = c_lm / r^|m| [Q_l^(|m|+1) C (e_z - mu n) / r
+                                + Q_l^|m| grad C - |m| Q_l^|m| C n / r],
+    grad Phi = -sum_lm [D_lm(r) Y_lm n + F_lm(r) grad Y_lm]; 0 at r = 0."""
+    px, py, pz = (np.atleast_1d(np.asarray(a, dtype=np.float64)) for a in (px, py, pz))
+    r = np.sqrt(px * px + py * py + pz * pz)
+    rs = np.where(r > 0, r, 1.0)
+    n = np.stack([px, py, pz]) / rs
+    mu = pz / rs
+    Q = _q_table(lmax + 1, mu)
+    Fr, Dr = radial_nodes(F, D, rn, r, lmax)
+    u = px + 1j * py
+    g = np.zeros((3,) + px.shape)
+    ez = np.array([0.0, 0.0, 1.0])[:, None]
+    for k, (l, m) in enumerate(index(lmax)):
+        am = abs(m)
+        N = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+        c = N if m == 0 else math.sqrt(2.0) * N
+        f = u ** am
+        gm = u ** (am - 1) if am > 0 else 0 * u
+        if m >= 0:
+            C = f.real
+            dC = np.stack([am * gm.real, -am * gm.imag, 0 * px])
+        else:
+            C = f.imag
+            dC = np.stack([am * gm.imag, am * gm.real, 0 * px])
+        rm = rs ** am
+        q0, q1 = Q(l, am), Q(l, am + 1)
+        Y = c * q0 * C / rm
+        gY = c / rm * (q1 * C * (ez - mu * n) / rs + q0 * dC - am * q0 * C * n / rs)
+        g += -(Dr[k] * Y * n + Fr[k] * gY)
+    return np.where(r > 0, -g, 0.0)

@@ -155,3 +155,54 @@ def test_tabulated_monopole_obeys_gauss_at_the_last_node():
     inside = (x * x + y * y) + z * z < rn[-1] ** 2
     Y00 = 1.0 / math.sqrt(4 * math.pi)
     assert Ft[0, -1] * Y00 == pytest.approx(np.sum(w[inside]) / rn[-1], rel=1e-13)
+
+
+def test_tabulated_force_axisymmetric_part_is_the_step_force():
+    """m = 0, even l only: the general force equals the step expansion's
+    force at any point, on and off the z axis."""
+    x, y, z, w = _cloud()
+    rn = SH.nodes(0.05, 20.0, 16)
+    A, B = F.coefficients_nodes(x, y, z, w, rn, 8)
+    Ft, Dt = F.tables_nodes(A, B, rn, 8)
+    keep = np.array([m == 0 and l % 2 == 0 for l, m in F.index(8)])
+    Ft[~keep] = 0.0
+    Dt[~keep] = 0.0
+    Fa, Da = SH.tables(*SH.coefficients(x, y, z, w, rn), rn)
+    g = np.random.default_rng(6)
+    p = g.normal(size=(3, 30)) * np.geomspace(0.01, 40.0, 30)
+    p[:2, :3] = 0.0                                        # on the z axis
+    ref = np.stack(SH.acceleration(*p, Fa, Da, rn))
+    np.testing.assert_allclose(F.acceleration_nodes(*p, Ft, Dt, rn, 8), ref, rtol=1e-10,
+                               atol=1e-12 * np.abs(ref).max())
+
+
+def test_tabulated_force_tangential_part_is_minus_the_angular_gradient():
+    """On a sphere r = const the tabulated potential is a finite sum of
+    harmonics: its derivative along a tangent t (central difference on the
+    sphere, error O(h^2)) is -a.t for every l, m (triaxial cloud, l <= 6),
+    on and near the z axis too."""
+    x, y, z, w = _cloud()
+    rn = SH.nodes(0.02, 30.0, 24)
+    A, B = F.coefficients_nodes(x, y, z, w, rn, 6)
+    Ft, Dt = F.tables_nodes(A, B, rn, 6)
+    g = np.random.default_rng(8)
+    pts = g.normal(size=(3, 12))
+    pts[:, 0] = [0.0, 0.0, 1.0]
+    pts[:, 1] = [1e-3, 0.0, 1.0]
+    pts = pts / np.linalg.norm(pts, axis=0) * 1.3
+    a = F.acceleration_nodes(*pts, Ft, Dt, rn, 6)
+    h = 1e-5
+    for j in range(pts.shape[1]):
+        p = pts[:, j]
+        nrm = p / np.linalg.norm(p)
+        for v in (np.array([1.0, 0.0, 0.0]), np.array([0.0, 1.0, 0.0]), np.array([0.0, 0.0, 1.0])):
+            t = v - nrm * (v @ nrm)
+            if np.linalg.norm(t) < 0.3:
+                continue
+            t = t / np.linalg.norm(t)
+            # move on the sphere: rotate p towards t by the angle h
+            pp = np.linalg.norm(p) * (np.cos(h) * nrm + np.sin(h) * t)
+            pm = np.linalg.norm(p) * (np.cos(h) * nrm - np.sin(h) * t)
+            dphi = (F.potential_nodes(*pp[:, None], Ft, Dt, rn, 6)[0]
+                    - F.potential_nodes(*pm[:, None], Ft, Dt, rn, 6)[0]) / (2 * h * np.linalg.norm(p))
+            assert -a[:, j] @ t == pytest.approx(dphi, rel=1e-6, abs=1e-9 * np.abs(a).max())
