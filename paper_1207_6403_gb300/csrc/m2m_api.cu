@@ -5,11 +5,17 @@
 //
 //   k_pass   [pending update at x_t] + push x_t -> x_{t+1} + scatter w_t
 //            at x_{t+1} + S, sum w of w_t      (+ (E, L_z) range if priors due)
-//   k_residual  y, Delta, Delta~, coef, chi^2, record t+1
+//   k_residual  y, Delta, Delta~, coef, chi^2; the record of step t+1 is
+//               written by the next pass (or k_record when none follows)
 //   -> the update w_t -> w_{t+1} (needs coef of this residual) is carried
 //      into the next k_pass, so each particle is read and written once per
-//      step; a call ends with an update-only pass so the arrays hold w_{t+1};
-//   every `period` steps: update + prior cells pass, cell means, gather.
+//      step; a call ends with an update-only pass so the arrays hold w_{t+1}
+//      (lazy updates: left to the next call, or to m2m_finish_update);
+//   every `period` steps: update + prior cells pass, cell means, gather;
+//   self-consistent SH potential: side sums and node tables every period.
+// Kernels are launched with programmatic dependent launch where one kernel
+// feeds the next; batches of models run one launch per stage for all models
+// from device argument arrays, captured as CUDA graphs.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
