@@ -126,3 +126,35 @@ def test_batch_record_gather_rejects_null():
 def test_velocity_moments_rejects_null():
     L = B.library()
     assert L.m2m_velocity_moments(None, None, 1, None) == -1
+
+
+def test_struct_field_offsets_match_the_header(tmp_path):
+    """Every field of every structure the binding passes has the offset and
+    the structure the size that a C compiler gives the header's definition
+    (gcc on the host: the layout rules of the C ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [B.m2m_potential_desc, B.m2m_obs_desc, B.m2m_prior_desc, B.m2m_params, B.m2m_tuning,
+               B.m2m_timing, B.m2m_model_desc, B.m2m_record]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "m2m.h"', "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in S._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "offsets.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "offsets"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.dirname(HDR), str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.check_output([str(exe)], text=True).splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for S in structs:
+        assert got[(S.__name__, "size")] == ctypes.sizeof(S), S.__name__
+        for f in S._fields_:
+            assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
