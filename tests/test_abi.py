@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_1207_6403_gb300 import m2m as B
@@ -158,3 +160,18 @@ def test_struct_field_offsets_match_the_header(tmp_path):
         assert got[(S.__name__, "size")] == ctypes.sizeof(S), S.__name__
         for f in S._fields_:
             assert got[(S.__name__, f[0])] == getattr(S, f[0]).offset, (S.__name__, f[0])
+
+
+def test_seeing_tables_marshal_with_their_bit_count():
+    from paper_1207_6403_gb300 import inputs as I
+    ex = I.uniform_edges(4, -1.0, 1.0)
+    keep = []
+    od = B._obs_array([I.ObservableSet("grid", "mass", ex, ex.copy(), psf_q=np.zeros(64), psf_seed=7)], keep)
+    assert od[0].psf_bits == 6 and od[0].psf_seed == 7 and od[0].geom == 3
+    with pytest.raises(ValueError):
+        B._obs_array([I.ObservableSet("grid", "mass", ex, ex.copy(), psf_q=np.zeros(48))], [])
+    lut = np.array([[0, 1, -1, 2]] * 4, np.int32)
+    od = B._obs_array([I.ObservableSet("lut", "gh", ex, ex.copy(), gh_V=np.zeros(3), gh_S=np.ones(3),
+                                       lut=lut, n_apertures=3)], keep)
+    assert od[0].geom == 4 and od[0].ncell == 3 and od[0].nx == 4 and od[0].ny == 4
+    assert [od[0].lut[k] for k in range(4)] == [0, 1, -1, 2]
