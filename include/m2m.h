@@ -1,15 +1,14 @@
 /*
  * m2m.h -- C-ABI of libm2m.so, a GB300 (sm_103a) implementation of the
- * made-to-measure (M2M) particle-model training step of Morganti & Gerhard,
- * "NMAGIC made-to-measure particle models of galaxies" (arXiv:1207.6403).
+ * made-to-measure (M2M) particle-model training step of Morganti & Gerhard
+ * (2012, arXiv:1207.6403).
  *
- * Section 2 of the paper: an N-body system with particle weights w_i is
- * trained to reproduce target observables Y_j (with errors sigma_j) by
- * maximising F = -1/2 chi^2 + mu S (Eq. 1), S = -sum_i w_i ln(w_i/w_hat_i)
- * (Eq. 2), adapting the weights while the particles are evolved in the
- * gravitational potential.  Section 2.1: the priors w_hat_i are flat (1/N)
- * or "moving": the mean weight of the particles sharing a cell of
- * integral-of-motion space.
+ * Section 2 of the paper: the weights w_i of an N-body model are adapted,
+ * while its particles orbit in the potential, until its observables match
+ * target values Y_j with errors sigma_j: F = -1/2 chi^2 + mu S (Eq. 1) with
+ * S = -sum_i w_i ln(w_i/w_hat_i) (Eq. 2) is maximised.  Section 2.1: the
+ * priors w_hat_i are flat (1/N) or moving: the mean weight of the
+ * particles that share a cell of integral-of-motion space.
  *
  * One step t -> t+1 (the order every entry point below follows):
  *   1. kick-drift-kick leapfrog push of every particle in the potential;
@@ -80,8 +79,8 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
  * NFW       p = {rho_s, r_s}:   Phi = -4 pi rho_s r_s^3 ln(1+r/r_s)/r
  * LOG       p = {v0, Rc, q}:    Phi = 1/2 v0^2 ln(Rc^2 + R^2 + z^2/q^2)
  * SH        p = {K, rmin, rmax, period}: the potential of the weighted
- *           particles themselves (Section 1 and 2: the potential may be
- *           evolved self-consistently from the particles), as the
+ *           particles themselves (Sections 1 and 2: the potential may
+ *           also be derived from the moving particles), as the
  *           axisymmetric multipole expansion with even l = 0..8,
  *             Phi = -sum_l P_l(cos theta) [A_l(r)/r^(l+1) + B_l(r) r^l],
  *             A_l(r) = sum_{r_i < r} w_i P_l r_i^l,

@@ -1,11 +1,11 @@
 """The M2M training step, written out plainly (oracle; test infrastructure only).
 
-Section 2 of the paper: an N-body system is trained to reproduce the
-observables of a target galaxy by maximising F = -1/2 chi^2 + mu S (Eq. 1)
-with respect to the particle weights w_i, S = -sum_i w_i ln(w_i/w_hat_i)
-(Eq. 2), while the particles are evolved in the potential.  Section 2.1: flat
-priors w_hat_i = 1/N, or moving priors that follow the weight distribution in
-integral-of-motion space.
+Section 2 of the paper: the weights w_i of an N-body model are adapted,
+while its particles orbit in the potential, so that its observables match
+those of a target galaxy: F = -1/2 chi^2 + mu S (Eq. 1) with
+S = -sum_i w_i ln(w_i/w_hat_i) (Eq. 2) is maximised over the weights.
+Section 2.1: flat priors w_hat_i = 1/N, or moving priors that follow the
+weight distribution in integral-of-motion space.
 
 One step t -> t+1, in this order:
 

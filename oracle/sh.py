@@ -1,9 +1,9 @@
 """Self-consistent potential by a spherical-harmonic expansion (oracle; test
 infrastructure only).
 
-The paper notes that the potential in which the particles move may be
-evolved self-consistently from the particles themselves (Section 1) and
-computed while the weights adapt (Section 2).  Reading used here: the
+The paper notes that the potential the particles orbit in may also be
+derived from the particles themselves (Section 1) and updated while the
+weights adapt (Section 2).  Reading used here: the
 axisymmetric (m = 0) multipole expansion of the weighted particles with even
 l = 0, 2, ..., 8, G = 1:
 
