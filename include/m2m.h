@@ -294,6 +294,18 @@ int m2m_finish_update(m2m_ctx *ctx);
  * rounding level).  Applies a pending weight update first.  Synchronises. */
 int m2m_velocity_moments(m2m_ctx *ctx, const double *r2_edges, int32_t nshell, double *out);
 
+/* The counter-based generator of the seeing draws (Philox4x32-10, Salmon
+ * et al. 2011; see m2m_obs_desc), evaluated by the same device routine the
+ * scatter uses, for n given counters and keys: a check of the device
+ * generator against the generator's published known-answer vectors.
+ *   counters  host, 4n uint32 (words c0..c3 of draw k at 4k..4k+3)
+ *   keys      host, 2n uint32 (k0, k1 of draw k at 2k, 2k+1)
+ *   out       host, 4n uint32 (the four output words of each draw)
+ * 1 <= n <= 2^24.  Runs on the current device and synchronises; allocates
+ * and frees its own device buffers.  Errors: M2M_ERR_ARG, M2M_ERR_NOMEM,
+ * M2M_ERR_CUDA (text in m2m_last_error(NULL)). */
+int m2m_philox4x32_10(int64_t n, const uint32_t *counters, const uint32_t *keys, uint32_t *out);
+
 /* Host copies (synchronise the stream).  Any pointer may be NULL.
  * y, Delta, Dt: observable count doubles (last scatter).  Returns the
  * sticky kernel error if one was raised. */
@@ -467,13 +479,13 @@ int m2m_batch_free(m2m_batch *batch);
 /* Observables of a particle set without any device allocation.
  *
  * The paper has no counterpart to this call: it serves callers that cannot
- * allocate device memory when they observe -- code running inside a CUDA
- * graph capture, under an external allocator that owns all device memory,
- * or in allocator-free real-time deployments, and callers that must not
- * incur the implicit synchronisation of cudaMalloc/cudaFree.  It computes
- * exactly what m2m_observe computes for an FP32C context over the same
- * particles (the same scatter kernel, exact fixed-point sums), without a
- * context.
+ * allocate device memory when they observe -- code running under an
+ * external allocator that owns all device memory, or in allocator-free
+ * real-time deployments, and callers that must not incur the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It computes what m2m_observe
+ * computes for an FP32C context over the same particles (the same scatter
+ * kernel, exact fixed-point sums at the same resolution when weight_scale
+ * is the context's initial sum of weights), without a context.
  *
  * All scratch memory -- the integer totals, an error word and the edge and
  * Gauss-Hermite tables -- is one fixed device array of
@@ -490,7 +502,8 @@ int m2m_batch_free(m2m_batch *batch);
  *                else M2M_ERR_ARG with the reason in m2m_last_error(NULL)
  *   incl_sin, incl_cos  line of sight as for m2m_params
  *   weight_scale a value of the order of sum(w) (> 0): the fixed-point
- *                resolution is 2^-50 * 2^ceil(log2(weight_scale))
+ *                resolution is 2^-25 of the average weight,
+ *                2^-25 * 2^ceil(log2(weight_scale)) / 2^ceil(log2(n))
  *   y_out        caller-owned device array of the observable count (double)
  *   stream       cudaStream_t (NULL = default stream); the work is enqueued
  *                on it and the call returns without synchronising

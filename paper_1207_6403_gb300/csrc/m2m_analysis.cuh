@@ -55,4 +55,18 @@ __global__ void k_gather_records(const m2m_record *const *src, const int *const 
     }
 }
 
+// Philox4x32-10 output words of given counters and keys, one thread per
+// draw: the generator of the seeing draws, exposed for its known-answer
+// check.
+__global__ void k_philox_words(const unsigned *ctr, const unsigned *key, long long n, unsigned *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 o = philox4x32_10(make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]),
+                                  make_uint2(key[2 * i], key[2 * i + 1]));
+    out[4 * i] = o.x;
+    out[4 * i + 1] = o.y;
+    out[4 * i + 2] = o.z;
+    out[4 * i + 3] = o.w;
+}
+
 }  // namespace m2m

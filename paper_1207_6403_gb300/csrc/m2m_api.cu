@@ -1119,6 +1119,34 @@ int m2m_velocity_moments(m2m_ctx *ctx, const double *r2_edges, int32_t nshell, d
     return check_err_word(ctx);
 }
 
+int m2m_philox4x32_10(int64_t n, const uint32_t *counters, const uint32_t *keys, uint32_t *out) {
+    if (n < 1 || n > (1 << 24) || !counters || !keys || !out) {
+        g_init_error = "m2m_philox4x32_10: 1 <= n <= 2^24 and non-NULL arrays";
+        return M2M_ERR_ARG;
+    }
+    const size_t cb = 16 * (size_t)n, kb = 8 * (size_t)n;
+    unsigned *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * cb + kb);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("m2m_philox4x32_10: ") + cudaGetErrorString(e);
+        return M2M_ERR_NOMEM;
+    }
+    unsigned *dc = d, *dk = d + 4 * n, *dout = dk + 2 * n;
+    e = cudaMemcpy(dc, counters, cb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, keys, kb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_philox_words<<<(unsigned)((n + 255) / 256), 256>>>(dc, dk, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, cb, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("m2m_philox4x32_10: ") + cudaGetErrorString(e);
+        return M2M_ERR_CUDA;
+    }
+    return M2M_OK;
+}
+
 int m2m_get_obs(m2m_ctx *ctx, double *y, double *Delta, double *Dt) {
     if (!ctx) return M2M_ERR_ARG;
     size_t b = 8 * (size_t)ctx->nobs;

@@ -2,10 +2,10 @@
 // allocation.
 //
 // Some callers cannot allocate device memory at the moment they need an
-// observation: code running inside a CUDA graph capture or under an external
-// memory manager that owns every allocation, allocator-free real-time or
-// embedded deployments, and callers that must not trigger the implicit
-// synchronisation a cudaMalloc/cudaFree can cause.  For them this entry
+// observation: code running under an external memory manager that owns
+// every allocation, allocator-free real-time or embedded deployments, and
+// callers that must not trigger the implicit synchronisation a
+// cudaMalloc/cudaFree can cause.  For them this entry
 // point runs the same scatter kernel as m2m_observe (FP32-compensated,
 // exact fixed-point sums) with all of its scratch -- the integer observable
 // totals, the error word and the edge and Gauss-Hermite tables -- kept in
@@ -232,8 +232,12 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
     if (e == cudaSuccess) e = cudaMemsetAsync(base + OFF_ERR, 0, 4, st);
     if (e != cudaSuccess) return fail(M2M_ERR_CUDA, "scratch upload: %s", cudaGetErrorString(e));
 
-    // the scatter pass of m2m_observe: FP32C, 1024 threads, no cell cache
+    // the scatter pass of m2m_observe: FP32C, 1024 threads, no cell cache;
+    // the fixed-point scale of a context: 2^-25 of the average weight
+    // weight_scale / n (both rounded up to powers of two)
     const int wexp = (int)ceil(log2(weight_scale));
+    int nbits = 0;
+    while ((1ll << nbits) < n) ++nbits;
     a.x = (void *)x; a.y = (void *)y; a.z = (void *)z; a.vx = (void *)vx; a.vy = (void *)vy; a.vz = (void *)vz;
     a.w = (double *)w; a.what = (double *)w;
     a.n = n; a.flags = F_SCAT; a.nsets = nsets; a.nobs = nobs; a.npot = 0;
@@ -241,7 +245,7 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
     a.f_sin_i = (float)incl_sin; a.f_cos_i = (float)incl_cos;
     a.edge_tab = base + OFF_EDGES; a.edge_len = (int)edges.size();
     a.gh_tab = base + OFF_GH; a.gh_len = (int)gh.size();
-    a.fx_shift = 50 - wexp;
+    a.fx_shift = FX_AVG_BITS + nbits - wexp;
     a.y_acc = (unsigned long long *)(base + OFF_TOT);
     a.fx_atomic = 1;
     a.err = (int *)(base + OFF_ERR);

@@ -122,6 +122,7 @@ def library():
         "m2m_autotune": (c_int32, [P, c_int32, ctypes.c_char_p, POINTER(m2m_tuning)]),
         "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
                                          c_double, c_double, c_double, P, P]),
+        "m2m_philox4x32_10": (c_int32, [c_int64, P, P, P]),
         "m2m_batch_init": (c_int32, [POINTER(P), c_int32, c_int32, POINTER(m2m_model_desc),
                                      POINTER(m2m_params), P]),
         "m2m_batch_step": (c_int32, [P, c_int64]),
@@ -412,6 +413,18 @@ def m2m_observe_static(pos, vel, w, obs, incl_sin, incl_cos, weight_scale, y_out
     rc = lib.m2m_observe_static(int(w.shape[0]), *ptrs, od, len(obs), float(incl_sin), float(incl_cos),
                                 float(weight_scale), c_void_p(y_out.data_ptr()), c_void_p(st))
     _check(rc, None)
+
+
+def m2m_philox4x32_10(counters, keys):
+    """Philox4x32-10 output words of the device routine: counters (n, 4)
+    and keys (n, 2) uint32 arrays; returns (n, 4) uint32."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(keys, dtype=np.uint32).reshape(-1, 2)
+    assert c.shape[0] == k.shape[0]
+    out = np.zeros_like(c)
+    _check(library().m2m_philox4x32_10(c.shape[0], c_void_p(c.ctypes.data), c_void_p(k.ctypes.data),
+                                       c_void_p(out.ctypes.data)), None)
+    return out
 
 
 def _obs_array(obs, keep):

@@ -175,3 +175,12 @@ def test_seeing_tables_marshal_with_their_bit_count():
                                        lut=lut, n_apertures=3)], keep)
     assert od[0].geom == 4 and od[0].ncell == 3 and od[0].nx == 4 and od[0].ny == 4
     assert [od[0].lut[k] for k in range(4)] == [0, 1, -1, 2]
+
+
+def test_philox_entry_rejects_bad_sizes_without_a_gpu():
+    L = B.library()
+    P = ctypes.c_void_p
+    buf = (ctypes.c_uint32 * 8)()
+    assert L.m2m_philox4x32_10(0, buf, buf, buf) == -1
+    assert L.m2m_philox4x32_10(1, None, buf, buf) == -1
+    assert "2^24" in L.m2m_last_error(None).decode()
