@@ -394,6 +394,27 @@ typedef struct {
 } m2m_tuning;
 int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, m2m_tuning *out);
 
+/* Persistent multi-step launches (on by default).  Where they apply -- an
+ * M2M_FP32C context with a compiled observable layout and potential
+ * signature (m2m_set_layout), no spherical-harmonic component, 1024-thread
+ * passes with integer-atomic histogram flushes (m2m_set_launch,
+ * m2m_set_pipeline), room for one block per SM -- m2m_step advances the
+ * steps up to the next prior recompute in one cooperative launch: one block
+ * per SM, each with a fixed range of particles, the residual of each step
+ * computed between two grid-wide barriers.  The state equals, bit for bit,
+ * that of the same steps taken as separate pass and residual launches
+ * (enable = 0).  Every barrier wait is bounded (2 s); a wait that runs out
+ * records M2M_ERR_TIMEOUT, returned by the next synchronising call. */
+int m2m_set_persistent(m2m_ctx *ctx, int32_t enable);
+
+/* Test only: the next persistent launch runs with its block 0 not arriving
+ * at the launch's first grid barrier, and with every barrier wait of that
+ * launch limited to wait_ns nanoseconds, so that the other blocks' waits
+ * run out: the launch records M2M_ERR_TIMEOUT (its results are invalid) and
+ * the next synchronising call returns it.  Nothing waits longer than the
+ * limit; no copy or other device operation is left outstanding. */
+int m2m_test_barrier_stall(m2m_ctx *ctx, int64_t wait_ns);
+
 /* Device timing of the library's own launches, by kernel class, with CUDA
  * events recorded on the context's stream around every launch while
  * enabled.  Classes: */
@@ -404,10 +425,13 @@ int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, 
 #define M2M_TK_PRIOR     4   /* update + prior-cell pass, cell means, gather */
 #define M2M_TK_OTHER     5   /* observe, push, range and cell-export passes */
 #define M2M_TK_SH        6   /* spherical-harmonic side sums and node table */
-#define M2M_TK_N         7
+#define M2M_TK_STEPS     7   /* persistent multi-step launches (see m2m_set_persistent) */
+#define M2M_TK_N         8
 typedef struct {
     int64_t launches[M2M_TK_N];  /* launches timed since the last read */
     double ms[M2M_TK_N];         /* summed device milliseconds */
+    int64_t steps[M2M_TK_N];     /* M2M steps those launches advanced (a step
+                                    pass: 1; a persistent launch: its steps) */
     int64_t kernels_total;       /* all kernels launched since the last read,
                                     timed or not */
 } m2m_timing;

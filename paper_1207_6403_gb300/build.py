@@ -13,8 +13,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRCS = [os.path.join(HERE, "csrc", f)
-        for f in ("m2m_api.cu", "m2m_pass_f32.cu", "m2m_pass_f32x.cu", "m2m_pass_f32b.cu", "m2m_pass_f64.cu", "m2m_static.cu")]
-HDRS = [os.path.join(HERE, "csrc", f) for f in ("m2m_device.cuh", "m2m_kernels.cuh", "m2m_analysis.cuh")] + [
+        for f in ("m2m_api.cu", "m2m_pass_f32.cu", "m2m_pass_f32x.cu", "m2m_pass_f32b.cu", "m2m_pass_f64.cu",
+                  "m2m_static.cu", "m2m_steps_f32.cu")]
+HDRS = [os.path.join(HERE, "csrc", f)
+        for f in ("m2m_device.cuh", "m2m_kernels.cuh", "m2m_analysis.cuh", "m2m_steps.cuh")] + [
     os.path.join(ROOT, "include", "m2m.h")]
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libm2m.so")

@@ -31,6 +31,7 @@
 #define M2M_COMMON_KERNELS
 #include "m2m_kernels.cuh"
 #include "m2m_analysis.cuh"
+#include "m2m_steps.cuh"
 
 using namespace m2m;
 static_assert(SH_ROW == M2M_SH_ROW, "node table row");
@@ -111,10 +112,17 @@ struct m2m_ctx {
     void *d_sh_e2, *d_sh_rn, *d_sh_irn, *d_sh_tab;
     double *d_sh_rnd;
     unsigned long long *d_sh_sum;
+    // persistent multi-step launches (FP32C compiled layouts)
+    bool persist = true;             // use them where they apply
+    unsigned long long *d_bar = nullptr;   // grid-barrier arrivals
+    double *d_st2 = nullptr, *d_chi2 = nullptr;   // per-block partials by step parity
+    long long wait_ns = 2000000000ll;      // limit of one grid-barrier wait
+    int test_stall = 0;              // test only: the next launch's block 0 skips its first arrival
+    long long test_wait_ns = 0;      //   and its barrier waits are limited to this
     // timing of the library's launches
     bool timing;
     long long kernels_total;
-    struct Ev { int kind; cudaEvent_t a, b; };
+    struct Ev { int kind; cudaEvent_t a, b; long long steps; };
     std::vector<Ev> evs;
     std::vector<cudaEvent_t> ev_free;
     std::string err;
@@ -156,8 +164,9 @@ cudaEvent_t ev_get(m2m_ctx *c) {
 struct LaunchTimer {
     m2m_ctx *c;
     int kind;
+    long long steps;
     cudaEvent_t a = nullptr;
-    LaunchTimer(m2m_ctx *c_, int kind_) : c(c_), kind(kind_) {
+    LaunchTimer(m2m_ctx *c_, int kind_, long long steps_ = -1) : c(c_), kind(kind_), steps(steps_) {
         c->kernels_total++;
         if (c->timing && (a = ev_get(c))) cudaEventRecord(a, c->st);
     }
@@ -166,7 +175,8 @@ struct LaunchTimer {
         cudaEvent_t b = ev_get(c);
         if (!b) { c->ev_free.push_back(a); return; }
         cudaEventRecord(b, c->st);
-        c->evs.push_back({kind, a, b});
+        const long long ns = steps >= 0 ? steps : (kind == M2M_TK_STEP_UPD || kind == M2M_TK_STEP ? 1 : 0);
+        c->evs.push_back({kind, a, b, ns});
     }
 };
 
@@ -420,6 +430,87 @@ int prior_recompute(m2m_ctx *ctx, int pass_flags) {
     return M2M_OK;
 }
 
+// The persistent multi-step kernel for this context, or NULL where it does
+// not apply (FP64, the run-time set walk, the spherical-harmonic potential,
+// the bulk-copy pipeline or per-block histogram slots chosen, a potential
+// signature without one, or no room for one block per SM).
+void *persistent_kernel(m2m_ctx *ctx, size_t *smem_out, int *grid_out) {
+    if (!ctx->persist || ctx->prec != M2M_FP32C || ctx->layout == 0 || ctx->sh_on || ctx->pipe || !ctx->fx_atomic ||
+        ctx->threads != 1024)
+        return nullptr;
+    void *fn = steps_kernel_f32(ctx->layout, potential_signature(ctx));
+    if (!fn) return nullptr;
+    const size_t sm = pass_smem(ctx, F_STEADY);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 1024, sm) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    long long grid = ctx->nsm;                       // one block per SM: every block resident
+    const long long need = (ctx->n + 1023) / 1024;
+    if (grid > need) grid = need;
+    if (grid > ctx->slot_cap) grid = ctx->slot_cap;
+    *smem_out = sm;
+    *grid_out = (int)grid;
+    return fn;
+}
+
+// m steps in one cooperative launch; the last takes the (E, L_z) range when
+// last_range.  Leaves the last step's weight update pending and its record
+// written.
+int launch_steps(m2m_ctx *ctx, void *fn, size_t sm, int grid, long long m, bool last_range) {
+    int rc0 = finish_record(ctx);
+    if (rc0) return rc0;
+    StepsArgs A;
+    memset(&A, 0, sizeof A);
+    fill_args(ctx, A.p, F_STEADY);
+    A.p.cache_write = 1;
+    A.p.rec_pending = 0;
+    ResArgs &r = A.r;
+    r.nobs = ctx->nobs; r.y_acc = ctx->d_y_acc; r.fx_atomic = 1; r.fixed = 1; r.q = ctx->fx_q;
+    r.Y = ctx->d_Y; r.inv_sigma = ctx->d_isig; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
+    r.coef_d = ctx->d_coef_d; r.coef_r = ctx->d_coef_r; r.r_float = 1;
+    r.mode = 1; r.alpha = ctx->par.alpha; r.mu = ctx->par.mu;
+    r.ring = ctx->d_ring; r.last = ctx->d_last; r.write_ring = 1; r.err = ctx->d_err;
+    A.nsteps = m;
+    A.t0 = ctx->t;
+    A.epoch0 = ctx->epoch;
+    A.first_upd = ctx->pending ? 1 : 0;
+    A.first_cache = ctx->cache_valid ? 1 : 0;
+    A.last_range = last_range ? 1 : 0;
+    A.bar = ctx->d_bar;
+    A.st2 = ctx->d_st2;
+    A.chi2 = ctx->d_chi2;
+    A.wait_ns = ctx->test_stall ? ctx->test_wait_ns : ctx->wait_ns;
+    A.test_stall = ctx->test_stall;
+    ctx->test_stall = 0;
+    CU(cudaMemsetAsync(ctx->d_bar, 0, 8, ctx->st));
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = ctx->st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    void *args[] = {&A};
+    {
+        LaunchTimer lt(ctx, M2M_TK_STEPS, m);
+        CU(cudaLaunchKernelExC(&cfg, fn, args));
+    }
+    ctx->t += m;
+    ctx->epoch += m;
+    ctx->pending = true;
+    ctx->cache_valid = true;
+    ctx->rec_pending = false;
+    ctx->last_grid = grid;
+    if (last_range) ctx->mm_nblocks = grid;
+    return M2M_OK;
+}
+
 // Applies a pending weight update with an update-only pass.
 int finish_update(m2m_ctx *ctx) {
     if (!ctx->pending) return M2M_OK;
@@ -448,7 +539,7 @@ int check_err_word(m2m_ctx *ctx) {
     CU(cudaStreamSynchronize(ctx->st));
     if (h & ERR_NONFINITE) return set_err(ctx, M2M_ERR_NONFINITE, "a weight or a reduction became non-finite");
     if (h & ERR_OVERFLOW) return set_err(ctx, M2M_ERR_OVERFLOW, "fixed-point histogram range exceeded");
-    if (h & ERR_TIMEOUT) return set_err(ctx, M2M_ERR_TIMEOUT, "a bulk-copy wait ran out (results invalid)");
+    if (h & ERR_TIMEOUT) return set_err(ctx, M2M_ERR_TIMEOUT, "a bounded device wait ran out (bulk copy or grid barrier; results invalid)");
     return M2M_OK;
 }
 
@@ -465,7 +556,8 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_psf};
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_psf,
+                    c->d_bar, c->d_st2, c->d_chi2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -808,6 +900,9 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_stat_slots, (size_t)32 * ctx->slot_cap);
     ALLOC(ctx->d_rec_ticket, 8);
     ALLOC(ctx->d_chi_slots, (size_t)24 * ((nobs + 31) / 32 + 1));
+    ALLOC(ctx->d_bar, 8);
+    ALLOC(ctx->d_st2, (size_t)32 * ctx->slot_cap);
+    ALLOC(ctx->d_chi2, (size_t)48 * ctx->slot_cap);
     ALLOC(ctx->d_ticket, 4);
     ALLOC(ctx->d_ring, sizeof(m2m_record) * M2M_HISTORY);
     ALLOC(ctx->d_last, sizeof(m2m_record));
@@ -892,6 +987,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         kfns.push_back(pass_kernel_f32_batch(lay));
         if (lay) kfns.push_back(pass_kernel_f32_batch(lay, true));
         if (lay == 2) kfns.push_back(pass_kernel_f32_batch(lay, true, PK_HERNQUIST_NFW));
+        for (int pk : {PK_HERNQUIST, PK_LOG, PK_HERNQUIST_NFW}) kfns.push_back(steps_kernel_f32(lay, pk));
     }
     for (void *f : kfns) {
         if (!f) continue;                    // no such variant compiled
@@ -1038,6 +1134,26 @@ int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
     const bool moving = ctx->prior.kind != M2M_PRIOR_FLAT;
     for (int64_t k = 0; k < nsteps; ++k) {
         long long t1 = ctx->t + 1;
+        size_t psm = 0;
+        int pgrid = 0;
+        if (void *pf = persistent_kernel(ctx, &psm, &pgrid)) {
+            // the steps up to the next prior recompute (inclusive) in one launch
+            long long m = nsteps - k;
+            if (moving) {
+                const long long due = ((t1 + ctx->prior.period - 1) / ctx->prior.period) * ctx->prior.period;
+                if (due - t1 + 1 < m) m = due - t1 + 1;
+            }
+            const bool range = moving && ((t1 + m - 1) % ctx->prior.period == 0);
+            int rc = launch_steps(ctx, pf, psm, pgrid, m, range);
+            if (rc) return rc;
+            if (range) {
+                rc = prior_recompute(ctx, F_UPD);
+                if (rc) return rc;
+                ctx->pending = false;
+            }
+            k += m - 1;
+            continue;
+        }
         bool prior_due = moving && (t1 % ctx->prior.period == 0);
         int fl = F_PUSH | F_SCAT | F_STATS | (ctx->pending ? F_UPD : 0) | (prior_due ? F_MINMAX : 0);
         int g = 0;
@@ -1344,6 +1460,22 @@ int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable) {
     return M2M_OK;
 }
 
+int m2m_set_persistent(m2m_ctx *ctx, int32_t enable) {
+    if (!ctx) return M2M_ERR_ARG;
+    int rc = finish_update(ctx);
+    if (rc) return rc;
+    ctx->persist = enable != 0;
+    return M2M_OK;
+}
+
+int m2m_test_barrier_stall(m2m_ctx *ctx, int64_t wait_ns) {
+    if (!ctx || wait_ns < 1000 || wait_ns > 2000000000ll)
+        return set_err(ctx, M2M_ERR_ARG, "wait_ns out of [1e3, 2e9]");
+    ctx->test_stall = 1;
+    ctx->test_wait_ns = wait_ns;
+    return M2M_OK;
+}
+
 int m2m_set_timing(m2m_ctx *ctx, int32_t enable) {
     if (!ctx) return M2M_ERR_ARG;
     ctx->timing = enable != 0;
@@ -1359,6 +1491,7 @@ int m2m_get_timing(m2m_ctx *ctx, m2m_timing *out) {
         CU(cudaEventElapsedTime(&ms, e.a, e.b));
         out->launches[e.kind]++;
         out->ms[e.kind] += ms;
+        out->steps[e.kind] += e.steps;
         ctx->ev_free.push_back(e.a);
         ctx->ev_free.push_back(e.b);
     }

@@ -36,6 +36,58 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Knuth's two-sum: s + e == a + b exactly (round to nearest, no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (h, l) += (bh, bl) in float-float arithmetic (about 44 significant bits).
+__device__ __forceinline__ void ff_add(float &h, float &l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e = e + (l + bl);
+    h = s + e;
+    l = e - (h - s);
+}
+
+// Deterministic block sums of two per-thread float partials (FP32C entropy
+// and weight partials) in float-float arithmetic: a fixed shuffle tree in
+// each warp, the same over the warps' pairs in warp 0, then one conversion
+// to double.  No FP64 work per thread or per warp: FP64 instructions issue
+// at a small fraction of the FP32 rate on this part (even with one active
+// lane), and a double tree over 1024 threads costs microseconds per block.
+// red: 128 floats of shared memory; results valid in thread 0.
+__device__ __forceinline__ void warp_ff2(float &ah, float &al, float &bh, float &bl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ph = __shfl_xor_sync(0xffffffffu, ah, o), pl = __shfl_xor_sync(0xffffffffu, al, o);
+        const float qh = __shfl_xor_sync(0xffffffffu, bh, o), ql = __shfl_xor_sync(0xffffffffu, bl, o);
+        ff_add(ah, al, ph, pl);
+        ff_add(bh, bl, qh, ql);
+    }
+}
+__device__ __forceinline__ void block_sum2_ff(float a, float b, float *red, double &ra, double &rb) {
+    float ah = a, al = 0.f, bh = b, bl = 0.f;
+    warp_ff2(ah, al, bh, bl);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (lane == 0) {
+        red[wp] = ah; red[32 + wp] = al; red[64 + wp] = bh; red[96 + wp] = bl;
+    }
+    __syncthreads();
+    if (wp == 0) {
+        const bool in = lane < nw;
+        ah = in ? red[lane] : 0.f; al = in ? red[32 + lane] : 0.f;
+        bh = in ? red[64 + lane] : 0.f; bl = in ? red[96 + lane] : 0.f;
+        warp_ff2(ah, al, bh, bl);
+        if (lane == 0) {
+            ra = (double)ah + (double)al;
+            rb = (double)bh + (double)bl;
+        }
+    }
+}
+
 // Deterministic block sum (fixed shape), result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double *red) {
     v = warp_sum(v);
@@ -162,9 +214,9 @@ __device__ __forceinline__ void record_warp(const double *chi, int nch, const do
         for (int u = 0; u < U; ++u) {
             const int b = b0 + 32 * u;
             const bool ok = b < nch;
-            t0[u] = ok ? chi[3 * b] : 0.0;
-            t1[u] = ok ? chi[3 * b + 1] : 0.0;
-            t2[u] = ok ? chi[3 * b + 2] : 0.0;
+            t0[u] = ok ? __ldcg(chi + 3 * b) : 0.0;
+            t1[u] = ok ? __ldcg(chi + 3 * b + 1) : 0.0;
+            t2[u] = ok ? __ldcg(chi + 3 * b + 2) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) { v0 += t0[u]; v1 += t1[u]; v2 = fmax(v2, t2[u]); }
@@ -175,8 +227,8 @@ __device__ __forceinline__ void record_warp(const double *chi, int nch, const do
         for (int u = 0; u < U; ++u) {
             const int b = b0 + 32 * u;
             const bool ok = b < nst;
-            t3[u] = ok ? st[2 * b] : 0.0;
-            t4[u] = ok ? st[2 * b + 1] : 0.0;
+            t3[u] = ok ? __ldcg(st + 2 * b) : 0.0;
+            t4[u] = ok ? __ldcg(st + 2 * b + 1) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) { v3 += t3[u]; v4 += t4[u]; }
@@ -343,6 +395,20 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
     return dot;
 }
 
+// The update's Gauss-Hermite term of one cell, sum_n coef_n u_n(nu) =
+// exp(-nu m / 2) P(m) with m = nu c1: the quartic P from the cell's
+// coefficients cf0..cf4, t2 and norm (E[H_n] over N(m, t2) as polynomials
+// in m, van der Marel & Franx H_0..H_4).
+template <class R>
+__device__ __forceinline__ void gh_quartic(R t2, R nrm, R cf0, R cf1, R cf2, R cf3, R cf4, R P[5]) {
+    const R r2 = R(1.4142135623730951), r3 = R(1.7320508075688772), r24 = R(4.898979485566356);
+    P[0] = nrm * (cf0 + cf2 * ((R(2) * t2 - R(1)) / r2) + cf4 * ((R(12) * t2 * t2 - R(12) * t2 + R(3)) / r24));
+    P[1] = nrm * (cf1 * r2 + cf3 * ((R(6) * t2 - R(3)) / r3));
+    P[2] = nrm * (cf2 * r2 + cf4 * ((R(24) * t2 - R(12)) / r24));
+    P[3] = nrm * (cf3 * (R(2) / r3));
+    P[4] = nrm * (cf4 * (R(4) / r24));
+}
+
 struct ThreadAcc {
     double s_d, w_d;     // FP64 path
     float s_f, w_f;      // FP32C path
@@ -500,8 +566,10 @@ __device__ __forceinline__ void cell_add<double>(const PassArgs &a, const PassSm
 template <class R, int L, int FL, int PK>
 __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S, int i,
                                          R &x, R &y, R &z, R &vx, R &vy, R &vz, double &w, R what,
-                                         unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs) {
-    // what: FP32C ln w_hat, FP64 w_hat
+                                         unsigned cc, ThreadAcc &t, R &emin, R &emax, R &lzm, float fs,
+                                         long long epoch, bool cache_read) {
+    // what: FP32C ln w_hat, FP64 w_hat; epoch: pushes the positions have had
+    // at the start of this pass; cache_read: cc holds the cells at x
     const int fl = FL ? FL : a.flags;
     const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
@@ -511,8 +579,8 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             R wr;
             if (fl & F_UPD) {
                 R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
-                const bool cached = L != 0 && a.cache_read;
-                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc, i, a.epoch);
+                const bool cached = L != 0 && cache_read;
+                R dot = obs_dot<R, L>(a, S, x, y, z, X, Ys, vlos, cached, cc, i, epoch);
                 wn = upd_weight(w, what, dot, a, wr, L1);
                 if (d_bad(wn)) t.bad = true;
             } else {
@@ -532,7 +600,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
         const R wv = to_r(wn, (R *)nullptr);
         // the scatter sees the positions after this pass's push, if any
         const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t, i,
-                                              a.epoch + ((fl & F_PUSH) ? 1 : 0));
+                                              epoch + ((fl & F_PUSH) ? 1 : 0));
         if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
     }
     if (fl & F_MINMAX) {
@@ -663,13 +731,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 R P[5] = {R(0), R(0), R(0), R(0), R(0)};
                 if (fl & F_UPD) {
                     const R *cf = (const R *)a.coef + st.obs_off + 5 * c;
-                    const R r2 = R(1.4142135623730951), r3 = R(1.7320508075688772), r24 = R(4.898979485566356);
-                    P[0] = nrm * (cf[0] + cf[2] * ((R(2) * t2 - R(1)) / r2) +
-                                  cf[4] * ((R(12) * t2 * t2 - R(12) * t2 + R(3)) / r24));
-                    P[1] = nrm * (cf[1] * r2 + cf[3] * ((R(6) * t2 - R(3)) / r3));
-                    P[2] = nrm * (cf[2] * r2 + cf[4] * ((R(24) * t2 - R(12)) / r24));
-                    P[3] = nrm * (cf[3] * (R(2) / r3));
-                    P[4] = nrm * (cf[4] * (R(4) / r24));
+                    gh_quartic<R>(t2, nrm, cf[0], cf[1], cf[2], cf[3], cf[4], P);
                 }
                 if constexpr (GHC) {
                     float4 *rc = (float4 *)S.ghc + 3 * (st.ghc_off + c);
@@ -807,7 +869,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 if (need_cc) cc = a.cell_cache[i];
             }
             if (i < (int)n) {
-                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs, a.epoch,
+                                       a.cache_read != 0);
                 if (wr_pos) {
                     __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
                     __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
@@ -865,7 +928,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 if (need_cc) ncc = a.cell_cache[j];
             }
             if (i < (int)n) {
-                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs);
+                particle<R, L, FL, PK>(a, S, i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs, a.epoch,
+                                       a.cache_read != 0);
                 if (wr_pos) {
                     __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
                     __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
@@ -922,10 +986,14 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         }
     }
     if (fl & F_STATS) {
-        double sv = FX ? (double)t.s_f : t.s_d;
-        double wv = FX ? (double)t.w_f : t.w_d;
-        double s_tot = block_sum(sv, red);
-        double w_tot = block_sum(wv, red);
+        double s_tot = 0.0, w_tot = 0.0;
+        if (FX) {
+            __shared__ float red2[128];
+            block_sum2_ff(t.s_f, t.w_f, red2, s_tot, w_tot);
+        } else {
+            s_tot = block_sum(t.s_d, red);
+            w_tot = block_sum(t.w_d, red);
+        }
         if (threadIdx.x == 0) {
             a.stat_slots[2 * bid] = s_tot;
             a.stat_slots[2 * bid + 1] = w_tot;
@@ -994,8 +1062,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pass_batch(const __grid_constant__
     pass_body<R, NT, L, 0, FL, PK>(a, b.blk_rank[blockIdx.x], b.blk_count[m]);
 }
 
-#ifdef M2M_COMMON_KERNELS
-// ------------------------------------------------------------- k_residual
+// ------------------------------------------------------------- residual
 struct ResArgs {
     const void *slots; int nblk; int nobs; int fixed; double q;
     unsigned long long *y_acc; int fx_atomic;
@@ -1008,6 +1075,29 @@ struct ResArgs {
     int tail;                       // 1: the last block writes the record; 0: the next pass does
     int *err;
 };
+
+// Eq. 1 for observable j with total yv: Delta_j = (y_j - Y_j)/sigma_j, the
+// smoothed Delta~_j (mode 1: alpha Delta + (1 - alpha) Delta~; 2: Delta; 0:
+// unchanged) and the update's coefficient Delta~_j/sigma_j (0 where the
+// observable is masked); returns the chi^2 terms Delta~^2, Delta^2, |Delta~|.
+__device__ __forceinline__ void residual_obs(const ResArgs &a, int j, double yv, double &c2, double &c2r,
+                                             double &mx) {
+    const double is = a.inv_sigma[j];
+    const bool valid = is > 0.0;
+    const double D = valid ? (yv - a.Y[j]) * is : 0.0;
+    const double dold = a.Dt[j];
+    const double dn = (a.mode == 1) ? a.alpha * D + (1.0 - a.alpha) * dold : (a.mode == 2 ? D : dold);
+    const double cf = valid ? dn * is : 0.0;
+    a.y[j] = yv;
+    a.Delta[j] = D;
+    if (a.mode != 0) a.Dt[j] = dn;
+    a.coef_d[j] = cf;
+    if (a.r_float) ((float *)a.coef_r)[j] = (float)cf;
+    else ((double *)a.coef_r)[j] = cf;
+    c2 = dn * dn; c2r = D * D; mx = fabs(dn);
+}
+
+#ifdef M2M_COMMON_KERNELS
 
 // Deterministic strided sum over the block: thread k adds k, k+NT, ... in
 // order, then a fixed shuffle tree.
@@ -1086,21 +1176,7 @@ __device__ __forceinline__ void residual_body(const ResArgs &a, const int bid, c
         }
     }
     double c2 = 0.0, c2r = 0.0, mx = 0.0;
-    if (have) {
-        const double is = a.inv_sigma[j];
-        const bool valid = is > 0.0;
-        const double D = valid ? (yv - a.Y[j]) * is : 0.0;
-        const double dold = a.Dt[j];
-        const double dn = (a.mode == 1) ? a.alpha * D + (1.0 - a.alpha) * dold : (a.mode == 2 ? D : dold);
-        const double cf = valid ? dn * is : 0.0;
-        a.y[j] = yv;
-        a.Delta[j] = D;
-        if (a.mode != 0) a.Dt[j] = dn;
-        a.coef_d[j] = cf;
-        if (a.r_float) ((float *)a.coef_r)[j] = (float)cf;
-        else ((double *)a.coef_r)[j] = cf;
-        c2 = dn * dn; c2r = D * D; mx = fabs(dn);
-    }
+    if (have) residual_obs(a, j, yv, c2, c2r, mx);
     c2 = warp_sum(c2);
     c2r = warp_sum(c2r);
 #pragma unroll
@@ -1425,6 +1501,7 @@ void *pass_kernel_f32_steady(int layout, int pk = PK_ANY);
 void *pass_kernel_f32_compiled(int flags, int layout, int pk);   // NULL if not compiled
 void *pass_kernel_f32_pipe_steady(int layout);
 void *pass_kernel_f32_batch(int layout, bool steady = false, int pk = PK_ANY);
+void *steps_kernel_f32(int layout, int pk);                      // NULL if not compiled
 void *pass_kernel_f64(int threads, int layout);
 void *cells_kernel_f32();
 void *cells_kernel_f64();

@@ -48,8 +48,8 @@ class m2m_params(ctypes.Structure):
                 ("entropy_const", c_double), ("incl_sin", c_double), ("incl_cos", c_double)]
 
 
-TK_N = 7
-TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other", "sh")
+TK_N = 8
+TIMING_KINDS = ("step_upd", "step", "residual", "update", "prior", "other", "sh", "steps")
 
 
 class m2m_tuning(ctypes.Structure):
@@ -58,7 +58,8 @@ class m2m_tuning(ctypes.Structure):
 
 
 class m2m_timing(ctypes.Structure):
-    _fields_ = [("launches", c_int64 * TK_N), ("ms", c_double * TK_N), ("kernels_total", c_int64)]
+    _fields_ = [("launches", c_int64 * TK_N), ("ms", c_double * TK_N), ("steps", c_int64 * TK_N),
+                ("kernels_total", c_int64)]
 
 
 class m2m_model_desc(ctypes.Structure):
@@ -117,6 +118,8 @@ def library():
         "m2m_get_record_async": (c_int32, [P, P]),
         "m2m_velocity_moments": (c_int32, [P, POINTER(c_double), c_int32, POINTER(c_double)]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
+        "m2m_set_persistent": (c_int32, [P, c_int32]),
+        "m2m_test_barrier_stall": (c_int32, [P, c_int64]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
         "m2m_autotune": (c_int32, [P, c_int32, ctypes.c_char_p, POINTER(m2m_tuning)]),
@@ -258,6 +261,12 @@ class Context:
     def m2m_finish_update(self):
         _check(library().m2m_finish_update(self.ptr), self.ptr)
 
+    def m2m_set_persistent(self, enable=True):
+        _check(library().m2m_set_persistent(self.ptr, 1 if enable else 0), self.ptr)
+
+    def m2m_test_barrier_stall(self, wait_ns):
+        _check(library().m2m_test_barrier_stall(self.ptr, int(wait_ns)), self.ptr)
+
     def m2m_set_timing(self, enable):
         _check(library().m2m_set_timing(self.ptr, 1 if enable else 0), self.ptr)
 
@@ -266,6 +275,7 @@ class Context:
         _check(library().m2m_get_timing(self.ptr, byref(t)), self.ptr)
         return {"launches": {k: t.launches[i] for i, k in enumerate(TIMING_KINDS)},
                 "ms": {k: t.ms[i] for i, k in enumerate(TIMING_KINDS)},
+                "steps": {k: t.steps[i] for i, k in enumerate(TIMING_KINDS)},
                 "kernels_total": t.kernels_total}
 
     def m2m_autotune(self, steps_per_trial=20, cache_path=None):

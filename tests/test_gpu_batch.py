@@ -48,10 +48,12 @@ def _compare(bt, problems, nsteps, alone_steps=None):
         assert np.array_equal(y, y1), m
         # S and sum w are accumulated per thread in float before the double
         # block sums, so they depend on how particles are grouped into blocks
-        # (~1e-8 relative); chi^2 comes from the exact sums and is identical
+        # (~1e-8 relative); chi^2 is a double sum of the same terms (exact
+        # observables), grouped by observable slices that differ between the
+        # fused batch and a persistent launch: equal to rounding
         for a, b in zip(h, h1):
             assert a["step"] == b["step"]
-            assert a["chi2"] == b["chi2"]
+            assert a["chi2"] == pytest.approx(b["chi2"], rel=1e-13)
             assert a["sum_w"] == pytest.approx(b["sum_w"], rel=1e-6)
             assert a["S"] == pytest.approx(b["S"], rel=1e-5, abs=1e-6)
 
