@@ -64,6 +64,7 @@ struct m2m_ctx {
     int edge_len, gh_len;
     void *d_edges, *d_gh;
     int *d_lut = nullptr;            // aperture lookup tables of the LUT sets
+    short *d_pmap = nullptr;         // layout 1, aligned grids: set 1's cell of each pixel of set 0
     void *d_psf = nullptr;           // seeing quantile tables (state precision)
     long long epoch = 0;             // pushes the positions have had since m2m_init
     double *d_Y, *d_sigma, *d_isig, *d_Dt, *d_y, *d_Delta, *d_coef_d;
@@ -217,7 +218,44 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
 
 size_t pass_smem(const m2m_ctx *c, int flags) {
     return pass_smem_bytes(c->prec == M2M_FP32C, c->layout, flags, c->nobs, c->edge_len, c->gh_len,
-                           c->sh_on ? SH_ROW * c->sh_K : 0, c->prior.nE, c->prior.nL, c->ncells);
+                           c->sh_on ? SH_ROW * c->sh_K : 0, c->prior.nE, c->prior.nL, c->ncells,
+                           c->layout == 1 ? c->sets[1].pmap_len : 0);
+}
+
+// Pixels of grid set g0 -> cell of grid set g1, when every edge of g1 is an
+// edge of g0 as the floats the cells are decided against (the smallest
+// float >= each double edge) and g1's range lies within g0's: then a float
+// coordinate's g1 cell is a function of its g0 pixel, and the table gives
+// it (-1 outside g1).  Empty when the grids are not so aligned.
+std::vector<short> aligned_pixel_map(const SetDev &g0, const SetDev &g1, const std::vector<double> &edges) {
+    std::vector<short> none;
+    if ((long long)g1.nx * g1.ny >= 32767) return none;
+    std::vector<int> ax_of[2];
+    for (int ax = 0; ax < 2; ++ax) {
+        const int n0 = ax ? g0.ny : g0.nx, n1 = ax ? g1.ny : g1.nx;
+        const double *e0 = edges.data() + (ax ? g0.ey_off : g0.ex_off);
+        const double *e1 = edges.data() + (ax ? g1.ey_off : g1.ex_off);
+        std::vector<float> f0(n0 + 1), f1(n1 + 1);
+        for (int k = 0; k <= n0; ++k) f0[k] = ceil_float(e0[k]);
+        for (int k = 0; k <= n1; ++k) f1[k] = ceil_float(e1[k]);
+        // every g1 edge is a g0 edge: its index in g0
+        std::vector<int> at(n1 + 1, -1);
+        for (int k = 0, j = 0; k <= n1; ++k) {
+            while (j <= n0 && f0[j] < f1[k]) ++j;
+            if (j > n0 || f0[j] != f1[k]) return none;
+            at[k] = j;
+        }
+        ax_of[ax].assign(n0, -1);
+        for (int k = 0; k < n1; ++k)
+            for (int j = at[k]; j < at[k + 1]; ++j) ax_of[ax][j] = k;
+    }
+    std::vector<short> map((size_t)g0.nx * g0.ny);
+    for (int iy = 0; iy < g0.ny; ++iy)
+        for (int ix = 0; ix < g0.nx; ++ix) {
+            const int a = ax_of[0][ix], b = ax_of[1][iy];
+            map[(size_t)iy * g0.nx + ix] = (short)(a >= 0 && b >= 0 ? b * g1.nx + a : -1);
+        }
+    return map;
 }
 
 // Compile-time observable layout matching the context's sets (see
@@ -556,7 +594,7 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_psf,
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_pmap, c->d_psf,
                     c->d_bar, c->d_st2, c->d_chi2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -852,6 +890,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ctx->layout = detect_layout(ctx);
     ctx->edge_len = (int)edges_d.size();
     ctx->gh_len = (int)gh_d.size();
+    std::vector<short> pmap_h;
+    if (f32 && ctx->layout == 1) pmap_h = aligned_pixel_map(ctx->sets[0], ctx->sets[1], edges_d);
 
     // priors
     if (prior && prior->kind != M2M_PRIOR_FLAT) {
@@ -910,6 +950,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     ALLOC(ctx->d_mm_slots, rs * 4 * ctx->slot_cap);
     ALLOC(ctx->d_cell_cache, 4 * (size_t)n);
     if (!lut_h.empty()) ALLOC(ctx->d_lut, 4 * lut_h.size());
+    if (!pmap_h.empty()) ALLOC(ctx->d_pmap, 2 * pmap_h.size());
     if (!psf_h.empty()) ALLOC(ctx->d_psf, rs * psf_h.size());
     if (f32) ALLOC(ctx->d_lnwhat, 4 * (size_t)n);
     if (ctx->ncells) {
@@ -953,6 +994,11 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
                                         : cudaMemcpy(ctx->d_lut, lut_h.data(), 4 * lut_h.size(), cudaMemcpyHostToDevice);
         for (int k = 0; k < nsets; ++k)
             if (ctx->sets[k].geom == M2M_GEOM_LUT) ctx->sets[k].lut = ctx->d_lut + lut_off[k];
+        if (e11 == cudaSuccess && !pmap_h.empty()) {
+            e11 = cudaMemcpy(ctx->d_pmap, pmap_h.data(), 2 * pmap_h.size(), cudaMemcpyHostToDevice);
+            ctx->sets[1].pmap = ctx->d_pmap;
+            ctx->sets[1].pmap_len = (int)pmap_h.size();
+        }
         // seeing tables in the state precision (FP32C: rounded once to float)
         std::vector<unsigned char> pb(rs * psf_h.size());
         for (size_t k = 0; k < psf_h.size(); ++k) {

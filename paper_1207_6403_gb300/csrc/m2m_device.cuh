@@ -37,6 +37,11 @@ struct SetDev {
     const void *psf;      // seeing: 2^bits displacement quantiles (state precision), or null
     int psf_shift;        // 32 - bits
     unsigned psf_seed;    // key word 0 of the draws
+    // a grid set whose every edge is an edge of the grid of set 0 (as the
+    // floats the cells are decided against): its cell as a function of set
+    // 0's pixel, from a table of set 0's nx*ny pixels (-1: none); 0 = off
+    int pmap_len;
+    const short *pmap;
 };
 
 struct PotDev {
@@ -114,6 +119,12 @@ __device__ __forceinline__ bool d_pos(double d) {          // d > 0 (NaN false)
 __device__ __forceinline__ bool d_bad(double d) {          // d < 0, NaN or +-inf
     long long b = __double_as_longlong(d);
     return b < 0 || (b & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+}
+
+// The element at byte offset off of an array.
+template <class T> __device__ __forceinline__ T *at(T *p, size_t off) { return (T *)((char *)p + off); }
+template <class T> __device__ __forceinline__ const T *at(const T *p, size_t off) {
+    return (const T *)((const char *)p + off);
 }
 
 // round-to-nearest integer of a float in [-2^22, 2^22] without F2I
@@ -197,6 +208,36 @@ __device__ __forceinline__ double f2d_fast(float f) {
     lo = ex == 0u ? 0u : lo;
     return __hiloint2double((int)hi, (int)lo);
 }
+
+// FP32C weights.  A double weight in the normal float range [2^-126, 2^128),
+// the case the per-particle float arithmetic handles on its fast path, is
+// recognised from its high word alone (negative values, zero, NaN and
+// infinities fall outside), and its float value truncated toward zero (the
+// d2f_fast result in this range) is the rebiased exponent and the top 23
+// mantissa bits: one subtraction and one funnel shift.
+__device__ __forceinline__ bool w_normal(unsigned hi) { return hi - 0x38100000u < 0x0FE00000u; }
+__device__ __forceinline__ float w_to_float(unsigned hi, unsigned lo) {
+    return __uint_as_float(__funnelshift_l(lo, hi - 0x38000000u, 3));
+}
+
+// Base-2 logarithm and exponential of the special-function unit with
+// subnormal arguments and results flushed to zero (PTX lg2/ex2.approx.ftz):
+// the logarithms here are of normal weights, and an exponential factor that
+// underflows contributes nothing at the histogram's fixed-point resolution.
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float LN2F = 0.693147180559945309f;      // ln 2
+constexpr float LOG2EF = 1.44269504088896341f;     // log2 e
+// e^x as 2^(x log2 e)
+__device__ __forceinline__ float exp_ftz(float x) { return ex2_ftz(x * LOG2EF); }
 
 // round(f * 2^sh) as a 64-bit integer from the float's bits (round half away
 // from zero); sets *ovf when |f| * 2^sh >= 2^63.
@@ -421,15 +462,34 @@ __device__ __forceinline__ void acc_nfw(R x, R y, R z, const PotDev &p, Acc3<R> 
     g.z = g.z + (-(f * z));
 }
 
+// A single component's acceleration itself (the sum over components below
+// starts from zero; 0 + v equals v except for the sign of a zero, which no
+// later comparison sees).
+template <class R>
+__device__ __forceinline__ Acc3<R> acc1_hernquist(R x, R y, R z, const PotDev &p) {
+    R GM = KC(R, p.c[0], p.cf[0]), aa = KC(R, p.c[1], p.cf[1]);
+    R r2 = (x * x + y * y) + z * z;
+    R r = sqrt(r2);
+    R s = r + aa;
+    R f = r2 > R(0) ? GM / ((r * s) * s) : R(0);
+    return Acc3<R>{-(f * x), -(f * y), -(f * z)};
+}
+template <class R>
+__device__ __forceinline__ Acc3<R> acc1_log(R x, R y, R z, const PotDev &p) {
+    R Rc2 = KC(R, p.c[0], p.cf[0]), iq2 = KC(R, p.c[1], p.cf[1]), v0sq = KC(R, p.c[2], p.cf[2]);
+    R R2 = x * x + y * y;
+    R D = (Rc2 + R2) + (z * z) * iq2;
+    R f = v0sq / D;
+    return Acc3<R>{-(f * x), -(f * y), -((f * iq2) * z)};
+}
+
 template <class R, int PK = PK_ANY>
 __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const R *sh = nullptr) {
     Acc3<R> g{R(0), R(0), R(0)};
     if constexpr (PK == PK_HERNQUIST) {
-        acc_hernquist<R>(x, y, z, a.pot[0], g);
-        return g;
+        return acc1_hernquist<R>(x, y, z, a.pot[0]);
     } else if constexpr (PK == PK_LOG) {
-        acc_log<R>(x, y, z, a.pot[0], g);
-        return g;
+        return acc1_log<R>(x, y, z, a.pot[0]);
     } else if constexpr (PK == PK_SH) {
         sh_accel<R>(x, y, z, sh, a.pot[0], g);
         return g;
@@ -565,7 +625,7 @@ __device__ __forceinline__ void gh_eval(float vlos, const float *g, float u[5]) 
                 ISQ24 = 0.204124145232f;
     float nu = (vlos - g[0]) * g[1];
     float c1 = g[2], t2 = g[3];
-    float gs = g[4] * __expf(-0.5f * nu * nu * c1);
+    float gs = g[4] * exp_ftz(-0.5f * nu * nu * c1);
     float m = nu * c1, m2 = m * m;
     float E2 = m2 + t2;
     float E3 = m * fmaf(3.f, t2, m2);
@@ -600,7 +660,7 @@ __device__ __forceinline__ void gh_eval_rec(float vlos, const float4 *r, float u
     gh_eval(vlos, g, u);
 }
 
-__device__ __forceinline__ float gh_exp(float x) { return __expf(x); }
+__device__ __forceinline__ float gh_exp(float x) { return exp_ftz(x); }
 __device__ __forceinline__ double gh_exp(double x) { return exp(x); }
 
 // Philox4x32 with 10 rounds (Salmon, Moraes, Dror and Shaw, SC'11): the
@@ -696,15 +756,16 @@ __device__ __forceinline__ int cell_t(const SetDev &s, const Pair<R> *edges, R x
 
 // Fixed-point histogram add of a float term v, V = round(v * 2^sh) (a
 // 64-bit integer), kept as three int32 sums per bin in shared memory:
-// V = A * 2^32 + B * 2^16 + L with B and L in [-2^15, 2^15].  Every part
+// V = A * 2^32 + B * 2^16 + L with |B| <= 2^15 and |L| <= 2^16.  Every part
 // goes in with a plain reduction (no returned value, no carry), and the bin
 // total is A_sum * 2^32 + B_sum * 2^16 + L_sum.  It is exact while at most
 // 2^15 terms reach a bin between two flushes (the pass flushes every
 // 32768 particles of a block), which keeps |B_sum|, |L_sum| < 2^31; A_sum
 // stays in range for any |V| < 2^62.  A is 0 for the usual terms (|V| <
-// 2^31) and its reduction is skipped.  For |V| < 2^38 the split takes two
-// exact float steps (1.5*2^23 "magic" rounding of V/2^16, then of the exact
-// remainder V - h*2^16), larger terms take the bit-level path.
+// 2^31, the fast path: V by one round-to-nearest conversion, L = V mod 2^16
+// and B = V >> 16) and its reduction is skipped.  For |V| < 2^38 the split
+// takes two exact float steps (1.5*2^23 "magic" rounding of V/2^16, then of
+// the exact remainder V - h*2^16), larger terms take the bit-level path.
 // fscale = 2^sh as a float (an exact power of two).
 constexpr float FX_MAGIC = 12582912.0f;            // 1.5 * 2^23
 // The common case of fx_red, for |S| = |v * 2^sh| < 2^31 (A = 0): the two
@@ -712,12 +773,10 @@ constexpr float FX_MAGIC = 12582912.0f;            // 1.5 * 2^23
 // of a particle's terms of one observable set.
 constexpr float FX_FAST = 2147483648.0f;           // 2^31
 __device__ __forceinline__ void fx_red_fast(int *Lo, int *Mid, int b, float S) {
-    const float t = fmaf(S, 1.52587890625e-05f, FX_MAGIC);     // round(S / 2^16) + M
-    const float r = fmaf(-(t - FX_MAGIC), 65536.0f, S);        // S - h * 2^16, exact
-    atomicAdd(Lo + b, __float_as_int(r + FX_MAGIC) - 0x4B400000);
-    atomicAdd(Mid + b, __float_as_int(t) - 0x4B400000);
+    const int V = __float2int_rn(S);                           // round to nearest even, |S| < 2^31
+    atomicAdd(Lo + b, V & 0xFFFF);
+    atomicAdd(Mid + b, V >> 16);
 }
-
 // The five Gauss-Hermite terms of one particle (the arithmetic of gh_eval),
 // each scaled by W = w 2^sh and added to the histogram as soon as it is
 // formed (|W u_n| < 2^31 is the caller's test), to keep few values live.
@@ -726,7 +785,7 @@ __device__ __forceinline__ void gh_red_stream(float vlos, const float4 *r, float
     const float4 a = r[0], c = r[2];
     const float nu = (vlos - a.x) * a.y;
     const float c1 = a.z, t2 = c.x;
-    const float gs = c.y * __expf(-0.5f * nu * nu * c1);
+    const float gs = c.y * exp_ftz(-0.5f * nu * nu * c1);
     const float m = nu * c1, m2 = m * m;
     fx_red_fast(Lo, Mid, b, W * gs);
     fx_red_fast(Lo, Mid, b + 1, W * (gs * (SQ2 * m)));

@@ -258,7 +258,7 @@ __device__ __forceinline__ void record_warp(const double *chi, int nch, const do
 // rounding as the carve-up at the top of pass_body, without the pipeline's
 // stage buffers).  sh_len: SH node-table values staged when the pass pushes.
 inline size_t pass_smem_bytes(bool f32, int layout, int flags, int nobs, int edge_len, int gh_len, int sh_len,
-                              int nE, int nL, int ncells) {
+                              int nE, int nL, int ncells, int pmap_len = 0) {
     const size_t rs = f32 ? 4 : 8;
     size_t b = 0;
     if (flags & F_SCAT) b += f32 ? 12 * (size_t)((nobs + 3) & ~3) : 8 * (size_t)((nobs + 1) & ~1);
@@ -268,6 +268,7 @@ inline size_t pass_smem_bytes(bool f32, int layout, int flags, int nobs, int edg
     b += rs * (size_t)((gh_len + 3) & ~3);
     if (f32 && layout != 0) b += 48 * (size_t)(gh_len / 5);          // combined GH records
     else if (flags & F_UPD) b += rs * (size_t)((gh_len + 3) & ~3);
+    if (f32 && layout == 1) b += 2 * (size_t)((pmap_len + 7) & ~7);   // pixel -> aperture table
     if (sh_len && (flags & (F_PUSH | F_MINMAX | F_CELLS))) b += rs * (size_t)((sh_len + 3) & ~3);
     if (flags & F_CELLS) {
         b += rs * (size_t)((nE + 4) & ~3) + rs * (size_t)((nL + 4) & ~3) + 16;
@@ -288,6 +289,7 @@ struct PassSmem {
     R *pe, *pl;
     float *gp;
     const R *sh;             // spherical-harmonic node table
+    const short *pmap;       // layout 1: set 1's cell of each pixel of set 0 (when aligned)
     unsigned *c_lo, *c_hi, *c_cnt;   // FP32C prior-cell sums / counts
     double *c_d;                     // FP64 prior-cell sums
     int *mmk;                        // FP32C range keys: min E, max E, max |L_z|
@@ -346,17 +348,21 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
             }
         }
     } else {
+        int c0 = -1;     // set 0's cell
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
             int c;
             if (cached) {
                 c = (int)((cc >> s.cshift) & (unsigned)s.cmask) - 1;
+            } else if (sizeof(R) == 4 && L == 1 && k == 1 && s.pmap_len) {
+                c = c0 >= 0 ? (int)S.pmap[c0] : -1;                       // aligned with set 0's pixels
             } else {
                 R Xk = X, Yk = Ys;
                 if (L == 4 && s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);   // seeing: lookup-table layout
                 c = cell_t<R, g>(s, S.epair, x, y, z, Xk, Yk);
             }
+            if (k == 0) c0 = c;
             if (c >= 0) {
                 if constexpr (q == M2M_Q_MASS) {
                     dot = dot + S.coef[s.obs_off + c];
@@ -448,12 +454,18 @@ __device__ __forceinline__ unsigned scatter(const PassArgs &a, const PassSmem<R>
             }
         }
     } else {
+        int c0 = -1;     // set 0's cell
         for_each_set<L>([&](auto K, auto G, auto Q) {
             constexpr int k = decltype(K)::value, g = decltype(G)::value, q = decltype(Q)::value;
             const SetDev &s = a.sets[k];
             R Xk = X, Yk = Ys;
             if (L == 4 && s.psf) seeing<R>(s, k, i, epoch, Xk, Yk);       // seeing: lookup-table layout
-            const int c = cell_t<R, g>(s, S.epair, x, y, z, Xk, Yk);
+            int c;
+            if (sizeof(R) == 4 && L == 1 && k == 1 && s.pmap_len)          // aligned with set 0's pixels
+                c = c0 >= 0 ? (int)S.pmap[c0] : -1;
+            else
+                c = cell_t<R, g>(s, S.epair, x, y, z, Xk, Yk);
+            if (k == 0) c0 = c;
             packed |= (unsigned)(c + 1) << s.cshift;
             if (c >= 0 && wv != R(0)) {
                 if constexpr (q == M2M_Q_MASS || q == M2M_Q_VLOS2) {
@@ -573,7 +585,32 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
     const int fl = FL ? FL : a.flags;
     const R sn = KC(R, a.sin_i, a.f_sin_i), cs = KC(R, a.cos_i, a.f_cos_i);
     double wn = w;
-    if (fl & (F_UPD | F_STATS)) {
+    // FP32C, a weight in the normal float range: the float arithmetic of
+    // the update and the entropy on the two words of the double directly
+    bool fast = false;
+    if constexpr (sizeof(R) == 4) {
+        const unsigned hi = (unsigned)__double2hiint(w), lo = (unsigned)__double2loint(w);
+        fast = w_normal(hi);
+        if (fast && (fl & (F_UPD | F_STATS))) {
+            const float wf = w_to_float(hi, lo);
+            if (fl & F_UPD) {
+                const float vlos = vy * sn + vz * cs;
+                const bool cached = L != 0 && cache_read;
+                const float dot = obs_dot<R, L>(a, S, x, y, z, x, z * sn - y * cs, vlos, cached, cc, i, epoch);
+                const float Lw = lg2_ftz(wf) * LN2F - what;
+                const float G = a.f_mu * (-Lw - a.f_ent_c) - dot;
+                const float d = a.f_eps_dt * G;
+                const float e = expm1_small(d);
+                wn = fma(w, (double)e, w);
+                // negative (or -0), infinite or NaN
+                if ((unsigned)__double2hiint(wn) >= 0x7FF00000u) t.bad = true;
+                if (fl & F_STATS) acc_stats(t, fmaf(wf, e, wf), Lw + d);
+            } else {
+                acc_stats(t, wf, lg2_ftz(wf) * LN2F - what);
+            }
+        }
+    }
+    if ((fl & (F_UPD | F_STATS)) && !fast) {
         if (d_pos(w)) {
             R L1;
             R wr;
@@ -597,11 +634,22 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         // the scattered weight is a function of the stored (double) weight
         // alone, whichever pass applied the update
-        const R wv = to_r(wn, (R *)nullptr);
+        R wv;
+        if constexpr (sizeof(R) == 4) {
+            // the truncated float in the normal range; 0 below it (d2f_fast
+            // gives 0 there too); beyond it no term is representable
+            const unsigned hn = (unsigned)__double2hiint(wn);
+            wv = w_normal(hn) ? w_to_float(hn, (unsigned)__double2loint(wn)) : 0.f;
+            if (hn - 0x47F00000u < 0x38000000u) t.ovf = true;   // 2^128 <= wn < inf
+        } else {
+            wv = to_r(wn, (R *)nullptr);
+        }
         // the scatter sees the positions after this pass's push, if any
         const unsigned packed = scatter<R, L>(a, S, x, y, z, X, Ys, vlos, wv, fs, t, i,
                                               epoch + ((fl & F_PUSH) ? 1 : 0));
-        if (L != 0 && a.cache_write) a.cell_cache[i] = packed;
+        // (a pass with its flags compiled in always belongs to a context
+        // with a cell cache; the run-time-flag passes ask)
+        if (L != 0 && (FL != 0 || a.cache_write)) a.cell_cache[i] = packed;
     }
     if (fl & F_MINMAX) {
         R E, Lz;
@@ -673,6 +721,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     constexpr bool GHC = FX && L != 0;      // combined GH records instead of gh + gpoly
     if (GHC) { S.ghc = (const float4 *)p; p += 48 * (a.gh_len / 5); }
     else if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
+    if (FX && L == 1) { S.pmap = (const short *)p; p += 2 * ((a.sets[1].pmap_len + 7) & ~7); }
     const int sh_len = (a.sh_tab && (fl & (F_PUSH | F_MINMAX | F_CELLS))) ? SH_ROW * a.sh_K : 0;
     if (sh_len) { S.sh = (const R *)p; p += sizeof(R) * ((sh_len + 3) & ~3); }
     if (fl & F_CELLS) {
@@ -713,6 +762,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
         ((Pair<R> *)S.epair)[k] = pr;
     }
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    if (FX && L == 1)
+        for (int k = threadIdx.x; k < a.sets[1].pmap_len; k += NT) ((short *)S.pmap)[k] = a.sets[1].pmap[k];
     griddep_wait();
     if (fl & F_UPD)
         for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];

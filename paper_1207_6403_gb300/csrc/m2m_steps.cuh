@@ -112,12 +112,15 @@ __device__ __forceinline__ void steps_particles(const PassArgs &a, const PassSme
     float x = 0.f, y = 0.f, z = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, wh = 0.f;
     double w = 0.0;
     unsigned cc = 0u;
+    // every array is addressed by the same byte offset from its base (4-
+    // and 8-byte elements), so one offset per element size serves them all
     if (i < n) {
-        x = __ldcs(px + i); y = __ldcs(py + i); z = __ldcs(pz + i);
-        vx = __ldcs(pvx + i); vy = __ldcs(pvy + i); vz = __ldcs(pvz + i);
-        w = __ldcs(a.w + i);
-        wh = __ldcs(a.lnwhat + i);
-        if (need_cc) cc = a.cell_cache[i];
+        const size_t o4 = (size_t)i * 4u, o8 = (size_t)i * 8u;
+        x = __ldcs(at(px, o4)); y = __ldcs(at(py, o4)); z = __ldcs(at(pz, o4));
+        vx = __ldcs(at(pvx, o4)); vy = __ldcs(at(pvy, o4)); vz = __ldcs(at(pvz, o4));
+        w = __ldcs(at(a.w, o8));
+        wh = __ldcs(at(a.lnwhat, o4));
+        if (need_cc) cc = *at(a.cell_cache, o4);
     }
     int it = 0;
 #pragma unroll 2
@@ -127,18 +130,20 @@ __device__ __forceinline__ void steps_particles(const PassArgs &a, const PassSme
         double nw = 0.0;
         unsigned ncc = 0u;
         if (j < n) {
-            nx = __ldcs(px + j); ny = __ldcs(py + j); nz = __ldcs(pz + j);
-            nvx = __ldcs(pvx + j); nvy = __ldcs(pvy + j); nvz = __ldcs(pvz + j);
-            nw = __ldcs(a.w + j);
-            nwh = __ldcs(a.lnwhat + j);
-            if (need_cc) ncc = a.cell_cache[j];
+            const size_t o4 = (size_t)j * 4u, o8 = (size_t)j * 8u;
+            nx = __ldcs(at(px, o4)); ny = __ldcs(at(py, o4)); nz = __ldcs(at(pz, o4));
+            nvx = __ldcs(at(pvx, o4)); nvy = __ldcs(at(pvy, o4)); nvz = __ldcs(at(pvz, o4));
+            nw = __ldcs(at(a.w, o8));
+            nwh = __ldcs(at(a.lnwhat, o4));
+            if (need_cc) ncc = *at(a.cell_cache, o4);
         }
         if (i < n) {
             particle<float, L, FL, PK>(a, S, (int)i, x, y, z, vx, vy, vz, w, wh, cc, t, emin, emax, lzm, fs, epoch,
                                        cache_read);
-            __stcs(px + i, x); __stcs(py + i, y); __stcs(pz + i, z);
-            __stcs(pvx + i, vx); __stcs(pvy + i, vy); __stcs(pvz + i, vz);
-            if (FL & F_UPD) __stcs(a.w + i, w);
+            const size_t o4 = (size_t)i * 4u, o8 = (size_t)i * 8u;
+            __stcs(at(px, o4), x); __stcs(at(py, o4), y); __stcs(at(pz, o4), z);
+            __stcs(at(pvx, o4), vx); __stcs(at(pvy, o4), vy); __stcs(at(pvz, o4), vz);
+            if (FL & F_UPD) __stcs(at(a.w, o8), w);
         }
         x = nx; y = ny; z = nz; vx = nvx; vy = nvy; vz = nvz; w = nw; wh = nwh; cc = ncc;
         if (++it == FX_SEG / NT && k + 1 < nit) {
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(1024, 1) k_steps(const __grid_constant__ Steps
     S.epair = (const Pair<R> *)p; p += 8 * ((a.edge_len + 1) & ~1);
     S.gh = (const R *)p; p += 4 * ((a.gh_len + 3) & ~3);
     S.ghc = (const float4 *)p; p += 48 * (a.gh_len / 5);
+    if (L == 1) { S.pmap = (const short *)p; p += 2 * ((a.sets[1].pmap_len + 7) & ~7); }
     S.mmk = mmk;
 
     const int G = (int)gridDim.x, b = (int)blockIdx.x;
@@ -202,6 +208,8 @@ __global__ void __launch_bounds__(1024, 1) k_steps(const __grid_constant__ Steps
         ((Pair<R> *)S.epair)[k] = pr;
     }
     for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    if (L == 1)
+        for (int k = threadIdx.x; k < a.sets[1].pmap_len; k += NT) ((short *)S.pmap)[k] = a.sets[1].pmap[k];
     if (threadIdx.x == 0) { mmk[0] = fkey(INFINITY); mmk[1] = fkey(-INFINITY); mmk[2] = 0; }
 
     const float fs = a.fx_shift <= 127 ? __int_as_float((a.fx_shift + 127) << 23) : INFINITY;
