@@ -29,6 +29,8 @@ import math
 
 import numpy as np
 
+from .flog import log_f32, log_f64
+
 
 def _cast(T, v):
     return np.asarray(v, dtype=np.float64).astype(T)
@@ -97,7 +99,11 @@ def potential(x, y, z, comps):
     """Potential Phi in the dtype of x, y, z (used for the prior cells).
 
     hernquist: r2 = (x*x + y*y) + z*z; Phi = -(GM / (sqrt(r2) + a))
-    log:       Phi = (0.5*v0sq) * ln(D), D as in :func:`acceleration`
+    log:       Phi = (0.5*v0sq) * ln(D), D as in :func:`acceleration`; ln
+               is :func:`oracle.flog.log_f32` / :func:`oracle.flog.log_f64`
+               (fixed sequences of float32 / float64 operations, so that the
+               prior cells do not depend on a library's rounding of the
+               logarithm)
     nfw:       float64 evaluation rounded to the state precision
     """
     T = x.dtype.type
@@ -115,7 +121,9 @@ def potential(x, y, z, comps):
                 hv = _cast(T, 0.5 * v0 * v0)
                 R2 = x * x + y * y
                 D = (Rc2 + R2) + (z * z) * iq2
-                phi = phi + hv * np.log(D)
+                # the fixed-order logarithm of oracle.flog in the state
+                # precision, which the GPU path evaluates identically
+                phi = phi + hv * (log_f32(D) if T is np.float32 else log_f64(D))
             elif c.kind == "nfw":
                 rho_s, r_s = c.params
                 xd, yd, zd = (np.asarray(v, dtype=np.float64) for v in (x, y, z))

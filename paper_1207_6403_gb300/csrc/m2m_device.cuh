@@ -513,8 +513,67 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
     return g;
 }
 
-__device__ __forceinline__ float plog(float v) { return logf(v); }
-__device__ __forceinline__ double plog(double v) { return log(v); }
+// ln x in float arithmetic with a fixed operation order, so that the
+// energy of the prior cells (and each particle's cell) does not depend on a
+// library's rounding of the logarithm.  From ln m = 2 atanh(s) = 2 (s +
+// s^3/3 + ... + s^9/9 + ...), s = (m - 1)/(m + 1), after x = 2^k m with m in
+// [sqrt(1/2), sqrt(2)] (|s| <= 0.1716: truncation error below 1e-9
+// relative): every product and sum rounded separately, the coefficients
+// 2/(2j+1) rounded to float, ln 2 = LN2_HI + LN2_LO with LN2_HI =
+// 0x3f317200 (k LN2_HI exact).  Subnormal x scaled by 2^24 first; 0 ->
+// -inf, negative or NaN -> NaN, +inf -> +inf.
+__device__ __forceinline__ float log_det(float x) {
+    if (!(x > 0.f) || x == INFINITY) return x == 0.f ? -INFINITY : (x == INFINITY ? INFINITY : __int_as_float(0x7fc00000));
+    int ks = 0;
+    if (x < 1.17549435e-38f) { x = __fmul_rn(x, 16777216.0f); ks = -24; }
+    const unsigned b = __float_as_uint(x);
+    int k = (int)(b >> 23) - 127 + ks;
+    unsigned mb = (b & 0x007FFFFFu) | 0x3F800000u;
+    if (mb > 0x3FB504F3u) { mb -= 0x00800000u; k += 1; }
+    const float m = __uint_as_float(mb);
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float z = __fmul_rn(s, s);
+    // 2/9, 2/7, 2/5, 2/3 and 2 as the floats nearest their double values
+    float p = __uint_as_float(0x3E638E39u);
+    p = __fadd_rn(__fmul_rn(p, z), __uint_as_float(0x3E924925u));
+    p = __fadd_rn(__fmul_rn(p, z), __uint_as_float(0x3ECCCCCDu));
+    p = __fadd_rn(__fmul_rn(p, z), __uint_as_float(0x3F2AAAABu));
+    p = __fadd_rn(__fmul_rn(p, z), 2.0f);
+    const float lm = __fmul_rn(s, p);
+    const float kf = (float)k;
+    const float LN2_HI = __uint_as_float(0x3F317200u), LN2_LO = __uint_as_float(0x35BFBE8Eu);
+    return __fadd_rn(__fmul_rn(kf, LN2_HI), __fadd_rn(__fmul_rn(kf, LN2_LO), lm));
+}
+// The same in double: terms to s^21 (truncation below 1e-17 relative),
+// LN2_HI = ln 2 with its low 32 mantissa bits cleared, LN2_LO the rest of
+// the double ln 2; subnormal x scaled by 2^54 first.
+__device__ __forceinline__ double log_det(double x) {
+    if (!(x > 0.0) || x == (double)INFINITY)
+        return x == 0.0 ? -(double)INFINITY : (x == (double)INFINITY ? (double)INFINITY : __longlong_as_double(0x7ff8000000000000ll));
+    int ks = 0;
+    if (x < 2.2250738585072014e-308) { x = __dmul_rn(x, 18014398509481984.0); ks = -54; }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int k = (int)(b >> 52) - 1023 + ks;
+    unsigned long long mb = (b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull;
+    if (mb > 0x3FF6A09E667F3BCCull) { mb -= 0x0010000000000000ull; k += 1; }
+    const double m = __longlong_as_double((long long)mb);
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double z = __dmul_rn(s, s);
+    // 2/21, 2/19, ..., 2/3, 2 as the doubles nearest them
+    const unsigned long long cb[11] = {0x3FB8618618618618ull, 0x3FBAF286BCA1AF28ull, 0x3FBE1E1E1E1E1E1Eull,
+                                       0x3FC1111111111111ull, 0x3FC3B13B13B13B14ull, 0x3FC745D1745D1746ull,
+                                       0x3FCC71C71C71C71Cull, 0x3FD2492492492492ull, 0x3FD999999999999Aull,
+                                       0x3FE5555555555555ull, 0x4000000000000000ull};
+    double p = __longlong_as_double((long long)cb[0]);
+#pragma unroll
+    for (int j = 1; j < 11; ++j) p = __dadd_rn(__dmul_rn(p, z), __longlong_as_double((long long)cb[j]));
+    const double lm = __dmul_rn(s, p);
+    const double kf = (double)k;
+    const double LN2_HI = __longlong_as_double(0x3FE62E4200000000ll), LN2_LO = __longlong_as_double(0x3E9FDF473DE00000ll);
+    return __dadd_rn(__dmul_rn(kf, LN2_HI), __dadd_rn(__dmul_rn(kf, LN2_LO), lm));
+}
+__device__ __forceinline__ float plog(float v) { return log_det(v); }
+__device__ __forceinline__ double plog(double v) { return log_det(v); }
 
 // One component's term of Phi (kinds 1 Hernquist, 3 flattened log, 2 NFW,
 // 4 spherical harmonics); the sum is taken in component order from 0.

@@ -96,6 +96,34 @@ def test_batch_of_different_layouts_falls_back_to_one_by_one():
     bt.m2m_batch_free()
 
 
+@pytest.mark.parametrize("model", [0, 2])
+def test_batch_model_weights_and_observables_on_the_gpu_orbits(model):
+    """A model of a fused batch (Hernquist + NFW halo; the NFW force is float
+    on the GPU and float64 rounded to float in the oracle, so the orbits part
+    by rounding): every step the oracle takes that model's new positions
+    from the GPU and does the scatter, residual and weight update itself;
+    after 300 steps every weight agrees to 1e-4 relative and every
+    observable to 1e-5 of its scale, no particle left out."""
+    problems = _batch_problems(nmodels=3, n_scale=0.01)
+    bt = B.m2m_batch_init("fp32c", problems)
+    P = problems[model]
+    st = O.init(P, "fp32c")
+    for _ in range(300):
+        bt.m2m_batch_step(1)
+        g = bt.m2m_batch_context(model).state()
+        st.x, st.y, st.z, st.vx, st.vy, st.vz = (g[k].copy() for k in ("x", "y", "z", "vx", "vy", "vz"))
+        O.step(st, P, push=False)
+    assert bt.m2m_batch_fused() >= 1
+    ctx = bt.m2m_batch_context(model)
+    g = ctx.state()
+    y, _, _ = ctx.m2m_get_obs()
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-4)
+    scale = np.maximum(np.maximum(np.abs(st.y_obs), P.sigma / 0.02), 1e-300)
+    err = np.abs(y - st.y_obs) / scale
+    assert err.max() <= 1e-5, (err.max(), err.argmax())
+    bt.m2m_batch_free()
+
+
 def test_batch_model_against_oracle():
     problems = _batch_problems(nmodels=3)
     bt = B.m2m_batch_init("fp32c", problems)
@@ -106,11 +134,8 @@ def test_batch_model_against_oracle():
     g = ctx.state()
     y, _, _ = ctx.m2m_get_obs()
     st = O.run(P, 40, precision="fp32c")
-    # NFW force: float32 evaluation vs float64 rounded to float32
+    # NFW force: float32 evaluation vs float64 rounded to float32 (the
+    # weights and observables are checked on the GPU's own orbits above)
     for k in ("x", "y", "z"):
         np.testing.assert_allclose(g[k], getattr(st, k), rtol=0, atol=2e-5 * np.abs(getattr(st, k)).max())
-    rel = np.abs(g["w"] / st.w - 1)
-    assert np.quantile(rel, 0.99) < 1e-5
-    scale = np.maximum(np.maximum(np.abs(st.y_obs), P.sigma / 0.02), 1e-300)
-    assert np.quantile(np.abs(y - st.y_obs) / scale, 0.99) < 1e-4
     bt.m2m_batch_free()

@@ -353,6 +353,46 @@ def test_philox_is_a_bijection_of_the_counter_with_uniform_words():
         assert np.mean(w[0] == u[0]) < 1e-3
 
 
+def test_fixed_order_log_is_within_three_ulp_of_the_logarithm():
+    """oracle.flog.log_f32 (the logarithm in the float energy of the
+    logarithmic potential) against float64 ln over normal and subnormal
+    floats: within 3 ulp of the float result everywhere; ln 1 = 0 exactly;
+    ln 2^k within 1 ulp of k ln 2; 0 -> -inf, negative and NaN -> NaN, inf ->
+    inf.  A wrong series coefficient, reduction bound or ln 2 split breaks
+    the first of these."""
+    from oracle.flog import log_f32
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(0.005, 200.0, 400_000), 2.0 ** rng.uniform(-149, 127.9, 400_000),
+                        1.0 + rng.uniform(-1e-3, 1e-3, 100_000)]).astype(np.float32)
+    x = x[x > 0]
+    y = log_f32(x).astype(np.float64)
+    ref = np.log(x.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert np.max(np.abs(y - ref) / ulp) <= 3.0
+    assert log_f32(np.float32(1.0)) == 0.0
+    k = np.arange(-126, 128)
+    pk = log_f32((2.0 ** k).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(pk - k * np.log(2.0)) <= np.spacing(np.abs(k * np.log(2.0)).astype(np.float32)) + 1e-30)
+    sp = log_f32(np.array([0.0, -1.0, np.nan, np.inf], dtype=np.float32))
+    assert sp[0] == -np.inf and np.isnan(sp[1]) and np.isnan(sp[2]) and sp[3] == np.inf
+
+
+def test_fixed_order_double_log_is_within_three_ulp_of_the_logarithm():
+    """oracle.flog.log_f64 against numpy's double logarithm over normal and
+    subnormal doubles (3 ulp), with ln 1 = 0 exactly and the special
+    values."""
+    from oracle.flog import log_f64
+    rng = np.random.default_rng(6)
+    x = np.concatenate([rng.uniform(0.005, 200.0, 300_000), 2.0 ** rng.uniform(-1074, 1023.9, 300_000),
+                        1.0 + rng.uniform(-1e-6, 1e-6, 50_000)])
+    x = x[x > 0]
+    ref = np.log(x)
+    assert np.max(np.abs(log_f64(x) - ref) / np.maximum(np.spacing(np.abs(ref)), 5e-324)) <= 3.0
+    assert log_f64(1.0) == 0.0
+    sp = log_f64(np.array([0.0, -1.0, np.nan, np.inf]))
+    assert sp[0] == -np.inf and np.isnan(sp[1]) and np.isnan(sp[2]) and sp[3] == np.inf
+
+
 def philox_kat():
     """The published known-answer vectors (tests/golden/philox4x32_10_kat.txt):
     a list of (counter words, key words, output words)."""
