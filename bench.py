@@ -222,15 +222,10 @@ def config(n, world):
 
 # ------------------------------------------------------------ oracle arm
 def time_oracle(P, nsteps, sample_stride):
-    """Oracle on a strided sample of the workload; returns (particle-steps/s, n_sample, s)."""
+    """Oracle on a strided sample of the workload, one process; returns
+    (particle-steps/s, n_sample, s)."""
     from oracle import m2m as O
-    from paper_1207_6403_gb300 import inputs as I
-    sl = slice(0, None, sample_stride)
-    # the sample carries the whole model's weight, so the residuals and
-    # updates it computes are those of the full workload
-    S = I.Problem(**{**P.__dict__, "n": P.pos[:, sl].shape[1], "pos": P.pos[:, sl].copy(),
-                     "vel": P.vel[:, sl].copy(), "w0": P.w0[sl] * sample_stride,
-                     "what0": P.what0[sl] * sample_stride})
+    S = sample_problem(P, sample_stride)
     st = O.init(S, "fp32c")
     t0 = time.perf_counter()
     for _ in range(nsteps):
@@ -239,25 +234,55 @@ def time_oracle(P, nsteps, sample_stride):
     return S.n * nsteps / dt, S.n, dt
 
 
+def sample_problem(P, sample_stride):
+    """Every sample_stride-th particle, carrying the whole model's weight (so
+    the residuals and updates it computes are those of the full workload)."""
+    from paper_1207_6403_gb300 import inputs as I
+    sl = slice(0, None, sample_stride)
+    return I.Problem(**{**P.__dict__, "n": P.pos[:, sl].shape[1], "pos": P.pos[:, sl].copy(),
+                        "vel": P.vel[:, sl].copy(), "w0": P.w0[sl] * sample_stride,
+                        "what0": P.what0[sl] * sample_stride})
+
+
+def time_oracle_cores(P, nsteps, sample_stride=1, warmup=0, nproc=None):
+    """The oracle on all host cores (oracle.parallel: worker processes started
+    with 'spawn', fixed chunks of 65,536 particles); returns (particle-steps/s,
+    n_sample, s, processes)."""
+    from oracle.parallel import ParallelOracle
+    S = P if sample_stride == 1 else sample_problem(P, sample_stride)
+    po = ParallelOracle(S, "fp32c", nproc=nproc)
+    try:
+        for _ in range(warmup):
+            po.step()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            po.step()
+        dt = time.perf_counter() - t0
+    finally:
+        po.close()
+    return S.n * nsteps / dt, S.n, dt, len(po.procs)
+
+
 def run_reference(args, D):
     if D.rank != 0:
         return
     P = workload(args.n, 0, targets_by="oracle")
-    # calibrate the sample so the whole warm-up + timed run takes ~2 minutes
-    rate, _, _ = time_oracle(P, 1, 40)
+    # the oracle on all host cores; the sample calibrated so that the whole
+    # warm-up + timed run takes about two minutes
+    rate, _, _, _ = time_oracle_cores(P, 1, 8)
     budget = 120.0
     per_step = budget / max(1, args.steps + args.warmup)
     n_sample = max(2000, min(args.n, int(rate * per_step)))
     stride = max(1, args.n // n_sample)
-    time_oracle(P, args.warmup, stride) if args.warmup else None
-    value, ns, secs = time_oracle(P, args.steps, stride)
+    value, ns, secs, nproc = time_oracle_cores(P, args.steps, stride, args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (state f32)", "data": "synthetic", "config": config(args.n, 1),
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": nproc, "kind": "oracle",
+                             "host_cpu_count": os.cpu_count(),
                              "sample": f"every {stride}th particle ({ns:,} of {args.n:,}) of the workload, "
-                                       f"{args.steps} oracle steps"},
+                                       f"{args.steps} oracle steps on {nproc} processes"},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -402,10 +427,16 @@ def run_ours(args, D):
 
     cpu = None
     if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
+        # all host cores on the whole workload (10 steps), and one core on a
+        # sample (every 8th particle, 3 steps)
+        rate_all, ns_all, secs_all, nproc = time_oracle_cores(P, 10)
         rate, ns, secs = time_oracle(P, 3, 8)
-        cpu = {"value": rate, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"every 8th particle ({ns:,} of {n:,}) of the workload, 3 oracle steps "
-                         f"({secs:.1f} s, numpy, one thread)"}
+        cpu = {"value": rate_all, "unit": "particle-steps/s", "cores": nproc, "kind": "oracle",
+               "host_cpu_count": os.cpu_count(),
+               "sample": f"the whole workload ({ns_all:,} particles), 10 oracle steps on {nproc} processes "
+                         f"(numpy, one thread each, fixed 65,536-particle chunks; {secs_all:.1f} s)",
+               "one_core": {"value": rate, "cores": 1,
+                            "sample": f"every 8th particle ({ns:,} of {n:,}), 3 oracle steps ({secs:.1f} s)"}}
 
     if D.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": D.world,

@@ -822,3 +822,31 @@ def test_constant_beta_realisation_has_its_anisotropy():
     for beta, (pos, vel) in ((-0.5, I.hernquist_const_beta(n, 4, -0.5)), (0.0, I.hernquist_isotropic(n, 4))):
         b = O.anisotropy(O.velocity_moments(*pos, *vel, np.full(n, 1.0 / n), e2))
         np.testing.assert_allclose(b, beta, atol=0.05)
+
+
+def test_parallel_oracle_equals_the_serial_oracle():
+    """The oracle on several processes (fixed chunks of 65,536 particles,
+    sums in chunk order) takes the same steps as the serial oracle: the same
+    trajectories bit for bit, weights, priors and observables to rounding
+    (1e-12), a prior recompute included."""
+    from oracle import m2m as O
+    from oracle.parallel import ParallelOracle
+    P = I.make_problem("flat-log", n=150_000, precision="fp32c")
+    Y = O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos)
+    P = P.with_targets(Y)
+    po = ParallelOracle(P, "fp32c", nproc=2)
+    try:
+        recs = [po.step() for _ in range(27)]
+        g = po.state()
+        y = po.y_obs
+    finally:
+        po.close()
+    st = O.run(P, 27, precision="fp32c")
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-12)
+    np.testing.assert_allclose(g["what"], st.what, rtol=1e-12)
+    np.testing.assert_allclose(y, st.y_obs, rtol=1e-12, atol=1e-15)
+    for a, b in zip(recs, st.history):
+        assert a["chi2"] == pytest.approx(b["chi2"], rel=1e-12)
+        assert a["sum_w"] == pytest.approx(b["sum_w"], rel=1e-12)
