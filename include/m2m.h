@@ -548,6 +548,50 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
                        int32_t nsets, double incl_sin, double incl_cos, double weight_scale,
                        double *y_out, void *stream);
 
+/* ---- particle shards: one model over several GPUs (data parallel) ----
+ * Each process holds one context over a contiguous shard of the model's
+ * particles (its own n; weights of the whole model).  The push, scatter and
+ * weight update of a particle need only that particle, so a step is: every
+ * shard scatters (m2m_shard_scatter); the shards' exchange buffers are
+ * summed over shards (the observable totals and the entropy / weight sums;
+ * at a prior recompute the range takes a minimum); every shard forms the
+ * residual from the sums (m2m_shard_residual); at a prior recompute every
+ * shard takes its particles' prior cells (m2m_shard_prior_cells), the cell
+ * sums and counts are summed over shards, and m2m_shard_prior_finish sets
+ * w_hat.  The collective is the caller's (NCCL or any all-reduce).  The
+ * observable totals and cell sums are integers (FP32C fixed point at the
+ * scale of the whole model), so a model split into shards takes exactly the
+ * steps it takes in one context: positions, weights, priors and
+ * observables bit for bit.  FP32C only; not with the spherical-harmonic
+ * potential; a shard context is stepped only through these calls.
+ * Buffers are caller-owned device memory:
+ *   totals   int64[m2m_nobs]  sum over shards
+ *   stats    double[2]        sum over shards (S, sum w of the scattered weights)
+ *   range    double[3]        minimum over shards (min E, -max E, -max |L_z|)
+ *   cell_sums int64[ncells], cell_counts int32[ncells]   sum over shards
+ *            (ncells = nE*nL, +1 for E_LC)
+ *
+ * m2m_shard_init: the fixed-point scale of the whole model (global_n
+ *   particles, initial sum of weights global_sum_w), as m2m_init sets it
+ *   for one context.  Call once, before the first m2m_shard_scatter.
+ * m2m_shard_scatter: with push = 1 one step's pass (the pending weight
+ *   update, the push, the scatter with the updated weights, their S and sum
+ *   w, and the (E, L_z) range when the step ends with a prior recompute:
+ *   *prior_due = 1); push = 0 scatters the current state (the initial
+ *   smoothing Delta~ := Delta, as at m2m_init).  Fills totals, stats (and
+ *   range when due).
+ * m2m_shard_residual: Eq. 1 and the smoothing from the summed totals, the
+ *   update's coefficients, the step record (from the summed stats); zeroes
+ *   totals.
+ * m2m_shard_prior_cells / m2m_shard_prior_finish: the prior recompute of a
+ *   step that ended with *prior_due = 1, from the summed range and the
+ *   summed cell sums and counts. */
+int m2m_shard_init(m2m_ctx *ctx, int64_t global_n, double global_sum_w);
+int m2m_shard_scatter(m2m_ctx *ctx, int32_t push, int32_t *prior_due, int64_t *totals, double *stats, double *range);
+int m2m_shard_residual(m2m_ctx *ctx, int64_t *totals, const double *stats);
+int m2m_shard_prior_cells(m2m_ctx *ctx, const double *range, int64_t *cell_sums, int32_t *cell_counts);
+int m2m_shard_prior_finish(m2m_ctx *ctx, const int64_t *cell_sums, const int32_t *cell_counts);
+
 /* Text of the last error on this context (or of the last failed m2m_init
  * or m2m_observe_static when ctx is NULL). */
 const char *m2m_last_error(const m2m_ctx *ctx);

@@ -55,6 +55,52 @@ __global__ void k_gather_records(const m2m_record *const *src, const int *const 
     }
 }
 
+// ----------------------------------------------------- particle shards
+// A shard's exchange buffers after its scatter pass (one warp): the int64
+// observable totals copied out (and cleared for the next scatter), the
+// entropy and weight partials of the pass's blocks summed in block order,
+// and, when the pass took the (E, L_z) range, the block ranges reduced to
+// (min E, -max E, -max |L_z|) so that a single minimum over shards gives
+// the global range.
+template <class R>
+__global__ void k_shard_pack(unsigned long long *y_acc, long long *totals, int nobs, const double *stat_slots,
+                             int nblk, double *stats, const void *mm_slots, int mm_nblk, double *range) {
+    for (int j = threadIdx.x; j < nobs; j += blockDim.x) {
+        totals[j] = (long long)y_acc[j];
+        y_acc[j] = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0, w = 0.0;
+        for (int b = 0; b < nblk; ++b) { s += stat_slots[2 * b]; w += stat_slots[2 * b + 1]; }
+        stats[0] = s;
+        stats[1] = w;
+        if (range && mm_nblk > 0) {
+            const R *mm = (const R *)mm_slots;
+            double e0 = (double)mm[0], e1 = (double)mm[1], l = (double)mm[2];
+            for (int b = 1; b < mm_nblk; ++b) {
+                e0 = fmin(e0, (double)mm[4 * b]);
+                e1 = fmax(e1, (double)mm[4 * b + 1]);
+                l = fmax(l, (double)mm[4 * b + 2]);
+            }
+            range[0] = e0;
+            range[1] = -e1;
+            range[2] = -l;
+        }
+    }
+}
+
+// The global range back into the range slots the prior-cell pass reads
+// (one slot), in the state precision (each value is one the shards' passes
+// produced, so the conversion is exact).
+template <class R>
+__global__ void k_shard_range(const double *range, void *mm_slots) {
+    R *mm = (R *)mm_slots;
+    mm[0] = (R)range[0];
+    mm[1] = (R)(-range[1]);
+    mm[2] = (R)(-range[2]);
+    mm[3] = R(0);
+}
+
 // Philox4x32-10 output words of given counters and keys, one thread per
 // draw: the generator of the seeing draws, exposed for its known-answer
 // check.

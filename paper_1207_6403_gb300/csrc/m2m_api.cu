@@ -120,6 +120,10 @@ struct m2m_ctx {
     long long wait_ns = 2000000000ll;      // limit of one grid-barrier wait
     int test_stall = 0;              // test only: the next launch's block 0 skips its first arrival
     long long test_wait_ns = 0;      //   and its barrier waits are limited to this
+    // particle shards (m2m_shard_*): this context holds one shard of a model
+    bool shard = false;
+    bool shard_push = false;         // the last shard scatter pushed
+    bool shard_due = false;          // a prior recompute is due after it
     // timing of the library's launches
     bool timing;
     long long kernels_total;
@@ -257,6 +261,12 @@ std::vector<short> aligned_pixel_map(const SetDev &g0, const SetDev &g1, const s
         }
     return map;
 }
+
+// The exponent of the fixed-point scale of a sum of weights W: ceil(log2 W),
+// with sums within 1e-12 above a power of two taken as that power (a sum of
+// N weights 1/N lands a few ulp either side of 1 depending on its order, and
+// a context over a whole model and its shards must agree on the scale).
+int scale_exp(double W) { return (int)ceil(log2(W * (1.0 - 1e-12))); }
 
 // Compile-time observable layout matching the context's sets (see
 // for_each_set); 0 = generic.  Layouts need index guesses good to one cell.
@@ -1079,7 +1089,7 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
         for (int b = 0; b < g; ++b) W += st[2 * b + 1];
         if (rc == M2M_OK && !(W >= 0 && isfinite(W))) rc = set_err(ctx, M2M_ERR_NONFINITE, "sum of weights not finite");
         if (rc == M2M_OK && W > 0) {
-            int e2 = (int)ceil(log2(W));
+            int e2 = scale_exp(W);
             ctx->fx_shift = FX_AVG_BITS + nbits - e2;
             ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
             ctx->cell_shift = 60 - e2;
@@ -1177,6 +1187,7 @@ int m2m_push(m2m_ctx *ctx, int64_t nsteps) {
 
 int m2m_step(m2m_ctx *ctx, int64_t nsteps) {
     if (!ctx || nsteps < 0) return set_err(ctx, M2M_ERR_ARG, "bad argument");
+    if (ctx->shard) return set_err(ctx, M2M_ERR_STATE, "a shard context steps through m2m_shard_*");
     const bool moving = ctx->prior.kind != M2M_PRIOR_FLAT;
     for (int64_t k = 0; k < nsteps; ++k) {
         long long t1 = ctx->t + 1;
@@ -1279,6 +1290,128 @@ int m2m_velocity_moments(m2m_ctx *ctx, const double *r2_edges, int32_t nshell, d
     cudaFreeAsync(d, ctx->st);
     if (e != cudaSuccess) return set_err(ctx, M2M_ERR_CUDA, "velocity moments: %s", cudaGetErrorString(e));
     return check_err_word(ctx);
+}
+
+// ---------------------------------------------------------------- shards
+int m2m_shard_init(m2m_ctx *ctx, int64_t global_n, double global_sum_w) {
+    if (!ctx) return M2M_ERR_ARG;
+    if (global_n < ctx->n || global_n >= (1ll << 40) || !(global_sum_w > 0) || !isfinite(global_sum_w))
+        return set_err(ctx, M2M_ERR_ARG, "global_n >= the shard's n and global_sum_w > 0 finite");
+    if (ctx->sh_on) return set_err(ctx, M2M_ERR_STATE, "shards: not with the spherical-harmonic potential");
+    if (ctx->prec != M2M_FP32C) return set_err(ctx, M2M_ERR_STATE, "shards: FP32C contexts (exact integer totals)");
+    int rc = finish_update(ctx);
+    if (rc) return rc;
+    rc = finish_record(ctx);
+    if (rc) return rc;
+    int nbits = 0;
+    while ((1ll << nbits) < global_n) ++nbits;
+    const int e2 = scale_exp(global_sum_w);
+    ctx->fx_shift = FX_AVG_BITS + nbits - e2;
+    ctx->fx_q = ldexp(1.0, -ctx->fx_shift);
+    ctx->cell_shift = 60 - e2;
+    ctx->fx_atomic = 1;
+    ctx->shard = true;
+    return M2M_OK;
+}
+
+int m2m_shard_scatter(m2m_ctx *ctx, int32_t push, int32_t *prior_due, int64_t *totals, double *stats, double *range) {
+    if (!ctx || !totals || !stats) return set_err(ctx, M2M_ERR_ARG, "NULL buffer");
+    if (!ctx->shard) return set_err(ctx, M2M_ERR_STATE, "call m2m_shard_init first");
+    const bool moving = ctx->prior.kind != M2M_PRIOR_FLAT;
+    const bool due = push && moving && ((ctx->t + 1) % ctx->prior.period == 0);
+    if (due && !range) return set_err(ctx, M2M_ERR_ARG, "a prior recompute is due: range buffer needed");
+    int rc = finish_record(ctx);
+    if (rc) return rc;
+    const int fl = F_SCAT | F_STATS | (push ? F_PUSH : 0) | (ctx->pending ? F_UPD : 0) | (due ? F_MINMAX : 0);
+    int g = 0;
+    rc = launch_pass(ctx, fl, &g);
+    if (rc) return rc;
+    {
+        LaunchTimer lt(ctx, M2M_TK_OTHER);
+        const double *ss = ctx->d_stat_slots + (size_t)2 * ctx->slot_cap * (ctx->stat_par ^ 1);
+        if (ctx->prec == M2M_FP32C)
+            k_shard_pack<float><<<1, 256, 0, ctx->st>>>(ctx->d_y_acc, (long long *)totals, ctx->nobs, ss, g, stats, ctx->d_mm_slots,
+                                                        due ? ctx->mm_nblocks : 0, due ? range : nullptr);
+        else
+            k_shard_pack<double><<<1, 256, 0, ctx->st>>>(ctx->d_y_acc, (long long *)totals, ctx->nobs, ss, g, stats, ctx->d_mm_slots,
+                                                         due ? ctx->mm_nblocks : 0, due ? range : nullptr);
+        CU(cudaGetLastError());
+    }
+    ctx->pending = false;                // applied by this pass, if it was
+    ctx->shard_push = push != 0;
+    ctx->shard_due = due;
+    if (prior_due) *prior_due = due ? 1 : 0;
+    return M2M_OK;
+}
+
+int m2m_shard_residual(m2m_ctx *ctx, int64_t *totals, const double *stats) {
+    if (!ctx || !totals || !stats) return set_err(ctx, M2M_ERR_ARG, "NULL buffer");
+    if (!ctx->shard) return set_err(ctx, M2M_ERR_STATE, "call m2m_shard_init first");
+    ResArgs r;
+    memset(&r, 0, sizeof r);
+    const bool push = ctx->shard_push;
+    const long long t1 = push ? ctx->t + 1 : ctx->t;
+    r.nobs = ctx->nobs; r.y_acc = (unsigned long long *)totals; r.fx_atomic = 1;
+    r.fixed = ctx->prec == M2M_FP32C; r.q = ctx->fx_q;
+    r.Y = ctx->d_Y; r.inv_sigma = ctx->d_isig; r.Dt = ctx->d_Dt; r.y = ctx->d_y; r.Delta = ctx->d_Delta;
+    r.coef_d = ctx->d_coef_d; r.coef_r = ctx->d_coef_r; r.r_float = ctx->prec == M2M_FP32C;
+    r.mode = push ? 1 : 2; r.alpha = ctx->par.alpha; r.mu = ctx->par.mu;
+    r.stat_slots = stats; r.stat_nblk = 1; r.tail = 1;
+    r.chi_slots = ctx->d_chi_slots; r.ticket = ctx->d_ticket;
+    r.ring = ctx->d_ring; r.last = ctx->d_last; r.rec_step = t1; r.write_ring = push ? 1 : 0;
+    r.err = ctx->d_err;
+    const int nb = (ctx->nobs + RES_NT_FX - 1) / RES_NT_FX;
+    void *args[] = {&r};
+    {
+        LaunchTimer lt(ctx, M2M_TK_RESIDUAL);
+        CU(launch_dependent((void *)k_residual, dim3(nb), dim3(RES_NT_FX), args, 0, ctx->st));
+    }
+    ctx->rec_chi_nblk = nb;
+    if (push) ctx->t = t1;
+    ctx->pending = push;                 // the update of this step goes into the next pass
+    return M2M_OK;
+}
+
+int m2m_shard_prior_cells(m2m_ctx *ctx, const double *range, int64_t *cell_sums, int32_t *cell_counts) {
+    if (!ctx || !range || !cell_sums || !cell_counts) return set_err(ctx, M2M_ERR_ARG, "NULL buffer");
+    if (!ctx->shard || !ctx->shard_due) return set_err(ctx, M2M_ERR_STATE, "no prior recompute is due");
+    {
+        LaunchTimer lt(ctx, M2M_TK_PRIOR);
+        if (ctx->prec == M2M_FP32C) k_shard_range<float><<<1, 1, 0, ctx->st>>>(range, ctx->d_mm_slots);
+        else k_shard_range<double><<<1, 1, 0, ctx->st>>>(range, ctx->d_mm_slots);
+        CU(cudaGetLastError());
+    }
+    ctx->mm_nblocks = 1;
+    CU(cudaMemsetAsync(ctx->d_cell_acc, 0, (size_t)ctx->ncells * 8, ctx->st));
+    CU(cudaMemsetAsync(ctx->d_cell_cnt, 0, (size_t)ctx->ncells * 4, ctx->st));
+    int rc = launch_pass(ctx, F_CELLS | (ctx->pending ? F_UPD : 0));
+    if (rc) return rc;
+    ctx->pending = false;
+    CU(cudaMemcpyAsync(cell_sums, ctx->d_cell_acc, (size_t)ctx->ncells * 8, cudaMemcpyDeviceToDevice, ctx->st));
+    CU(cudaMemcpyAsync(cell_counts, ctx->d_cell_cnt, (size_t)ctx->ncells * 4, cudaMemcpyDeviceToDevice, ctx->st));
+    return M2M_OK;
+}
+
+int m2m_shard_prior_finish(m2m_ctx *ctx, const int64_t *cell_sums, const int32_t *cell_counts) {
+    if (!ctx || !cell_sums || !cell_counts) return set_err(ctx, M2M_ERR_ARG, "NULL buffer");
+    if (!ctx->shard || !ctx->shard_due) return set_err(ctx, M2M_ERR_STATE, "no prior recompute is due");
+    const int nb = (ctx->ncells + 255) / 256;
+    {
+        LaunchTimer lt(ctx, M2M_TK_PRIOR);
+        k_prior_mean<<<nb, 256, 0, ctx->st>>>(cell_sums, (const unsigned *)cell_counts, ctx->ncells,
+                                              ctx->prec == M2M_FP32C, ldexp(1.0, -ctx->cell_shift), ctx->d_cell_mean);
+        CU(cudaGetLastError());
+    }
+    int g = ctx->nsm * 8;
+    const long long need = (ctx->n + 255) / 256;
+    if (g > need) g = (int)need;
+    {
+        LaunchTimer lt(ctx, M2M_TK_PRIOR);
+        k_prior_gather<<<g, 256, 0, ctx->st>>>(ctx->d_cell_ids, ctx->d_cell_mean, ctx->what, ctx->d_lnwhat, ctx->n);
+        CU(cudaGetLastError());
+    }
+    ctx->shard_due = false;
+    return M2M_OK;
 }
 
 int m2m_philox4x32_10(int64_t n, const uint32_t *counters, const uint32_t *keys, uint32_t *out) {

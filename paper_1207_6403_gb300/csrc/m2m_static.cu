@@ -235,7 +235,9 @@ int m2m_observe_static(int64_t n, const void *x, const void *y, const void *z, c
     // the scatter pass of m2m_observe: FP32C, 1024 threads, no cell cache;
     // the fixed-point scale of a context: 2^-25 of the average weight
     // weight_scale / n (both rounded up to powers of two)
-    const int wexp = (int)ceil(log2(weight_scale));
+    // (sums within 1e-12 above a power of two taken as that power, as for
+    // contexts)
+    const int wexp = (int)ceil(log2(weight_scale * (1.0 - 1e-12)));
     int nbits = 0;
     while ((1ll << nbits) < n) ++nbits;
     a.x = (void *)x; a.y = (void *)y; a.z = (void *)z; a.vx = (void *)vx; a.vy = (void *)vy; a.vz = (void *)vz;

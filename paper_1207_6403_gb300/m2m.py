@@ -126,6 +126,11 @@ def library():
         "m2m_observe_static": (c_int32, [c_int64, P, P, P, P, P, P, P, POINTER(m2m_obs_desc), c_int32,
                                          c_double, c_double, c_double, P, P]),
         "m2m_philox4x32_10": (c_int32, [c_int64, P, P, P]),
+        "m2m_shard_init": (c_int32, [P, c_int64, c_double]),
+        "m2m_shard_scatter": (c_int32, [P, c_int32, POINTER(c_int32), P, P, P]),
+        "m2m_shard_residual": (c_int32, [P, P, P]),
+        "m2m_shard_prior_cells": (c_int32, [P, P, P, P]),
+        "m2m_shard_prior_finish": (c_int32, [P, P, P]),
         "m2m_batch_init": (c_int32, [POINTER(P), c_int32, c_int32, POINTER(m2m_model_desc),
                                      POINTER(m2m_params), P]),
         "m2m_batch_step": (c_int32, [P, c_int64]),
@@ -260,6 +265,29 @@ class Context:
 
     def m2m_finish_update(self):
         _check(library().m2m_finish_update(self.ptr), self.ptr)
+
+    # -- particle shards: the exchange buffers are device tensors (int64
+    # totals, float64 stats and range, int64 cell sums, int32 cell counts)
+    def m2m_shard_init(self, global_n, global_sum_w):
+        _check(library().m2m_shard_init(self.ptr, int(global_n), float(global_sum_w)), self.ptr)
+
+    def m2m_shard_scatter(self, push, totals, stats, rng):
+        due = c_int32(0)
+        _check(library().m2m_shard_scatter(self.ptr, 1 if push else 0, byref(due), c_void_p(totals.data_ptr()),
+                                           c_void_p(stats.data_ptr()), c_void_p(rng.data_ptr())), self.ptr)
+        return bool(due.value)
+
+    def m2m_shard_residual(self, totals, stats):
+        _check(library().m2m_shard_residual(self.ptr, c_void_p(totals.data_ptr()), c_void_p(stats.data_ptr())),
+               self.ptr)
+
+    def m2m_shard_prior_cells(self, rng, cell_sums, cell_counts):
+        _check(library().m2m_shard_prior_cells(self.ptr, c_void_p(rng.data_ptr()), c_void_p(cell_sums.data_ptr()),
+                                               c_void_p(cell_counts.data_ptr())), self.ptr)
+
+    def m2m_shard_prior_finish(self, cell_sums, cell_counts):
+        _check(library().m2m_shard_prior_finish(self.ptr, c_void_p(cell_sums.data_ptr()),
+                                                c_void_p(cell_counts.data_ptr())), self.ptr)
 
     def m2m_set_persistent(self, enable=True):
         _check(library().m2m_set_persistent(self.ptr, 1 if enable else 0), self.ptr)
