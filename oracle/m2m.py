@@ -39,6 +39,7 @@ import numpy as np
 from . import gh as _gh
 from . import philox as _philox
 from . import sh as _sh
+from . import sh_full as _shf
 from .potentials import acceleration as _analytic_acceleration
 from .potentials import potential as _analytic_potential
 
@@ -52,16 +53,24 @@ def state_dtype(precision):
 # spherical-harmonic component (kind 'sh', params (K, rmin, rmax, period),
 # last in the list) whose tables are part of the state
 # --------------------------------------------------------------------------
+SH_KINDS = ("sh", "sh_tri")
+
+
 def _split(comps):
-    an = [c for c in comps if c.kind != "sh"]
-    sh = [c for c in comps if c.kind == "sh"]
+    an = [c for c in comps if c.kind not in SH_KINDS]
+    sh = [c for c in comps if c.kind in SH_KINDS]
     return an, (sh[0] if sh else None)
 
 
 def sh_tables(x, y, z, w, comp):
-    """(F, D, nodes) of the expansion of the weighted particles."""
+    """(F, D, nodes) of the expansion of the weighted particles: the
+    axisymmetric even-l expansion (kind 'sh', :mod:`oracle.sh`) or the
+    triaxial one (kind 'sh_tri': even l, even m >= 0, l <= 8,
+    :mod:`oracle.sh_full`)."""
     K, rmin, rmax = int(comp.params[0]), comp.params[1], comp.params[2]
     rn = _sh.nodes(rmin, rmax, K)
+    if comp.kind == "sh_tri":
+        return _shf.tri_tables(x, y, z, w, rn)
     A, B = _sh.coefficients(x, y, z, w, rn)
     F, D = _sh.tables(A, B, rn)
     return F, D, rn
@@ -73,7 +82,10 @@ def acceleration(x, y, z, comps, sh=None):
     ax, ay, az = _analytic_acceleration(x, y, z, _split(comps)[0])
     if sh is not None:
         T = x.dtype.type
-        bx, by, bz = _sh.acceleration(x, y, z, *sh)
+        if _split(comps)[1].kind == "sh_tri":
+            bx, by, bz = _shf.tri_acceleration(x, y, z, *sh)
+        else:
+            bx, by, bz = _sh.acceleration(x, y, z, *sh)
         ax, ay, az = ax + bx.astype(T), ay + by.astype(T), az + bz.astype(T)
     return ax, ay, az
 
@@ -81,7 +93,10 @@ def acceleration(x, y, z, comps, sh=None):
 def potential(x, y, z, comps, sh=None):
     phi = _analytic_potential(x, y, z, _split(comps)[0])
     if sh is not None:
-        phi = phi + _sh.potential(x, y, z, *sh).astype(x.dtype)
+        if _split(comps)[1].kind == "sh_tri":
+            phi = phi + _shf.tri_potential(x, y, z, *sh).astype(x.dtype)
+        else:
+            phi = phi + _sh.potential(x, y, z, *sh).astype(x.dtype)
     return phi
 
 
@@ -311,6 +326,11 @@ def prior_cells(x, y, z, vx, vy, vz, prior, comps, sh=None):
     Computed in the state precision, in this order:
       v2 = (vx*vx + vy*vy) + vz*vz;  E = 0.5*v2 + Phi(x)
       'e_lz': Lz = x*vy - y*vx; cells on [min E, max E] x [-max|Lz|, max|Lz|]
+      'e_l2': L = x cross v, L2 = (Lx*Lx + Ly*Ly) + Lz*Lz; cells on
+              [min E, max E] x [0, max L2] (for potentials without a
+              symmetry axis, where L_z is not conserved: E is, and L^2 is
+              approximately conserved while the potential is nearly round;
+              Section 2.1's cells of approximately conserved quantities)
       'e_lc': L = x cross v, L2 = (Lx*Lx + Ly*Ly) + Lz*Lz; for the Hernquist
               (GM, a) circular orbit of energy E (E < 0):
                 ed = E*k (k = a/GM), sq = sqrt(1 - 8*ed),
@@ -330,6 +350,15 @@ def prior_cells(x, y, z, vx, vy, vz, prior, comps, sh=None):
             Lm = np.float64(np.abs(Lz).max())
             iE = _count_edges_le(E, lo, hi, prior.nE)
             iL = _count_edges_le(Lz, -Lm, Lm, prior.nL)
+            return iE * prior.nL + iL
+        if prior.kind == "e_l2":
+            Lx = y * vz - z * vy
+            Ly = z * vx - x * vz
+            Lz = x * vy - y * vx
+            L2 = (Lx * Lx + Ly * Ly) + Lz * Lz
+            lo, hi = np.float64(E.min()), np.float64(E.max())
+            iE = _count_edges_le(E, lo, hi, prior.nE)
+            iL = _count_edges_le(L2, 0.0, np.float64(L2.max()), prior.nL)
             return iE * prior.nL + iL
         if prior.kind == "e_lc":
             GM, a = prior.hernquist

@@ -46,6 +46,20 @@ def index(lmax):
     return [(l, m) for l in range(lmax + 1) for m in range(-l, l + 1)]
 
 
+def triaxial_terms(lmax):
+    """(l, m) of the harmonics a triaxial (mirror-symmetric about the three
+    coordinate planes) set of particles can have: even l, even m >= 0 (the
+    cosine harmonics); the others vanish (see the pins).  At lmax = 8: 15
+    terms."""
+    return [(l, m) for l in range(0, lmax + 1, 2) for m in range(0, l + 1, 2)]
+
+
+def _rows(lmax, terms):
+    """Rows of :func:`real_harmonics` for the given terms (all by default)."""
+    idx = index(lmax)
+    return list(range(len(idx))) if terms is None else [idx.index(t) for t in terms]
+
+
 def real_harmonics(lmax, x, y, z):
     """Y_lm at the directions of (x, y, z), shape ((lmax+1)^2, n) in the
     order of :func:`index`; the direction of the origin is taken as +z."""
@@ -102,8 +116,9 @@ def potential(px, py, pz, x, y, z, w, lmax):
 # sides by r^2 in the state precision against float64 r_k^2, F and D linear
 # in r between nodes, the exterior and interior laws outside them.
 # --------------------------------------------------------------------------
-def coefficients_nodes(x, y, z, w, rn, lmax):
-    """A_lm(r_k), B_lm(r_k), shape ((lmax+1)^2, K)."""
+def coefficients_nodes(x, y, z, w, rn, lmax, terms=None):
+    """A_lm(r_k), B_lm(r_k), shape ((lmax+1)^2, K) (one row per term when
+    `terms` is given)."""
     from . import sh as _sh
     K = len(rn)
     j = _sh.node_side(x, y, z, rn)
@@ -113,10 +128,10 @@ def coefficients_nodes(x, y, z, w, rn, lmax):
     j = j[keep]
     r = np.sqrt(xd * xd + yd * yd + zd * zd)
     rs = np.where(r > 0, r, 1.0)
-    Y = real_harmonics(lmax, xd, yd, zd)
+    Y = real_harmonics(lmax, xd, yd, zd)[_rows(lmax, terms)]
     A = np.zeros((Y.shape[0], K))
     B = np.zeros((Y.shape[0], K))
-    for n, (l, m) in enumerate(index(lmax)):
+    for n, (l, m) in enumerate(terms or index(lmax)):
         ta = np.bincount(j, weights=w * Y[n] * r ** l, minlength=K)
         tb = np.bincount(j, weights=np.where(j > 0, w * Y[n] * rs ** (-(l + 1)), 0.0), minlength=K)
         A[n] = np.cumsum(ta)
@@ -124,18 +139,18 @@ def coefficients_nodes(x, y, z, w, rn, lmax):
     return A, B
 
 
-def tables_nodes(A, B, rn, lmax):
+def tables_nodes(A, B, rn, lmax, terms=None):
     """F_lm(k), D_lm(k) with the 4 pi/(2l+1) of the addition theorem."""
     F = np.zeros_like(A)
     D = np.zeros_like(A)
-    for n, (l, m) in enumerate(index(lmax)):
+    for n, (l, m) in enumerate(terms or index(lmax)):
         c = 4 * math.pi / (2 * l + 1)
         F[n] = c * (A[n] / rn ** (l + 1) + B[n] * rn ** l)
         D[n] = c * (-(l + 1) * A[n] / rn ** (l + 2) + (l * B[n] * rn ** (l - 1) if l > 0 else 0.0))
     return F, D
 
 
-def radial_nodes(F, D, rn, r, lmax):
+def radial_nodes(F, D, rn, r, lmax, terms=None):
     """F_lm(r), D_lm(r): linear between nodes; beyond r_(K-1)
     F(K-1) (r_(K-1)/r)^(l+1); inside r_0 F(0) (r/r_0)^l and
     D(0) (r/r_0)^max(l-1, 1)."""
@@ -146,7 +161,7 @@ def radial_nodes(F, D, rn, r, lmax):
     t = (rc - rn[k]) / (rn[k + 1] - rn[k])
     Fr = F[:, k] * (1 - t) + F[:, k + 1] * t
     Dr = D[:, k] * (1 - t) + D[:, k + 1] * t
-    ls = np.array([l for l, _ in index(lmax)], np.float64)[:, None]
+    ls = np.array([l for l, _ in (terms or index(lmax))], np.float64)[:, None]
     out = r >= rn[-1]
     ro = np.where(out, r, rn[-1])
     Fo = F[:, -1:] * (rn[-1] / ro) ** (ls + 1)
@@ -159,12 +174,12 @@ def radial_nodes(F, D, rn, r, lmax):
     return Fr, Dr
 
 
-def potential_nodes(px, py, pz, F, D, rn, lmax):
+def potential_nodes(px, py, pz, F, D, rn, lmax, terms=None):
     """Phi of the tabulated expansion at the points (px, py, pz)."""
     px, py, pz = (np.atleast_1d(np.asarray(a, dtype=np.float64)) for a in (px, py, pz))
     r = np.sqrt(px * px + py * py + pz * pz)
-    Y = real_harmonics(lmax, px, py, pz)
-    return -np.sum(Y * radial_nodes(F, D, rn, r, lmax)[0], axis=0)
+    Y = real_harmonics(lmax, px, py, pz)[_rows(lmax, terms)]
+    return -np.sum(Y * radial_nodes(F, D, rn, r, lmax, terms)[0], axis=0)
 
 
 def _q_table(lmax, mu):
@@ -186,7 +201,7 @@ def _q_table(lmax, mu):
     return lambda l, m: Q[(l, m)] if m <= l else zero
 
 
-def acceleration_nodes(px, py, pz, F, D, rn, lmax):
+def acceleration_nodes(px, py, pz, F, D, rn, lmax, terms=None):
     """-grad Phi of the tabulated expansion at (px, py, pz), shape (3, n).
 
     Written with terms that stay regular on the z axis:
@@ -202,11 +217,11 @@ def acceleration_nodes(px, py, pz, F, D, rn, lmax):
     n = np.stack([px, py, pz]) / rs
     mu = pz / rs
     Q = _q_table(lmax + 1, mu)
-    Fr, Dr = radial_nodes(F, D, rn, r, lmax)
+    Fr, Dr = radial_nodes(F, D, rn, r, lmax, terms)
     u = px + 1j * py
     g = np.zeros((3,) + px.shape)
     ez = np.array([0.0, 0.0, 1.0])[:, None]
-    for k, (l, m) in enumerate(index(lmax)):
+    for k, (l, m) in enumerate(terms or index(lmax)):
         am = abs(m)
         N = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
         c = N if m == 0 else math.sqrt(2.0) * N
@@ -224,3 +239,28 @@ def acceleration_nodes(px, py, pz, F, D, rn, lmax):
         gY = c / rm * (q1 * C * (ez - mu * n) / rs + q0 * dC - am * q0 * C * n / rs)
         g += -(Dr[k] * Y * n + Fr[k] * gY)
     return np.where(r > 0, -g, 0.0)
+
+
+# --------------------------------------------------------------------------
+# The triaxial expansion of the step (potential kind 'sh_tri', parameters
+# (K, rmin, rmax, period)): the terms of :func:`triaxial_terms` at lmax = 8
+# tabulated on the nodes of :func:`oracle.sh.nodes`, recomputed from the
+# particles every `period` steps like the axisymmetric expansion.
+# --------------------------------------------------------------------------
+LMAX_TRI = 8
+
+
+def tri_tables(x, y, z, w, rn):
+    """(F, D, rn) of the triaxial expansion of the weighted particles."""
+    terms = triaxial_terms(LMAX_TRI)
+    A, B = coefficients_nodes(x, y, z, w, rn, LMAX_TRI, terms)
+    F, D = tables_nodes(A, B, rn, LMAX_TRI, terms)
+    return F, D, rn
+
+
+def tri_acceleration(x, y, z, F, D, rn):
+    return acceleration_nodes(x, y, z, F, D, rn, LMAX_TRI, triaxial_terms(LMAX_TRI))
+
+
+def tri_potential(x, y, z, F, D, rn):
+    return potential_nodes(x, y, z, F, D, rn, LMAX_TRI, triaxial_terms(LMAX_TRI))

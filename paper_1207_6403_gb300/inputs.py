@@ -134,6 +134,9 @@ class PriorSpec:
                   on [min E, 0), unbound particles share one extra cell.
     kind 'e_lz' : the same on an nE x nL grid in (E, L_z), uniform on
                   [min E, max E] x [-max|L_z|, max|L_z|].
+    kind 'e_l2' : the same on an nE x nL grid in (E, L^2), uniform on
+                  [min E, max E] x [0, max L^2] (potentials without a
+                  symmetry axis).
     """
     kind: str = "flat"
     nE: int = 1
@@ -489,10 +492,22 @@ def error_model(Y, obs_sets, frac=0.02):
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
-WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons", "ifu-lut")
+WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons", "ifu-lut", "sh-tri")
 
 _DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000, "sh-selfcons": 8_000_000,
-              "flat-log": 4_000_000, "ifu-lut": 4_000_000}
+              "flat-log": 4_000_000, "ifu-lut": 4_000_000, "sh-tri": 4_000_000}
+
+# axis ratios of the triaxial workload (x : y : z)
+TRI_AXES = (1.0, 0.8, 0.6)
+
+
+def triaxial_hernquist(n, seed, axes=TRI_AXES):
+    """A triaxial Hernquist-like particle set: an isotropic Hernquist
+    realisation with positions and velocities stretched along the axes by
+    `axes` (a synthetic triaxial mass distribution; not an equilibrium)."""
+    pos, vel = hernquist_isotropic(n, seed)
+    k = np.asarray(axes, np.float64)[:, None]
+    return pos * k, vel * k
 
 
 # --------------------------------------------------------------------------
@@ -646,6 +661,22 @@ def make_problem(name, n=None, precision=None, seed_model=None,
         prior = PriorSpec("e_lz", nE=128, nL=64, period=25)
         inc = math.radians(60.0)
         sin_i, cos_i = math.sin(inc), math.cos(inc)
+        prec = precision or "fp32c"
+        steps = nsteps or 5000
+    elif name == "sh-tri":
+        sm, st = seed_model or 12, seed_target or 13
+        pos, vel = triaxial_hernquist(n, sm)
+        tp = tv = None
+        if with_target:
+            tp, tv = triaxial_hernquist(n, st)
+        e = log_shell_edges(60, 0.05, 20.0)
+        rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+        S = np.maximum(np.sqrt(hernquist_sigma_iso(1.0, 1.0)(rmid)), 0.05)
+        obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+               ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
+        pot = [PotentialComponent("sh_tri", (256, 1e-3, 100.0, 50))]
+        prior = PriorSpec("e_l2", 64, 32, 25)
+        sin_i, cos_i = 0.0, 1.0
         prec = precision or "fp32c"
         steps = nsteps or 5000
     elif name == "sh-selfcons":

@@ -850,3 +850,32 @@ def test_parallel_oracle_equals_the_serial_oracle():
     for a, b in zip(recs, st.history):
         assert a["chi2"] == pytest.approx(b["chi2"], rel=1e-12)
         assert a["sum_w"] == pytest.approx(b["sum_w"], rel=1e-12)
+
+
+def test_e_l2_prior_cells_against_a_brute_force_loop():
+    """(E, L^2) cells (triaxial priors): each particle's E and L^2 formed
+    one at a time in float32 in the stated order, its cell found by scanning
+    the float64 edges of the [min E, max E] x [0, max L^2] grid; equal
+    weights give w_hat = w exactly."""
+    P = I.make_problem("sh-tri", n=3000, precision="fp32c")
+    P = P.with_targets(O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos))
+    P.prior = I.PriorSpec("e_l2", 8, 5, 25)
+    st = O.init(P, "fp32c")
+    s = (st.x, st.y, st.z, st.vx, st.vy, st.vz)
+    cells = O.prior_cells(*s, P.prior, P.potential, st.sh)
+    T = np.float32
+    phi = O.potential(st.x, st.y, st.z, P.potential, st.sh)
+    E = np.empty(P.n, T)
+    L2 = np.empty(P.n, T)
+    for i in range(P.n):
+        x, y, z, vx, vy, vz = (T(a[i]) for a in s)
+        E[i] = T(0.5) * ((vx * vx + vy * vy) + vz * vz) + phi[i]
+        lx, ly, lz = y * vz - z * vy, z * vx - x * vz, x * vy - y * vx
+        L2[i] = (lx * lx + ly * ly) + lz * lz
+    lo, hi, lm = float(E.min()), float(E.max()), float(L2.max())
+    for i in range(0, P.n, 7):
+        iE = sum(1 for k in range(1, 8) if lo + k * ((hi - lo) / 8) <= float(E[i]))
+        iL = sum(1 for k in range(1, 5) if k * (lm / 5) <= float(L2[i]))
+        assert cells[i] == iE * 5 + iL, i
+    w = np.full(P.n, 2.0 ** -20)
+    assert np.array_equal(O.prior_means(w, cells, P.prior.ncells), w)

@@ -206,3 +206,48 @@ def test_tabulated_force_tangential_part_is_minus_the_angular_gradient():
             dphi = (F.potential_nodes(*pp[:, None], Ft, Dt, rn, 6)[0]
                     - F.potential_nodes(*pm[:, None], Ft, Dt, rn, 6)[0]) / (2 * h * np.linalg.norm(p))
             assert -a[:, j] @ t == pytest.approx(dphi, rel=1e-6, abs=1e-9 * np.abs(a).max())
+
+
+def _mirrored(n=300, seed=13):
+    g = np.random.default_rng(seed)
+    x, y, z = np.abs(g.normal(size=(3, n))) * np.array([[1.0], [0.8], [0.6]])
+    sx, sy, sz = np.meshgrid([1, -1], [1, -1], [1, -1], indexing="ij")
+    X = np.concatenate([a * x for a in sx.ravel()])
+    Y = np.concatenate([a * y for a in sy.ravel()])
+    Z = np.concatenate([a * z for a in sz.ravel()])
+    w = np.tile(g.uniform(0.5, 1.5, n) / n, 8)
+    return X, Y, Z, w
+
+
+def test_triaxial_expansion_is_the_full_expansion_of_a_triaxial_set():
+    """For particles mirrored in the three coordinate planes the 15 terms of
+    the triaxial expansion (even l, even m >= 0, l <= 8) carry the whole
+    lmax = 8 expansion: their node tables are the full tables' rows, every
+    other row vanishes, and the tabulated potential and force of the subset
+    are those of all 81 terms (at nodes, between them and outside them)."""
+    from oracle import sh as SH0
+    X, Y, Z, w = _mirrored()
+    rn = SH0.nodes(0.05, 5.0, 48)
+    Af, Bf = F.coefficients_nodes(X, Y, Z, w, rn, 8)
+    Ff, Df = F.tables_nodes(Af, Bf, rn, 8)
+    Ft, Dt, _ = F.tri_tables(X, Y, Z, w, rn)
+    terms = F.triaxial_terms(8)
+    assert len(terms) == 15
+    idx = F.index(8)
+    scale = np.abs(Ff).max()
+    for k, t in enumerate(idx):
+        if t in terms:
+            j = terms.index(t)
+            assert np.abs(Ft[j] - Ff[k]).max() <= 1e-12 * scale and np.abs(Dt[j] - Df[k]).max() <= 1e-10 * scale
+        else:
+            assert np.abs(Ff[k]).max() <= 1e-12 * scale, t
+    g = np.random.default_rng(3)
+    p = g.normal(size=(3, 200)) * np.array([[2.0], [1.5], [1.0]])
+    p[:, :10] *= 5.0                       # beyond the last node
+    p[:, 10:20] *= 0.005                   # inside the first
+    phi_f = F.potential_nodes(*p, Ff, Df, rn, 8)
+    phi_t = F.tri_potential(*p, Ft, Dt, rn)
+    np.testing.assert_allclose(phi_t, phi_f, rtol=1e-11, atol=1e-12 * np.abs(phi_f).max())
+    a_f = F.acceleration_nodes(*p, Ff, Df, rn, 8)
+    a_t = F.tri_acceleration(*p, Ft, Dt, rn)
+    np.testing.assert_allclose(a_t, a_f, rtol=1e-10, atol=1e-11 * np.abs(a_f).max())
