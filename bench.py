@@ -9,7 +9,7 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|scan|sh|ifu-lut|ifu-lut-seeing|recovery]
+                  [--workload flat-log|batched|scan|sh|sh-tri|ifu-lut|ifu-lut-seeing|recovery]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
@@ -19,6 +19,9 @@ particles each) and gathers every model's record (the potential scan).
 --workload sh times the self-consistent disc + bulge (N = 8,000,000) in the
 spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
 recomputed every 50 steps).
+--workload sh-tri times a triaxial model (N = 4,000,000) in the triaxial
+expansion of its own particles (even l <= 8, even m >= 0: 15 terms, 256
+nodes, recomputed every 50 steps) with (E, L^2) moving priors.
 --workload ifu-lut times the flat-log galaxy observed through 300 Voronoi
 bins and a long slit (apertures given by sky-pixel lookup tables);
 --workload ifu-lut-seeing the same through a Gaussian PSF.
@@ -569,6 +572,15 @@ SINGLE = {
         describe="sh-selfcons: N={n:,} Miyamoto-Nagai disc (a=1, b=0.2) + Hernquist bulge (a=0.3), 1:3, in "
                  "the even-l <= 8 multipole expansion of its own weighted particles on 256 log nodes in "
                  "[1e-3, 100], recomputed every 50 steps; 100 shells + 60 annuli x h0..h4, flat priors, dt=0.01"),
+    "sh-tri": dict(
+        problem="sh-tri", n=4_000_000, seeds=(12, 13), stride=64,
+        metric="M2M particle-steps/s, self-consistent triaxial expansion (N=4M)",
+        dtype="f32 (FP32-compensated; f64 weights, exact fixed-point expansion sums)",
+        kernel="k_pass (step pass: update + push in the triaxial expansion + scatter)",
+        describe="sh-tri: N={n:,} triaxial Hernquist-like particles (a=1, axes 1:0.8:0.6) in the even-l, "
+                 "even-m >= 0, l <= 8 expansion (15 terms) of its own weighted particles on 256 log nodes in "
+                 "[1e-3, 100], recomputed every 50 steps; 100 shells + 60 annuli x h0..h4, (E, L^2) 64x32 "
+                 "moving priors every 25 steps, dt=0.01"),
     "ifu-lut": dict(
         problem="ifu-lut", n=4_000_000, seeds=(5, 6), stride=8,
         metric="M2M particle-steps/s, IFU Voronoi bins + long slit by aperture lookup tables (N=4M)",
@@ -710,8 +722,8 @@ def main():
     ap.add_argument("--n", "--particles", dest="n", type=int, default=N_DEFAULT,
                     help="particles per GPU (--particles also passes through torchrun)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "ifu-lut",
-                                                               "ifu-lut-seeing", "recovery"])
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "sh-tri",
+                                                               "ifu-lut", "ifu-lut-seeing", "recovery"])
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()

@@ -96,13 +96,28 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
  *           (x_{t+1}, w_{t+1}) after the update of every step t+1 that is a
  *           multiple of `period` (integer >= 1), at m2m_init and by
  *           m2m_potential.  At most one SH component, listed last; added
- *           after the analytic ones.  Errors: M2M_ERR_ARG for bad p. */
+ *           after the analytic ones.  Errors: M2M_ERR_ARG for bad p.
+ *   SH_TRI  p = {K, rmin, rmax, period}: the triaxial generalisation of SH
+ *           (Section 2's self-consistent potential for models without a
+ *           symmetry axis): the real harmonics of even l <= 8 and even
+ *           m >= 0 (the terms a set mirror-symmetric about the three
+ *           coordinate planes has), with n = x/r, mu = n_z, u = n_x + i n_y
+ *             Y_lm = c_lm Q_l^m(mu) Re u^m,  Q_l^m = d^m P_l/dmu^m,
+ *             c_l0 = N_l0, c_lm = sqrt(2) N_lm,
+ *             N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+ *             Phi = -sum_lm Y_lm F_lm(r),
+ *             F_lm(r) = 4 pi/(2l+1) [A_lm(r)/r^(l+1) + B_lm(r) r^l],
+ *           A_lm, B_lm the sums of w_i Y_lm(x_i) r_i^l and w_i Y_lm(x_i)
+ *           r_i^-(l+1) inside / outside r; nodes, interpolation, side sums,
+ *           schedule and placement as for SH. */
 #define M2M_MAX_POT 4
 #define M2M_POT_HERNQUIST 1
 #define M2M_POT_NFW       2
 #define M2M_POT_LOG       3
 #define M2M_POT_SH        4
-#define M2M_SH_ROW        21   /* values per node in m2m_get_sh_table */
+#define M2M_POT_SH_TRI    5
+#define M2M_SH_ROW        21   /* values per node in m2m_get_sh_table (SH) */
+#define M2M_TRI_ROW       61   /* values per node in m2m_get_sh_table (SH_TRI) */
 typedef struct {
     int32_t kind;
     int32_t reserved;
@@ -171,10 +186,15 @@ typedef struct {
  *       E cells uniform on [min E, 0), unbound particles in one extra cell.
  * E_LZ: the same on an nE x nL grid in (E, L_z) uniform on
  *       [min E, max E] x [-max|L_z|, max|L_z|].
+ * E_L2: the same on an nE x nL grid in (E, L^2) uniform on
+ *       [min E, max E] x [0, max L^2], L^2 = (Lx*Lx + Ly*Ly) + Lz*Lz: cells
+ *       of integrals that hold (E) or nearly hold (L^2) where the potential
+ *       has no symmetry axis (triaxial models, where L_z is not conserved).
  * E = 1/2 v^2 + Phi(x) in the state precision. */
 #define M2M_PRIOR_FLAT 0
 #define M2M_PRIOR_E_LC 1
 #define M2M_PRIOR_E_LZ 2
+#define M2M_PRIOR_E_L2 3
 typedef struct {
     int32_t kind, nE, nL, period;
     double hernquist_GM, hernquist_a;
@@ -235,8 +255,11 @@ int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot);
 /* Copy the SH node table to host memory as doubles, K rows of M2M_SH_ROW:
  * F_l(r_k) for l = 0,2,4,6,8; the slopes of F_l to node k+1; D_l(r_k) =
  * dF_l/dr; the slopes of D_l; r_k (last row: zero slopes).  Phi =
- * -sum P_l F_l.  out must hold K * M2M_SH_ROW doubles.  Synchronises.
- * M2M_ERR_STATE if the potential has no SH component. */
+ * -sum P_l F_l.  out must hold K * M2M_SH_ROW doubles.  For SH_TRI: K rows
+ * of M2M_TRI_ROW, the same five blocks with the 15 terms (l, m) = (0,0),
+ * (2,0), (2,2), (4,0), .., (8,8) each (F_lm, slopes, D_lm, slopes, r_k);
+ * out must hold K * M2M_TRI_ROW doubles.  Synchronises.
+ * M2M_ERR_STATE if the potential has no SH or SH_TRI component. */
 int m2m_get_sh_table(m2m_ctx *ctx, double *out);
 
 /* Scatter + residual at the current state, no push and no weight change.

@@ -104,9 +104,10 @@ struct m2m_ctx {
     bool cache_valid;    // cell cache holds the cells of the current positions
     bool pipe;           // use the bulk-copy pipelined pass where it applies
     int fx_atomic;       // FP32C histogram flush: global integer atomics (1) or slots (0)
-    // self-consistent spherical-harmonic potential (kind M2M_POT_SH)
-    bool sh_on;
-    int sh_K, sh_period;
+    // self-consistent expansion potential (kind M2M_POT_SH, or M2M_POT_SH_TRI
+    // with sh_tri set): sh_row table values per radial node
+    bool sh_on, sh_tri;
+    int sh_K, sh_period, sh_row;
     double sh_rmin, sh_rmax;
     int sh_gmode;
     float sh_ga, sh_gb;
@@ -222,7 +223,7 @@ void guess_params(const double *e, int nb, int *mode, float *ga, float *gb) {
 
 size_t pass_smem(const m2m_ctx *c, int flags) {
     return pass_smem_bytes(c->prec == M2M_FP32C, c->layout, flags, c->nobs, c->edge_len, c->gh_len,
-                           c->sh_on ? SH_ROW * c->sh_K : 0, c->prior.nE, c->prior.nL, c->ncells,
+                           c->sh_on ? c->sh_row * c->sh_K : 0, c->prior.nE, c->prior.nL, c->ncells,
                            c->layout == 1 ? c->sets[1].pmap_len : 0);
 }
 
@@ -335,7 +336,7 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.pgma = c->prior.hernquist_GM * c->prior.hernquist_a;
     a.f_pk = (float)a.pk; a.f_pgma = (float)a.pgma;
     a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
-    a.sh_tab = c->sh_on ? c->d_sh_tab : nullptr; a.sh_K = c->sh_K;
+    a.sh_tab = c->sh_on ? c->d_sh_tab : nullptr; a.sh_K = c->sh_K; a.sh_row = c->sh_row;
     a.cell_cache = c->d_cell_cache;
     a.cache_read = (flags & F_UPD) && c->cache_valid && c->layout != 0;
     a.cache_write = (flags & F_SCAT) && c->layout != 0;
@@ -367,6 +368,7 @@ int potential_signature(const m2m_ctx *c) {
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_HERNQUIST) return PK_HERNQUIST;
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_LOG) return PK_LOG;
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH) return PK_SH;
+    if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH_TRI) return PK_SH_TRI;
     if (c->npot == 2 && c->pot[0].kind == M2M_POT_HERNQUIST && c->pot[1].kind == M2M_POT_NFW) return PK_HERNQUIST_NFW;
     return PK_ANY;
 }
@@ -628,7 +630,7 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         } else if (pot[k].kind == M2M_POT_NFW) {
             if (!(p[0] > 0 && p[1] > 0)) return set_err(ctx, M2M_ERR_ARG, "nfw needs rho_s>0, r_s>0");
             d.c[0] = 4.0 * M_PI * p[0] * p[1] * p[1] * p[1]; d.c[1] = p[1]; d.c[2] = 1.0 / p[1];
-        } else if (pot[k].kind == M2M_POT_SH) {
+        } else if (pot[k].kind == M2M_POT_SH || pot[k].kind == M2M_POT_SH_TRI) {
             const int K = (int)p[0];
             if (k != npot - 1) return set_err(ctx, M2M_ERR_ARG, "the spherical-harmonic component must be last");
             if (!((double)K == p[0] && K >= 4 && K <= SH_MAXK && p[1] > 0 && p[2] > p[1] && isfinite(p[2]) &&
@@ -646,7 +648,9 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         for (int j = 0; j < 6; ++j) tmp[k].cf[j] = (float)tmp[k].c[j];
     memcpy(ctx->pot, tmp, sizeof tmp);
     ctx->npot = npot;
-    ctx->sh_on = npot > 0 && pot[npot - 1].kind == M2M_POT_SH;
+    ctx->sh_tri = npot > 0 && pot[npot - 1].kind == M2M_POT_SH_TRI;
+    ctx->sh_on = npot > 0 && (pot[npot - 1].kind == M2M_POT_SH || ctx->sh_tri);
+    ctx->sh_row = ctx->sh_tri ? TRI_ROW : SH_ROW;
     if (ctx->sh_on) {
         const double *p = pot[npot - 1].p;
         ctx->sh_K = (int)p[0];
@@ -656,6 +660,10 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
     }
     return M2M_OK;
 }
+
+// Side sums of the expansion: 10 per node (A_l, B_l of 5 even l), 30 for
+// the triaxial one (A_lm, B_lm of its 15 terms).
+size_t sh_sums(const m2m_ctx *c) { return (size_t)(c->sh_tri ? 2 * TRI_NT : 10) * c->sh_K; }
 
 // Node tables of the expansion: r_k = rmin (rmax/rmin)^(k/(K-1)), r_(K-1) =
 // rmax, and r_k^2 (for R = float the smallest float >= the double square).
@@ -669,9 +677,9 @@ int sh_setup(m2m_ctx *ctx) {
     CU(cudaMalloc(&ctx->d_sh_e2, rs * K));
     CU(cudaMalloc(&ctx->d_sh_rn, rs * K));
     CU(cudaMalloc(&ctx->d_sh_irn, rs * K));
-    CU(cudaMalloc(&ctx->d_sh_tab, rs * SH_ROW * K));
+    CU(cudaMalloc(&ctx->d_sh_tab, rs * ctx->sh_row * K));
     CU(cudaMalloc((void **)&ctx->d_sh_rnd, 8 * (size_t)K));
-    CU(cudaMalloc((void **)&ctx->d_sh_sum, 80 * (size_t)K));
+    CU(cudaMalloc((void **)&ctx->d_sh_sum, sh_sums(ctx) * 8));
     std::vector<double> rn(K), e2(K), irn(K);
     const double ratio = ctx->sh_rmax / ctx->sh_rmin;
     for (int k = 0; k < K; ++k) rn[k] = ctx->sh_rmin * pow(ratio, (double)k / (double)(K - 1));
@@ -696,7 +704,7 @@ int sh_setup(m2m_ctx *ctx) {
 }
 
 size_t sh_coef_smem(const m2m_ctx *c) {
-    const size_t NS = 10 * (size_t)c->sh_K;
+    const size_t NS = sh_sums(c);
     return 8 * NS + (c->prec == M2M_FP32C ? 4 : 8) * 3 * (size_t)c->sh_K;
 }
 
@@ -704,7 +712,7 @@ size_t sh_coef_smem(const m2m_ctx *c) {
 // the node table the push reads.
 int sh_recompute(m2m_ctx *ctx) {
     const int K = ctx->sh_K;
-    CU(cudaMemsetAsync(ctx->d_sh_sum, 0, 80 * (size_t)K, ctx->st));
+    CU(cudaMemsetAsync(ctx->d_sh_sum, 0, 8 * sh_sums(ctx), ctx->st));
     ShArgs a;
     memset(&a, 0, sizeof a);
     a.x = ctx->x; a.y = ctx->y; a.z = ctx->z; a.w = ctx->w; a.n = ctx->n;
@@ -713,7 +721,8 @@ int sh_recompute(m2m_ctx *ctx) {
     a.sh = ctx->fx_shift + 6;
     a.sum = ctx->d_sh_sum; a.err = ctx->d_err;
     const bool f32 = ctx->prec == M2M_FP32C;
-    void *fn = f32 ? (void *)k_sh_coef<float> : (void *)k_sh_coef<double>;
+    void *fn = ctx->sh_tri ? (f32 ? (void *)k_tri_coef<float> : (void *)k_tri_coef<double>)
+                           : (f32 ? (void *)k_sh_coef<float> : (void *)k_sh_coef<double>);
     const size_t sm = sh_coef_smem(ctx);
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, sm));
@@ -726,8 +735,17 @@ int sh_recompute(m2m_ctx *ctx) {
         CU(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, sm, ctx->st));
     }
     const double q = ldexp(1.0, -a.sh);
-    const size_t tsm = 160 * (size_t)K;
-    {
+    const size_t tsm = ctx->sh_tri ? 8 * sh_sums(ctx) : 160 * (size_t)K;
+    if (ctx->sh_tri) {
+        LaunchTimer lt(ctx, M2M_TK_SH);
+        if (f32)
+            k_tri_tables<float><<<1, 512, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
+                                                          (float *)ctx->d_sh_tab, ctx->d_err);
+        else
+            k_tri_tables<double><<<1, 512, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
+                                                           (double *)ctx->d_sh_tab, ctx->d_err);
+        CU(cudaGetLastError());
+    } else {
         LaunchTimer lt(ctx, M2M_TK_SH);
         if (f32)
             k_sh_tables<float><<<1, 256, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
@@ -906,7 +924,8 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     // priors
     if (prior && prior->kind != M2M_PRIOR_FLAT) {
         ctx->prior = *prior;
-        if ((prior->kind != M2M_PRIOR_E_LC && prior->kind != M2M_PRIOR_E_LZ) || prior->nE < 1 ||
+        if ((prior->kind != M2M_PRIOR_E_LC && prior->kind != M2M_PRIOR_E_LZ && prior->kind != M2M_PRIOR_E_L2) ||
+            prior->nE < 1 ||
             prior->nL < 1 || prior->period < 1 ||
             (long long)prior->nE * prior->nL + 1 > MAXCELLS ||
             (prior->kind == M2M_PRIOR_E_LC && !(prior->hernquist_GM > 0 && prior->hernquist_a > 0))) {
@@ -1030,12 +1049,14 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64(), (void *)k_sh_coef<float>,
-                                (void *)k_sh_coef<double>, (void *)k_sh_tables<float>, (void *)k_sh_tables<double>};
+                                (void *)k_sh_coef<double>, (void *)k_sh_tables<float>, (void *)k_sh_tables<double>,
+                                (void *)k_tri_coef<float>, (void *)k_tri_coef<double>,
+                                (void *)k_tri_tables<float>, (void *)k_tri_tables<double>};
     for (int lay = 0; lay < 5; ++lay) {
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
-        for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW})
+        for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW, PK_SH_TRI})
                 for (int fl : {F_STEADY, F_STEADY | F_MINMAX, F_PUSH | F_SCAT | F_STATS,
                                F_PUSH | F_SCAT | F_STATS | F_MINMAX, F_CELLS | F_UPD})
                     if (void *f = pass_kernel_f32_compiled(fl, lay, pk)) kfns.push_back(f);
@@ -1124,10 +1145,11 @@ int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
     int rc0 = finish_update(ctx);
     if (rc0) return rc0;
     const int oldK = ctx->sh_on ? ctx->sh_K : 0;
+    const bool oldtri = ctx->sh_tri;
     const double oldr0 = ctx->sh_rmin, oldr1 = ctx->sh_rmax;
     int rc = build_potential(ctx, pot, npot);
     if (rc || !ctx->sh_on) return rc;
-    if (ctx->sh_K != oldK || ctx->sh_rmin != oldr0 || ctx->sh_rmax != oldr1) {
+    if (ctx->sh_K != oldK || ctx->sh_tri != oldtri || ctx->sh_rmin != oldr0 || ctx->sh_rmax != oldr1) {
         rc = sh_setup(ctx);
         if (rc) { ctx->sh_on = false; ctx->npot = 0; return rc; }
     }
@@ -1137,7 +1159,7 @@ int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
 int m2m_get_sh_table(m2m_ctx *ctx, double *out) {
     if (!ctx || !out) return set_err(ctx, M2M_ERR_ARG, "NULL argument");
     if (!ctx->sh_on) return set_err(ctx, M2M_ERR_STATE, "the potential has no SH component");
-    const size_t cnt = (size_t)SH_ROW * ctx->sh_K;
+    const size_t cnt = (size_t)ctx->sh_row * ctx->sh_K;
     if (ctx->prec == M2M_FP32C) {
         std::vector<float> f(cnt);
         CU(cudaMemcpyAsync(f.data(), ctx->d_sh_tab, 4 * cnt, cudaMemcpyDeviceToHost, ctx->st));
@@ -1535,7 +1557,7 @@ int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, 
         for (int k = 0; k < 8; ++k) { h ^= (unsigned long long)((v >> (8 * k)) & 0xff); h *= 1099511628211ull; }
     };
     mix(ctx->prec); mix(ctx->n); mix(ctx->layout); mix(potential_signature(ctx)); mix(ctx->nobs);
-    mix(ctx->prior.kind); mix(ctx->sh_on ? ctx->sh_K : 0); mix(ctx->edge_len); mix(ctx->gh_len);
+    mix(ctx->prior.kind); mix(ctx->sh_on ? ctx->sh_K * ctx->sh_row : 0); mix(ctx->edge_len); mix(ctx->gh_len);
     snprintf(out->key, sizeof out->key, "%016llx", h);
     std::string devname(prop.name);
     for (char &ch : devname)

@@ -88,7 +88,7 @@ struct PassArgs {
     int prior_kind, nE, nL, ncells;
     double pk, pgma;                        // e_lc: a/GM, GM*a
     void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
-    const void *sh_tab; int sh_K;           // spherical-harmonic node table (R, SH_ROW per node) or NULL
+    const void *sh_tab; int sh_K, sh_row;   // expansion node table (R, sh_row values per node) or NULL
     // record of the preceding step, left by its residual to this pass (the
     // first block to finish its particles writes it; see record_warp)
     int rec_pending, rec_write_ring, rec_chi_nblk, rec_stat_nblk;
@@ -428,9 +428,170 @@ __device__ __forceinline__ R sh_phi(R x, R y, R z, const R *T, const PotDev &p) 
     return -s;
 }
 
+// ------------------------------------------------------------ triaxial
+// The triaxial expansion (potential kind 5): the real harmonics a set of
+// particles mirror-symmetric about the three coordinate planes can have,
+// even l <= 8 and even m >= 0 (cosine harmonics), 15 terms indexed
+// t(l, m) = (l/2)(l/2 + 1)/2 + m/2, i.e. (0,0) (2,0) (2,2) (4,0) ... (8,8).
+// With n = x/r, mu = n_z and u = n_x + i n_y,
+//   Y_lm = c_lm Q_l^m(mu) Re u^m,   Q_l^m = d^m P_l / dmu^m,
+//   c_l0 = N_l0, c_lm = sqrt(2) N_lm, N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+// which stays regular on the z axis.  Node tables hold, per radial node,
+//   [0..14] F_lm(r_k) = 4 pi/(2l+1) [A_lm(r_k)/r_k^(l+1) + B_lm(r_k) r_k^l]
+//   [15..29] slopes of F to node k+1, [30..44] D_lm = dF_lm/dr,
+//   [45..59] slopes of D, [60] r_k;
+// Phi = -sum Y_lm F_lm(r), a = sum [D_lm Y_lm n + F_lm grad Y_lm] with
+//   grad Y_lm = c_lm [Q_l^(m+1) Re u^m (e_z - mu n) + m Q_l^m (Re u^(m-1),
+//               -Im u^(m-1), 0) - m Q_l^m Re u^m n] / r.
+// The terms are generated one at a time (m outer, l inner, the Q_l^m and
+// Q_l^(m+1) recurrences in l carried along) so that no per-term arrays are
+// live: the particle pass runs it at 64 registers a thread.
+constexpr int TRI_NT = 15;
+constexpr int TRI_ROW = 4 * TRI_NT + 1;
+__host__ __device__ constexpr int tri_t(int l, int m) { return (l / 2) * (l / 2 + 1) / 2 + m / 2; }
+__host__ __device__ constexpr int tri_l(int t) { return t < 1 ? 0 : t < 3 ? 2 : t < 6 ? 4 : t < 10 ? 6 : 8; }
+
+// c_lm of term t: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), times sqrt(2) for m > 0
+__host__ __device__ constexpr double tri_c(int t) {
+    return t == 0 ? 0.28209479177387814 : t == 1 ? 0.6307831305050401 : t == 2 ? 0.18209140509867988
+         : t == 3 ? 0.8462843753216345 : t == 4 ? 0.063078313050504 : t == 5 ? 0.005960340337611203
+         : t == 6 ? 1.0171072362820548 : t == 7 ? 0.03509353369580661 : t == 8 ? 0.0010678622237644956
+         : t == 9 ? 6.57223766418388e-05 : t == 10 ? 1.1631066229203195 : t == 11 ? 0.023169638523677944
+         : t == 12 ? 0.00036818972564450655 : t == 13 ? 7.878532816214047e-06 : 3.596041786237614e-07;
+}
+
+// Calls f(t, l, m, Q_l^m, Q_l^(m+1), Re u^m, Re u^(m-1), Im u^(m-1)) for
+// the 15 terms, m = 0, 2, .., 8 outer and l = m, m+2, .., 8 inner.  Q_l^m by
+// Q_m^m = (2m-1)!!, Q_(m+1)^m = (2m+1) mu Q_m^m, (l-m) Q_l^m = (2l-1) mu
+// Q_(l-1)^m - (l+m-1) Q_(l-2)^m.
+template <class R, class Fn>
+__device__ __forceinline__ void tri_terms(R mu, R nx, R ny, Fn &&f) {
+    R re = R(1), im = R(0), rp = R(0), ip = R(0);    // u^m, u^(m-1)
+#pragma unroll
+    for (int m = 0; m <= 8; m += 2) {
+        double dfm = 1.0;                              // (2m-1)!!
+        for (int k = 1; k <= m; ++k) dfm *= 2 * k - 1;
+        R a1 = R(dfm), a2 = R(0);                      // Q_l^m, Q_(l-1)^m at l = m
+        R b1 = R(0), b2 = R(0);                        // Q_l^(m+1), Q_(l-1)^(m+1) at l = m
+#pragma unroll
+        for (int l = m; l <= 8; ++l) {
+            if ((l & 1) == 0) f(tri_t(l, m), l, m, a1, b1, re, rp, ip);
+            if (l == 8) break;
+            // step to l + 1
+            R an, bn;
+            if (l == m) an = R(2 * m + 1) * mu * a1;
+            else an = (R(2 * l + 1) * mu * a1 - R(l + m) * a2) * R(1.0 / (l + 1 - m));
+            if (l == m) bn = R(dfm * (2 * m + 1));     // Q_(m+1)^(m+1) = (2m+1)!!
+            else if (l == m + 1) bn = R(2 * m + 3) * mu * b1;
+            else bn = (R(2 * l + 1) * mu * b1 - R(l + m + 1) * b2) * R(1.0 / (l - m));
+            a2 = a1; a1 = an; b2 = b1; b1 = bn;
+        }
+        // u^(m+1), u^(m+2)
+        rp = re * nx - im * ny;
+        ip = re * ny + im * nx;
+        re = rp * nx - ip * ny;
+        im = rp * ny + ip * nx;
+    }
+}
+
+// Radial factors of a point: F_t(r) = T[t] fa_(l/2) + dr T[15+t] and
+// D_t(r) = T[30+t] da_(l/2) + dr T[45+t] + (l+1) dbs F_t(r) from one table
+// row: linear between nodes (fa = da = 1, dbs = 0); beyond the last node
+// F(K-1) (r_(K-1)/r)^(l+1) and D = -(l+1) F/r (dr = 0, da = 0, dbs = -1/r);
+// inside the first F(0) (r/r_0)^l and D(0) (r/r_0)^max(l-1, 1) (dr = 0).
+template <class R> struct TriRad {
+    const R *row;
+    R dr, dbs, fa[5], da[5];
+};
+
+template <class R>
+__device__ __forceinline__ void tri_rad(R r, R ir, const R *T, const PotDev &p, TriRad<R> &g) {
+    const int K = p.ik;
+    const R r0 = KC(R, p.c[1], p.cf[1]), rK = KC(R, p.c[2], p.cf[2]);
+    g.dbs = R(0);
+    g.dr = R(0);
+    if (r >= rK) {
+        g.row = T + (K - 1) * TRI_ROW;
+        const R q = rK * ir, q2 = q * q;
+        g.fa[0] = q;
+#pragma unroll
+        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * q2;
+#pragma unroll
+        for (int n = 0; n < 5; ++n) g.da[n] = R(0);
+        g.dbs = -ir;
+    } else if (r < r0) {
+        g.row = T;
+        const R q = r * KC(R, p.c[5], p.cf[5]), q2 = q * q;
+        g.fa[0] = R(1);
+        g.da[0] = q;
+#pragma unroll
+        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * q2;
+        g.da[1] = q;
+#pragma unroll
+        for (int n = 2; n < 5; ++n) g.da[n] = g.da[n - 1] * q2;
+    } else {
+        const float lg = fmaf(__log2f((float)r), p.cf[3], p.cf[4]) - 0.5f;
+        int k = rint_small(fminf(fmaxf(lg, 0.0f), (float)(K - 2)));
+        while (k > 0 && r < T[k * TRI_ROW + 60]) --k;
+        while (k < K - 2 && r >= T[(k + 1) * TRI_ROW + 60]) ++k;
+        g.row = T + k * TRI_ROW;
+        g.dr = r - g.row[60];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) { g.fa[n] = R(1); g.da[n] = R(1); }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ R tri_F(const TriRad<R> &g, int t, int l) {
+    return g.row[t] * g.fa[l / 2] + g.dr * g.row[15 + t];
+}
+
+template <class R>
+__device__ __forceinline__ void tri_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
+    const R r2 = (x * x + y * y) + z * z;
+    if (!(r2 > R(0))) return;
+    const R r = sqrt(r2), ir = R(1) / r;
+    const R nx = x * ir, ny = y * ir, mu = z * ir;
+    TriRad<R> rd;
+    tri_rad<R>(r, ir, T, p, rd);
+    R ar = R(0), az = R(0), ax = R(0), ay = R(0);   // along n, e_z, and the (Re, -Im) direction (the last two / r)
+    tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
+        const R F = tri_F<R>(rd, t, l);
+        const R D = rd.row[30 + t] * rd.da[l / 2] + rd.dr * rd.row[45 + t] + R(l + 1) * rd.dbs * F;
+        const R c = R(tri_c(t));
+        const R cq0C = c * q0 * C, Fc = F * c;
+        // D Y n + F c [q1 C (e_z - mu n) - m q0 C n + m q0 (Re u^(m-1), -Im u^(m-1), 0)] / r
+        ar = ar + (D * cq0C - (Fc * q1 * C * mu + F * R(m) * cq0C) * ir);
+        az = az + Fc * q1 * C;
+        if (m > 0) {
+            const R s = Fc * R(m) * q0;
+            ax = ax + s * cp;
+            ay = ay - s * sp;
+        }
+    });
+    g.x = g.x + (ar * nx + ax * ir);
+    g.y = g.y + (ar * ny + ay * ir);
+    g.z = g.z + (ar * mu + az * ir);
+}
+
+template <class R>
+__device__ __forceinline__ R tri_phi(R x, R y, R z, const R *T, const PotDev &p) {
+    const R r2 = (x * x + y * y) + z * z;
+    const R r = sqrt(r2);
+    const R ir = r2 > R(0) ? R(1) / r : R(0);
+    const R nx = x * ir, ny = y * ir, mu = r2 > R(0) ? z * ir : R(1);
+    TriRad<R> rd;
+    tri_rad<R>(r, ir, T, p, rd);
+    R s = R(0);
+    tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
+        s = s + R(tri_c(t)) * q0 * C * tri_F<R>(rd, t, l);
+    });
+    return -s;
+}
+
 // Potential signatures compiled into the steady-state kernels (the generic
 // form walks the component list at run time):
-enum { PK_ANY = 0, PK_HERNQUIST = 1, PK_LOG = 3, PK_SH = 4, PK_HERNQUIST_NFW = 5 };
+enum { PK_ANY = 0, PK_HERNQUIST = 1, PK_LOG = 3, PK_SH = 4, PK_HERNQUIST_NFW = 5, PK_SH_TRI = 6 };
 
 template <class R>
 __device__ __forceinline__ void acc_hernquist(R x, R y, R z, const PotDev &p, Acc3<R> &g) {
@@ -493,6 +654,9 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
     } else if constexpr (PK == PK_SH) {
         sh_accel<R>(x, y, z, sh, a.pot[0], g);
         return g;
+    } else if constexpr (PK == PK_SH_TRI) {
+        tri_accel<R>(x, y, z, sh, a.pot[0], g);
+        return g;
     } else if constexpr (PK == PK_HERNQUIST_NFW) {
         acc_hernquist<R>(x, y, z, a.pot[0], g);
         acc_nfw<R>(x, y, z, a.pot[1], g);
@@ -508,6 +672,8 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
             acc_nfw<R>(x, y, z, p, g);
         } else if (p.kind == 4) {     // spherical harmonics of the particles
             sh_accel<R>(x, y, z, sh, p, g);
+        } else if (p.kind == 5) {     // the triaxial expansion of the particles
+            tri_accel<R>(x, y, z, sh, p, g);
         }
     }
     return g;
@@ -598,6 +764,8 @@ __device__ __forceinline__ R phi_term(int kind, R x, R y, R z, const PotDev &p, 
         return (R)v;
     } else if (kind == 4) {
         return sh_phi<R>(x, y, z, sh, p);
+    } else if (kind == 5) {
+        return tri_phi<R>(x, y, z, sh, p);
     }
     return R(0);
 }
@@ -613,6 +781,8 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R
         return phi + phi_term<R>(3, x, y, z, a.pot[0], sh);
     } else if constexpr (PK == PK_SH) {
         return phi + phi_term<R>(4, x, y, z, a.pot[0], sh);
+    } else if constexpr (PK == PK_SH_TRI) {
+        return phi + phi_term<R>(5, x, y, z, a.pot[0], sh);
     } else if constexpr (PK == PK_HERNQUIST_NFW) {
         phi = phi + phi_term<R>(1, x, y, z, a.pot[0], sh);
         return phi + phi_term<R>(2, x, y, z, a.pot[1], sh);

@@ -131,9 +131,12 @@ __device__ void prior_setup(const PassArgs &a, R *pe, R *pl, float *gp) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
             a0 = fmin(a0, red[0][k]); a1 = fmax(a1, red[1][k]); a2 = fmax(a2, red[2][k]);
         }
-        double lo = a0, hi = (a.prior_kind == M2M_PRIOR_E_LZ) ? a1 : 0.0;
-        double l0 = (a.prior_kind == M2M_PRIOR_E_LZ) ? -a2 : 0.0;
-        double l1 = (a.prior_kind == M2M_PRIOR_E_LZ) ? a2 : 1.0;
+        // (E, L_z): [min E, max E] x [-max |L_z|, max |L_z|]; (E, L^2):
+        // [min E, max E] x [0, max L^2]; (E, L/L_c): [min E, 0) x [0, 1]
+        const bool lz = a.prior_kind == M2M_PRIOR_E_LZ, l2 = a.prior_kind == M2M_PRIOR_E_L2;
+        double lo = a0, hi = (lz || l2) ? a1 : 0.0;
+        double l0 = lz ? -a2 : 0.0;
+        double l1 = (lz || l2) ? a2 : 1.0;
         rng[0] = lo; rng[1] = (hi - lo) / (double)a.nE;
         rng[2] = l0; rng[3] = (l1 - l0) / (double)a.nL;
     }
@@ -160,12 +163,19 @@ __device__ __forceinline__ int fkey(float v) {
 }
 __device__ __forceinline__ float fkey_inv(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
+// E and the second integral of the prior: L_z, or L^2 = (Lx*Lx + Ly*Ly) +
+// Lz*Lz for the (E, L^2) cells (its range is [0, max |L^2|] as the L_z
+// range is [-max |L_z|, max |L_z|]).
 template <class R, int PK = PK_ANY>
 __device__ __forceinline__ void energy_lz(R x, R y, R z, R vx, R vy, R vz, const PassArgs &a, const R *sh,
                                           R &E, R &Lz) {
     R v2 = (vx * vx + vy * vy) + vz * vz;
     E = R(0.5) * v2 + potential<R, PK>(x, y, z, a, sh);
     Lz = x * vy - y * vx;
+    if (a.prior_kind == M2M_PRIOR_E_L2) {
+        const R Lx = y * vz - z * vy, Ly = z * vx - x * vz;
+        Lz = (Lx * Lx + Ly * Ly) + Lz * Lz;
+    }
 }
 
 template <class R, int PK = PK_ANY>
@@ -173,9 +183,9 @@ __device__ __forceinline__ int prior_cell(R x, R y, R z, R vx, R vy, R vz, const
                                           const R *pe, const R *pl, const float *gp, const R *sh) {
     R E, Lz;
     energy_lz<R, PK>(x, y, z, vx, vy, vz, a, sh, E, Lz);
-    if (a.prior_kind == M2M_PRIOR_E_LZ) {
+    if (a.prior_kind == M2M_PRIOR_E_LZ || a.prior_kind == M2M_PRIOR_E_L2) {
         int iE = count_le<R>(E, pe, a.nE, gp[0], gp[1]);
-        int iL = count_le<R>(Lz, pl, a.nL, gp[2], gp[3]);
+        int iL = count_le<R>(Lz, pl, a.nL, gp[2], gp[3]);       // L_z or L^2
         return iE * a.nL + iL;
     }
     // E_LC: Hernquist circular-orbit angular momentum at energy E
@@ -722,7 +732,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     if (GHC) { S.ghc = (const float4 *)p; p += 48 * (a.gh_len / 5); }
     else if (fl & F_UPD) { S.gpoly = (const R *)p; p += sizeof(R) * ((a.gh_len + 3) & ~3); }
     if (FX && L == 1) { S.pmap = (const short *)p; p += 2 * ((a.sets[1].pmap_len + 7) & ~7); }
-    const int sh_len = (a.sh_tab && (fl & (F_PUSH | F_MINMAX | F_CELLS))) ? SH_ROW * a.sh_K : 0;
+    const int sh_len = (a.sh_tab && (fl & (F_PUSH | F_MINMAX | F_CELLS))) ? a.sh_row * a.sh_K : 0;
     if (sh_len) { S.sh = (const R *)p; p += sizeof(R) * ((sh_len + 3) & ~3); }
     if (fl & F_CELLS) {
         S.pe = (R *)p; p += sizeof(R) * ((a.nE + 4) & ~3);
@@ -1514,6 +1524,176 @@ __global__ void k_sh_tables(const long long *sum, int K, const double *rn, doubl
             row[15 + n] = last ? R(0) : (R)((FD[(5 + n) * K + k + 1] - D) * h);
         }
         row[20] = (R)rn[k];
+    }
+}
+
+// The triaxial expansion (kind 5): per radial side j, for each of its 15
+// terms t, A terms w Y_t (r/r_j)^l and B terms w Y_t (r_(j-1)/r)^(l+1)
+// (j > 0), each at most 1.7 w in size, summed exactly in 64-bit fixed point
+// (FP32C) or in double (FP64) as for the axisymmetric expansion; [30][K]
+// side sums, row t for A and 15 + t for B.  The terms are generated one at
+// a time; a warp whose particles share one side adds warp sums.
+template <class R>
+__global__ void __launch_bounds__(512) k_tri_coef(const __grid_constant__ ShArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr bool FX = sizeof(R) == 4;
+    const int K = a.K, NS = 2 * TRI_NT * K;
+    unsigned *lo = (unsigned *)smem, *hi = lo + NS;
+    double *acc = (double *)smem;
+    R *e2 = (R *)(hi + NS), *rn = e2 + K, *irn = rn + K;
+    for (int k = threadIdx.x; k < 2 * NS; k += blockDim.x) lo[k] = 0u;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        e2[k] = ((const R *)a.e2)[k];
+        rn[k] = ((const R *)a.rn)[k];
+        irn[k] = ((const R *)a.irn)[k];
+    }
+    __syncthreads();
+    bool ovf = false, bad = false;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (shuffles)
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += stride) {
+        const long long i = base + threadIdx.x;
+        int j = K;
+        R mu = R(1), nx = R(0), ny = R(0), ta[5], tb[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) { ta[n] = R(0); tb[n] = R(0); }
+        if (i < a.n) {
+            const R x = ((const R *)a.x)[i], y = ((const R *)a.y)[i], z = ((const R *)a.z)[i];
+            const double wd = a.w[i];
+            const R r2 = (x * x + y * y) + z * z;
+            if (r2 < e2[0]) {
+                j = 0;
+            } else {
+                const int c = find_bin<R>(r2, e2, K - 1, a.gmode, a.ga, a.gb);
+                j = c < 0 ? K : c + 1;                  // NaN or r >= r_(K-1): left out
+            }
+            if (d_bad(wd) && __double_as_longlong(wd) != 0ll) bad = true;
+            if (j < K && d_pos(wd)) {
+                const R wr = to_r(wd, (R *)nullptr);
+                const R r = sqrt(r2), ir = r2 > R(0) ? R(1) / r : R(0);
+                nx = x * ir; ny = y * ir;
+                mu = r2 > R(0) ? z * ir : R(1);
+                // w (r/r_j)^l and w (r_(j-1)/r)^(l+1), l = 0, 2, .., 8
+                const R rho = r * irn[j], rho2 = rho * rho;
+                const R sg = j > 0 ? rn[j - 1] * ir : R(0), sg2 = sg * sg;
+                ta[0] = wr;
+                tb[0] = wr * sg;
+#pragma unroll
+                for (int n = 1; n < 5; ++n) { ta[n] = ta[n - 1] * rho2; tb[n] = tb[n - 1] * sg2; }
+            } else {
+                j = j < K ? K + 1 : j;      // a particle of zero weight adds nothing
+            }
+        }
+        const int j0 = __shfl_sync(0xffffffffu, j, 0);
+        const bool same = __all_sync(0xffffffffu, j == j0);
+        tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
+            const R Y = R(tri_c(t)) * q0 * C;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const R v = (side == 0 ? ta[l / 2] : tb[l / 2]) * Y;
+                const int row = side * TRI_NT + t;
+                if (same) {
+                    if (j0 < K) {
+                        if (FX) {
+                            long long u = to_fixed(v, a.sh, ovf);
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                            if (lane == 0 && u) fixed_add(lo, hi, row * K + j0, u);
+                        } else {
+                            const R u = warp_sum(v);
+                            if (lane == 0 && u != R(0)) atomicAdd(acc + row * K + j0, (double)u);
+                        }
+                    }
+                } else if (j < K && v != R(0)) {
+                    if (FX) {
+                        const long long u = to_fixed(v, a.sh, ovf);
+                        if (u) fixed_add(lo, hi, row * K + j, u);
+                    } else {
+                        atomicAdd(acc + row * K + j, (double)v);
+                    }
+                }
+            }
+        });
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) {
+        if (FX) {
+            const unsigned long long u = ((unsigned long long)hi[k] << 32) | lo[k];
+            if (u) atomicAdd(a.sum + k, u);
+        } else if (acc[k] != 0.0) {
+            atomicAdd((double *)a.sum + k, acc[k]);
+        }
+    }
+    if (ovf) atomicOr(a.err, ERR_OVERFLOW);
+    if (bad) atomicOr(a.err, ERR_NONFINITE);
+}
+
+// F_t and D_t at node k from the node sums A (rows 0..14) and B (rows
+// 15..29) held in S ([30][K]), with the 4 pi/(2l+1) of the addition theorem.
+__device__ __forceinline__ void tri_node_FD(const double *S, int K, const double *rn, int k, int t, double &F,
+                                            double &D) {
+    const int l = tri_l(t);
+    const double r = rn[k], ir = 1.0 / r;
+    double rl = 1.0;
+    for (int e = 0; e < l; ++e) rl *= r;                           // r^l
+    const double A = S[t * K + k], B = S[(TRI_NT + t) * K + k];
+    const double c = 12.566370614359172 / (double)(2 * l + 1);     // 4 pi/(2l+1)
+    const double irl1 = ir / rl;                                   // r^-(l+1)
+    F = c * (A * irl1 + B * rl);
+    D = c * (-(double)(l + 1) * A * (irl1 * ir) + (l > 0 ? (double)l * B * (rl * ir) : 0.0));
+}
+
+// Node tables of the triaxial expansion from its side sums (one block):
+// scale back, prefix sums (A) and suffix sums (B), then F_lm, D_lm and the
+// slopes to the next node.
+template <class R>
+__global__ void k_tri_tables(const long long *sum, int K, const double *rn, double q, R *tab, int *err) {
+    extern __shared__ __align__(16) double sd[];
+    constexpr int NR = 2 * TRI_NT;
+    double *S = sd;                // [30][K] side sums, then A, B at the nodes
+    for (int k = threadIdx.x; k < NR * K; k += blockDim.x) {
+        const int row = k / K, j = k - row * K, t = row % TRI_NT, l = tri_l(t);
+        const double v = sizeof(R) == 4 ? (double)sum[k] * q : ((const double *)sum)[k];
+        double s = 1.0;
+        if (row < TRI_NT) {
+            for (int e = 0; e < l; ++e) s *= rn[j];                       // r_j^l
+        } else if (j > 0) {
+            for (int e = 0; e <= l; ++e) s *= rn[j - 1];                  // r_(j-1)^(l+1)
+            s = 1.0 / s;
+        } else {
+            s = 0.0;
+        }
+        S[k] = v * s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NR) {
+        double *row = S + threadIdx.x * K;
+        double acc = 0.0;
+        if (threadIdx.x < TRI_NT) {
+            for (int k = 0; k < K; ++k) { acc += row[k]; row[k] = acc; }
+        } else {
+            for (int k = K - 1; k >= 0; --k) { const double b = row[k]; row[k] = acc; acc += b; }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        R *row = tab + (size_t)k * TRI_ROW;
+        const bool last = k == K - 1;
+        const double h = last ? 1.0 : 1.0 / (rn[k + 1] - rn[k]);
+        bool fin = true;
+        for (int t = 0; t < TRI_NT; ++t) {
+            double F, D, F1 = 0.0, D1 = 0.0;
+            tri_node_FD(S, K, rn, k, t, F, D);
+            if (!last) tri_node_FD(S, K, rn, k + 1, t, F1, D1);
+            fin = fin && isfinite(F) && isfinite(D);
+            row[t] = (R)F;
+            row[30 + t] = (R)D;
+            row[15 + t] = last ? R(0) : (R)((F1 - F) * h);
+            row[45 + t] = last ? R(0) : (R)((D1 - D) * h);
+        }
+        row[60] = (R)rn[k];
+        if (!fin) atomicOr(err, ERR_NONFINITE);
     }
 }
 
