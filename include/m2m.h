@@ -38,6 +38,12 @@
  *    particle) so that the next weight update need not look them up again.
  *    A caller that changes x..vz itself (not through m2m_step/m2m_push)
  *    must call m2m_observe before the next m2m_update_weights.
+ *  - With a self-consistent expansion potential (SH, SH_TRI) every push
+ *    keeps the force at the new positions (library-owned, 3 values of the
+ *    state precision per particle) and the next push starts from it instead
+ *    of evaluating the expansion again; a recompute of the expansion drops
+ *    it.  A caller that changes x..z itself must call m2m_observe (which
+ *    drops it too) before the next push.
  *  - M2M_FP32C keeps ln w_hat_i per particle in float (library-owned, 4
  *    bytes per particle) for the weight update; it is taken from w_hat at
  *    m2m_init and rewritten with w_hat at every prior recompute.  A caller
@@ -416,6 +422,13 @@ typedef struct {
     char key[64];             /* the configuration key */
 } m2m_tuning;
 int m2m_autotune(m2m_ctx *ctx, int32_t steps_per_trial, const char *cache_path, m2m_tuning *out);
+
+/* Keep the force of a self-consistent expansion potential between pushes
+ * (default 1; see the conventions at the top): 0 evaluates the expansion
+ * twice per push, at the old and at the new positions.  The kept force is
+ * the same function of the same positions and node table, so the results
+ * are bit-identical either way.  Applies from the next push. */
+int m2m_set_force_cache(m2m_ctx *ctx, int32_t enable);
 
 /* Persistent multi-step launches (on by default).  Where they apply -- an
  * M2M_FP32C context with a compiled observable layout and potential

@@ -112,6 +112,9 @@ struct m2m_ctx {
     int sh_gmode;
     float sh_ga, sh_gb;
     void *d_sh_e2, *d_sh_rn, *d_sh_irn, *d_sh_tab;
+    void *d_facc;        // force at the current positions ([3][n], state precision)
+    bool facc_valid;     // d_facc holds it for the current positions and node table
+    bool facc_off;       // m2m_set_force_cache(0): evaluate the force twice per push
     double *d_sh_rnd;
     unsigned long long *d_sh_sum;
     // persistent multi-step launches (FP32C compiled layouts)
@@ -337,6 +340,8 @@ void fill_args(const m2m_ctx *c, PassArgs &a, int flags) {
     a.f_pk = (float)a.pk; a.f_pgma = (float)a.pgma;
     a.mm_slots = c->d_mm_slots; a.mm_nblocks = c->mm_nblocks;
     a.sh_tab = c->sh_on ? c->d_sh_tab : nullptr; a.sh_K = c->sh_K; a.sh_row = c->sh_row;
+    a.facc = (c->sh_on && !c->facc_off) ? c->d_facc : nullptr;
+    a.facc_read = (flags & F_PUSH) && a.facc && c->facc_valid;
     a.cell_cache = c->d_cell_cache;
     a.cache_read = (flags & F_UPD) && c->cache_valid && c->layout != 0;
     a.cache_write = (flags & F_SCAT) && c->layout != 0;
@@ -411,6 +416,7 @@ int launch_pass(m2m_ctx *ctx, int flags, int *grid_out = nullptr) {
     if (flags & F_MINMAX) ctx->mm_nblocks = (int)grid;
     if (flags & F_SCAT) ctx->cache_valid = ctx->layout != 0;
     else if (flags & F_PUSH) ctx->cache_valid = false;
+    if (flags & F_PUSH) ctx->facc_valid = a.facc != nullptr;
     if (flags & F_PUSH) ++ctx->epoch;
     if (grid_out) *grid_out = (int)grid;
     return M2M_OK;
@@ -606,7 +612,7 @@ void free_all(m2m_ctx *c) {
                     c->d_coef_r, c->d_slots, c->d_stat_slots, c->d_chi_slots, c->d_ticket, c->d_rec_ticket, c->d_ring,
                     c->d_last, c->d_err, c->d_mm_slots, c->d_cell_ids, c->d_cell_acc, c->d_cell_cnt,
                     c->d_cell_mean, c->d_cell_cache, c->d_y_acc, c->d_sh_e2, c->d_sh_rn, c->d_sh_irn,
-                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_lnwhat, c->d_lut, c->d_pmap, c->d_psf,
+                    c->d_sh_tab, c->d_sh_rnd, c->d_sh_sum, c->d_facc, c->d_lnwhat, c->d_lut, c->d_pmap, c->d_psf,
                     c->d_bar, c->d_st2, c->d_chi2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -680,6 +686,8 @@ int sh_setup(m2m_ctx *ctx) {
     CU(cudaMalloc(&ctx->d_sh_tab, rs * ctx->sh_row * K));
     CU(cudaMalloc((void **)&ctx->d_sh_rnd, 8 * (size_t)K));
     CU(cudaMalloc((void **)&ctx->d_sh_sum, sh_sums(ctx) * 8));
+    if (!ctx->d_facc) CU(cudaMalloc(&ctx->d_facc, rs * 3 * (size_t)ctx->n));
+    ctx->facc_valid = false;
     std::vector<double> rn(K), e2(K), irn(K);
     const double ratio = ctx->sh_rmax / ctx->sh_rmin;
     for (int k = 0; k < K; ++k) rn[k] = ctx->sh_rmin * pow(ratio, (double)k / (double)(K - 1));
@@ -712,6 +720,7 @@ size_t sh_coef_smem(const m2m_ctx *c) {
 // the node table the push reads.
 int sh_recompute(m2m_ctx *ctx) {
     const int K = ctx->sh_K;
+    ctx->facc_valid = false;       // a new node table: the kept forces are of the old one
     CU(cudaMemsetAsync(ctx->d_sh_sum, 0, 8 * sh_sums(ctx), ctx->st));
     ShArgs a;
     memset(&a, 0, sizeof a);
@@ -1176,6 +1185,7 @@ int m2m_observe(m2m_ctx *ctx, int32_t mode) {
     if (!ctx || mode < 0 || mode > 2) return set_err(ctx, M2M_ERR_ARG, "bad context or mode");
     int rc = finish_update(ctx);
     if (rc) return rc;
+    ctx->facc_valid = false;       // the caller may have moved the particles
     return observe_now(ctx, 0, mode, ctx->t, 0);
 }
 
@@ -1658,6 +1668,13 @@ int m2m_set_pipeline(m2m_ctx *ctx, int32_t enable) {
     ctx->pipe = (enable & 1) != 0;
     if (enable & 2) ctx->fx_atomic = 0;      // FP32C: per-block slots instead of atomics
     if (enable & 4) ctx->fx_atomic = 1;      // FP32C: global integer atomics (default)
+    return M2M_OK;
+}
+
+int m2m_set_force_cache(m2m_ctx *ctx, int32_t enable) {
+    if (!ctx) return M2M_ERR_ARG;
+    ctx->facc_off = enable == 0;
+    ctx->facc_valid = false;
     return M2M_OK;
 }
 

@@ -89,6 +89,7 @@ struct PassArgs {
     double pk, pgma;                        // e_lc: a/GM, GM*a
     void *mm_slots; int mm_nblocks;         // [mm_nblocks][4] R: min E, max E, max|Lz|, pad
     const void *sh_tab; int sh_K, sh_row;   // expansion node table (R, sh_row values per node) or NULL
+    void *facc; int facc_read;              // expansion potentials: force at the positions (R, [3][n]) or NULL
     // record of the preceding step, left by its residual to this pass (the
     // first block to finish its particles writes it; see record_warp)
     int rec_pending, rec_write_ring, rec_chi_nblk, rec_stat_nblk;
@@ -791,11 +792,25 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R
     return phi;
 }
 
+// With an expansion potential the force at the new positions is kept
+// (a.facc, [3][n] in the state precision) and, while neither the positions
+// nor the node table have changed since (a.facc_read), taken instead of a
+// second evaluation at the start of the next push: the same function of the
+// same arguments, so the same bits.
 template <class R, int PK = PK_ANY>
 __device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a,
-                                    const R *sh = nullptr) {
+                                    const R *sh = nullptr, long long i = 0) {
     R h = KC(R, a.hdt, a.f_hdt), d = KC(R, a.dt, a.f_dt);
-    Acc3<R> g = accel<R, PK>(x, y, z, a, sh);
+    constexpr bool CACHE = PK == PK_ANY || PK == PK_SH || PK == PK_SH_TRI;
+    R *fc = CACHE ? (R *)a.facc : nullptr;
+    Acc3<R> g;
+    if (CACHE && fc && a.facc_read) {
+        g.x = fc[i];
+        g.y = fc[a.n + i];
+        g.z = fc[2 * a.n + i];
+    } else {
+        g = accel<R, PK>(x, y, z, a, sh);
+    }
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;
@@ -803,6 +818,11 @@ __device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const
     y = y + d * vy;
     z = z + d * vz;
     g = accel<R, PK>(x, y, z, a, sh);
+    if (CACHE && fc) {
+        fc[i] = g.x;
+        fc[a.n + i] = g.y;
+        fc[2 * a.n + i] = g.z;
+    }
     vx = vx + h * g.x;
     vy = vy + h * g.y;
     vz = vz + h * g.z;
@@ -881,12 +901,39 @@ __device__ __forceinline__ void gh_eval(double vlos, const double *g, double u[5
     u[4] = gs * ((4.0 * E4 - 12.0 * E2 + 3.0) / SQ24);
 }
 
-// gh_eval from the combined per-cell record of the compiled layouts:
-// r[0] = (V, 1/S, c1, P0), r[1] = (P1..P4), r[2] = (t2, norm, 0, 0).
+// The per-cell record of the compiled FP32C layouts (three float4):
+//   r[0] = (V, c1/S, -log2(e)/(2S), log2 norm), r[1] = (P0, P1, P2, P3),
+//   r[2] = (P4, d/sqrt 2, sqrt 3 d, 12 d/sqrt 24),  d = 2 t2 - 1,
+// P0..P4 the update's quartic of the step (without the norm).  With
+// dv = v_los - V and m = dv c1/S (= nu c1), the Gaussian factor of every
+// term is g = norm exp(-nu m/2) = 2^(dv m (-log2(e)/(2S)) + log2 norm), and
+// the van der Marel & Franx moments of gh_eval become, with m2 = m^2,
+//   u0 = g, u1 = g sqrt2 m, u2 = g (sqrt2 m2 + d/sqrt2),
+//   u3 = g m (2/sqrt3 m2 + sqrt3 d),
+//   u4 = g (4/sqrt24 m2^2 + 12 d/sqrt24 m2 + 3 d^2/sqrt24)
+// (E2 = m2 + t2 etc. expanded: 2 E2 - 1 = 2 m2 + d, 2 E3 - 3 m = m (2 m2 +
+// 3 d), 4 E4 - 12 E2 + 3 = 4 m2^2 + 12 d m2 + 3 d^2), the last constant
+// 3 d^2/sqrt24 = (12 d/sqrt24)^2 / (2 sqrt24).
+__device__ __forceinline__ void gh_record(float V, float iS, float c1, float t2, float nrm, const float P[5],
+                                          float4 r[3]) {
+    const float d = fmaf(2.f, t2, -1.f);
+    r[0] = make_float4(V, c1 * iS, (-0.5f * 1.44269504088896341f) * iS, log2f(nrm));
+    r[1] = make_float4(P[0], P[1], P[2], P[3]);
+    r[2] = make_float4(P[4], d * 0.707106781187f, d * 1.73205080757f, d * 2.44948974278f);
+}
+
+// The five moments of one particle from a cell record (the arithmetic of
+// the scatter's fast path, which adds each term as it is formed).
 __device__ __forceinline__ void gh_eval_rec(float vlos, const float4 *r, float u[5]) {
+    const float SQ2 = 1.41421356237f, K3 = 1.15470053838f, K4 = 0.816496580928f, C4 = 0.102062072616f;
     const float4 a = r[0], c = r[2];
-    const float g[5] = {a.x, a.y, a.z, c.x, c.y};
-    gh_eval(vlos, g, u);
+    const float dv = vlos - a.x, m = dv * a.y, m2 = m * m;
+    const float g = ex2_ftz(fmaf(dv * m, a.z, a.w));
+    u[0] = g;
+    u[1] = g * (SQ2 * m);
+    u[2] = g * fmaf(SQ2, m2, c.y);
+    u[3] = g * (m * fmaf(K3, m2, c.z));
+    u[4] = g * fmaf(m2, fmaf(K4, m2, c.w), (c.w * c.w) * C4);
 }
 
 __device__ __forceinline__ float gh_exp(float x) { return exp_ftz(x); }
@@ -1006,24 +1053,21 @@ __device__ __forceinline__ void fx_red_fast(int *Lo, int *Mid, int b, float S) {
     atomicAdd(Lo + b, V & 0xFFFF);
     atomicAdd(Mid + b, V >> 16);
 }
-// The five Gauss-Hermite terms of one particle (the arithmetic of gh_eval),
-// each scaled by W = w 2^sh and added to the histogram as soon as it is
-// formed (|W u_n| < 2^31 is the caller's test), to keep few values live.
+// The five Gauss-Hermite terms of one particle (the arithmetic of
+// gh_eval_rec), each scaled by W = w 2^sh and added to the histogram as soon
+// as it is formed (|W u_n| < 2^31 is the caller's test), to keep few values
+// live.
 __device__ __forceinline__ void gh_red_stream(float vlos, const float4 *r, float W, int *Lo, int *Mid, int b) {
-    const float SQ2 = 1.41421356237f, ISQ2 = 0.707106781187f, ISQ3 = 0.57735026919f, ISQ24 = 0.204124145232f;
+    const float SQ2 = 1.41421356237f, K3 = 1.15470053838f, K4 = 0.816496580928f, C4 = 0.102062072616f;
     const float4 a = r[0], c = r[2];
-    const float nu = (vlos - a.x) * a.y;
-    const float c1 = a.z, t2 = c.x;
-    const float gs = c.y * exp_ftz(-0.5f * nu * nu * c1);
-    const float m = nu * c1, m2 = m * m;
-    fx_red_fast(Lo, Mid, b, W * gs);
-    fx_red_fast(Lo, Mid, b + 1, W * (gs * (SQ2 * m)));
-    const float E2 = m2 + t2;
-    fx_red_fast(Lo, Mid, b + 2, W * (gs * (fmaf(2.f, E2, -1.f) * ISQ2)));
-    const float E3 = m * fmaf(3.f, t2, m2);
-    fx_red_fast(Lo, Mid, b + 3, W * (gs * (fmaf(2.f, E3, -3.f * m) * ISQ3)));
-    const float E4 = fmaf(m2, m2, fmaf(6.f * m2, t2, 3.f * t2 * t2));
-    fx_red_fast(Lo, Mid, b + 4, W * (gs * (fmaf(4.f, E4, fmaf(-12.f, E2, 3.f)) * ISQ24)));
+    const float dv = vlos - a.x, m = dv * a.y;
+    const float Wg = W * ex2_ftz(fmaf(dv * m, a.z, a.w));
+    const float m2 = m * m;
+    fx_red_fast(Lo, Mid, b, Wg);
+    fx_red_fast(Lo, Mid, b + 1, Wg * (SQ2 * m));
+    fx_red_fast(Lo, Mid, b + 2, Wg * fmaf(SQ2, m2, c.y));
+    fx_red_fast(Lo, Mid, b + 3, Wg * (m * fmaf(K3, m2, c.z)));
+    fx_red_fast(Lo, Mid, b + 4, Wg * fmaf(m2, fmaf(K4, m2, c.w), (c.w * c.w) * C4));
 }
 
 __device__ __forceinline__ void fx_red(int *Lo, int *Mid, int *Hi, int b, float v, float fscale, int sh,

@@ -295,7 +295,7 @@ struct PassSmem {
     const R *coef, *edges, *gh;
     const Pair<R> *epair;    // (e[k], e[k+1]) for every edge-table index k
     const R *gpoly;          // per GH cell: norm * sum_n coef_n E[H_n] as a quartic in m
-    const float4 *ghc;       // FP32C compiled layouts: per GH cell (V, 1/S, c1, P0), (P1..P4), (t2, norm)
+    const float4 *ghc;       // FP32C compiled layouts: per GH cell the three float4 of gh_record
     R *pe, *pl;
     float *gp;
     const R *sh;             // spherical-harmonic node table
@@ -382,15 +382,16 @@ __device__ __forceinline__ R obs_dot(const PassArgs &a, const PassSmem<R> &S, R 
                     // sum_n coef_n u_n(nu) = exp(-nu m / 2) * P(m), m = nu c1,
                     // with the quartic P of this cell built in the prologue
                     if constexpr (sizeof(R) == 4) {
+                        // the record of gh_record: the norm in the exponent
                         const float4 *r = S.ghc + 3 * (s.ghc_off + c);
                         const float4 g0 = r[0], g1 = r[1];
-                        const float nu = (vlos - g0.x) * g0.y;
-                        const float m = nu * g0.z;
-                        const float e = gh_exp(-0.5f * nu * m);
-                        float q = fmaf(g1.w, m, g1.z);
+                        const float P4 = r[2].x;
+                        const float dv = vlos - g0.x, m = dv * g0.y;
+                        const float e = ex2_ftz(fmaf(dv * m, g0.z, g0.w));
+                        float q = fmaf(P4, m, g1.w);
+                        q = fmaf(q, m, g1.z);
                         q = fmaf(q, m, g1.y);
                         q = fmaf(q, m, g1.x);
-                        q = fmaf(q, m, g0.w);
                         dot = dot + e * q;
                     } else {
                         const R *g = S.gh + s.gh_off + 5 * c;
@@ -639,7 +640,7 @@ __device__ __forceinline__ void particle(const PassArgs &a, const PassSmem<R> &S
             t.bad = true;       // negative, -0 or NaN weight
         }
     }
-    if (fl & F_PUSH) kdk<R, PK>(x, y, z, vx, vy, vz, a, S.sh);
+    if (fl & F_PUSH) kdk<R, PK>(x, y, z, vx, vy, vz, a, S.sh, i);
     if (fl & F_SCAT) {
         R X = x, Ys = z * sn - y * cs, vlos = vy * sn + vz * cs;
         // the scattered weight is a function of the stored (double) weight
@@ -792,13 +793,14 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
                 R P[5] = {R(0), R(0), R(0), R(0), R(0)};
                 if (fl & F_UPD) {
                     const R *cf = (const R *)a.coef + st.obs_off + 5 * c;
-                    gh_quartic<R>(t2, nrm, cf[0], cf[1], cf[2], cf[3], cf[4], P);
+                    // the compiled FP32C record carries the norm in its exponent
+                    gh_quartic<R>(t2, GHC ? R(1) : nrm, cf[0], cf[1], cf[2], cf[3], cf[4], P);
                 }
                 if constexpr (GHC) {
+                    float4 rec[3];
+                    gh_record(g[0], g[1], g[2], t2, nrm, (const float *)P, rec);
                     float4 *rc = (float4 *)S.ghc + 3 * (st.ghc_off + c);
-                    rc[0] = make_float4(g[0], g[1], g[2], P[0]);
-                    rc[1] = make_float4(P[1], P[2], P[3], P[4]);
-                    rc[2] = make_float4(t2, nrm, 0.f, 0.f);
+                    rc[0] = rec[0]; rc[1] = rec[1]; rc[2] = rec[2];
                 } else {
                     R *Pd = (R *)S.gpoly + st.gh_off + 5 * c;
                     for (int q = 0; q < 5; ++q) Pd[q] = P[q];

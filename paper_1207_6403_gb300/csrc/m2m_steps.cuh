@@ -244,12 +244,12 @@ __global__ void __launch_bounds__(1024, 1) k_steps(const __grid_constant__ Steps
                 R P[5] = {R(0), R(0), R(0), R(0), R(0)};
                 if (upd) {
                     const R *cf = S.coef + st.obs_off + 5 * c;
-                    gh_quartic<R>(t2, nrm, cf[0], cf[1], cf[2], cf[3], cf[4], P);
+                    gh_quartic<R>(t2, R(1), cf[0], cf[1], cf[2], cf[3], cf[4], P);   // the norm: in the exponent
                 }
+                float4 rec[3];
+                gh_record(g[0], g[1], g[2], t2, nrm, P, rec);
                 float4 *rc = (float4 *)S.ghc + 3 * (st.ghc_off + c);
-                rc[0] = make_float4(g[0], g[1], g[2], P[0]);
-                rc[1] = make_float4(P[1], P[2], P[3], P[4]);
-                rc[2] = make_float4(t2, nrm, 0.f, 0.f);
+                rc[0] = rec[0]; rc[1] = rec[1]; rc[2] = rec[2];
             }
         }
         __syncthreads();

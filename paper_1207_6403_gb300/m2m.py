@@ -120,6 +120,7 @@ def library():
         "m2m_velocity_moments": (c_int32, [P, POINTER(c_double), c_int32, POINTER(c_double)]),
         "m2m_set_timing": (c_int32, [P, c_int32]),
         "m2m_set_persistent": (c_int32, [P, c_int32]),
+        "m2m_set_force_cache": (c_int32, [P, c_int32]),
         "m2m_test_barrier_stall": (c_int32, [P, c_int64]),
         "m2m_get_timing": (c_int32, [P, POINTER(m2m_timing)]),
         "m2m_get_sh_table": (c_int32, [P, POINTER(c_double)]),
@@ -289,6 +290,9 @@ class Context:
     def m2m_shard_prior_finish(self, cell_sums, cell_counts):
         _check(library().m2m_shard_prior_finish(self.ptr, c_void_p(cell_sums.data_ptr()),
                                                 c_void_p(cell_counts.data_ptr())), self.ptr)
+
+    def m2m_set_force_cache(self, enable=True):
+        _check(library().m2m_set_force_cache(self.ptr, 1 if enable else 0), self.ptr)
 
     def m2m_set_persistent(self, enable=True):
         _check(library().m2m_set_persistent(self.ptr, 1 if enable else 0), self.ptr)

@@ -282,3 +282,22 @@ def test_full_size_triaxial_tables_and_push_sampled():
     s1 = O.kdk(*s0, P.potential, P.dt, ref)
     for a, k in zip(s1, ("x", "y", "z", "vx", "vy", "vz")):
         np.testing.assert_allclose(g1[k][idx], a, rtol=0, atol=2e-6 * np.abs(a).max())
+
+
+def test_kept_forces_equal_evaluated_forces():
+    """As for the axisymmetric expansion: FP32C steps with the force kept
+    between pushes equal the steps that evaluate it twice, bit for bit."""
+    P = tri_problem(6001, "fp32c", K=64, period=5)
+    out = []
+    for keep in (True, False):
+        ctx = B.from_problem(P, "fp32c")
+        ctx.m2m_set_force_cache(keep)
+        ctx.m2m_step(12)
+        ctx.m2m_push(3)
+        ctx.m2m_step(9)
+        out.append((ctx.state(), ctx.m2m_get_obs()[0]))
+        ctx.m2m_free()
+    (g1, y1), (g0, y0) = out
+    for k in ("x", "y", "z", "vx", "vy", "vz", "w"):
+        assert np.array_equal(g1[k], g0[k]), k
+    assert np.array_equal(y1, y0)
