@@ -263,6 +263,34 @@ __device__ __forceinline__ void record_warp(const double *chi, int nch, const do
     }
 }
 
+// ----------------------------------------------------------------- staging
+// Copy n elements of T from global to shared memory, every load of a thread
+// issued before its stores: 16-byte vectors (src and dst 16-byte aligned),
+// up to U per thread in registers, then the scalar tail.  A plain loop that
+// stores each element before loading the next waits one memory latency per
+// element, since a store through a generic pointer may alias the next load.
+// `src` may be written by the preceding kernel (read past L1).
+template <int U, class T>
+__device__ __forceinline__ void stage(T *dst, const T *src, int n, int tid, int nt) {
+    constexpr int V = 16 / sizeof(T);
+    const int n4 = n / V;
+    const int4 *s4 = (const int4 *)src;
+    int4 *d4 = (int4 *)dst;
+    int4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int k = tid + u * nt;
+        if (k < n4) v[u] = __ldcg(s4 + k);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int k = tid + u * nt;
+        if (k < n4) d4[k] = v[u];
+    }
+    for (int k = tid + U * nt; k < n4; k += nt) d4[k] = __ldcg(s4 + k);
+    for (int k = V * n4 + tid; k < n; k += nt) dst[k] = src[k];
+}
+
 // ----------------------------------------------------------------- k_pass
 // Dynamic shared memory of pass_body (host side; the same order and
 // rounding as the carve-up at the top of pass_body, without the pipeline's
@@ -766,19 +794,18 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const int bid, cons
     }
     for (int k = threadIdx.x; k < a.edge_len; k += NT) {
         const R *et = (const R *)a.edge_tab;
-        ((R *)S.edges)[k] = et[k];
+        const R e0 = et[k], e1 = k + 1 < a.edge_len ? et[k + 1] : R(INFINITY);
+        ((R *)S.edges)[k] = e0;
         Pair<R> pr;
-        pr.x = et[k];
-        pr.y = k + 1 < a.edge_len ? et[k + 1] : R(INFINITY);
+        pr.x = e0;
+        pr.y = e1;
         ((Pair<R> *)S.epair)[k] = pr;
     }
-    for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
-    if (FX && L == 1)
-        for (int k = threadIdx.x; k < a.sets[1].pmap_len; k += NT) ((short *)S.pmap)[k] = a.sets[1].pmap[k];
+    stage<2>((R *)S.gh, (const R *)a.gh_tab, a.gh_len, threadIdx.x, NT);
+    if (FX && L == 1) stage<1>((short *)S.pmap, a.sets[1].pmap, a.sets[1].pmap_len, threadIdx.x, NT);
     griddep_wait();
-    if (fl & F_UPD)
-        for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = ((const R *)a.coef)[k];
-    for (int k = threadIdx.x; k < sh_len; k += NT) ((R *)S.sh)[k] = ((const R *)a.sh_tab)[k];
+    if (fl & F_UPD) stage<4>((R *)S.coef, (const R *)a.coef, nobs, threadIdx.x, NT);
+    if (sh_len) stage<4>((R *)S.sh, (const R *)a.sh_tab, sh_len, threadIdx.x, NT);
     if (L != 0 && (GHC || (fl & F_UPD))) {
         // E[H_n] over N(m, t2) as polynomials in m (van der Marel & Franx
         // H_0..H_4), weighted by this step's coefficients of the cell (0
