@@ -196,19 +196,20 @@ __global__ void __launch_bounds__(1024, 1) k_steps(const __grid_constant__ Steps
     const int nit = (int)((nch - b + gw - 1) / gw);
     // the block's observables in the residual
     const int j0 = (int)((long long)nobs * b / G), j1 = (int)((long long)nobs * (b + 1) / G);
+    const bool vec = (nobs & 3) == 0;       // coefficients readable as float4
 
     // fixed tables, once per launch
     for (int k = threadIdx.x; k < a.edge_len; k += NT) {
         const R *et = (const R *)a.edge_tab;
-        const R e0 = et[k], e1 = k + 1 < a.edge_len ? et[k + 1] : R(INFINITY);
-        ((R *)S.edges)[k] = e0;
+        ((R *)S.edges)[k] = et[k];
         Pair<R> pr;
-        pr.x = e0;
-        pr.y = e1;
+        pr.x = et[k];
+        pr.y = k + 1 < a.edge_len ? et[k + 1] : R(INFINITY);
         ((Pair<R> *)S.epair)[k] = pr;
     }
-    stage<2>((R *)S.gh, (const R *)a.gh_tab, a.gh_len, threadIdx.x, NT);
-    if (L == 1) stage<1>((short *)S.pmap, a.sets[1].pmap, a.sets[1].pmap_len, threadIdx.x, NT);
+    for (int k = threadIdx.x; k < a.gh_len; k += NT) ((R *)S.gh)[k] = ((const R *)a.gh_tab)[k];
+    if (L == 1)
+        for (int k = threadIdx.x; k < a.sets[1].pmap_len; k += NT) ((short *)S.pmap)[k] = a.sets[1].pmap[k];
     if (threadIdx.x == 0) { mmk[0] = fkey(INFINITY); mmk[1] = fkey(-INFINITY); mmk[2] = 0; }
 
     const float fs = a.fx_shift <= 127 ? __int_as_float((a.fx_shift + 127) << 23) : INFINITY;
@@ -223,7 +224,14 @@ __global__ void __launch_bounds__(1024, 1) k_steps(const __grid_constant__ Steps
         // this step's coefficients (the previous step's residual wrote them
         // during this launch: read past L1); the histogram cleared while
         // they arrive
-        if (upd) stage<2>((R *)S.coef, (const R *)r.coef_r, nobs, threadIdx.x, NT);
+        if (upd) {
+            if (vec) {
+                for (int k = threadIdx.x; k < nobs / 4; k += NT)
+                    ((float4 *)S.coef)[k] = __ldcg((const float4 *)r.coef_r + k);
+            } else {
+                for (int k = threadIdx.x; k < nobs; k += NT) ((R *)S.coef)[k] = __ldcg((const R *)r.coef_r + k);
+            }
+        }
         for (int k = threadIdx.x; k < 3 * nobs4 / 4; k += NT) ((int4 *)S.hL)[k] = make_int4(0, 0, 0, 0);
         __syncthreads();
         // the GH records of this step's update
