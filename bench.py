@@ -60,7 +60,7 @@ PROFILE_JSON = os.path.join(ROOT, "profiles", "k_pass_flat_log_4M.json")
 # the device code of the profiled step pass (its template, the helpers it
 # inlines and the unit that instantiates it): the recorded DRAM traffic is
 # used only while these are unchanged
-KERNEL_SOURCES = ("m2m_device.cuh", "m2m_kernels.cuh", "m2m_steps.cuh", "m2m_steps_f32.cu")
+KERNEL_SOURCES = ("m2m_device.cuh", "m2m_kernels.cuh", "m2m_steps.cuh", "m2m_steps_f32.cu", "m2m_pass_f32.cu")
 
 
 def src_hash():
@@ -70,6 +70,22 @@ def src_hash():
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, n, steps_per_launch):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the
+    committed ncu capture (profiles/k_pass_flat_log_4M.json: one entry per
+    kernel, per step), or None when the capture is of other device code or
+    another particle count."""
+    try:
+        with open(PROFILE_JSON) as f:
+            prof = json.load(f)
+    except Exception:
+        return None
+    e = prof.get("k_steps" if kernel.startswith("k_steps") else "k_pass")
+    if not e or e.get("src_sha") != src_hash() or e.get("n") != n:
+        return None
+    return e["dram_bytes_per_step"] * steps_per_launch
 
 
 def peaks():
@@ -292,6 +308,7 @@ def run_reference(args, D):
 
 # ------------------------------------------------------------ our arm
 def run_ours(args, D):
+    import numpy as np
     import torch
     from paper_1207_6403_gb300 import m2m as B
     dev = f"cuda:{D.local}"
@@ -304,6 +321,9 @@ def run_ours(args, D):
     # histogram privatisation autotuned on warm-up steps)
     ctx = B.from_problem(P, "fp32c", device=dev)
     tuning = ctx.m2m_autotune(max(25, args.warmup // 4), args.tune_cache)
+    if args.launch != "auto":
+        ctx.m2m_set_persistent(args.launch == "persistent")
+        tuning["launch"] = args.launch
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()                     # reset the launch counter
@@ -337,14 +357,7 @@ def run_ours(args, D):
     pass_ms = launch_ms / steps_per_launch
     achieved = BYTES_PER_PARTICLE_FP32C * n * steps_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = None
-    try:
-        with open(PROFILE_JSON) as f:
-            prof = json.load(f)
-        if prof.get("src_sha") == src_hash():
-            traffic = prof.get("traffic_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = measured_traffic(kernel, n, steps_per_launch)
     rec = ctx.m2m_get_record()
     ctx.m2m_free()
 
@@ -373,14 +386,26 @@ def run_ours(args, D):
     wrel = float(((ca.t["w"] - cb.t["w"]).abs() / cb.t["w"].abs().clamp_min(1e-300)).max().item())
     ca.m2m_free()
     cb.m2m_free()
-    ca, cb = B.from_problem(P, "fp32c", device=dev), B.from_problem(P, "fp64", device=dev)
+    # (the FP64 form starts from the FP32 positions, so both compare the
+    # same values against the edges; the projected coordinates are still
+    # computed in each form's precision, so a particle within rounding of a
+    # sky-cell edge can fall on either side: those are counted apart)
+    from paper_1207_6403_gb300 import inputs as I
+    P32 = I.Problem(**{**P.__dict__, "pos": P.pos.astype(np.float32).astype(np.float64),
+                       "vel": P.vel.astype(np.float32).astype(np.float64)})
+    ca, cb = B.from_problem(P, "fp32c", device=dev), B.from_problem(P32, "fp64", device=dev)
     for _ in range(50):
         for c in (ca, cb):
             c.m2m_observe(1)
             c.m2m_update_weights()
     torch.cuda.synchronize()
     wdiff = ((ca.t["w"] - cb.t["w"]).abs() / cb.t["w"].abs().clamp_min(1e-300))
+    same = (ca.m2m_get_cells()[0] == cb.m2m_get_cells()[0]).all(dim=0)
+    nd = int((~same).sum().item())
     wrel_fixed = {"max": float(wdiff.max().item()), "median": float(wdiff.median().item()),
+                  "max_same_cells": float(wdiff[same].max().item()),
+                  "particles_in_other_cells": nd,
+                  "max_other_cells": float(wdiff[~same].max().item()) if nd else 0.0,
                   "w_change_median": float(((cb.t["w"] - torch.as_tensor(P.w0, device=dev)).abs()
                                             / torch.as_tensor(P.w0, device=dev)).median().item())}
     ca.m2m_free()
@@ -616,6 +641,9 @@ def run_single(args, D):
     stream = torch.cuda.current_stream()
     ctx = B.from_problem(P, "fp32c", device=dev)
     tuning = ctx.m2m_autotune(max(25, args.warmup // 4), args.tune_cache)
+    if args.launch != "auto":
+        ctx.m2m_set_persistent(args.launch == "persistent")
+        tuning["launch"] = args.launch
     ctx.m2m_step(args.warmup)
     torch.cuda.synchronize()
     ctx.m2m_get_timing()
@@ -724,6 +752,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "sh-tri",
                                                                "ifu-lut", "ifu-lut-seeing", "recovery"])
+    ap.add_argument("--launch", default="auto", choices=["auto", "separate", "persistent"],
+                    help="FP32C step launches: the autotuner's choice, one launch per stage, or persistent "
+                         "multi-step launches (for profiling one kind)")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON-lines autotuning cache: a run under a profiler reuses the plain run's choice")
     args = ap.parse_args()
