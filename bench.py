@@ -720,7 +720,7 @@ def run_recovery(args, D):
     r_edges = np.geomspace(0.2, 5.0, 9)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out, target = RC.recovery(n, steps, r_edges, device=dev)
+    out, target = RC.recovery(n, steps, r_edges, device=dev, eps_scale=args.eps_scale)
     secs = D.max(time.perf_counter() - t0)
     if D.rank == 0:
         rm = np.sqrt(r_edges[:-1] * r_edges[1:])
@@ -734,6 +734,7 @@ def run_recovery(args, D):
                 "config": {"workload": f"moving-priors: N={n:,} Hernquist stars, Osipkov-Merritt-like target "
                                        "r_a = 1; initial models isotropic, radial (r_a = 0.3), tangential "
                                        "(beta = -0.5); (E, L^2/L_c^2) 64x32 priors every 25 steps",
+                           "eps_scale": args.eps_scale,
                            "shell_radii": [round(float(v), 3) for v in rm]},
                 "beta_target": [round(float(v), 3) for v in target],
                 "beta_target_formula": [round(float(v * v / (v * v + 1.0)), 3) for v in rm],
@@ -752,6 +753,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "sh-tri",
                                                                "ifu-lut", "ifu-lut-seeing", "recovery"])
+    ap.add_argument("--eps-scale", type=float, default=1.0,
+                    help="recovery workload: multiply the adaptation rate epsilon")
     ap.add_argument("--launch", default="auto", choices=["auto", "separate", "persistent"],
                     help="FP32C step launches: the autotuner's choice, one launch per stage, or persistent "
                          "multi-step launches (for profiling one kind)")

@@ -23,10 +23,13 @@ def anisotropy(moments):
         return 1.0 - (m[:, 2] + m[:, 3]) / (2.0 * m[:, 1])
 
 
-def recovery(n, nsteps, r_edges, seed=3, precision="fp32c", device="cuda:0", initial=INITIAL):
+def recovery(n, nsteps, r_edges, seed=3, precision="fp32c", device="cuda:0", initial=INITIAL,
+             eps_scale=1.0):
     """Returns {name: (beta_initial, beta_final, record)} for every initial
-    model, and the target's beta on the same shells (r_edges: edges of r)."""
+    model, and the target's beta on the same shells (r_edges: edges of r).
+    eps_scale multiplies the workload's adaptation rate epsilon."""
     P = I.make_problem("moving-priors", n=n, precision=precision)
+    P.eps = P.eps * eps_scale
     Y = B.observe_targets(P, precision, device)
     P = P.with_targets(Y)
     e2 = np.asarray(r_edges, np.float64) ** 2
