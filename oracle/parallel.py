@@ -60,6 +60,10 @@ def _worker(conn):
                 E = T(0.5) * ((c["vx"] * c["vx"] + c["vy"] * c["vy"]) + c["vz"] * c["vz"]) + \
                     O.potential(c["x"], c["y"], c["z"], P.potential)
                 Lz = c["x"] * c["vy"] - c["y"] * c["vx"]
+                if P.prior.kind == "e_l2":          # L^2 = (Lx*Lx + Ly*Ly) + Lz*Lz, range [0, max]
+                    Lx = c["y"] * c["vz"] - c["z"] * c["vy"]
+                    Ly = c["z"] * c["vx"] - c["x"] * c["vz"]
+                    Lz = (Lx * Lx + Ly * Ly) + Lz * Lz
                 c["E"], c["Lz"] = E, Lz
                 out.append((cid, float(E.min()), float(E.max()), float(np.abs(Lz).max())))
             conn.send(out)
@@ -69,7 +73,7 @@ def _worker(conn):
             for cid in sorted(chunks):
                 c = chunks[cid]
                 iE = O._count_edges_le(c["E"], lo, hi, P.prior.nE)
-                iL = O._count_edges_le(c["Lz"], -lm, lm, P.prior.nL)
+                iL = O._count_edges_le(c["Lz"], 0.0 if P.prior.kind == "e_l2" else -lm, lm, P.prior.nL)
                 c["cell"] = iE * P.prior.nL + iL
                 out.append((cid, np.bincount(c["cell"], weights=c["w"], minlength=P.prior.ncells),
                             np.bincount(c["cell"], minlength=P.prior.ncells)))
@@ -150,7 +154,7 @@ class ParallelOracle:
         Delta, Dt, coef, chi2, chi2_raw = O.residual(yv, P.Y, P.sigma, self.Dt, P.alpha, False)
         self._all(("update", coef))
         self.t += 1
-        if P.prior.kind == "e_lz" and self.t % P.prior.period == 0:
+        if P.prior.kind in ("e_lz", "e_l2") and self.t % P.prior.period == 0:
             rng = self._all(("energy",))
             lo, hi, lm = min(r[1] for r in rng), max(r[2] for r in rng), max(r[3] for r in rng)
             cs = self._all(("cells", lo, hi, lm))
@@ -160,8 +164,8 @@ class ParallelOracle:
                 sums = sums + c[1]
                 cnt = cnt + c[2]
             self._all(("gather", sums, cnt))
-        elif P.prior.kind not in ("flat", "e_lz") and self.t % P.prior.period == 0:
-            raise NotImplementedError("parallel oracle: (E, L_z) or flat priors only")
+        elif P.prior.kind not in ("flat", "e_lz", "e_l2") and self.t % P.prior.period == 0:
+            raise NotImplementedError("parallel oracle: (E, L_z), (E, L^2) or flat priors only")
         self.Dt, self.y_obs = Dt, yv
         return dict(t=self.t, chi2=chi2, chi2_raw=chi2_raw, S=S, sum_w=W, F=O.merit(chi2, S, P.mu))
 

@@ -852,6 +852,28 @@ def test_parallel_oracle_equals_the_serial_oracle():
         assert a["sum_w"] == pytest.approx(b["sum_w"], rel=1e-12)
 
 
+def test_parallel_oracle_with_e_l2_priors_equals_the_serial_oracle():
+    """The same with (E, L^2) prior cells in a Hernquist potential."""
+    from oracle import m2m as O
+    from oracle.parallel import ParallelOracle
+    P = I.make_problem("moving-priors", n=70_000, precision="fp32c")
+    P.prior = I.PriorSpec("e_l2", 16, 8, 25)
+    Y = O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos)
+    P = P.with_targets(Y)
+    po = ParallelOracle(P, "fp32c", nproc=2)
+    try:
+        for _ in range(26):
+            po.step()
+        g = po.state()
+    finally:
+        po.close()
+    st = O.run(P, 26, precision="fp32c")
+    assert np.array_equal(g["x"], st.x)
+    np.testing.assert_allclose(g["w"], st.w, rtol=1e-12)
+    np.testing.assert_allclose(g["what"], st.what, rtol=1e-12)
+    assert not np.allclose(st.what, P.what0)       # the recompute after step 25 changed w_hat
+
+
 def test_e_l2_prior_cells_against_a_brute_force_loop():
     """(E, L^2) cells (triaxial priors): each particle's E and L^2 formed
     one at a time in float32 in the stated order, its cell found by scanning
