@@ -9,7 +9,7 @@ synthetic (Philox-seeded realisations), resident in HBM when timing starts;
 the particle arrays (288 MB per step of traffic) are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload flat-log|batched|scan|sh|sh-tri|ifu-lut|ifu-lut-seeing|recovery]
+                  [--workload flat-log|batched|scan|sh|sh-tri|sh-full|ifu-lut|ifu-lut-seeing|recovery]
 
 --workload batched times the 48 trial-potential models (Hernquist stars in
 Hernquist + NFW halos on a 6 x 8 grid, N log-uniform in [1e5, 2e6], about
@@ -21,7 +21,9 @@ spherical-harmonic expansion of its own particles (even l <= 8, 256 nodes,
 recomputed every 50 steps).
 --workload sh-tri times a triaxial model (N = 4,000,000) in the triaxial
 expansion of its own particles (even l <= 8, even m >= 0: 15 terms, 256
-nodes, recomputed every 50 steps) with (E, L^2) moving priors.
+nodes, recomputed every 50 steps) with (E, L^2) moving priors;
+--workload sh-full the same model rotated and shifted (no symmetry) in the
+expansion with every l <= 4 and every m (25 terms, 128 nodes).
 --workload ifu-lut times the flat-log galaxy observed through 300 Voronoi
 bins and a long slit (apertures given by sky-pixel lookup tables);
 --workload ifu-lut-seeing the same through a Gaussian PSF.
@@ -606,6 +608,16 @@ SINGLE = {
                  "even-m >= 0, l <= 8 expansion (15 terms) of its own weighted particles on 256 log nodes in "
                  "[1e-3, 100], recomputed every 50 steps; 100 shells + 60 annuli x h0..h4, (E, L^2) 64x32 "
                  "moving priors every 25 steps, dt=0.01"),
+    "sh-full": dict(
+        problem="sh-full", n=4_000_000, seeds=(14, 15), stride=64,
+        metric="M2M particle-steps/s, self-consistent full expansion l <= 4 (N=4M)",
+        dtype="f32 (FP32-compensated; f64 weights, exact fixed-point expansion sums)",
+        kernel="k_pass (step pass: update + push in the full expansion + scatter)",
+        describe="sh-full: N={n:,} triaxial Hernquist-like particles (a=1, axes 1:0.8:0.6) rotated by z-y-z "
+                 "Euler angles (0.5, 0.7, 0.3) and shifted by (0.05, -0.03, 0.02), in the every-l <= 4, every-m "
+                 "expansion (25 terms) of its own weighted particles on 128 log nodes in [1e-3, 100], "
+                 "recomputed every 50 steps; 100 shells + 60 annuli x h0..h4, (E, L^2) 64x32 moving priors "
+                 "every 25 steps, dt=0.01"),
     "ifu-lut": dict(
         problem="ifu-lut", n=4_000_000, seeds=(5, 6), stride=8,
         metric="M2M particle-steps/s, IFU Voronoi bins + long slit by aperture lookup tables (N=4M)",
@@ -751,7 +763,7 @@ def main():
     ap.add_argument("--n", "--particles", dest="n", type=int, default=N_DEFAULT,
                     help="particles per GPU (--particles also passes through torchrun)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "sh-tri",
+    ap.add_argument("--workload", default="flat-log", choices=["flat-log", "batched", "scan", "sh", "sh-tri", "sh-full",
                                                                "ifu-lut", "ifu-lut-seeing", "recovery"])
     ap.add_argument("--eps-scale", type=float, default=1.0,
                     help="recovery workload: multiply the adaptation rate epsilon")

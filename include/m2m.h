@@ -115,15 +115,21 @@ typedef struct m2m_ctx m2m_ctx;          /* opaque, library-owned */
  *             F_lm(r) = 4 pi/(2l+1) [A_lm(r)/r^(l+1) + B_lm(r) r^l],
  *           A_lm, B_lm the sums of w_i Y_lm(x_i) r_i^l and w_i Y_lm(x_i)
  *           r_i^-(l+1) inside / outside r; nodes, interpolation, side sums,
- *           schedule and placement as for SH. */
+ *           schedule and placement as for SH.
+ *   SH_FULL p = {K, rmin, rmax, period}: the same for models with no
+ *           symmetry: every term up to l = 4, t = l*l + l + m for
+ *           m = -l..l (25 terms), Y_lm = c_l|m| Q_l^|m|(mu) C_m with
+ *           C_m = Re u^m for m >= 0 and Im u^|m| for m < 0. */
 #define M2M_MAX_POT 4
 #define M2M_POT_HERNQUIST 1
 #define M2M_POT_NFW       2
 #define M2M_POT_LOG       3
 #define M2M_POT_SH        4
 #define M2M_POT_SH_TRI    5
+#define M2M_POT_SH_FULL   6
 #define M2M_SH_ROW        21   /* values per node in m2m_get_sh_table (SH) */
 #define M2M_TRI_ROW       61   /* values per node in m2m_get_sh_table (SH_TRI) */
+#define M2M_FULL_ROW      101  /* values per node in m2m_get_sh_table (SH_FULL) */
 typedef struct {
     int32_t kind;
     int32_t reserved;
@@ -264,7 +270,9 @@ int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot);
  * -sum P_l F_l.  out must hold K * M2M_SH_ROW doubles.  For SH_TRI: K rows
  * of M2M_TRI_ROW, the same five blocks with the 15 terms (l, m) = (0,0),
  * (2,0), (2,2), (4,0), .., (8,8) each (F_lm, slopes, D_lm, slopes, r_k);
- * out must hold K * M2M_TRI_ROW doubles.  Synchronises.
+ * out must hold K * M2M_TRI_ROW doubles.  For SH_FULL: K rows of
+ * M2M_FULL_ROW, the blocks of its 25 terms in the order t = l*l + l + m;
+ * out must hold K * M2M_FULL_ROW doubles.  Synchronises.
  * M2M_ERR_STATE if the potential has no SH or SH_TRI component. */
 int m2m_get_sh_table(m2m_ctx *ctx, double *out);
 

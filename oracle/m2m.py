@@ -53,7 +53,7 @@ def state_dtype(precision):
 # spherical-harmonic component (kind 'sh', params (K, rmin, rmax, period),
 # last in the list) whose tables are part of the state
 # --------------------------------------------------------------------------
-SH_KINDS = ("sh", "sh_tri")
+SH_KINDS = ("sh", "sh_tri", "sh_full")
 
 
 def _split(comps):
@@ -64,13 +64,15 @@ def _split(comps):
 
 def sh_tables(x, y, z, w, comp):
     """(F, D, nodes) of the expansion of the weighted particles: the
-    axisymmetric even-l expansion (kind 'sh', :mod:`oracle.sh`) or the
-    triaxial one (kind 'sh_tri': even l, even m >= 0, l <= 8,
-    :mod:`oracle.sh_full`)."""
+    axisymmetric even-l expansion (kind 'sh', :mod:`oracle.sh`), the
+    triaxial one (kind 'sh_tri': even l, even m >= 0, l <= 8) or the general
+    one (kind 'sh_full': every l <= 4 and m, :mod:`oracle.sh_full`)."""
     K, rmin, rmax = int(comp.params[0]), comp.params[1], comp.params[2]
     rn = _sh.nodes(rmin, rmax, K)
     if comp.kind == "sh_tri":
         return _shf.tri_tables(x, y, z, w, rn)
+    if comp.kind == "sh_full":
+        return _shf.full_tables(x, y, z, w, rn)
     A, B = _sh.coefficients(x, y, z, w, rn)
     F, D = _sh.tables(A, B, rn)
     return F, D, rn
@@ -82,8 +84,11 @@ def acceleration(x, y, z, comps, sh=None):
     ax, ay, az = _analytic_acceleration(x, y, z, _split(comps)[0])
     if sh is not None:
         T = x.dtype.type
-        if _split(comps)[1].kind == "sh_tri":
+        kind = _split(comps)[1].kind
+        if kind == "sh_tri":
             bx, by, bz = _shf.tri_acceleration(x, y, z, *sh)
+        elif kind == "sh_full":
+            bx, by, bz = _shf.full_acceleration(x, y, z, *sh)
         else:
             bx, by, bz = _sh.acceleration(x, y, z, *sh)
         ax, ay, az = ax + bx.astype(T), ay + by.astype(T), az + bz.astype(T)
@@ -93,8 +98,11 @@ def acceleration(x, y, z, comps, sh=None):
 def potential(x, y, z, comps, sh=None):
     phi = _analytic_potential(x, y, z, _split(comps)[0])
     if sh is not None:
-        if _split(comps)[1].kind == "sh_tri":
+        kind = _split(comps)[1].kind
+        if kind == "sh_tri":
             phi = phi + _shf.tri_potential(x, y, z, *sh).astype(x.dtype)
+        elif kind == "sh_full":
+            phi = phi + _shf.full_potential(x, y, z, *sh).astype(x.dtype)
         else:
             phi = phi + _sh.potential(x, y, z, *sh).astype(x.dtype)
     return phi

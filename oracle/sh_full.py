@@ -264,3 +264,28 @@ def tri_acceleration(x, y, z, F, D, rn):
 
 def tri_potential(x, y, z, F, D, rn):
     return potential_nodes(x, y, z, F, D, rn, LMAX_TRI, triaxial_terms(LMAX_TRI))
+
+
+# --------------------------------------------------------------------------
+# The general expansion of the step (potential kind 'sh_full', parameters
+# (K, rmin, rmax, period)): every term of :func:`index` up to l = 4 (25
+# terms, cosine and sine harmonics), for models with no symmetry, on the
+# same nodes and schedule.
+# --------------------------------------------------------------------------
+LMAX_FULL = 4
+
+
+def full_tables(x, y, z, w, rn):
+    """(F, D, rn) of the general expansion (l <= 4) of the weighted particles."""
+    A, B = coefficients_nodes(x, y, z, w, rn, LMAX_FULL)
+    F, D = tables_nodes(A, B, rn, LMAX_FULL)
+    return F, D, rn
+
+
+def full_acceleration(x, y, z, F, D, rn):
+    return acceleration_nodes(x, y, z, F, D, rn, LMAX_FULL)
+
+
+def full_potential(x, y, z, F, D, rn):
+    return potential_nodes(x, y, z, F, D, rn, LMAX_FULL)
+

@@ -105,8 +105,9 @@ struct m2m_ctx {
     bool pipe;           // use the bulk-copy pipelined pass where it applies
     int fx_atomic;       // FP32C histogram flush: global integer atomics (1) or slots (0)
     // self-consistent expansion potential (kind M2M_POT_SH, or M2M_POT_SH_TRI
-    // with sh_tri set): sh_row table values per radial node
-    bool sh_on, sh_tri;
+    // or M2M_POT_SH_FULL with sh_basis 1 or 2): sh_row table values per node
+    bool sh_on;
+    int sh_basis;        // 0 axisymmetric, 1 triaxial, 2 full (l <= 4)
     int sh_K, sh_period, sh_row;
     double sh_rmin, sh_rmax;
     int sh_gmode;
@@ -374,6 +375,7 @@ int potential_signature(const m2m_ctx *c) {
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_LOG) return PK_LOG;
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH) return PK_SH;
     if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH_TRI) return PK_SH_TRI;
+    if (c->npot == 1 && c->pot[0].kind == M2M_POT_SH_FULL) return PK_SH_FULL;
     if (c->npot == 2 && c->pot[0].kind == M2M_POT_HERNQUIST && c->pot[1].kind == M2M_POT_NFW) return PK_HERNQUIST_NFW;
     return PK_ANY;
 }
@@ -636,7 +638,7 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         } else if (pot[k].kind == M2M_POT_NFW) {
             if (!(p[0] > 0 && p[1] > 0)) return set_err(ctx, M2M_ERR_ARG, "nfw needs rho_s>0, r_s>0");
             d.c[0] = 4.0 * M_PI * p[0] * p[1] * p[1] * p[1]; d.c[1] = p[1]; d.c[2] = 1.0 / p[1];
-        } else if (pot[k].kind == M2M_POT_SH || pot[k].kind == M2M_POT_SH_TRI) {
+        } else if (pot[k].kind == M2M_POT_SH || pot[k].kind == M2M_POT_SH_TRI || pot[k].kind == M2M_POT_SH_FULL) {
             const int K = (int)p[0];
             if (k != npot - 1) return set_err(ctx, M2M_ERR_ARG, "the spherical-harmonic component must be last");
             if (!((double)K == p[0] && K >= 4 && K <= SH_MAXK && p[1] > 0 && p[2] > p[1] && isfinite(p[2]) &&
@@ -654,9 +656,10 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
         for (int j = 0; j < 6; ++j) tmp[k].cf[j] = (float)tmp[k].c[j];
     memcpy(ctx->pot, tmp, sizeof tmp);
     ctx->npot = npot;
-    ctx->sh_tri = npot > 0 && pot[npot - 1].kind == M2M_POT_SH_TRI;
-    ctx->sh_on = npot > 0 && (pot[npot - 1].kind == M2M_POT_SH || ctx->sh_tri);
-    ctx->sh_row = ctx->sh_tri ? TRI_ROW : SH_ROW;
+    const int lastk = npot > 0 ? pot[npot - 1].kind : 0;
+    ctx->sh_basis = lastk == M2M_POT_SH_TRI ? 1 : lastk == M2M_POT_SH_FULL ? 2 : 0;
+    ctx->sh_on = lastk == M2M_POT_SH || lastk == M2M_POT_SH_TRI || lastk == M2M_POT_SH_FULL;
+    ctx->sh_row = ctx->sh_basis == 1 ? TRI_ROW : ctx->sh_basis == 2 ? FULL_ROW : SH_ROW;
     if (ctx->sh_on) {
         const double *p = pot[npot - 1].p;
         ctx->sh_K = (int)p[0];
@@ -669,7 +672,9 @@ int build_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int npot) {
 
 // Side sums of the expansion: 10 per node (A_l, B_l of 5 even l), 30 for
 // the triaxial one (A_lm, B_lm of its 15 terms).
-size_t sh_sums(const m2m_ctx *c) { return (size_t)(c->sh_tri ? 2 * TRI_NT : 10) * c->sh_K; }
+size_t sh_sums(const m2m_ctx *c) {
+    return (size_t)(c->sh_basis == 1 ? 2 * TriBasis::NT : c->sh_basis == 2 ? 2 * FullBasis::NT : 10) * c->sh_K;
+}
 
 // Node tables of the expansion: r_k = rmin (rmax/rmin)^(k/(K-1)), r_(K-1) =
 // rmax, and r_k^2 (for R = float the smallest float >= the double square).
@@ -730,8 +735,9 @@ int sh_recompute(m2m_ctx *ctx) {
     a.sh = ctx->fx_shift + 6;
     a.sum = ctx->d_sh_sum; a.err = ctx->d_err;
     const bool f32 = ctx->prec == M2M_FP32C;
-    void *fn = ctx->sh_tri ? (f32 ? (void *)k_tri_coef<float> : (void *)k_tri_coef<double>)
-                           : (f32 ? (void *)k_sh_coef<float> : (void *)k_sh_coef<double>);
+    void *fn = ctx->sh_basis == 1 ? (f32 ? (void *)k_ex_coef<TriBasis, float> : (void *)k_ex_coef<TriBasis, double>)
+             : ctx->sh_basis == 2 ? (f32 ? (void *)k_ex_coef<FullBasis, float> : (void *)k_ex_coef<FullBasis, double>)
+                                  : (f32 ? (void *)k_sh_coef<float> : (void *)k_sh_coef<double>);
     const size_t sm = sh_coef_smem(ctx);
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 512, sm));
@@ -744,15 +750,22 @@ int sh_recompute(m2m_ctx *ctx) {
         CU(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(512), args, sm, ctx->st));
     }
     const double q = ldexp(1.0, -a.sh);
-    const size_t tsm = ctx->sh_tri ? 8 * sh_sums(ctx) : 160 * (size_t)K;
-    if (ctx->sh_tri) {
+    const size_t tsm = ctx->sh_basis ? 8 * sh_sums(ctx) : 160 * (size_t)K;
+    if (ctx->sh_basis) {
         LaunchTimer lt(ctx, M2M_TK_SH);
-        if (f32)
-            k_tri_tables<float><<<1, 512, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
-                                                          (float *)ctx->d_sh_tab, ctx->d_err);
+        const long long *sum = (const long long *)ctx->d_sh_sum;
+        if (ctx->sh_basis == 1 && f32)
+            k_ex_tables<TriBasis, float><<<1, 512, tsm, ctx->st>>>(sum, K, ctx->d_sh_rnd, q, (float *)ctx->d_sh_tab,
+                                                                   ctx->d_err);
+        else if (ctx->sh_basis == 1)
+            k_ex_tables<TriBasis, double><<<1, 512, tsm, ctx->st>>>(sum, K, ctx->d_sh_rnd, q, (double *)ctx->d_sh_tab,
+                                                                    ctx->d_err);
+        else if (f32)
+            k_ex_tables<FullBasis, float><<<1, 512, tsm, ctx->st>>>(sum, K, ctx->d_sh_rnd, q, (float *)ctx->d_sh_tab,
+                                                                    ctx->d_err);
         else
-            k_tri_tables<double><<<1, 512, tsm, ctx->st>>>((const long long *)ctx->d_sh_sum, K, ctx->d_sh_rnd, q,
-                                                           (double *)ctx->d_sh_tab, ctx->d_err);
+            k_ex_tables<FullBasis, double><<<1, 512, tsm, ctx->st>>>(sum, K, ctx->d_sh_rnd, q,
+                                                                     (double *)ctx->d_sh_tab, ctx->d_err);
         CU(cudaGetLastError());
     } else {
         LaunchTimer lt(ctx, M2M_TK_SH);
@@ -1059,13 +1072,15 @@ int m2m_init(m2m_ctx **ctx_out, int32_t precision, int64_t n, void *x, void *y, 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     std::vector<void *> kfns = {cells_kernel_f32(), cells_kernel_f64(), (void *)k_sh_coef<float>,
                                 (void *)k_sh_coef<double>, (void *)k_sh_tables<float>, (void *)k_sh_tables<double>,
-                                (void *)k_tri_coef<float>, (void *)k_tri_coef<double>,
-                                (void *)k_tri_tables<float>, (void *)k_tri_tables<double>};
+                                (void *)k_ex_coef<TriBasis, float>, (void *)k_ex_coef<TriBasis, double>,
+                                (void *)k_ex_tables<TriBasis, float>, (void *)k_ex_tables<TriBasis, double>,
+                                (void *)k_ex_coef<FullBasis, float>, (void *)k_ex_coef<FullBasis, double>,
+                                (void *)k_ex_tables<FullBasis, float>, (void *)k_ex_tables<FullBasis, double>};
     for (int lay = 0; lay < 5; ++lay) {
         for (int nt : {256, 512, 1024}) kfns.push_back(pass_kernel_f32(nt, lay));
         for (int nt : {256, 512}) kfns.push_back(pass_kernel_f64(nt, lay));
         if (lay) kfns.push_back(pass_kernel_f32_pipe(lay));
-        for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW, PK_SH_TRI})
+        for (int pk : {PK_ANY, PK_HERNQUIST, PK_LOG, PK_SH, PK_HERNQUIST_NFW, PK_SH_TRI, PK_SH_FULL})
                 for (int fl : {F_STEADY, F_STEADY | F_MINMAX, F_PUSH | F_SCAT | F_STATS,
                                F_PUSH | F_SCAT | F_STATS | F_MINMAX, F_CELLS | F_UPD})
                     if (void *f = pass_kernel_f32_compiled(fl, lay, pk)) kfns.push_back(f);
@@ -1154,11 +1169,11 @@ int m2m_potential(m2m_ctx *ctx, const m2m_potential_desc *pot, int32_t npot) {
     int rc0 = finish_update(ctx);
     if (rc0) return rc0;
     const int oldK = ctx->sh_on ? ctx->sh_K : 0;
-    const bool oldtri = ctx->sh_tri;
+    const int oldbasis = ctx->sh_basis;
     const double oldr0 = ctx->sh_rmin, oldr1 = ctx->sh_rmax;
     int rc = build_potential(ctx, pot, npot);
     if (rc || !ctx->sh_on) return rc;
-    if (ctx->sh_K != oldK || ctx->sh_tri != oldtri || ctx->sh_rmin != oldr0 || ctx->sh_rmax != oldr1) {
+    if (ctx->sh_K != oldK || ctx->sh_basis != oldbasis || ctx->sh_rmin != oldr0 || ctx->sh_rmax != oldr1) {
         rc = sh_setup(ctx);
         if (rc) { ctx->sh_on = false; ctx->npot = 0; return rc; }
     }

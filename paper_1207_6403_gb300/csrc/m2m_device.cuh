@@ -429,56 +429,88 @@ __device__ __forceinline__ R sh_phi(R x, R y, R z, const R *T, const PotDev &p) 
     return -s;
 }
 
-// ------------------------------------------------------------ triaxial
-// The triaxial expansion (potential kind 5): the real harmonics a set of
-// particles mirror-symmetric about the three coordinate planes can have,
-// even l <= 8 and even m >= 0 (cosine harmonics), 15 terms indexed
-// t(l, m) = (l/2)(l/2 + 1)/2 + m/2, i.e. (0,0) (2,0) (2,2) (4,0) ... (8,8).
+// ------------------------------------------------- expansions with m != 0
+// Two expansions of the weighted particles in real spherical harmonics
+// beyond the axisymmetric one, each a fixed list of terms t = (l, m):
+//  * triaxial (potential kind 5): the terms a set mirror-symmetric about the
+//    three coordinate planes can have, even l <= 8 and even m >= 0 (cosine
+//    harmonics), 15 terms (0,0) (2,0) (2,2) (4,0) .. (8,8);
+//  * full (kind 6): every term up to l = 4, t = l^2 + l + m for m = -l..l,
+//    25 terms (cosine harmonics for m >= 0, sine harmonics for m < 0).
 // With n = x/r, mu = n_z and u = n_x + i n_y,
-//   Y_lm = c_lm Q_l^m(mu) Re u^m,   Q_l^m = d^m P_l / dmu^m,
-//   c_l0 = N_l0, c_lm = sqrt(2) N_lm, N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
-// which stays regular on the z axis.  Node tables hold, per radial node,
-//   [0..14] F_lm(r_k) = 4 pi/(2l+1) [A_lm(r_k)/r_k^(l+1) + B_lm(r_k) r_k^l]
-//   [15..29] slopes of F to node k+1, [30..44] D_lm = dF_lm/dr,
-//   [45..59] slopes of D, [60] r_k;
-// Phi = -sum Y_lm F_lm(r), a = sum [D_lm Y_lm n + F_lm grad Y_lm] with
-//   grad Y_lm = c_lm [Q_l^(m+1) Re u^m (e_z - mu n) + m Q_l^m (Re u^(m-1),
-//               -Im u^(m-1), 0) - m Q_l^m Re u^m n] / r.
+//   Y_lm = c_l|m| Q_l^|m|(mu) C_m,  C_m = Re u^m (m >= 0), Im u^|m| (m < 0),
+//   Q_l^m = d^m P_l / dmu^m,  c_l0 = N_l0, c_lm = sqrt(2) N_lm,
+//   N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!),
+// regular on the z axis.  Node tables hold, per radial node, NT values of
+//   F_t(r_k) = 4 pi/(2l+1) [A_t(r_k)/r_k^(l+1) + B_t(r_k) r_k^l],
+// then their slopes to node k+1, D_t = dF_t/dr, the slopes of D, and r_k
+// (4 NT + 1 values); Phi = -sum Y_t F_t(r) and, with grad C_m = |m| G_m / r,
+// G_m = (Re u^(m-1), -Im u^(m-1), 0) for m > 0 and (Im u^(|m|-1),
+// Re u^(|m|-1), 0) for m < 0,
+//   a = sum_t [D_t Y_t n + F_t c (Q_l^(|m|+1) C (e_z - mu n)
+//                                + |m| Q_l^|m| (G_m - C n)) / r].
 // The terms are generated one at a time (m outer, l inner, the Q_l^m and
-// Q_l^(m+1) recurrences in l carried along) so that no per-term arrays are
+// Q_l^(m+1) recurrences in l carried along), so that no per-term arrays are
 // live: the particle pass runs it at 64 registers a thread.
-constexpr int TRI_NT = 15;
-constexpr int TRI_ROW = 4 * TRI_NT + 1;
-__host__ __device__ constexpr int tri_t(int l, int m) { return (l / 2) * (l / 2 + 1) / 2 + m / 2; }
-__host__ __device__ constexpr int tri_l(int t) { return t < 1 ? 0 : t < 3 ? 2 : t < 6 ? 4 : t < 10 ? 6 : 8; }
+struct TriBasis {
+    static constexpr int NT = 15, ROW = 4 * NT + 1, LMAX = 8, MSTEP = 2, LSTEP = 2;
+    // slot of l in the radial power tables: l = 0, 2, .., 8 -> 0..4
+    __host__ __device__ static constexpr int slot(int l) { return l / 2; }
+    __host__ __device__ static constexpr int l_of(int t) { return t < 1 ? 0 : t < 3 ? 2 : t < 6 ? 4 : t < 10 ? 6 : 8; }
+    __host__ __device__ static constexpr int t_of(int l, int m) { return (l / 2) * (l / 2 + 1) / 2 + m / 2; }
+    static constexpr bool SINES = false;
+};
+struct FullBasis {
+    static constexpr int NT = 25, ROW = 4 * NT + 1, LMAX = 4, MSTEP = 1, LSTEP = 1;
+    __host__ __device__ static constexpr int slot(int l) { return l; }
+    __host__ __device__ static constexpr int l_of(int t) { return t < 1 ? 0 : t < 4 ? 1 : t < 9 ? 2 : t < 16 ? 3 : 4; }
+    __host__ __device__ static constexpr int t_of(int l, int m) { return l * l + l + m; }
+    static constexpr bool SINES = true;
+};
+// backward names of the triaxial table geometry
+constexpr int TRI_NT = TriBasis::NT;
+constexpr int TRI_ROW = TriBasis::ROW;
+constexpr int FULL_ROW = FullBasis::ROW;
 
-// c_lm of term t: sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), times sqrt(2) for m > 0
-__host__ __device__ constexpr double tri_c(int t) {
-    return t == 0 ? 0.28209479177387814 : t == 1 ? 0.6307831305050401 : t == 2 ? 0.18209140509867988
-         : t == 3 ? 0.8462843753216345 : t == 4 ? 0.063078313050504 : t == 5 ? 0.005960340337611203
-         : t == 6 ? 1.0171072362820548 : t == 7 ? 0.03509353369580661 : t == 8 ? 0.0010678622237644956
-         : t == 9 ? 6.57223766418388e-05 : t == 10 ? 1.1631066229203195 : t == 11 ? 0.023169638523677944
-         : t == 12 ? 0.00036818972564450655 : t == 13 ? 7.878532816214047e-06 : 3.596041786237614e-07;
+// c_lm for l <= 8, 0 <= m <= l (m even or l <= 4 as the bases need)
+__host__ __device__ constexpr double harm_c(int l, int m) {
+    return l == 0 ? 0.28209479177387814
+         : l == 1 ? (m == 0 ? 0.4886025119029199 : 0.48860251190292)
+         : l == 2 ? (m == 0 ? 0.6307831305050401 : m == 1 ? 0.36418281019735976 : 0.18209140509867988)
+         : l == 3 ? (m == 0 ? 0.7463526651802308 : m == 1 ? 0.3046971996429772 : m == 2 ? 0.09635371475468515
+                                                                                 : 0.03933623932844291)
+         : l == 4 ? (m == 0 ? 0.8462843753216345 : m == 1 ? 0.2676186174229157 : m == 2 ? 0.063078313050504
+                     : m == 3 ? 0.016858388283618388 : 0.005960340337611203)
+         : l == 6 ? (m == 0 ? 1.0171072362820548 : m == 2 ? 0.03509353369580661 : m == 4 ? 0.0010678622237644956
+                                                                                 : 6.57223766418388e-05)
+         : (m == 0 ? 1.1631066229203195 : m == 2 ? 0.023169638523677944 : m == 4 ? 0.00036818972564450655
+            : m == 6 ? 7.878532816214047e-06 : 3.596041786237614e-07);
 }
 
-// Calls f(t, l, m, Q_l^m, Q_l^(m+1), Re u^m, Re u^(m-1), Im u^(m-1)) for
-// the 15 terms, m = 0, 2, .., 8 outer and l = m, m+2, .., 8 inner.  Q_l^m by
-// Q_m^m = (2m-1)!!, Q_(m+1)^m = (2m+1) mu Q_m^m, (l-m) Q_l^m = (2l-1) mu
-// Q_(l-1)^m - (l+m-1) Q_(l-2)^m.
-template <class R, class Fn>
-__device__ __forceinline__ void tri_terms(R mu, R nx, R ny, Fn &&f) {
+// Calls f(t, l, m, c, Q_l^|m|, Q_l^(|m|+1), C, Gx, Gy) for every term of
+// basis B: m = 0, MSTEP, .. LMAX outer, l = m, m + LSTEP, .. LMAX inner (the
+// sine term of (l, m) right after the cosine one).  Q_l^m by Q_m^m =
+// (2m-1)!!, Q_(m+1)^m = (2m+1) mu Q_m^m, (l-m) Q_l^m = (2l-1) mu Q_(l-1)^m -
+// (l+m-1) Q_(l-2)^m.
+template <class B, class R, class Fn>
+__device__ __forceinline__ void ex_terms(R mu, R nx, R ny, Fn &&f) {
     R re = R(1), im = R(0), rp = R(0), ip = R(0);    // u^m, u^(m-1)
 #pragma unroll
-    for (int m = 0; m <= 8; m += 2) {
+    for (int m = 0; m <= B::LMAX; m += B::MSTEP) {
         double dfm = 1.0;                              // (2m-1)!!
         for (int k = 1; k <= m; ++k) dfm *= 2 * k - 1;
         R a1 = R(dfm), a2 = R(0);                      // Q_l^m, Q_(l-1)^m at l = m
         R b1 = R(0), b2 = R(0);                        // Q_l^(m+1), Q_(l-1)^(m+1) at l = m
 #pragma unroll
-        for (int l = m; l <= 8; ++l) {
-            if ((l & 1) == 0) f(tri_t(l, m), l, m, a1, b1, re, rp, ip);
-            if (l == 8) break;
-            // step to l + 1
+        for (int l = m; l <= B::LMAX; ++l) {
+            if ((l - m) % B::LSTEP == 0 || B::LSTEP == 1) {
+                if (B::LSTEP == 1 || (l & 1) == 0) {
+                    const R c = R(harm_c(l, m));
+                    f(B::t_of(l, m), l, m, c, a1, b1, re, rp, -ip);
+                    if (B::SINES && m > 0) f(B::t_of(l, -m), l, m, c, a1, b1, im, ip, rp);
+                }
+            }
+            if (l == B::LMAX) break;
             R an, bn;
             if (l == m) an = R(2 * m + 1) * mu * a1;
             else an = (R(2 * l + 1) * mu * a1 - R(l + m) * a2) * R(1.0 / (l + 1 - m));
@@ -487,87 +519,93 @@ __device__ __forceinline__ void tri_terms(R mu, R nx, R ny, Fn &&f) {
             else bn = (R(2 * l + 1) * mu * b1 - R(l + m + 1) * b2) * R(1.0 / (l - m));
             a2 = a1; a1 = an; b2 = b1; b1 = bn;
         }
-        // u^(m+1), u^(m+2)
-        rp = re * nx - im * ny;
-        ip = re * ny + im * nx;
-        re = rp * nx - ip * ny;
-        im = rp * ny + ip * nx;
+        // u^m -> u^(m + MSTEP), keeping u^(m + MSTEP - 1)
+#pragma unroll
+        for (int k = 0; k < B::MSTEP; ++k) {
+            rp = re; ip = im;
+            re = rp * nx - ip * ny;
+            im = rp * ny + ip * nx;
+        }
     }
 }
 
-// Radial factors of a point: F_t(r) = T[t] fa_(l/2) + dr T[15+t] and
-// D_t(r) = T[30+t] da_(l/2) + dr T[45+t] + (l+1) dbs F_t(r) from one table
+// Radial factors of a point: F_t(r) = T[t] fa_slot + dr T[NT+t] and
+// D_t(r) = T[2NT+t] da_slot + dr T[3NT+t] + (l+1) dbs F_t(r) from one table
 // row: linear between nodes (fa = da = 1, dbs = 0); beyond the last node
 // F(K-1) (r_(K-1)/r)^(l+1) and D = -(l+1) F/r (dr = 0, da = 0, dbs = -1/r);
 // inside the first F(0) (r/r_0)^l and D(0) (r/r_0)^max(l-1, 1) (dr = 0).
-template <class R> struct TriRad {
+template <class R> struct ExRad {
     const R *row;
     R dr, dbs, fa[5], da[5];
 };
 
-template <class R>
-__device__ __forceinline__ void tri_rad(R r, R ir, const R *T, const PotDev &p, TriRad<R> &g) {
+template <class B, class R>
+__device__ __forceinline__ void ex_rad(R r, R ir, const R *T, const PotDev &p, ExRad<R> &g) {
+    constexpr int NT = B::NT, ROW = B::ROW, S = B::LSTEP;
     const int K = p.ik;
     const R r0 = KC(R, p.c[1], p.cf[1]), rK = KC(R, p.c[2], p.cf[2]);
     g.dbs = R(0);
     g.dr = R(0);
     if (r >= rK) {
-        g.row = T + (K - 1) * TRI_ROW;
-        const R q = rK * ir, q2 = q * q;
+        g.row = T + (K - 1) * ROW;
+        const R q = rK * ir, qs = S == 2 ? q * q : q;
         g.fa[0] = q;
 #pragma unroll
-        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * q2;
+        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * qs;
 #pragma unroll
         for (int n = 0; n < 5; ++n) g.da[n] = R(0);
         g.dbs = -ir;
     } else if (r < r0) {
         g.row = T;
-        const R q = r * KC(R, p.c[5], p.cf[5]), q2 = q * q;
+        const R q = r * KC(R, p.c[5], p.cf[5]), qs = S == 2 ? q * q : q;
         g.fa[0] = R(1);
+#pragma unroll
+        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * qs;
+        // (r/r_0)^max(l-1, 1): q for l <= 2, then q^(l-1)
         g.da[0] = q;
 #pragma unroll
-        for (int n = 1; n < 5; ++n) g.fa[n] = g.fa[n - 1] * q2;
-        g.da[1] = q;
-#pragma unroll
-        for (int n = 2; n < 5; ++n) g.da[n] = g.da[n - 1] * q2;
+        for (int n = 1; n < 5; ++n) {
+            const int l = n * S;
+            g.da[n] = l <= 2 ? q : g.da[n - 1] * qs;
+        }
     } else {
         const float lg = fmaf(__log2f((float)r), p.cf[3], p.cf[4]) - 0.5f;
         int k = rint_small(fminf(fmaxf(lg, 0.0f), (float)(K - 2)));
-        while (k > 0 && r < T[k * TRI_ROW + 60]) --k;
-        while (k < K - 2 && r >= T[(k + 1) * TRI_ROW + 60]) ++k;
-        g.row = T + k * TRI_ROW;
-        g.dr = r - g.row[60];
+        while (k > 0 && r < T[k * ROW + 4 * NT]) --k;
+        while (k < K - 2 && r >= T[(k + 1) * ROW + 4 * NT]) ++k;
+        g.row = T + k * ROW;
+        g.dr = r - g.row[4 * NT];
 #pragma unroll
         for (int n = 0; n < 5; ++n) { g.fa[n] = R(1); g.da[n] = R(1); }
     }
 }
 
-template <class R>
-__device__ __forceinline__ R tri_F(const TriRad<R> &g, int t, int l) {
-    return g.row[t] * g.fa[l / 2] + g.dr * g.row[15 + t];
+template <class B, class R>
+__device__ __forceinline__ R ex_F(const ExRad<R> &g, int t, int l) {
+    return g.row[t] * g.fa[B::slot(l)] + g.dr * g.row[B::NT + t];
 }
 
-template <class R>
-__device__ __forceinline__ void tri_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
+template <class B, class R>
+__device__ __forceinline__ void ex_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
     const R r2 = (x * x + y * y) + z * z;
     if (!(r2 > R(0))) return;
     const R r = sqrt(r2), ir = R(1) / r;
     const R nx = x * ir, ny = y * ir, mu = z * ir;
-    TriRad<R> rd;
-    tri_rad<R>(r, ir, T, p, rd);
-    R ar = R(0), az = R(0), ax = R(0), ay = R(0);   // along n, e_z, and the (Re, -Im) direction (the last two / r)
-    tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
-        const R F = tri_F<R>(rd, t, l);
-        const R D = rd.row[30 + t] * rd.da[l / 2] + rd.dr * rd.row[45 + t] + R(l + 1) * rd.dbs * F;
-        const R c = R(tri_c(t));
+    ExRad<R> rd;
+    ex_rad<B, R>(r, ir, T, p, rd);
+    R ar = R(0), az = R(0), ax = R(0), ay = R(0);   // along n, e_z, and G (the last two / r)
+    ex_terms<B, R>(mu, nx, ny, [&](int t, int l, int m, R c, R q0, R q1, R C, R gx, R gy) {
+        const R F = ex_F<B, R>(rd, t, l);
+        const R D = rd.row[2 * B::NT + t] * rd.da[B::slot(l)] + rd.dr * rd.row[3 * B::NT + t] +
+                    R(l + 1) * rd.dbs * F;
         const R cq0C = c * q0 * C, Fc = F * c;
-        // D Y n + F c [q1 C (e_z - mu n) - m q0 C n + m q0 (Re u^(m-1), -Im u^(m-1), 0)] / r
+        // D Y n + F c [q1 C (e_z - mu n) - m q0 C n + m q0 G] / r
         ar = ar + (D * cq0C - (Fc * q1 * C * mu + F * R(m) * cq0C) * ir);
         az = az + Fc * q1 * C;
         if (m > 0) {
             const R s = Fc * R(m) * q0;
-            ax = ax + s * cp;
-            ay = ay - s * sp;
+            ax = ax + s * gx;
+            ay = ay + s * gy;
         }
     });
     g.x = g.x + (ar * nx + ax * ir);
@@ -575,24 +613,41 @@ __device__ __forceinline__ void tri_accel(R x, R y, R z, const R *T, const PotDe
     g.z = g.z + (ar * mu + az * ir);
 }
 
-template <class R>
-__device__ __forceinline__ R tri_phi(R x, R y, R z, const R *T, const PotDev &p) {
+template <class B, class R>
+__device__ __forceinline__ R ex_phi(R x, R y, R z, const R *T, const PotDev &p) {
     const R r2 = (x * x + y * y) + z * z;
     const R r = sqrt(r2);
     const R ir = r2 > R(0) ? R(1) / r : R(0);
     const R nx = x * ir, ny = y * ir, mu = r2 > R(0) ? z * ir : R(1);
-    TriRad<R> rd;
-    tri_rad<R>(r, ir, T, p, rd);
+    ExRad<R> rd;
+    ex_rad<B, R>(r, ir, T, p, rd);
     R s = R(0);
-    tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
-        s = s + R(tri_c(t)) * q0 * C * tri_F<R>(rd, t, l);
+    ex_terms<B, R>(mu, nx, ny, [&](int t, int l, int m, R c, R q0, R q1, R C, R gx, R gy) {
+        s = s + c * q0 * C * ex_F<B, R>(rd, t, l);
     });
     return -s;
 }
 
+template <class R>
+__device__ __forceinline__ void tri_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
+    ex_accel<TriBasis, R>(x, y, z, T, p, g);
+}
+template <class R>
+__device__ __forceinline__ R tri_phi(R x, R y, R z, const R *T, const PotDev &p) {
+    return ex_phi<TriBasis, R>(x, y, z, T, p);
+}
+template <class R>
+__device__ __forceinline__ void full_accel(R x, R y, R z, const R *T, const PotDev &p, Acc3<R> &g) {
+    ex_accel<FullBasis, R>(x, y, z, T, p, g);
+}
+template <class R>
+__device__ __forceinline__ R full_phi(R x, R y, R z, const R *T, const PotDev &p) {
+    return ex_phi<FullBasis, R>(x, y, z, T, p);
+}
+
 // Potential signatures compiled into the steady-state kernels (the generic
 // form walks the component list at run time):
-enum { PK_ANY = 0, PK_HERNQUIST = 1, PK_LOG = 3, PK_SH = 4, PK_HERNQUIST_NFW = 5, PK_SH_TRI = 6 };
+enum { PK_ANY = 0, PK_HERNQUIST = 1, PK_LOG = 3, PK_SH = 4, PK_HERNQUIST_NFW = 5, PK_SH_TRI = 6, PK_SH_FULL = 7 };
 
 template <class R>
 __device__ __forceinline__ void acc_hernquist(R x, R y, R z, const PotDev &p, Acc3<R> &g) {
@@ -658,6 +713,9 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
     } else if constexpr (PK == PK_SH_TRI) {
         tri_accel<R>(x, y, z, sh, a.pot[0], g);
         return g;
+    } else if constexpr (PK == PK_SH_FULL) {
+        full_accel<R>(x, y, z, sh, a.pot[0], g);
+        return g;
     } else if constexpr (PK == PK_HERNQUIST_NFW) {
         acc_hernquist<R>(x, y, z, a.pot[0], g);
         acc_nfw<R>(x, y, z, a.pot[1], g);
@@ -675,6 +733,8 @@ __device__ __forceinline__ Acc3<R> accel(R x, R y, R z, const PassArgs &a, const
             sh_accel<R>(x, y, z, sh, p, g);
         } else if (p.kind == 5) {     // the triaxial expansion of the particles
             tri_accel<R>(x, y, z, sh, p, g);
+        } else if (p.kind == 6) {     // the full expansion (l <= 4) of the particles
+            full_accel<R>(x, y, z, sh, p, g);
         }
     }
     return g;
@@ -767,6 +827,8 @@ __device__ __forceinline__ R phi_term(int kind, R x, R y, R z, const PotDev &p, 
         return sh_phi<R>(x, y, z, sh, p);
     } else if (kind == 5) {
         return tri_phi<R>(x, y, z, sh, p);
+    } else if (kind == 6) {
+        return full_phi<R>(x, y, z, sh, p);
     }
     return R(0);
 }
@@ -784,6 +846,8 @@ __device__ __forceinline__ R potential(R x, R y, R z, const PassArgs &a, const R
         return phi + phi_term<R>(4, x, y, z, a.pot[0], sh);
     } else if constexpr (PK == PK_SH_TRI) {
         return phi + phi_term<R>(5, x, y, z, a.pot[0], sh);
+    } else if constexpr (PK == PK_SH_FULL) {
+        return phi + phi_term<R>(6, x, y, z, a.pot[0], sh);
     } else if constexpr (PK == PK_HERNQUIST_NFW) {
         phi = phi + phi_term<R>(1, x, y, z, a.pot[0], sh);
         return phi + phi_term<R>(2, x, y, z, a.pot[1], sh);
@@ -801,7 +865,7 @@ template <class R, int PK = PK_ANY>
 __device__ __forceinline__ void kdk(R &x, R &y, R &z, R &vx, R &vy, R &vz, const PassArgs &a,
                                     const R *sh = nullptr, long long i = 0) {
     R h = KC(R, a.hdt, a.f_hdt), d = KC(R, a.dt, a.f_dt);
-    constexpr bool CACHE = PK == PK_ANY || PK == PK_SH || PK == PK_SH_TRI;
+    constexpr bool CACHE = PK == PK_ANY || PK == PK_SH || PK == PK_SH_TRI || PK == PK_SH_FULL;
     R *fc = CACHE ? (R *)a.facc : nullptr;
     Acc3<R> g;
     if (CACHE && fc && a.facc_read) {

@@ -1556,17 +1556,19 @@ __global__ void k_sh_tables(const long long *sum, int K, const double *rn, doubl
     }
 }
 
-// The triaxial expansion (kind 5): per radial side j, for each of its 15
-// terms t, A terms w Y_t (r/r_j)^l and B terms w Y_t (r_(j-1)/r)^(l+1)
-// (j > 0), each at most 1.7 w in size, summed exactly in 64-bit fixed point
-// (FP32C) or in double (FP64) as for the axisymmetric expansion; [30][K]
-// side sums, row t for A and 15 + t for B.  The terms are generated one at
-// a time; a warp whose particles share one side adds warp sums.
-template <class R>
-__global__ void __launch_bounds__(512) k_tri_coef(const __grid_constant__ ShArgs a) {
+// The expansions with m != 0 (kinds 5 and 6, basis B): per radial side j,
+// for each of its NT terms t, A terms w Y_t (r/r_j)^l and B terms
+// w Y_t (r_(j-1)/r)^(l+1) (j > 0), each at most 1.7 w in size, summed exactly
+// in 64-bit fixed point (FP32C) or in double (FP64) as for the axisymmetric
+// expansion; [2 NT][K] side sums, row t for A and NT + t for B.  The terms
+// are generated one at a time; a warp whose particles share one side adds
+// warp sums.
+template <class B, class R>
+__global__ void __launch_bounds__(512) k_ex_coef(const __grid_constant__ ShArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr bool FX = sizeof(R) == 4;
-    const int K = a.K, NS = 2 * TRI_NT * K;
+    constexpr int NT = B::NT;
+    const int K = a.K, NS = 2 * NT * K;
     unsigned *lo = (unsigned *)smem, *hi = lo + NS;
     double *acc = (double *)smem;
     R *e2 = (R *)(hi + NS), *rn = e2 + K, *irn = rn + K;
@@ -1603,25 +1605,25 @@ __global__ void __launch_bounds__(512) k_tri_coef(const __grid_constant__ ShArgs
                 const R r = sqrt(r2), ir = r2 > R(0) ? R(1) / r : R(0);
                 nx = x * ir; ny = y * ir;
                 mu = r2 > R(0) ? z * ir : R(1);
-                // w (r/r_j)^l and w (r_(j-1)/r)^(l+1), l = 0, 2, .., 8
-                const R rho = r * irn[j], rho2 = rho * rho;
-                const R sg = j > 0 ? rn[j - 1] * ir : R(0), sg2 = sg * sg;
+                // w (r/r_j)^l and w (r_(j-1)/r)^(l+1) for the basis's l
+                const R rho = r * irn[j], sg = j > 0 ? rn[j - 1] * ir : R(0);
+                const R rs = B::LSTEP == 2 ? rho * rho : rho, ss = B::LSTEP == 2 ? sg * sg : sg;
                 ta[0] = wr;
                 tb[0] = wr * sg;
 #pragma unroll
-                for (int n = 1; n < 5; ++n) { ta[n] = ta[n - 1] * rho2; tb[n] = tb[n - 1] * sg2; }
+                for (int n = 1; n < 5; ++n) { ta[n] = ta[n - 1] * rs; tb[n] = tb[n - 1] * ss; }
             } else {
                 j = j < K ? K + 1 : j;      // a particle of zero weight adds nothing
             }
         }
         const int j0 = __shfl_sync(0xffffffffu, j, 0);
         const bool same = __all_sync(0xffffffffu, j == j0);
-        tri_terms<R>(mu, nx, ny, [&](int t, int l, int m, R q0, R q1, R C, R cp, R sp) {
-            const R Y = R(tri_c(t)) * q0 * C;
+        ex_terms<B, R>(mu, nx, ny, [&](int t, int l, int m, R c, R q0, R q1, R C, R gx, R gy) {
+            const R Y = c * q0 * C;
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
-                const R v = (side == 0 ? ta[l / 2] : tb[l / 2]) * Y;
-                const int row = side * TRI_NT + t;
+                const R v = (side == 0 ? ta[B::slot(l)] : tb[B::slot(l)]) * Y;
+                const int row = side * NT + t;
                 if (same) {
                     if (j0 < K) {
                         if (FX) {
@@ -1658,34 +1660,36 @@ __global__ void __launch_bounds__(512) k_tri_coef(const __grid_constant__ ShArgs
     if (bad) atomicOr(a.err, ERR_NONFINITE);
 }
 
-// F_t and D_t at node k from the node sums A (rows 0..14) and B (rows
-// 15..29) held in S ([30][K]), with the 4 pi/(2l+1) of the addition theorem.
-__device__ __forceinline__ void tri_node_FD(const double *S, int K, const double *rn, int k, int t, double &F,
-                                            double &D) {
-    const int l = tri_l(t);
+// F_t and D_t at node k from the node sums A (rows 0..NT-1) and B (rows
+// NT..2NT-1) held in S ([2NT][K]), with the 4 pi/(2l+1) of the addition
+// theorem.
+template <class B>
+__device__ __forceinline__ void ex_node_FD(const double *S, int K, const double *rn, int k, int t, double &F,
+                                           double &D) {
+    const int l = B::l_of(t);
     const double r = rn[k], ir = 1.0 / r;
     double rl = 1.0;
     for (int e = 0; e < l; ++e) rl *= r;                           // r^l
-    const double A = S[t * K + k], B = S[(TRI_NT + t) * K + k];
+    const double A = S[t * K + k], Bs = S[(B::NT + t) * K + k];
     const double c = 12.566370614359172 / (double)(2 * l + 1);     // 4 pi/(2l+1)
     const double irl1 = ir / rl;                                   // r^-(l+1)
-    F = c * (A * irl1 + B * rl);
-    D = c * (-(double)(l + 1) * A * (irl1 * ir) + (l > 0 ? (double)l * B * (rl * ir) : 0.0));
+    F = c * (A * irl1 + Bs * rl);
+    D = c * (-(double)(l + 1) * A * (irl1 * ir) + (l > 0 ? (double)l * Bs * (rl * ir) : 0.0));
 }
 
-// Node tables of the triaxial expansion from its side sums (one block):
-// scale back, prefix sums (A) and suffix sums (B), then F_lm, D_lm and the
+// Node tables of an expansion with m != 0 from its side sums (one block):
+// scale back, prefix sums (A) and suffix sums (B), then F_t, D_t and the
 // slopes to the next node.
-template <class R>
-__global__ void k_tri_tables(const long long *sum, int K, const double *rn, double q, R *tab, int *err) {
+template <class B, class R>
+__global__ void k_ex_tables(const long long *sum, int K, const double *rn, double q, R *tab, int *err) {
     extern __shared__ __align__(16) double sd[];
-    constexpr int NR = 2 * TRI_NT;
-    double *S = sd;                // [30][K] side sums, then A, B at the nodes
+    constexpr int NT = B::NT, NR = 2 * NT, ROW = B::ROW;
+    double *S = sd;                // [2NT][K] side sums, then A, B at the nodes
     for (int k = threadIdx.x; k < NR * K; k += blockDim.x) {
-        const int row = k / K, j = k - row * K, t = row % TRI_NT, l = tri_l(t);
+        const int row = k / K, j = k - row * K, t = row % NT, l = B::l_of(t);
         const double v = sizeof(R) == 4 ? (double)sum[k] * q : ((const double *)sum)[k];
         double s = 1.0;
-        if (row < TRI_NT) {
+        if (row < NT) {
             for (int e = 0; e < l; ++e) s *= rn[j];                       // r_j^l
         } else if (j > 0) {
             for (int e = 0; e <= l; ++e) s *= rn[j - 1];                  // r_(j-1)^(l+1)
@@ -1699,7 +1703,7 @@ __global__ void k_tri_tables(const long long *sum, int K, const double *rn, doub
     if (threadIdx.x < NR) {
         double *row = S + threadIdx.x * K;
         double acc = 0.0;
-        if (threadIdx.x < TRI_NT) {
+        if (threadIdx.x < NT) {
             for (int k = 0; k < K; ++k) { acc += row[k]; row[k] = acc; }
         } else {
             for (int k = K - 1; k >= 0; --k) { const double b = row[k]; row[k] = acc; acc += b; }
@@ -1707,21 +1711,21 @@ __global__ void k_tri_tables(const long long *sum, int K, const double *rn, doub
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        R *row = tab + (size_t)k * TRI_ROW;
+        R *row = tab + (size_t)k * ROW;
         const bool last = k == K - 1;
         const double h = last ? 1.0 : 1.0 / (rn[k + 1] - rn[k]);
         bool fin = true;
-        for (int t = 0; t < TRI_NT; ++t) {
+        for (int t = 0; t < NT; ++t) {
             double F, D, F1 = 0.0, D1 = 0.0;
-            tri_node_FD(S, K, rn, k, t, F, D);
-            if (!last) tri_node_FD(S, K, rn, k + 1, t, F1, D1);
+            ex_node_FD<B>(S, K, rn, k, t, F, D);
+            if (!last) ex_node_FD<B>(S, K, rn, k + 1, t, F1, D1);
             fin = fin && isfinite(F) && isfinite(D);
             row[t] = (R)F;
-            row[30 + t] = (R)D;
-            row[15 + t] = last ? R(0) : (R)((F1 - F) * h);
-            row[45 + t] = last ? R(0) : (R)((D1 - D) * h);
+            row[2 * NT + t] = (R)D;
+            row[NT + t] = last ? R(0) : (R)((F1 - F) * h);
+            row[3 * NT + t] = last ? R(0) : (R)((D1 - D) * h);
         }
-        row[60] = (R)rn[k];
+        row[4 * NT] = (R)rn[k];
         if (!fin) atomicOr(err, ERR_NONFINITE);
     }
 }

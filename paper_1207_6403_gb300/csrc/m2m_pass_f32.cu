@@ -37,6 +37,9 @@ static void *steady_pk(int pk) {
         case PK_SH_TRI:     // the triaxial expansion: the layout of its workload (shells + annuli)
             if constexpr (L == 2) return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY, PK_SH_TRI>;
             return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY>;
+        case PK_SH_FULL:    // the full expansion (l <= 4): the same layout
+            if constexpr (L == 2) return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY, PK_SH_FULL>;
+            return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY>;
         case PK_HERNQUIST_NFW: return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY, PK_HERNQUIST_NFW>;
         default: return (void *)k_pass<float, 1024, 1, L, 0, F_STEADY>;
     }

@@ -19,6 +19,7 @@ static void *other_pk(int layout, int pk) {
     if (layout == 2 && pk == PK_HERNQUIST) return one<FL, 2, PK_HERNQUIST>();
     if (layout == 2 && pk == PK_SH) return one<FL, 2, PK_SH>();
     if (layout == 2 && pk == PK_SH_TRI) return one<FL, 2, PK_SH_TRI>();
+    if (layout == 2 && pk == PK_SH_FULL) return one<FL, 2, PK_SH_FULL>();
     if (layout == 2 && pk == PK_HERNQUIST_NFW) return one<FL, 2, PK_HERNQUIST_NFW>();
     if (layout == 3 && pk == PK_HERNQUIST) return one<FL, 3, PK_HERNQUIST>();
     if (layout == 4 && pk == PK_LOG) return one<FL, 4, PK_LOG>();

@@ -492,13 +492,36 @@ def error_model(Y, obs_sets, frac=0.02):
 # --------------------------------------------------------------------------
 # Workloads
 # --------------------------------------------------------------------------
-WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons", "ifu-lut", "sh-tri")
+WORKLOADS = ("plain-fp64", "moving-priors", "flat-log", "sh-selfcons", "ifu-lut", "sh-tri", "sh-full")
 
 _DEFAULT_N = {"plain-fp64": 20_000, "moving-priors": 1_000_000, "sh-selfcons": 8_000_000,
-              "flat-log": 4_000_000, "ifu-lut": 4_000_000, "sh-tri": 4_000_000}
+              "flat-log": 4_000_000, "ifu-lut": 4_000_000, "sh-tri": 4_000_000,
+              "sh-full": 4_000_000}
 
 # axis ratios of the triaxial workload (x : y : z)
 TRI_AXES = (1.0, 0.8, 0.6)
+
+
+# orientation and offset of the particle set of the workload with no symmetry
+# (Euler angles z-y-z, radians; centre offset)
+FULL_EULER = (0.5, 0.7, 0.3)
+FULL_SHIFT = (0.05, -0.03, 0.02)
+
+
+def rotated(pos, vel, euler=FULL_EULER, shift=FULL_SHIFT):
+    """Positions rotated by the z-y-z Euler angles and shifted by `shift`,
+    velocities rotated: a set with no mirror symmetry about the coordinate
+    planes (every harmonic appears in its expansion)."""
+    a, b, c = euler
+
+    def rz(t):
+        return np.array([[math.cos(t), -math.sin(t), 0.0], [math.sin(t), math.cos(t), 0.0], [0.0, 0.0, 1.0]])
+
+    def ry(t):
+        return np.array([[math.cos(t), 0.0, math.sin(t)], [0.0, 1.0, 0.0], [-math.sin(t), 0.0, math.cos(t)]])
+
+    M = rz(a) @ ry(b) @ rz(c)
+    return M @ pos + np.asarray(shift, np.float64)[:, None], M @ vel
 
 
 def triaxial_hernquist(n, seed, axes=TRI_AXES):
@@ -675,6 +698,22 @@ def make_problem(name, n=None, precision=None, seed_model=None,
         obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
                ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
         pot = [PotentialComponent("sh_tri", (256, 1e-3, 100.0, 50))]
+        prior = PriorSpec("e_l2", 64, 32, 25)
+        sin_i, cos_i = 0.0, 1.0
+        prec = precision or "fp32c"
+        steps = nsteps or 5000
+    elif name == "sh-full":
+        sm, st = seed_model or 14, seed_target or 15
+        pos, vel = rotated(*triaxial_hernquist(n, sm))
+        tp = tv = None
+        if with_target:
+            tp, tv = rotated(*triaxial_hernquist(n, st))
+        e = log_shell_edges(60, 0.05, 20.0)
+        rmid = np.sqrt(np.sqrt(e[:-1] * e[1:]))
+        S = np.maximum(np.sqrt(hernquist_sigma_iso(1.0, 1.0)(rmid)), 0.05)
+        obs = [ObservableSet("shell", "mass", log_shell_edges(100, 0.05, 20.0)),
+               ObservableSet("annulus", "gh", e, gh_V=np.zeros(60), gh_S=S, sigma_kernel=0.1)]
+        pot = [PotentialComponent("sh_full", (128, 1e-3, 100.0, 50))]
         prior = PriorSpec("e_l2", 64, 32, 25)
         sin_i, cos_i = 0.0, 1.0
         prec = precision or "fp32c"

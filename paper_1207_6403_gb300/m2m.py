@@ -18,9 +18,10 @@ M2M_OK = 0
 ERRORS = {-1: "M2M_ERR_ARG", -2: "M2M_ERR_CUDA", -3: "M2M_ERR_NONFINITE", -4: "M2M_ERR_TIMEOUT",
           -5: "M2M_ERR_STATE", -6: "M2M_ERR_NOMEM", -7: "M2M_ERR_OVERFLOW"}
 FP64, FP32C = 0, 1
-POT = {"hernquist": 1, "nfw": 2, "log": 3, "sh": 4, "sh_tri": 5}
+POT = {"hernquist": 1, "nfw": 2, "log": 3, "sh": 4, "sh_tri": 5, "sh_full": 6}
 SH_ROW = 21
 TRI_ROW = 61
+FULL_ROW = 101
 GEOM = {"shell": 1, "annulus": 2, "grid": 3, "lut": 4}
 QUANT = {"mass": 1, "vlos2": 2, "gh": 3}
 PRIOR = {"flat": 0, "e_lc": 1, "e_lz": 2, "e_l2": 3}
@@ -320,11 +321,11 @@ class Context:
         return {"threads": t.threads, "pipeline": t.pipeline, "us_per_step": t.us_per_step,
                 "candidates": t.candidates, "from_cache": bool(t.from_cache), "key": t.key.decode()}
 
-    def m2m_get_sh_table(self, K, triaxial=False):
+    def m2m_get_sh_table(self, K, triaxial=False, full=False):
         """(K, 21) node table of the spherical-harmonic component, (K, 61)
-        of the triaxial one (float64)."""
+        of the triaxial one, (K, 101) of the full one (float64)."""
         import numpy as np
-        out = np.zeros((K, TRI_ROW if triaxial else SH_ROW), dtype=np.float64)
+        out = np.zeros((K, FULL_ROW if full else TRI_ROW if triaxial else SH_ROW), dtype=np.float64)
         _check(library().m2m_get_sh_table(self.ptr, out.ctypes.data_as(POINTER(c_double))), self.ptr)
         return out
 

@@ -6,6 +6,7 @@ import pytest
 
 from oracle import sh as SH
 from oracle import sh_full as F
+from paper_1207_6403_gb300 import inputs as I
 
 
 def test_real_harmonics_are_orthonormal_by_quadrature():
@@ -251,3 +252,28 @@ def test_triaxial_expansion_is_the_full_expansion_of_a_triaxial_set():
     a_f = F.acceleration_nodes(*p, Ff, Df, rn, 8)
     a_t = F.tri_acceleration(*p, Ft, Dt, rn)
     np.testing.assert_allclose(a_t, a_f, rtol=1e-10, atol=1e-11 * np.abs(a_f).max())
+
+
+def test_full_expansion_of_the_step_on_a_set_with_no_symmetry():
+    """The step's full expansion (kind 'sh_full': every l <= 4, every m) of
+    a rotated and shifted triaxial set: every harmonic is present (odd l
+    and sine terms included), and at node radii its potential is the
+    direct double sum of the same truncation over the particles inside
+    r_max."""
+    from oracle import m2m as M
+    P = I.make_problem("sh-full", n=3000, precision="fp64", with_target=False)
+    x, y, z = P.pos
+    w = P.w0
+    comp = P.potential[0]
+    Ft, Dt, rn = M.sh_tables(x, y, z, w, comp)
+    assert Ft.shape == (25, 128)
+    mono = np.abs(Ft[0]).max()
+    for t in range(1, 25):                 # (1,-1), (1,0), .., (4,4): none vanishes
+        assert np.abs(Ft[t]).max() > 1e-6 * mono, t
+    inside = np.sqrt(x * x + y * y + z * z) < rn[-1]
+    g = np.random.default_rng(5)
+    for k in (20, 64, 100):
+        d = g.normal(size=(3, 4))
+        d = d / np.linalg.norm(d, axis=0) * rn[k]
+        np.testing.assert_allclose(M.potential(*d, P.potential, (Ft, Dt, rn)),
+                                   F.potential(*d, x[inside], y[inside], z[inside], w[inside], 4), rtol=1e-11)
