@@ -3,8 +3,13 @@ contexts (halves of its particles, exchange buffers summed on the device
 by the driver's local reduction) against the same model in one context:
 positions, weights, priors, observables, Delta and Delta~ bit for bit after
 60 steps (two prior recomputes); the records' sums to rounding.  Between
-GPUs the exchange is a torch.distributed all-reduce of the same buffers
-(tests/test_shard_cpu.py runs it over gloo)."""
+processes the exchange is a torch.distributed all-reduce of the same
+buffers: two processes, each with one shard context on this GPU, reduce
+over gloo (the exchange runs between launches on the host, so no kernel
+of one process waits on the other's)."""
+import os
+import socket
+
 import numpy as np
 import pytest
 
@@ -62,3 +67,55 @@ def test_shard_calls_check_their_state():
     with pytest.raises(B.M2MError):         # no prior recompute is due
         ctx.m2m_shard_prior_finish(bufs.cell_sums, bufs.cell_counts)
     ctx.m2m_free()
+
+
+def _port():
+    with socket.socket() as s_:
+        s_.bind(("127.0.0.1", 0))
+        return s_.getsockname()[1]
+
+
+def _rank_main(rank, port, out, nsteps):
+    import torch as T
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    T.cuda.set_device(0)
+    P = I.make_problem("flat-log", n=50_003, precision="fp32c")
+    P = P.with_targets(O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos))
+    ctx, bufs = SH.make_shard(P, 2, rank, device="cuda:0")
+    red = SH.DistReduce(dist)
+    SH.start([(ctx, bufs)], red)
+    for _ in range(nsteps):
+        SH.step([(ctx, bufs)], red)
+    g = ctx.state()
+    y, D, Dt = ctx.m2m_get_obs()
+    np.savez(f"{out}.{rank}.npz", yobs=y, Dt=Dt, **{k: g[k] for k in ("x", "y", "z", "vx", "vy", "vz", "w", "what")})
+    ctx.m2m_free()
+    dist.destroy_process_group()
+
+
+def test_two_processes_with_shard_contexts_equal_one_context(tmp_path):
+    nsteps = 30
+    mp = torch.multiprocessing.get_context("spawn")
+    port = _port()
+    out = str(tmp_path / "shard")
+    procs = [mp.Process(target=_rank_main, args=(r, port, out, nsteps)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=600)
+        assert p.exitcode == 0
+    r0, r1 = np.load(f"{out}.0.npz"), np.load(f"{out}.1.npz")
+    P = I.make_problem("flat-log", n=50_003, precision="fp32c")
+    P = P.with_targets(O.observe(*P.target_pos, *P.target_vel, P.target_w, P.obs, P.incl_sin, P.incl_cos))
+    one = B.from_problem(P, "fp32c")
+    one.m2m_step(nsteps)
+    g1 = one.state()
+    y1, _, Dt1 = one.m2m_get_obs()
+    for k in ("x", "y", "z", "vx", "vy", "vz", "w", "what"):
+        assert np.array_equal(np.concatenate([r0[k], r1[k]]), g1[k]), k
+    for r in (r0, r1):
+        assert np.array_equal(r["yobs"], y1) and np.array_equal(r["Dt"], Dt1)
+    one.m2m_free()
+
